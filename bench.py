@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput of the cascade (states/s) on the BF16-split precision workload.
+
+Workload (seeded, synthetic): HiPPO-LegS state matrix, m = 256, p = q = 1,
+64 sequences of L = 16384 steps, one trapezoidal step size per sequence drawn
+log-uniform in [1e-4, 1e-1] (64 systems), N = 13 (14 stages, 2^14 >= L),
+u ~ N(0, 1).  A step is one forward pass of the whole cascade over the batch:
+first stage fused with Bbar u, stages 1..13 on the tensor cores, y = C v + D u
+fused into the last stage.  The powers Abar^(2^k) are prepared once (FP64
+squaring chain) outside the timed region; their cost is reported separately.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run: every rank runs an independent
+replica of the whole workload on its own GPU (no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cascade states/s (fwd)"
+WORKLOAD = ("precision_form: HiPPO-LegS m=256 p=q=1, 64 seqs x L=16384, N=13, "
+            "delta log-uniform [1e-4,1e-1] per sequence, BF16 hi/lo split, FP32 accumulate")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 cascade comparator")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# --------------------------------------------------------------------- helpers
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads") for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_states_per_s(w, budget_s=12.0):
+    """The oracle as it stands, on whole sequences of the workload until the
+    time budget is used (at least one sequence)."""
+    import oracle
+    t0 = time.perf_counter()
+    states = 0
+    seqs = 0
+    cache = {}
+    for i in range(w.nseq):
+        sl = w.seq(i)
+        s = int(w.sys_of_seq[i])
+        if s not in cache:
+            cache[s] = oracle.system_matrices(w, s)
+        Abar, Bbar, C, D = cache[s]
+        oracle.cascade_forward_seq(Abar, Bbar, C, D, w.u[sl], w.N)
+        states += sl.stop - sl.start
+        seqs += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return states / dt, f"{seqs} of {w.nseq} sequences (L={int(w.lengths[0])}), powers included", dt
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu=uuid,{self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+# --------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle (CPU FP64) timed on the host cores on bounded samples of the
+    same workload: each step runs whole sequences for a fixed time budget."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    import workloads as wl
+    w = wl.precision_form()
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_states_per_s(w, budget_s=min(per_step, 2.0))
+    vals, samples, secs = [], [], 0.0
+    for _ in range(args.steps):
+        v, sample, dt = oracle_states_per_s(w, budget_s=per_step)
+        vals.append(v)
+        samples.append(sample)
+        secs += dt
+    value = statistics.median(vals)
+    cores = blas_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "states/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * secs / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "oracle": "numpy float64 cascade (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "states/s", "cores": cores,
+                             "kind": "oracle", "sample": samples[-1]},
+            "e2e": {"value": value, "unit": "states/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import workloads as wl
+    from paper_2411_17729_gb300 import build
+    build()
+    from paper_2411_17729_gb300 import cascade
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    w = wl.precision_form()
+    m = w.m
+    t_prep0 = time.perf_counter()
+    c = cascade.from_workload(w, precision="bf16_split", device=dev)
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t_prep0
+    u = torch.as_tensor(w.u, dtype=torch.float32).to(dev).contiguous()
+    y = torch.empty((w.rows, w.q), dtype=torch.float32, device=dev)
+    ws = c.workspace()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = c.lib
+
+    def step():
+        c.forward(u, y)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if c.device_error() != 0:
+        raise RuntimeError("device wait timed out during warm-up")
+
+    # ---- timed region: K forward passes, L2 flushed before each
+    c.enable_stage_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stage_ms = {}
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = lib.cascade_launch_count()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        for k, ms in c.stage_times():
+            stage_ms.setdefault(k, []).append(ms)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = lib.cascade_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    c.enable_stage_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_per_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms_per_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    states_per_step = int(w.rows)
+    value = states_per_step * world / (ms_per_step / 1000.0)
+    if c.device_error() != 0:
+        raise RuntimeError("device wait timed out in the timed region")
+
+    # ---- roofline of the dominant kernel (tensor-core stage), per launch
+    hbm_peak, bf16_peak, peak_kind = peaks()
+    Ls = w.lengths.astype(np.int64)
+    tot_ms = {k: sum(v) for k, v in stage_ms.items()}
+    avg_ms = sum(tot_ms.values()) / max(1, sum(len(v) for v in stage_ms.values()))
+    launches_per_step = len(stage_ms)
+    bytes_per_launch, flops_per_launch = [], []
+    for k in stage_ms:
+        s = 1 << k
+        upd = int(np.maximum(Ls - s, 0).sum())
+        rows_read = int(Ls.sum())
+        # read every row of V^(k) once, write the updated rows of V^(k+1): 4 bytes per
+        # element each way (BF16 hi + lo); plus the power's hi/lo planes per system
+        bytes_per_launch.append(4 * m * (rows_read + upd) + w.nsys * m * m * 4)
+        flops_per_launch.append(3 * 2 * m * m * upd)
+    alg_bytes = float(np.mean(bytes_per_launch))
+    alg_flops = float(np.mean(flops_per_launch))
+    achieved_gbs = alg_bytes / (avg_ms / 1000.0) / 1e9
+    achieved_tfs = alg_flops / (avg_ms / 1000.0) / 1e12
+    stage_share = sum(tot_ms.values()) / max(1e-9, sum(step_ms))
+
+    # ---- end to end through the public API with host buffers
+    u_host = torch.as_tensor(w.u, dtype=torch.float32).pin_memory()
+    y_host = torch.empty((w.rows, w.q), dtype=torch.float32).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e2e_ev[i][0].record(stream)
+        u.copy_(u_host, non_blocking=True)
+        c.forward(u, y)
+        y_host.copy_(y, non_blocking=True)
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = states_per_step * world / (e2e_ms / 1000.0)
+
+    # ---- FP64 plain cascade on the same GPU (comparator), on 8 sequences
+    fp64 = None
+    if not args.no_fp64:
+        sub = w.subset(range(8))
+        c64 = cascade.from_workload(sub, precision="fp64", device=dev)
+        u64 = torch.as_tensor(sub.u, dtype=torch.float64).to(dev)
+        c64.forward(u64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c64.forward(u64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"value": sub.rows / (a.elapsed_time(b) / 1000.0), "unit": "states/s",
+                "sample": "8 of 64 sequences, one pass"}
+        c64.close()
+
+    # ---- oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, _ = oracle_states_per_s(w, budget_s=12.0)
+        cpu = {"value": v, "unit": "states/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": int(w.nseq) * world, "seq_len": 16384,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "flushed before each timed step (256 MiB write)",
+                       "timing": "CUDA events on the launching stream, sum over steps"},
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "traffic": None,
+                         "kernel": "stage_tc_kernel<bf16,q=1> (stages 1..13)",
+                         "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": avg_ms, "launches_per_step": launches_per_step,
+                         "share_of_step": stage_share,
+                         "tensor": {"achieved": achieved_tfs, "peak": bf16_peak, "unit": "TFLOP/s",
+                                    "frac": achieved_tfs / bf16_peak,
+                                    "alg_flops_per_launch": alg_flops}},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "states/s",
+                    "h2d_bytes_per_step": int(u.numel() * 4), "d2h_bytes_per_step": int(y.numel() * 4)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "fp64_cascade": fp64,
+            "precompute_s": prep_s,
+            "stage_ms": {str(k): statistics.median(v) for k, v in sorted(stage_ms.items())},
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    c.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * cascade.h -- C ABI of the GB300 (sm_103a) cascade library.
+ *
+ * The library applies the transfer function of a discrete linear
+ * time-invariant system,
+ *
+ *     H(z) = C (I - z^-1 Abar)^-1 Bbar + D                       (Eq. 1.3)
+ *
+ * to packed input sequences in the time domain, with the unconditionally
+ * stable cascade of Beylkin, "Fast convolution algorithm for state space
+ * models" (arXiv 2411.17729): the resolvent is truncated to the product of
+ * N+1 factors I + (z^-1 Abar)^(2^k) (Eq. 2.2), the powers Abar^(2^k) are
+ * formed by repeated squaring in FP64 (end of §2, §4), and the stages
+ *
+ *     v_l <- v_l + Abar^(2^k) v_(l - 2^k),   k = 0..N             (Eqs. 3.2-3.4)
+ *
+ * are applied to v^(0) = Bbar u, followed by y = C v + D u (end of §3).
+ *
+ * Conventions shared by every call:
+ *   - Matrices are row-major (last index fastest).  System matrices carry a
+ *     leading system axis: A is [nsys, m, m], B is [nsys, m, p], C is
+ *     [nsys, q, m], D is [nsys, q, p], delta is [nsys].
+ *   - Sequences are packed time-major: u is [rows, p], y is [rows, q], with
+ *     rows = offsets[nseq]; sequence i occupies rows offsets[i]..offsets[i+1]-1.
+ *   - Pointers named d_* are DEVICE pointers (caller-owned; the library never
+ *     frees them); pointers named h_* are HOST pointers read during the call.
+ *   - u/y/du/dy element type is double for CASCADE_FP64 plans and float
+ *     otherwise.  System matrices and their gradients are always double.
+ *   - `stream` is a cudaStream_t (0 = legacy default stream).  Calls that
+ *     launch work are asynchronous on that stream unless stated otherwise.
+ *   - Every call returns a cascade_status_t; no call aborts or throws.  On
+ *     failure the plan keeps its previous state and cascade_last_error()
+ *     returns a one-line description.
+ */
+#ifndef GB300_CASCADE_H
+#define GB300_CASCADE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CASCADE_OK = 0,
+  CASCADE_ERR_INVALID_ARG = 1,   /* bad pointer, size, shape or layout        */
+  CASCADE_ERR_UNSUPPORTED = 2,   /* valid request this build does not serve   */
+  CASCADE_ERR_OOM = 3,           /* device allocation failed                  */
+  CASCADE_ERR_CUDA = 4,          /* a CUDA runtime/driver call failed         */
+  CASCADE_ERR_TIMEOUT = 5,       /* a bounded device wait expired             */
+  CASCADE_ERR_STATE = 6          /* call order violated (e.g. no system set)  */
+} cascade_status_t;
+
+typedef enum {
+  /* FP64 storage and FP64 arithmetic on the CUDA cores.                     */
+  CASCADE_FP64 = 0,
+  /* Stage contractions as three TF32 tensor-core products
+     (hi*hi + hi*lo + lo*hi) with FP32 accumulation in TMEM; states stored
+     as a pair of TF32-exact FP32 planes (hi + lo carries ~22 bits).         */
+  CASCADE_FP32 = 1,
+  /* Stage contractions as three BF16 tensor-core products with FP32
+     accumulation in TMEM; states stored as a BF16 (hi, lo) pair.            */
+  CASCADE_BF16_SPLIT = 2
+} cascade_precision_t;
+
+enum {
+  /* Keep every stage output V^(k) in the workspace so that cascade_backward
+     can run (without it, backward recomputes them: see CASCADE_FLAG_RECOMPUTE). */
+  CASCADE_FLAG_SAVE_STATES = 1,
+  /* Backward recomputes stage outputs from checkpoints every c stages
+     instead of keeping all of them (lower workspace, one extra forward).    */
+  CASCADE_FLAG_RECOMPUTE = 2,
+  /* Do not fuse y = C v + D u into the last stage (diagnostics).            */
+  CASCADE_FLAG_NO_FUSED_OUTPUT = 4,
+  /* Record the forward launch sequence once per (u, y, workspace) triple in
+     a CUDA graph and replay it on later calls.                             */
+  CASCADE_FLAG_GRAPH = 8
+};
+
+typedef struct cascade_plan_s* cascade_plan_t;
+
+typedef struct {
+  int32_t m, p, q;      /* state, input and output sizes, 1 <= p, q; m >= 1 (§1, Eq. 1.1) */
+  int32_t nsys;         /* number of distinct systems (each sequence names one)          */
+  int32_t N;            /* stages k = 0..N; N < 0 chooses N per system from eps          */
+  int32_t precision;    /* cascade_precision_t                                            */
+  int32_t max_len;      /* longest sequence the plan will see (sizes the power table)    */
+  int32_t flags;        /* CASCADE_FLAG_*                                                 */
+  int64_t max_rows;     /* most packed rows one batch may hold                            */
+  double eps;           /* accuracy target when N < 0 (Lemma 1, remainder reading)        */
+} cascade_desc_t;
+
+/* Human-readable name of a status code.  Never NULL. */
+const char* cascade_status_string(cascade_status_t status);
+
+/* Last error message recorded on `plan` ("" if none).  Valid until the next
+   call on the same plan.  plan may be NULL (returns the last global error). */
+const char* cascade_last_error(cascade_plan_t plan);
+
+/* Create a plan for the problem shape of §1 (Eq. 1.1) on the current CUDA
+   device.  Validates the descriptor (INVALID_ARG) and the precision x m
+   combination (UNSUPPORTED: the tensor-core precisions need m % 64 == 0 for
+   BF16 and m % 32 == 0 for FP32, m <= 4096).  The plan owns the device
+   copies of the discretised systems and their powers; nothing is allocated
+   for sequences (see cascade_workspace_size).  *plan is NULL on failure. */
+cascade_status_t cascade_plan_create(cascade_plan_t* plan, const cascade_desc_t* desc);
+
+/* Release every resource the plan owns.  Synchronises the device first.
+   NULL is ignored. */
+void cascade_plan_destroy(cascade_plan_t plan);
+
+/* Set continuous systems and discretise them with the trapezoidal rule of
+   §1 (after Eq. 1.2) and Eq. (4.2):
+       Abar = (I - delta/2 A)^-1 (I + delta/2 A),   Bbar = delta (I - delta/2 A)^-1 B,
+   then multiply Abar by d_abar_scale[s] if that pointer is not NULL (used to
+   place eigenvalues just outside the unit circle, §6).  Afterwards the powers
+   Abar^(2^k) are formed by FP64 repeated squaring on the device (end of §2),
+   N is chosen per system (desc.N, or from eps when desc.N < 0: the smallest
+   N with 2^(N+1) >= max_len or ||Abar^(2^(N+1))||_F <= eps), and the powers
+   are converted to the plan's operand format.
+   Device inputs: d_A [nsys,m,m], d_B [nsys,m,p], d_delta [nsys],
+   d_abar_scale [nsys] or NULL, d_C [nsys,q,m], d_D [nsys,q,p], all double.
+   Synchronises `stream` before returning (N is read back to the host).
+   Returns CASCADE_ERR_INVALID_ARG for a singular I - delta/2 A. */
+cascade_status_t cascade_set_system_continuous(cascade_plan_t plan, const double* d_A,
+                                               const double* d_B, const double* d_delta,
+                                               const double* d_abar_scale, const double* d_C,
+                                               const double* d_D, void* stream);
+
+/* Set already-discrete systems (Eq. 1.2): d_Abar [nsys,m,m], d_Bbar
+   [nsys,m,p], d_C, d_D as above, all double.  Then as the continuous call
+   (powers, N, operand conversion).  Synchronises `stream`. */
+cascade_status_t cascade_set_system_discrete(cascade_plan_t plan, const double* d_Abar,
+                                             const double* d_Bbar, const double* d_C,
+                                             const double* d_D, void* stream);
+
+/* Copy the per-system N chosen by the last set_system call into h_N[nsys]. */
+cascade_status_t cascade_get_N(cascade_plan_t plan, int32_t* h_N);
+
+/* Copy the FP64 powers Abar^(2^k), k = 0..kmax, of system `sys` to the
+   device buffer d_out [kmax+1, m, m] (double).  kmax may not exceed the
+   plan's power-table size minus one (INVALID_ARG).  Asynchronous. */
+cascade_status_t cascade_get_powers(cascade_plan_t plan, int32_t sys, int32_t kmax,
+                                    double* d_out, void* stream);
+
+/* Describe the packed batch the next forward/backward calls process:
+   h_offsets [nseq+1] (int64, offsets[0] == 0, non-decreasing, last <=
+   desc.max_rows, every length <= desc.max_len) and h_sys_of_seq [nseq]
+   (each in 0..nsys-1; NULL means system 0 for every sequence).  Empty
+   sequences are allowed.  Builds the per-stage tile schedules on the host
+   and uploads them (synchronous).  Requires a system (CASCADE_ERR_STATE). */
+cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets, int32_t nseq,
+                                   const int32_t* h_sys_of_seq);
+
+/* Per-sequence N actually run (N of its system clipped so that 2^N < L):
+   h_N [nseq]. */
+cascade_status_t cascade_get_seq_N(cascade_plan_t plan, int32_t* h_N);
+
+/* Bytes of caller-provided device workspace that forward (and, for plans
+   with CASCADE_FLAG_SAVE_STATES, backward) need for the current batch. */
+cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes);
+
+/* Apply the truncated transfer function to the current batch (§3):
+   v^(0) = Bbar u, stages k = 0..N_i, y = C v + D u.  d_u [rows,p] and d_y
+   [rows,q] in the plan's element type; d_workspace of at least
+   cascade_workspace_size bytes, 256-byte aligned.  Asynchronous on stream;
+   device-side wait timeouts are reported by cascade_get_device_error. */
+cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y,
+                                 void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Reverse-mode derivative of sum(dy * y) for the last forward (which must
+   have run with CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE on this
+   workspace).  Writes d_du [rows,p] (plan element type) and, per system,
+   d_dAbar [nsys,m,m], d_dBbar [nsys,m,p], d_dC [nsys,q,m], d_dD [nsys,q,p]
+   (double).  For continuous systems d_dA [nsys,m,m] and d_dB [nsys,m,p] are
+   the gradients through Eq. (4.2) (may be NULL to skip).  Gradient pointers
+   may be NULL individually.  Asynchronous. */
+cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_dy, void* d_du,
+                                  double* d_dAbar, double* d_dBbar, double* d_dC, double* d_dD,
+                                  double* d_dA, double* d_dB, void* d_workspace,
+                                  size_t workspace_bytes, void* stream);
+
+/* FP64 sequential recursion of Eq. (1.2), x_n = Abar x_(n-1) + Bbar u_n,
+   y_n = C x_n + D u_n, one device thread block per sequence (the baseline
+   the cascade replaces).  Uses the plan's systems and batch; d_u/d_y are
+   double.  Asynchronous. */
+cascade_status_t cascade_recursion_forward(cascade_plan_t plan, const double* d_u, double* d_y,
+                                           void* stream);
+
+/* Read and clear the device error word set by bounded waits in the plan's
+   kernels (0 = none, otherwise a CASCADE_ERR_* code).  Synchronises the
+   plan's last stream. */
+cascade_status_t cascade_get_device_error(cascade_plan_t plan, int32_t* h_code);
+
+/* Self-test of the bounded-wait path: launches one block that waits on an
+   mbarrier no one arrives at, with a limit of `limit_us` microseconds, and
+   returns CASCADE_ERR_TIMEOUT when the wait gave up (as it must).  The GPU
+   context stays usable.  Synchronous. */
+cascade_status_t cascade_selftest_timeout(int32_t limit_us);
+
+/* Number of kernels this library launched since load (host-side count). */
+int64_t cascade_launch_count(void);
+
+/* Per-launch timing of the stage kernels.  When enabled, every later
+   forward records a CUDA event pair on its stream around each tensor-core
+   (or FP64) stage launch.  cascade_get_stage_times synchronises that stream
+   and copies up to `cap` entries (stage index k, milliseconds) of the LAST
+   forward into h_k / h_ms, returning the count in *n. */
+cascade_status_t cascade_enable_stage_timing(cascade_plan_t plan, int32_t enable);
+cascade_status_t cascade_get_stage_times(cascade_plan_t plan, int32_t cap, int32_t* h_k,
+                                         float* h_ms, int32_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_CASCADE_H */

@@ -1,0 +1,737 @@
+// api.cu -- the C ABI declared in include/cascade.h: plan lifecycle, system
+// preparation (discretisation, squaring chain, accuracy rule, operand
+// planes), the per-stage tile schedule of a packed batch, and the forward.
+#include "common.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+namespace cascade {
+
+long long g_launches = 0;
+static std::mutex g_err_mu;
+static std::string g_err;
+
+void set_global_error(const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = msg;
+}
+std::string global_error() {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_err;
+}
+
+int tile_rows(const Plan& p) { return p.d.precision == CASCADE_FP64 ? 64 : 128; }
+
+// N extent of one tensor-core tile.  BF16: up to 256 (one accumulator per
+// tile, two tiles in flight = 512 TMEM columns).  FP32: up to 128, because
+// that path keeps the two small correction products in a second accumulator.
+int block_n(int m, int precision) {
+  const int cap = precision == CASCADE_FP32 ? 128 : 256;
+  if (m <= cap) return m;
+  for (int bn : {256, 128, 64, 32})
+    if (bn <= cap && m % bn == 0) return bn;
+  return 0;
+}
+
+size_t plane_elem_bytes(int precision) {
+  switch (precision) {
+    case CASCADE_FP64: return 8;
+    case CASCADE_FP32: return 4;
+    default: return 2;
+  }
+}
+
+size_t state_bytes_per_row(const Plan& p) {
+  const size_t e = plane_elem_bytes(p.d.precision);
+  return (size_t)p.d.m * e * (p.d.precision == CASCADE_FP64 ? 1 : 2);
+}
+
+// ----------------------------------------------------------------- tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  });
+  return fn;
+}
+
+bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
+                    uint64_t outer, uint32_t box_inner, uint32_t box_outer, std::string* err) {
+  EncodeTiledFn enc = get_encoder();
+  if (!enc) {
+    *err = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  const CUtensorMapDataType dt =
+      elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * (uint64_t)elem_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled returned %d", (int)r);
+    *err = buf;
+    return false;
+  }
+  return true;
+}
+
+}  // namespace cascade
+
+using namespace cascade;
+
+struct cascade_plan_s : public Plan {};
+
+namespace {
+
+cascade_status_t fail(Plan* p, cascade_status_t st, const std::string& msg) {
+  if (p) p->last_error = msg;
+  set_global_error(msg);
+  return st;
+}
+
+cascade_status_t cuda_fail(Plan* p, cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(p, e == cudaErrorMemoryAllocation ? CASCADE_ERR_OOM : CASCADE_ERR_CUDA, msg);
+}
+
+#define CK(call, where)                                   \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return cuda_fail(p, _e, where); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T));
+}
+
+void dfree(void* ptr) {
+  if (ptr) cudaFree(ptr);
+}
+
+int ceil_log2(int64_t L) {
+  int k = 0;
+  while ((int64_t(1) << k) < L) ++k;
+  return k;
+}
+
+// Stages with shift 2^k >= L do nothing; a sequence of length L runs k = 0..min(N, ceil(log2 L)-1).
+int effective_N(int N, int64_t L) {
+  if (L <= 1) return 0;
+  return std::min(N, ceil_log2(L) - 1);
+}
+
+void free_batch(Plan* p) {
+  for (Tile* t : p->d_tiles) dfree(t);
+  p->d_tiles.clear();
+  p->h_tiles.clear();
+  p->n_tiles.clear();
+  dfree(p->d_seqs);
+  p->d_seqs = nullptr;
+  dfree(p->d_out_tiles);
+  p->d_out_tiles = nullptr;
+  dfree(p->d_stage0_tiles);
+  p->d_stage0_tiles = nullptr;
+  p->n_out_tiles = p->n_stage0_tiles = 0;
+  p->have_batch = false;
+  if (p->graph) {
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+}
+
+void free_system(Plan* p) {
+  void* ptrs[] = {p->P64, p->Phi, p->Plo, p->Bbar64, p->ABbar64, p->C64, p->D64, p->Bbar32,
+                  p->ABbar32, p->C32, p->D32, p->A64, p->B64, p->delta64, p->scale64};
+  for (void* q : ptrs) dfree(q);
+  p->P64 = nullptr;
+  p->Phi = p->Plo = nullptr;
+  p->Bbar64 = p->ABbar64 = p->C64 = p->D64 = nullptr;
+  p->Bbar32 = p->ABbar32 = p->C32 = p->D32 = nullptr;
+  p->A64 = p->B64 = p->delta64 = p->scale64 = nullptr;
+}
+
+// Squaring chain, accuracy rule, Abar*Bbar, operand planes; P64[:,0] and
+// Bbar64, C64, D64 are set.  Synchronises st.
+cascade_status_t finish_system(Plan* p, cudaStream_t st) {
+  const int m = p->d.m, pp = p->d.p, q = p->d.q, ns = p->d.nsys;
+  const int64_t mm = (int64_t)m * m;
+  const int64_t sys_stride = (int64_t)p->kmax1 * mm;
+  // P_{k+1} = P_k P_k  (end of §2), batched over systems
+  for (int k = 0; k + 1 < p->kmax1; ++k) {
+    CK(launch_dgemm(p->P64 + k * mm, p->P64 + k * mm, p->P64 + (k + 1) * mm, m, m, m, m, m, m,
+                    sys_stride, sys_stride, sys_stride, ns, 1.0, 0.0, false, false, st),
+       "squaring chain");
+  }
+  // Abar Bbar for the first stage fused with the input projection
+  CK(launch_dgemm(p->P64, p->Bbar64, p->ABbar64, m, pp, m, m, pp, pp, sys_stride, (int64_t)m * pp,
+                  (int64_t)m * pp, ns, 1.0, 0.0, false, false, st),
+     "Abar*Bbar");
+  // Accuracy rule
+  const int Nmax = std::max(0, ceil_log2(p->d.max_len) - 1);
+  p->N_sys.assign(ns, 0);
+  if (p->d.N >= 0) {
+    for (int s = 0; s < ns; ++s) p->N_sys[s] = std::min(p->d.N, Nmax);
+  } else {
+    double* d_norms = nullptr;
+    CK(dalloc(&d_norms, (size_t)ns * p->kmax1), "norm buffer");
+    cudaError_t e = launch_frob_norms(p->P64, ns * p->kmax1, mm, d_norms, st);
+    std::vector<double> h((size_t)ns * p->kmax1);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h.data(), d_norms, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(d_norms);
+    if (e != cudaSuccess) return cuda_fail(p, e, "norms");
+    for (int s = 0; s < ns; ++s) {
+      int N = Nmax;
+      for (int n = 0; n <= Nmax; ++n) {
+        if ((int64_t(1) << (n + 1)) >= (int64_t)p->d.max_len) { N = n; break; }
+        if (p->d.eps > 0 && h[(size_t)s * p->kmax1 + n + 1] <= p->d.eps) { N = n; break; }
+      }
+      p->N_sys[s] = N;
+    }
+  }
+  // Operand formats
+  if (p->d.precision != CASCADE_FP64) {
+    CK(launch_split_planes(p->P64, p->Phi, p->Plo, (int64_t)ns * sys_stride, p->d.precision, st),
+       "operand planes");
+    CK(launch_to_f32(p->Bbar64, p->Bbar32, (int64_t)ns * m * pp, st), "Bbar f32");
+    CK(launch_to_f32(p->ABbar64, p->ABbar32, (int64_t)ns * m * pp, st), "ABbar f32");
+    CK(launch_to_f32(p->C64, p->C32, (int64_t)ns * q * m, st), "C f32");
+    CK(launch_to_f32(p->D64, p->D32, (int64_t)ns * q * pp, st), "D f32");
+  }
+  CK(cudaStreamSynchronize(st), "set_system sync");
+  p->have_system = true;
+  if (p->have_batch) {   // the batch schedule depends on N: rebuild it
+    std::vector<int64_t> offs = p->offsets;
+    std::vector<int32_t> sys = p->sys_of_seq;
+    free_batch(p);
+    cascade_status_t r = cascade_set_batch(static_cast<cascade_plan_t>(p), offs.data(),
+                                           (int32_t)(offs.size() - 1), sys.data());
+    if (r != CASCADE_OK) return r;
+  }
+  return CASCADE_OK;
+}
+
+cascade_status_t alloc_system(Plan* p) {
+  const int m = p->d.m, pp = p->d.p, q = p->d.q, ns = p->d.nsys;
+  const size_t mm = (size_t)m * m;
+  if (p->P64) return CASCADE_OK;
+  CK(dalloc(&p->P64, (size_t)ns * p->kmax1 * mm), "alloc powers");
+  CK(dalloc(&p->Bbar64, (size_t)ns * m * pp), "alloc Bbar");
+  CK(dalloc(&p->ABbar64, (size_t)ns * m * pp), "alloc ABbar");
+  CK(dalloc(&p->C64, (size_t)ns * q * m), "alloc C");
+  CK(dalloc(&p->D64, (size_t)ns * q * pp), "alloc D");
+  if (p->d.precision != CASCADE_FP64) {
+    const size_t e = plane_elem_bytes(p->d.precision);
+    uint8_t* hi = nullptr;
+    uint8_t* lo = nullptr;
+    CK(dalloc(&hi, (size_t)ns * p->kmax1 * mm * e), "alloc planes");
+    CK(dalloc(&lo, (size_t)ns * p->kmax1 * mm * e), "alloc planes");
+    p->Phi = hi;
+    p->Plo = lo;
+    CK(dalloc(&p->Bbar32, (size_t)ns * m * pp), "alloc Bbar32");
+    CK(dalloc(&p->ABbar32, (size_t)ns * m * pp), "alloc ABbar32");
+    CK(dalloc(&p->C32, (size_t)ns * q * m), "alloc C32");
+    CK(dalloc(&p->D32, (size_t)ns * q * pp), "alloc D32");
+  }
+  return CASCADE_OK;
+}
+
+struct Planes {
+  void* hi[2];
+  void* lo[2];
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t forward_workspace(const Plan& p, int64_t rows) {
+  const size_t plane = align256((size_t)rows * p.d.m * plane_elem_bytes(p.d.precision));
+  const int nplanes = p.d.precision == CASCADE_FP64 ? 1 : 2;
+  return 2 * nplanes * plane + 256;
+}
+
+Planes carve(const Plan& p, void* ws) {
+  Planes pl{};
+  const size_t plane = align256((size_t)p.rows * p.d.m * plane_elem_bytes(p.d.precision));
+  uint8_t* base = static_cast<uint8_t*>(ws);
+  if (p.d.precision == CASCADE_FP64) {
+    pl.hi[0] = base;
+    pl.hi[1] = base + plane;
+    pl.lo[0] = pl.lo[1] = nullptr;
+  } else {
+    pl.hi[0] = base;
+    pl.lo[0] = base + plane;
+    pl.hi[1] = base + 2 * plane;
+    pl.lo[1] = base + 3 * plane;
+  }
+  return pl;
+}
+
+cudaError_t ensure_events(Plan* p, int pairs) {
+  while ((int)p->ev.size() < 2 * pairs) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    p->ev.push_back(e);
+  }
+  return cudaSuccess;
+}
+
+cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStream_t st) {
+  Planes pl = carve(*p, ws);
+  const bool timing = p->timing;
+  if (timing) {
+    CK(ensure_events(p, std::max(p->maxN, 1)), "timing events");
+    p->ev_k.clear();
+    p->n_ev = 0;
+  }
+  // stage 0 fused with v^(0) = Bbar u: writes buffer 1
+  CK(launch_stage0(*p, u, pl.hi[1], pl.lo[1], st), "first stage");
+  for (int k = 1; k <= p->maxN; ++k) {
+    const int in = k & 1, out = (k + 1) & 1;
+    if (timing && p->n_tiles[k] > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
+    if (p->d.precision == CASCADE_FP64) {
+      CK(launch_stage_f64(*p, k, static_cast<const double*>(pl.hi[in]),
+                          static_cast<double*>(pl.hi[out]), st),
+         "stage (fp64)");
+    } else {
+      CK(launch_stage_tc(*p, k, pl.hi[in], pl.lo[in], pl.hi[out], pl.lo[out],
+                         static_cast<const float*>(u), static_cast<float*>(y), st),
+         "stage (tensor core)");
+    }
+    if (timing && p->n_tiles[k] > 0) {
+      CK(cudaEventRecord(p->ev[2 * p->n_ev + 1], st), "event");
+      p->ev_k.push_back(k);
+      p->n_ev++;
+    }
+  }
+  CK(launch_output(*p, u, y, pl.hi, pl.lo, st), "output projection");
+  return CASCADE_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* cascade_status_string(cascade_status_t s) {
+  switch (s) {
+    case CASCADE_OK: return "ok";
+    case CASCADE_ERR_INVALID_ARG: return "invalid argument";
+    case CASCADE_ERR_UNSUPPORTED: return "unsupported";
+    case CASCADE_ERR_OOM: return "out of device memory";
+    case CASCADE_ERR_CUDA: return "CUDA error";
+    case CASCADE_ERR_TIMEOUT: return "device wait timed out";
+    case CASCADE_ERR_STATE: return "call order violated";
+  }
+  return "unknown status";
+}
+
+const char* cascade_last_error(cascade_plan_t plan) {
+  static thread_local std::string tmp;
+  if (plan) return plan->last_error.c_str();
+  tmp = global_error();
+  return tmp.c_str();
+}
+
+int64_t cascade_launch_count(void) { return g_launches; }
+
+cascade_status_t cascade_plan_create(cascade_plan_t* out, const cascade_desc_t* desc) {
+  Plan* p = nullptr;
+  if (!out) return fail(p, CASCADE_ERR_INVALID_ARG, "plan output pointer is NULL");
+  *out = nullptr;
+  if (!desc) return fail(p, CASCADE_ERR_INVALID_ARG, "descriptor is NULL");
+  const cascade_desc_t& d = *desc;
+  if (d.m < 1 || d.p < 1 || d.q < 1 || d.nsys < 1 || d.max_len < 1 || d.max_rows < 0)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "m, p, q, nsys, max_len must be >= 1, max_rows >= 0");
+  if (d.precision != CASCADE_FP64 && d.precision != CASCADE_FP32 &&
+      d.precision != CASCADE_BF16_SPLIT)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "unknown precision");
+  if (d.N < -1 || d.N > 40) return fail(p, CASCADE_ERR_INVALID_ARG, "N must be in -1..40");
+  if (d.N < 0 && !(d.eps >= 0.0)) return fail(p, CASCADE_ERR_INVALID_ARG, "eps must be >= 0");
+  if (d.precision != CASCADE_FP64) {
+    const int kc = d.precision == CASCADE_BF16_SPLIT ? 64 : 32;
+    if (d.m % kc != 0 || d.m > 4096 || block_n(d.m, d.precision) == 0)
+      return fail(p, CASCADE_ERR_UNSUPPORTED,
+                  "tensor-core precisions need m a multiple of 64 (BF16) or 32 (FP32), m <= 4096");
+    if (d.max_rows >= (int64_t(1) << 31))
+      return fail(p, CASCADE_ERR_UNSUPPORTED, "max_rows must be < 2^31 (TMA coordinates)");
+  } else if (d.m > 4096) {
+    return fail(p, CASCADE_ERR_UNSUPPORTED, "m must be <= 4096");
+  }
+  p = new (std::nothrow) cascade_plan_s();
+  if (!p) return fail(nullptr, CASCADE_ERR_OOM, "host allocation failed");
+  p->d = d;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    delete static_cast<cascade_plan_s*>(p);
+    return fail(nullptr, CASCADE_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  const int Nmax = std::max(0, ceil_log2(d.max_len) - 1);
+  p->kmax1 = (d.N >= 0) ? std::min(d.N, Nmax) + 1 : Nmax + 2;
+  p->fuse_output = d.precision != CASCADE_FP64 && !(d.flags & CASCADE_FLAG_NO_FUSED_OUTPUT) &&
+                   block_n(d.m, d.precision) == d.m && d.q <= 16;
+  e = cudaMalloc(&p->err, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int32_t));
+  if (e != cudaSuccess) {
+    delete static_cast<cascade_plan_s*>(p);
+    return fail(nullptr, CASCADE_ERR_OOM, "device error word allocation failed");
+  }
+  *out = static_cast<cascade_plan_t>(p);
+  return CASCADE_OK;
+}
+
+void cascade_plan_destroy(cascade_plan_t plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
+  if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+  free_batch(plan);
+  free_system(plan);
+  dfree(plan->err);
+  delete plan;
+}
+
+cascade_status_t cascade_set_system_continuous(cascade_plan_t plan, const double* d_A,
+                                               const double* d_B, const double* d_delta,
+                                               const double* d_abar_scale, const double* d_C,
+                                               const double* d_D, void* stream) {
+  Plan* p = plan;
+  if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
+  if (!d_A || !d_B || !d_delta || !d_C || !d_D)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "A, B, delta, C, D must be device pointers");
+  cascade_status_t r = alloc_system(p);
+  if (r != CASCADE_OK) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int m = p->d.m, pp = p->d.p, q = p->d.q, ns = p->d.nsys;
+  // keep the continuous system for the discretisation adjoint
+  if (!p->A64) {
+    CK(dalloc(&p->A64, (size_t)ns * m * m), "alloc A");
+    CK(dalloc(&p->B64, (size_t)ns * m * pp), "alloc B");
+    CK(dalloc(&p->delta64, (size_t)ns), "alloc delta");
+    CK(dalloc(&p->scale64, (size_t)ns), "alloc scale");
+  }
+  CK(cudaMemcpyAsync(p->A64, d_A, sizeof(double) * ns * m * m, cudaMemcpyDeviceToDevice, st), "copy A");
+  CK(cudaMemcpyAsync(p->B64, d_B, sizeof(double) * ns * m * pp, cudaMemcpyDeviceToDevice, st), "copy B");
+  CK(cudaMemcpyAsync(p->delta64, d_delta, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st), "copy delta");
+  if (d_abar_scale) {
+    CK(cudaMemcpyAsync(p->scale64, d_abar_scale, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st),
+       "copy scale");
+  } else {
+    std::vector<double> ones(ns, 1.0);
+    CK(cudaMemcpyAsync(p->scale64, ones.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st),
+       "copy scale");
+    CK(cudaStreamSynchronize(st), "sync");
+  }
+  CK(cudaMemcpyAsync(p->C64, d_C, sizeof(double) * ns * q * m, cudaMemcpyDeviceToDevice, st), "copy C");
+  CK(cudaMemcpyAsync(p->D64, d_D, sizeof(double) * ns * q * pp, cudaMemcpyDeviceToDevice, st), "copy D");
+  double* work = nullptr;
+  int32_t* sing = nullptr;
+  CK(dalloc(&work, (size_t)ns * m * (2 * m + pp)), "discretisation workspace");
+  cudaError_t e = cudaMalloc(&sing, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(sing, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess)
+    e = launch_discretise(p->A64, p->B64, p->delta64, p->scale64, p->P64,
+                          (int64_t)p->kmax1 * m * m, p->Bbar64, work, ns, m, pp, sing, st);
+  int32_t h_sing = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_sing, sing, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dfree(work);
+  dfree(sing);
+  if (e != cudaSuccess) return cuda_fail(p, e, "discretisation");
+  if (h_sing) return fail(p, CASCADE_ERR_INVALID_ARG, "I - delta/2 A is singular for some system");
+  p->continuous = true;
+  return finish_system(p, st);
+}
+
+cascade_status_t cascade_set_system_discrete(cascade_plan_t plan, const double* d_Abar,
+                                             const double* d_Bbar, const double* d_C,
+                                             const double* d_D, void* stream) {
+  Plan* p = plan;
+  if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
+  if (!d_Abar || !d_Bbar || !d_C || !d_D)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "Abar, Bbar, C, D must be device pointers");
+  cascade_status_t r = alloc_system(p);
+  if (r != CASCADE_OK) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int m = p->d.m, pp = p->d.p, q = p->d.q, ns = p->d.nsys;
+  const size_t mm = (size_t)m * m;
+  CK(cudaMemcpy2DAsync(p->P64, sizeof(double) * mm * p->kmax1, d_Abar, sizeof(double) * mm,
+                       sizeof(double) * mm, ns, cudaMemcpyDeviceToDevice, st),
+     "copy Abar");
+  CK(cudaMemcpyAsync(p->Bbar64, d_Bbar, sizeof(double) * ns * m * pp, cudaMemcpyDeviceToDevice, st),
+     "copy Bbar");
+  CK(cudaMemcpyAsync(p->C64, d_C, sizeof(double) * ns * q * m, cudaMemcpyDeviceToDevice, st), "copy C");
+  CK(cudaMemcpyAsync(p->D64, d_D, sizeof(double) * ns * q * pp, cudaMemcpyDeviceToDevice, st), "copy D");
+  p->continuous = false;
+  return finish_system(p, st);
+}
+
+cascade_status_t cascade_get_N(cascade_plan_t plan, int32_t* h_N) {
+  Plan* p = plan;
+  if (!p || !h_N) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  if (!p->have_system) return fail(p, CASCADE_ERR_STATE, "no system set");
+  memcpy(h_N, p->N_sys.data(), sizeof(int32_t) * p->N_sys.size());
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_get_powers(cascade_plan_t plan, int32_t sys, int32_t kmax, double* d_out,
+                                    void* stream) {
+  Plan* p = plan;
+  if (!p || !d_out) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  if (!p->have_system) return fail(p, CASCADE_ERR_STATE, "no system set");
+  if (sys < 0 || sys >= p->d.nsys || kmax < 0 || kmax >= p->kmax1)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "sys or kmax out of range");
+  const size_t mm = (size_t)p->d.m * p->d.m;
+  CK(cudaMemcpyAsync(d_out, p->P64 + (size_t)sys * p->kmax1 * mm, sizeof(double) * mm * (kmax + 1),
+                     cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)),
+     "copy powers");
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets, int32_t nseq,
+                                   const int32_t* h_sys_of_seq) {
+  Plan* p = plan;
+  if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->have_system) return fail(p, CASCADE_ERR_STATE, "set a system before the batch");
+  if (nseq < 0 || (nseq > 0 && !h_offsets))
+    return fail(p, CASCADE_ERR_INVALID_ARG, "offsets missing or nseq < 0");
+  if (nseq > 0 && h_offsets[0] != 0) return fail(p, CASCADE_ERR_INVALID_ARG, "offsets[0] != 0");
+  for (int i = 0; i < nseq; ++i) {
+    const int64_t L = h_offsets[i + 1] - h_offsets[i];
+    if (L < 0) return fail(p, CASCADE_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    if (L > p->d.max_len) return fail(p, CASCADE_ERR_INVALID_ARG, "sequence longer than max_len");
+    if (h_sys_of_seq && (h_sys_of_seq[i] < 0 || h_sys_of_seq[i] >= p->d.nsys))
+      return fail(p, CASCADE_ERR_INVALID_ARG, "sys_of_seq out of range");
+  }
+  const int64_t rows = nseq > 0 ? h_offsets[nseq] : 0;
+  if (rows > p->d.max_rows) return fail(p, CASCADE_ERR_INVALID_ARG, "more rows than max_rows");
+
+  free_batch(p);
+  p->nseq = nseq;
+  p->rows = rows;
+  p->offsets.assign(h_offsets, h_offsets + (nseq > 0 ? nseq + 1 : 0));
+  if (nseq == 0) p->offsets.assign(1, 0);
+  p->sys_of_seq.assign(nseq, 0);
+  if (h_sys_of_seq) p->sys_of_seq.assign(h_sys_of_seq, h_sys_of_seq + nseq);
+  p->seq_N.assign(nseq, -1);
+  const int BM = tile_rows(*p);
+  int maxN = -1;
+  std::vector<Tile> t0s, outs;
+  std::vector<Seq> seqs;
+  for (int i = 0; i < nseq; ++i) {
+    const int64_t L = h_offsets[i + 1] - h_offsets[i];
+    const int sys = p->sys_of_seq[i];
+    if (L == 0) continue;
+    const int N = effective_N(p->N_sys[sys], L);
+    p->seq_N[i] = N;
+    maxN = std::max(maxN, N);
+    seqs.push_back(Seq{h_offsets[i], (int32_t)L, sys, N, 0});
+    for (int64_t t = 0; t < L; t += BM) t0s.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, 0, 0, 0});
+  }
+  p->maxN = maxN;
+  p->h_tiles.assign(std::max(maxN + 1, 1), {});
+  for (int i = 0; i < nseq; ++i) {
+    const int64_t L = h_offsets[i + 1] - h_offsets[i];
+    if (L == 0) continue;
+    const int N = p->seq_N[i], sys = p->sys_of_seq[i];
+    const bool fused_last = p->fuse_output && N >= 1;
+    for (int k = 1; k <= N; ++k) {
+      const bool fused = fused_last && k == N;
+      const int64_t prev_shift = int64_t(1) << (k - 1);
+      for (int64_t t = 0; t < L; t += BM) {
+        // rows below 2^(k-1) already hold their final value in the output buffer
+        if (!fused && k >= 2 && t + BM <= prev_shift) continue;
+        p->h_tiles[k].push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys,
+                                     fused ? (int32_t)TILE_FINAL_FUSED : 0, 0, 0});
+      }
+    }
+    if (!fused_last) {
+      for (int64_t t = 0; t < L; t += BM)
+        outs.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, (N + 1) & 1, 0, 0});
+    }
+  }
+  auto upload = [&](const std::vector<Tile>& v, Tile** d) -> cudaError_t {
+    *d = nullptr;
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc(d, v.size() * sizeof(Tile));
+    if (e == cudaSuccess) e = cudaMemcpy(*d, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    return e;
+  };
+  p->d_tiles.assign(p->h_tiles.size(), nullptr);
+  p->n_tiles.assign(p->h_tiles.size(), 0);
+  for (size_t k = 0; k < p->h_tiles.size(); ++k) {
+    CK(upload(p->h_tiles[k], &p->d_tiles[k]), "upload stage schedule");
+    p->n_tiles[k] = (int32_t)p->h_tiles[k].size();
+  }
+  CK(upload(t0s, &p->d_stage0_tiles), "upload first-stage schedule");
+  p->n_stage0_tiles = (int)t0s.size();
+  CK(upload(outs, &p->d_out_tiles), "upload output schedule");
+  p->n_out_tiles = (int)outs.size();
+  if (!seqs.empty()) {
+    CK(cudaMalloc(&p->d_seqs, seqs.size() * sizeof(Seq)), "alloc sequences");
+    CK(cudaMemcpy(p->d_seqs, seqs.data(), seqs.size() * sizeof(Seq), cudaMemcpyHostToDevice),
+       "upload sequences");
+  }
+  p->nseq = (int)seqs.size() == nseq ? nseq : nseq;
+  p->have_batch = true;
+  p->batch_id++;
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_get_seq_N(cascade_plan_t plan, int32_t* h_N) {
+  Plan* p = plan;
+  if (!p || !h_N) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  if (!p->have_batch) return fail(p, CASCADE_ERR_STATE, "no batch set");
+  memcpy(h_N, p->seq_N.data(), sizeof(int32_t) * p->seq_N.size());
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes) {
+  Plan* p = plan;
+  if (!p || !bytes) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  if (!p->have_batch) return fail(p, CASCADE_ERR_STATE, "no batch set");
+  *bytes = forward_workspace(*p, p->rows);
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y,
+                                 void* d_workspace, size_t workspace_bytes, void* stream) {
+  Plan* p = plan;
+  if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->have_system || !p->have_batch) return fail(p, CASCADE_ERR_STATE, "system and batch must be set");
+  if (p->rows == 0) return CASCADE_OK;
+  if (!d_u || !d_y || !d_workspace)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "u, y, workspace must be device pointers");
+  if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  if (workspace_bytes < forward_workspace(*p, p->rows))
+    return fail(p, CASCADE_ERR_INVALID_ARG, "workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  p->last_stream = stream;
+  if (p->d.flags & CASCADE_FLAG_GRAPH) {
+    const bool hit = p->graph && p->graph_key[0] == d_u && p->graph_key[1] == d_y &&
+                     p->graph_key[2] == d_workspace && p->graph_batch_id == p->batch_id;
+    if (!hit) {
+      if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+      }
+      if (!p->cap_stream)
+        CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "capture stream");
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      cascade_status_t r = run_forward(p, d_u, d_y, d_workspace, p->cap_stream);
+      cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+      if (r != CASCADE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess) return cuda_fail(p, e, "end capture");
+      e = cudaGraphInstantiate(&p->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(p, e, "graph instantiate");
+      p->graph_key[0] = d_u;
+      p->graph_key[1] = d_y;
+      p->graph_key[2] = d_workspace;
+      p->graph_batch_id = p->batch_id;
+    }
+    CK(cudaGraphLaunch(p->graph, st), "graph launch");
+    return CASCADE_OK;
+  }
+  return run_forward(p, d_u, d_y, d_workspace, st);
+}
+
+cascade_status_t cascade_backward(cascade_plan_t plan, const void*, void*, double*, double*,
+                                  double*, double*, double*, double*, void*, size_t, void*) {
+  return fail(plan, CASCADE_ERR_UNSUPPORTED, "backward not available in this build");
+}
+
+cascade_status_t cascade_recursion_forward(cascade_plan_t plan, const double* d_u, double* d_y,
+                                           void* stream) {
+  Plan* p = plan;
+  if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->have_system || !p->have_batch) return fail(p, CASCADE_ERR_STATE, "system and batch must be set");
+  if (p->rows == 0) return CASCADE_OK;
+  if (!d_u || !d_y) return fail(p, CASCADE_ERR_INVALID_ARG, "u, y must be device pointers");
+  CK(launch_recursion_f64(*p, d_u, d_y, static_cast<cudaStream_t>(stream)), "recursion");
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_get_device_error(cascade_plan_t plan, int32_t* h_code) {
+  Plan* p = plan;
+  if (!p || !h_code) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(p->last_stream);
+  CK(cudaStreamSynchronize(st), "sync");
+  CK(cudaMemcpy(h_code, p->err, sizeof(int32_t), cudaMemcpyDeviceToHost), "read error word");
+  CK(cudaMemset(p->err, 0, sizeof(int32_t)), "clear error word");
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_enable_stage_timing(cascade_plan_t plan, int32_t enable) {
+  Plan* p = plan;
+  if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
+  if (enable && (p->d.flags & CASCADE_FLAG_GRAPH))
+    return fail(p, CASCADE_ERR_UNSUPPORTED, "stage timing is not available with graph replay");
+  p->timing = enable != 0;
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_get_stage_times(cascade_plan_t plan, int32_t cap, int32_t* h_k,
+                                         float* h_ms, int32_t* n) {
+  Plan* p = plan;
+  if (!p || !n || (cap > 0 && (!h_k || !h_ms))) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  CK(cudaStreamSynchronize(static_cast<cudaStream_t>(p->last_stream)), "sync");
+  const int cnt = std::min(cap, p->n_ev);
+  for (int i = 0; i < cnt; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]), "elapsed");
+    h_k[i] = p->ev_k[i];
+    h_ms[i] = ms;
+  }
+  *n = p->n_ev;
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_selftest_timeout(int32_t limit_us) {
+  Plan* p = nullptr;
+  if (limit_us <= 0 || limit_us > 10000000)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "limit_us must be in 1..1e7");
+  int32_t* d_err = nullptr;
+  CK(cudaMalloc(&d_err, sizeof(int32_t)), "alloc");
+  cudaError_t e = cudaMemset(d_err, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = launch_selftest_timeout(limit_us, d_err, 0);
+  int32_t h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return cuda_fail(p, e, "self-test");
+  return h == CASCADE_ERR_TIMEOUT ? CASCADE_ERR_TIMEOUT : CASCADE_OK;
+}
+
+}  // extern "C"

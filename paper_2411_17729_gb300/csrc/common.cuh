@@ -1,0 +1,173 @@
+// common.cuh -- shared declarations of the cascade library (host + device).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cascade.h"
+
+namespace cascade {
+
+// ---------------------------------------------------------------- host side
+extern long long g_launches;                      // kernels launched (host count)
+void set_global_error(const std::string& msg);
+std::string global_error();
+
+#define CASCADE_LAUNCHED() (++::cascade::g_launches)
+
+// Tile of one stage: BM consecutive time steps of one sequence.
+struct Tile {
+  int64_t seq_row0;   // packed row of the sequence's first time step
+  int32_t t0;         // first time step of the tile within the sequence
+  int32_t len;        // sequence length L_i
+  int32_t sys;        // system index
+  int32_t flags;      // TILE_FINAL_FUSED: last stage with y = Cv + Du fused
+  int32_t pad0, pad1;
+};
+static_assert(sizeof(Tile) == 32, "Tile is 32 bytes");
+enum { TILE_FINAL_FUSED = 1 };
+
+// Sequence record (output kernel, recursion, backward).
+struct Seq {
+  int64_t row0;
+  int32_t len;
+  int32_t sys;
+  int32_t N;          // last stage index run for this sequence
+  int32_t flags;      // SEQ_FUSED: output already written by the last stage
+};
+enum { SEQ_FUSED = 1 };
+
+// Everything a stage launch needs besides tensor maps.
+struct StageArgs {
+  const Tile* tiles;
+  int32_t ntiles;
+  int32_t nblocks;        // m / BN
+  int32_t m, p, q;
+  int32_t BN;
+  int32_t stages;         // SMEM pipeline depth
+  int32_t shift;          // 2^k
+  int32_t k;              // stage index
+  int32_t kmax1;          // power-table entries per system
+  const void* vin_hi;     // residual planes (row-major [rows, m])
+  const void* vin_lo;
+  void* vout_hi;
+  void* vout_lo;
+  const float* C32;       // [nsys, q, m]   (fused output)
+  const float* D32;       // [nsys, q, p]
+  const float* u;         // [rows, p]
+  float* y;               // [rows, q]
+  int32_t* err;           // device error word
+  unsigned long long timeout_ns;
+};
+
+// ---------------------------------------------------------------- device side
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+#endif
+
+// ------------------------------------------------------------- plan (host)
+struct Plan {
+  cascade_desc_t d;
+  int device = 0;
+  int num_sms = 0;
+  std::string last_error;
+  // systems
+  bool have_system = false;
+  bool continuous = false;
+  int kmax1 = 0;                 // entries in the power table per system
+  double* P64 = nullptr;         // [nsys, kmax1, m, m]
+  void* Phi = nullptr;           // operand planes [nsys, kmax1, m, m] (bf16 or fp32)
+  void* Plo = nullptr;
+  double* Bbar64 = nullptr;      // [nsys, m, p]
+  double* ABbar64 = nullptr;     // [nsys, m, p]   Abar * Bbar (first stage fused with Bbar u)
+  double* C64 = nullptr;         // [nsys, q, m]
+  double* D64 = nullptr;         // [nsys, q, p]
+  float* Bbar32 = nullptr;
+  float* ABbar32 = nullptr;
+  float* C32 = nullptr;
+  float* D32 = nullptr;
+  double* A64 = nullptr;         // continuous A (for the discretisation adjoint) [nsys,m,m]
+  double* B64 = nullptr;         // continuous B [nsys,m,p]
+  double* delta64 = nullptr;     // [nsys]
+  double* scale64 = nullptr;     // [nsys] or null
+  std::vector<int32_t> N_sys;
+  int32_t* err = nullptr;        // device error word
+  // batch
+  bool have_batch = false;
+  int64_t rows = 0;
+  int nseq = 0;
+  int maxN = -1;                 // largest per-sequence N in the batch
+  std::vector<int64_t> offsets;
+  std::vector<int32_t> sys_of_seq;
+  std::vector<int32_t> seq_N;
+  std::vector<std::vector<Tile>> h_tiles;   // per stage k = 1..maxN
+  std::vector<Tile*> d_tiles;                // device copies
+  std::vector<int32_t> n_tiles;
+  Seq* d_seqs = nullptr;                     // all sequences
+  int n_out_tiles = 0;                       // tiles of sequences whose output is not fused
+  Tile* d_out_tiles = nullptr;               // (flags = workspace buffer of the final states)
+  Tile* d_stage0_tiles = nullptr;            // tiles for the first stage (all rows)
+  int n_stage0_tiles = 0;
+  bool fuse_output = false;
+  void* last_stream = nullptr;
+  // per-launch stage timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;            // pairs per stage
+  std::vector<int32_t> ev_k;
+  int n_ev = 0;
+  // graph cache (recorded on a plan-owned stream: the legacy default stream
+  // cannot be captured; the graph is then launched on the caller's stream)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_key[3] = {nullptr, nullptr, nullptr};
+  int64_t graph_batch_id = -1;
+  int64_t batch_id = 0;
+};
+
+// Geometry helpers shared by host code.
+int tile_rows(const Plan& p);                 // BM for the plan's precision
+int block_n(int m, int precision);            // BN for tensor-core precisions
+size_t plane_elem_bytes(int precision);       // bytes per element per plane
+size_t state_bytes_per_row(const Plan& p);    // bytes of one state row (all planes)
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_discretise(const double* A, const double* B, const double* delta,
+                              const double* scale, double* Abar_out, int64_t abar_sys_stride,
+                              double* Bbar_out, double* work, int nsys, int m, int p,
+                              int32_t* singular, cudaStream_t st);
+cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
+                         int lda, int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC,
+                         int batch, double alpha, double beta, bool transA, bool transB,
+                         cudaStream_t st);
+cudaError_t launch_frob_norms(const double* P, int nmat, int64_t elems, double* out,
+                              cudaStream_t st);
+cudaError_t launch_split_planes(const double* src, void* hi, void* lo, int64_t n, int precision,
+                                cudaStream_t st);
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
+
+cudaError_t launch_stage0(const Plan& p, const void* u, void* out_hi, void* out_lo,
+                          cudaStream_t st);
+cudaError_t launch_stage_f64(const Plan& p, int k, const double* vin, double* vout,
+                             cudaStream_t st);
+cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
+                            void* vout_hi, void* vout_lo, const float* u, float* y,
+                            cudaStream_t st);
+cudaError_t launch_output(const Plan& p, const void* u, void* y, void* const* ws_planes_hi,
+                          void* const* ws_planes_lo, cudaStream_t st);
+cudaError_t launch_recursion_f64(const Plan& p, const double* u, double* y, cudaStream_t st);
+cudaError_t launch_selftest_timeout(int32_t limit_us, int32_t* err, cudaStream_t st);
+
+// Tensor-map encoder resolved through the runtime's driver entry point.
+bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
+                    uint64_t outer, uint32_t box_inner, uint32_t box_outer, std::string* err);
+
+}  // namespace cascade

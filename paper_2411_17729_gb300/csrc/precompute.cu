@@ -1,0 +1,302 @@
+// precompute.cu -- FP64 system preparation on the device:
+//   trapezoidal discretisation (§1 after Eq. 1.2, Eq. 4.2),
+//   powers Abar^(2^k) by repeated squaring (end of §2, §4),
+//   Frobenius norms for the accuracy rule (Lemma 1, remainder reading),
+//   conversion of the powers into tensor-core operand planes (hi + lo).
+#include "common.cuh"
+
+#include <math.h>
+
+namespace cascade {
+
+// ----------------------------------------------------------------------------
+// Discretisation: one thread block per system solves
+//   (I - delta/2 A) [Abar | Bbar] = [I + delta/2 A | delta B]
+// by Gauss-Jordan elimination with partial pivoting, in FP64, on an augmented
+// m x (2m + p) matrix held in global memory.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) discretise_kernel(
+    const double* __restrict__ A, const double* __restrict__ B, const double* __restrict__ delta,
+    const double* __restrict__ scale, double* __restrict__ Abar, int64_t abar_stride,
+    double* __restrict__ Bbar, double* __restrict__ work, int m, int p, int32_t* singular) {
+  extern __shared__ double fac[];          // m elimination factors
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_piv;
+  __shared__ double s_inv;
+  const int s = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int W = 2 * m + p;
+  const double dl = delta[s];
+  const double h = 0.5 * dl;
+  const double* As = A + (int64_t)s * m * m;
+  const double* Bs = B + (int64_t)s * m * p;
+  double* T = work + (int64_t)s * m * W;
+
+  for (int64_t idx = tid; idx < (int64_t)m * W; idx += nt) {
+    const int i = (int)(idx / W), j = (int)(idx % W);
+    double v;
+    if (j < m) v = (i == j ? 1.0 : 0.0) - h * As[(int64_t)i * m + j];
+    else if (j < 2 * m) v = (i == j - m ? 1.0 : 0.0) + h * As[(int64_t)i * m + (j - m)];
+    else v = dl * Bs[(int64_t)i * p + (j - 2 * m)];
+    T[idx] = v;
+  }
+  __syncthreads();
+
+  for (int c = 0; c < m; ++c) {
+    // pivot: largest |T[i][c]| for i >= c (smallest index on ties)
+    double best = -1.0;
+    int bi = c;
+    for (int i = c + tid; i < m; i += nt) {
+      const double a = fabs(T[(int64_t)i * W + c]);
+      if (a > best) { best = a; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = red_v[0];
+      int i0 = red_i[0];
+      for (int w = 1; w < (nt + 31) / 32; ++w)
+        if (red_v[w] > b || (red_v[w] == b && red_i[w] < i0)) { b = red_v[w]; i0 = red_i[w]; }
+      s_piv = i0;
+      if (!(b > 0.0)) atomicExch(singular, 1);
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != c) {
+      for (int j = c + tid; j < W; j += nt) {
+        const double t = T[(int64_t)c * W + j];
+        T[(int64_t)c * W + j] = T[(int64_t)piv * W + j];
+        T[(int64_t)piv * W + j] = t;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const double d = T[(int64_t)c * W + c];
+      s_inv = d != 0.0 ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    for (int j = c + tid; j < W; j += nt) T[(int64_t)c * W + j] *= inv;
+    for (int i = tid; i < m; i += nt) fac[i] = (i == c) ? 0.0 : T[(int64_t)i * W + c];
+    __syncthreads();
+    const int wc = W - c;
+    for (int64_t idx = tid; idx < (int64_t)m * wc; idx += nt) {
+      const int i = (int)(idx / wc), j = c + (int)(idx % wc);
+      const double f = fac[i];
+      if (f != 0.0) T[(int64_t)i * W + j] -= f * T[(int64_t)c * W + j];
+    }
+    __syncthreads();
+  }
+
+  const double sc = scale ? scale[s] : 1.0;
+  double* Ab = Abar + (int64_t)s * abar_stride;
+  for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    Ab[idx] = sc * T[(int64_t)i * W + m + j];
+  }
+  double* Bb = Bbar + (int64_t)s * m * p;
+  for (int64_t idx = tid; idx < (int64_t)m * p; idx += nt) {
+    const int i = (int)(idx / p), j = (int)(idx % p);
+    Bb[idx] = T[(int64_t)i * W + 2 * m + j];
+  }
+}
+
+cudaError_t launch_discretise(const double* A, const double* B, const double* delta,
+                              const double* scale, double* Abar_out, int64_t abar_sys_stride,
+                              double* Bbar_out, double* work, int nsys, int m, int p,
+                              int32_t* singular, cudaStream_t st) {
+  const size_t smem = sizeof(double) * (size_t)m;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(discretise_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  discretise_kernel<<<nsys, 1024, smem, st>>>(A, B, delta, scale, Abar_out, abar_sys_stride,
+                                               Bbar_out, work, m, p, singular);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Batched FP64 GEMM  C = alpha op(A) op(B) + beta C  (row-major), 64x64 tiles,
+// 4x4 outputs per thread.  Used for the squaring chain P_{k+1} = P_k P_k, the
+// product Abar Bbar, and the adjoint of the squaring chain.
+// ----------------------------------------------------------------------------
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) dgemm_kernel(const double* __restrict__ A,
+                                                    const double* __restrict__ B,
+                                                    double* __restrict__ C, int M, int N, int K,
+                                                    int lda, int ldb, int ldc, int64_t sA,
+                                                    int64_t sB, int64_t sC, double alpha,
+                                                    double beta) {
+  __shared__ double As[16][65];
+  __shared__ double Bs[16][65];
+  A += (int64_t)blockIdx.z * sA;
+  B += (int64_t)blockIdx.z * sB;
+  C += (int64_t)blockIdx.z * sC;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int mm, kk;
+      if (!TA) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      double v = 0.0;
+      if (gm < M && gk < K) v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int nn, kk;
+      if (!TB) { nn = e & 63; kk = e >> 6; } else { kk = e & 15; nn = e >> 4; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      double v = 0.0;
+      if (gn < N && gk < K) v = TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      double* c = C + (int64_t)gm * ldc + gn;
+      *c = alpha * acc[i][j] + (beta != 0.0 ? beta * *c : 0.0);
+    }
+  }
+}
+
+cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
+                         int lda, int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC,
+                         int batch, double alpha, double beta, bool transA, bool transB,
+                         cudaStream_t st) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+  if (!transA && !transB)
+    dgemm_kernel<false, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+  else if (transA && !transB)
+    dgemm_kernel<true, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+  else if (!transA && transB)
+    dgemm_kernel<false, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+  else
+    dgemm_kernel<true, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Frobenius norm of each of nmat contiguous matrices of `elems` entries.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) frob_kernel(const double* __restrict__ P, int64_t elems,
+                                                   double* __restrict__ out) {
+  __shared__ double red[8];
+  const double* X = P + (int64_t)blockIdx.x * elems;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < elems; i += blockDim.x) s = fma(X[i], X[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    out[blockIdx.x] = sqrt(t);
+  }
+}
+
+cudaError_t launch_frob_norms(const double* P, int nmat, int64_t elems, double* out,
+                              cudaStream_t st) {
+  if (nmat <= 0) return cudaSuccess;
+  frob_kernel<<<nmat, 256, 0, st>>>(P, elems, out);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Operand planes: x (FP64) -> (hi, lo) with hi + lo ~ x.
+//   BF16 split: hi = RN_bf16(x), lo = RN_bf16(x - hi).
+//   FP32 (TF32 pair): hi = RNA_tf32(x), lo = RNA_tf32(x - hi); both are exact TF32
+//   values, so the tensor core's use of the top 19 bits does not truncate them.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__global__ void split_bf16_kernel(const double* __restrict__ src, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = src[i];
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    hi[i] = h;
+    lo[i] = __double2bfloat16(x - (double)__bfloat162float(h));
+  }
+}
+
+__global__ void split_tf32_kernel(const double* __restrict__ src, float* __restrict__ hi,
+                                  float* __restrict__ lo, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = src[i];
+    const float h = tf32_rna((float)x);
+    hi[i] = h;
+    lo[i] = tf32_rna((float)(x - (double)h));
+  }
+}
+
+cudaError_t launch_split_planes(const double* src, void* hi, void* lo, int64_t n, int precision,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (precision == CASCADE_BF16_SPLIT)
+    split_bf16_kernel<<<blocks, 256, 0, st>>>(src, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, n);
+  else
+    split_tf32_kernel<<<blocks, 256, 0, st>>>(src, (float*)hi, (float*)lo, n);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  to_f32_kernel<<<blocks, 256, 0, st>>>(src, dst, n);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+}  // namespace cascade

@@ -1,0 +1,346 @@
+// stage_simt.cu -- cascade kernels on the CUDA cores:
+//   * the first stage fused with the input projection,
+//       v^(1)_l = Bbar u_l + (Abar Bbar) u_(l-1)      (§3: v^(0) = Bbar u, Eq. 3.2),
+//     so v^(0) never exists in memory and the m x m product of stage 0 becomes
+//     an m x 2p one;
+//   * the FP64 stage v_l <- v_l + P v_(l-s) (general step of §3) for the FP64
+//     path, tiled 64 x 64 with FP64 FMAs;
+//   * the output projection y = C v + D u (end of §3) where it is not fused;
+//   * the FP64 sequential recursion of Eq. (1.2), the baseline the cascade
+//     replaces;
+//   * a bounded-wait self-test.
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace cascade {
+namespace {
+
+// Storage formats of a state row.
+enum { FMT_F64 = 0, FMT_BF16 = 2, FMT_F32 = 4 };
+
+template <int FMT>
+struct Store;
+template <>
+struct Store<FMT_F64> {
+  static __device__ __forceinline__ void put(void* hi, void*, int64_t i, double v) {
+    static_cast<double*>(hi)[i] = v;
+  }
+  static __device__ __forceinline__ double get(const void* hi, const void*, int64_t i) {
+    return static_cast<const double*>(hi)[i];
+  }
+};
+template <>
+struct Store<FMT_BF16> {
+  static __device__ __forceinline__ void put(void* hi, void* lo, int64_t i, double v) {
+    const float x = (float)v;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    static_cast<__nv_bfloat16*>(hi)[i] = h;
+    static_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+  static __device__ __forceinline__ double get(const void* hi, const void* lo, int64_t i) {
+    return (double)(__bfloat162float(static_cast<const __nv_bfloat16*>(hi)[i]) +
+                    __bfloat162float(static_cast<const __nv_bfloat16*>(lo)[i]));
+  }
+};
+template <>
+struct Store<FMT_F32> {
+  static __device__ __forceinline__ void put(void* hi, void* lo, int64_t i, double v) {
+    const float x = (float)v;
+    const float h = ptx::tf32_rna(x);
+    static_cast<float*>(hi)[i] = h;
+    static_cast<float*>(lo)[i] = ptx::tf32_rna(x - h);
+  }
+  static __device__ __forceinline__ double get(const void* hi, const void* lo, int64_t i) {
+    return (double)(static_cast<const float*>(hi)[i] + static_cast<const float*>(lo)[i]);
+  }
+};
+
+// ---------------------------------------------------------------- first stage
+// One block per tile of BM rows; thread items (row, column) with the column
+// fastest.  T is the element type of u and of the coefficient matrices.
+template <int FMT, typename T>
+__global__ void __launch_bounds__(256) stage0_kernel(const Tile* __restrict__ tiles, int BM, int m,
+                                                     int p, const T* __restrict__ u,
+                                                     const T* __restrict__ Bbar,
+                                                     const T* __restrict__ ABbar, void* out_hi,
+                                                     void* out_lo) {
+  const Tile t = tiles[blockIdx.x];
+  const int rows = min(BM, t.len - t.t0);
+  const T* Bs = Bbar + (int64_t)t.sys * m * p;
+  const T* ABs = ABbar + (int64_t)t.sys * m * p;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)rows * m; idx += blockDim.x) {
+    const int r = (int)(idx / m), c = (int)(idx % m);
+    const int l = t.t0 + r;
+    const int64_t row = t.seq_row0 + l;
+    const T* ur = u + row * p;
+    double acc = 0.0;
+    for (int j = 0; j < p; ++j) acc = fma((double)Bs[(int64_t)c * p + j], (double)ur[j], acc);
+    if (l >= 1) {
+      const T* up = ur - p;
+      for (int j = 0; j < p; ++j) acc = fma((double)ABs[(int64_t)c * p + j], (double)up[j], acc);
+    }
+    Store<FMT>::put(out_hi, out_lo, row * m + c, acc);
+  }
+}
+
+// ---------------------------------------------------------------- FP64 stage
+// Block: 64 rows x 64 state columns of one tile, 256 threads, 4x4 outputs each.
+__global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__ tiles, int m,
+                                                        int shift, const double* __restrict__ P,
+                                                        int64_t p_sys_stride,
+                                                        const double* __restrict__ vin,
+                                                        double* __restrict__ vout) {
+  constexpr int BMF = 64;
+  __shared__ double As[16][65];   // [k][row]
+  __shared__ double Bs[16][65];   // [k][col]
+  const Tile t = tiles[blockIdx.x];
+  const int n0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const double* Ps = P + (int64_t)t.sys * p_sys_stride;
+  const bool copy = t.t0 + BMF <= shift;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  if (!copy) {
+    for (int k0 = 0; k0 < m; k0 += 16) {
+      for (int e = threadIdx.x; e < 1024; e += 256) {
+        const int kk = e & 15, rr = e >> 4;
+        const int l = t.t0 + rr - shift;           // source time step
+        const int gk = k0 + kk;
+        double v = 0.0;
+        if (l >= 0 && t.t0 + rr < t.len && gk < m) v = vin[(t.seq_row0 + l) * (int64_t)m + gk];
+        As[kk][rr] = v;
+      }
+      for (int e = threadIdx.x; e < 1024; e += 256) {
+        const int kk = e & 15, nn = e >> 4;
+        const int gn = n0 + nn, gk = k0 + kk;
+        Bs[kk][nn] = (gn < m && gk < m) ? Ps[(int64_t)gn * m + gk] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = ty + 16 * i;
+    if (t.t0 + rr >= t.len) continue;
+    const int64_t row = t.seq_row0 + t.t0 + rr;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= m) continue;
+      vout[row * m + gn] = vin[row * m + gn] + acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- output
+// One block per output tile (tile.flags = which workspace buffer holds the
+// final states); one warp per row: y[row, :] = C v + D u.
+template <int FMT, typename T>
+__global__ void __launch_bounds__(256) output_kernel(const Tile* __restrict__ tiles, int BM, int m,
+                                                     int p, int q, const T* __restrict__ u,
+                                                     T* __restrict__ y, const T* __restrict__ C,
+                                                     const T* __restrict__ D, const void* b0_hi,
+                                                     const void* b0_lo, const void* b1_hi,
+                                                     const void* b1_lo) {
+  const Tile t = tiles[blockIdx.x];
+  const void* vh = (t.flags & 1) ? b1_hi : b0_hi;
+  const void* vl = (t.flags & 1) ? b1_lo : b0_lo;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int rows = min(BM, t.len - t.t0);
+  const T* Cs = C + (int64_t)t.sys * q * m;
+  const T* Ds = D + (int64_t)t.sys * q * p;
+  for (int r = warp; r < rows; r += nw) {
+    const int64_t row = t.seq_row0 + t.t0 + r;
+    for (int q0 = 0; q0 < q; q0 += 8) {
+      double acc[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+      for (int c = lane; c < m; c += 32) {
+        const double v = Store<FMT>::get(vh, vl, row * m + c);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (q0 + i < q) acc[i] = fma((double)Cs[(int64_t)(q0 + i) * m + c], v, acc[i]);
+      }
+      for (int c = lane; c < p; c += 32) {
+        const double uv = (double)u[row * p + c];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (q0 + i < q) acc[i] = fma((double)Ds[(int64_t)(q0 + i) * p + c], uv, acc[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        double s = acc[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0 && q0 + i < q) y[row * q + q0 + i] = (T)s;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- recursion
+// Eq. (1.2) one step at a time: x_n = Abar x_(n-1) + Bbar u_n, y_n = C x_n + D u_n.
+// One block per sequence; the state lives in shared memory (double buffer).
+__global__ void __launch_bounds__(256) recursion_f64_kernel(const Seq* __restrict__ seqs, int m,
+                                                            int p, int q,
+                                                            const double* __restrict__ Abar,
+                                                            int64_t a_sys_stride,
+                                                            const double* __restrict__ Bbar,
+                                                            const double* __restrict__ C,
+                                                            const double* __restrict__ D,
+                                                            const double* __restrict__ u,
+                                                            double* __restrict__ y) {
+  extern __shared__ double xs[];   // 2 * m
+  const Seq sq = seqs[blockIdx.x];
+  const double* As = Abar + (int64_t)sq.sys * a_sys_stride;
+  const double* Bs = Bbar + (int64_t)sq.sys * m * p;
+  const double* Cs = C + (int64_t)sq.sys * q * m;
+  const double* Ds = D + (int64_t)sq.sys * q * p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* x = xs;
+  double* xn = xs + m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) x[i] = 0.0;
+  __syncthreads();
+  for (int l = 0; l < sq.len; ++l) {
+    const double* ur = u + (sq.row0 + l) * p;
+    for (int i = warp; i < m; i += nw) {
+      double s = 0.0;
+      for (int j = lane; j < m; j += 32) s = fma(As[(int64_t)i * m + j], x[j], s);
+      for (int j = lane; j < p; j += 32) s = fma(Bs[(int64_t)i * p + j], ur[j], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) xn[i] = s;
+    }
+    __syncthreads();
+    for (int qq = warp; qq < q; qq += nw) {
+      double s = 0.0;
+      for (int j = lane; j < m; j += 32) s = fma(Cs[(int64_t)qq * m + j], xn[j], s);
+      for (int j = lane; j < p; j += 32) s = fma(Ds[(int64_t)qq * p + j], ur[j], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) y[(sq.row0 + l) * q + qq] = s;
+    }
+    double* tmp = x;
+    x = xn;
+    xn = tmp;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- self-test
+// Waits on an mbarrier that nothing arrives at; the bounded wait must give up.
+__global__ void selftest_timeout_kernel(unsigned long long limit_ns, int32_t* err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&bar, 1);
+    abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool ok = ptx::mbar_wait(&bar, 0u, limit_ns, &abort_flag);
+    *err = ok ? 0 : (int32_t)CASCADE_ERR_TIMEOUT;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stage0(const Plan& p, const void* u, void* out_hi, void* out_lo,
+                          cudaStream_t st) {
+  const int n = p.n_stage0_tiles;
+  if (n == 0) return cudaSuccess;
+  const int BM = tile_rows(p);
+  switch (p.d.precision) {
+    case CASCADE_FP64:
+      stage0_kernel<FMT_F64, double><<<n, 256, 0, st>>>(p.d_stage0_tiles, BM, p.d.m, p.d.p,
+                                                        (const double*)u, p.Bbar64, p.ABbar64,
+                                                        out_hi, out_lo);
+      break;
+    case CASCADE_BF16_SPLIT:
+      stage0_kernel<FMT_BF16, float><<<n, 256, 0, st>>>(p.d_stage0_tiles, BM, p.d.m, p.d.p,
+                                                        (const float*)u, p.Bbar32, p.ABbar32,
+                                                        out_hi, out_lo);
+      break;
+    default:
+      stage0_kernel<FMT_F32, float><<<n, 256, 0, st>>>(p.d_stage0_tiles, BM, p.d.m, p.d.p,
+                                                       (const float*)u, p.Bbar32, p.ABbar32,
+                                                       out_hi, out_lo);
+  }
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_f64(const Plan& p, int k, const double* vin, double* vout,
+                             cudaStream_t st) {
+  const int n = p.n_tiles[k];
+  if (n == 0) return cudaSuccess;
+  dim3 grid(n, (p.d.m + 63) / 64);
+  stage_f64_kernel<<<grid, 256, 0, st>>>(p.d_tiles[k], p.d.m, 1 << k,
+                                         p.P64 + (int64_t)k * p.d.m * p.d.m,
+                                         (int64_t)p.kmax1 * p.d.m * p.d.m, vin, vout);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_output(const Plan& p, const void* u, void* y, void* const* hi,
+                          void* const* lo, cudaStream_t st) {
+  const int n = p.n_out_tiles;
+  if (n == 0) return cudaSuccess;
+  const int BM = tile_rows(p);
+  const Tile* tiles = p.d_out_tiles;
+  switch (p.d.precision) {
+    case CASCADE_FP64:
+      output_kernel<FMT_F64, double><<<n, 256, 0, st>>>(tiles, BM, p.d.m, p.d.p, p.d.q,
+                                                        (const double*)u, (double*)y, p.C64,
+                                                        p.D64, hi[0], lo[0], hi[1], lo[1]);
+      break;
+    case CASCADE_BF16_SPLIT:
+      output_kernel<FMT_BF16, float><<<n, 256, 0, st>>>(tiles, BM, p.d.m, p.d.p, p.d.q,
+                                                        (const float*)u, (float*)y, p.C32, p.D32,
+                                                        hi[0], lo[0], hi[1], lo[1]);
+      break;
+    default:
+      output_kernel<FMT_F32, float><<<n, 256, 0, st>>>(tiles, BM, p.d.m, p.d.p, p.d.q,
+                                                       (const float*)u, (float*)y, p.C32, p.D32,
+                                                       hi[0], lo[0], hi[1], lo[1]);
+  }
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recursion_f64(const Plan& p, const double* u, double* y, cudaStream_t st) {
+  if (p.nseq == 0) return cudaSuccess;
+  const size_t smem = 2 * sizeof(double) * (size_t)p.d.m;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(recursion_f64_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  recursion_f64_kernel<<<p.nseq, 256, smem, st>>>(p.d_seqs, p.d.m, p.d.p, p.d.q, p.P64,
+                                                  (int64_t)p.kmax1 * p.d.m * p.d.m, p.Bbar64,
+                                                  p.C64, p.D64, u, y);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_timeout(int32_t limit_us, int32_t* err, cudaStream_t st) {
+  selftest_timeout_kernel<<<1, 32, 0, st>>>((unsigned long long)limit_us * 1000ull, err);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+}  // namespace cascade

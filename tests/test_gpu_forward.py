@@ -1,0 +1,266 @@
+"""GPU parity of the forward cascade (through the C ABI) against the CPU FP64
+oracle, on the same seeded inputs.
+
+Bars (relative Frobenius error per sequence, max over sequences, on y and on
+Cx = y - Du): 1e-12 for the FP64 path, 1e-5 for FP32 (three TF32 products),
+2e-3 for the BF16 split.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from _parity import OUT_EPS, TOL, cast_inputs, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_17729_gb300 import build
+    build()
+    from paper_2411_17729_gb300 import cascade
+    return cascade
+
+
+def run_gpu(cascade, w, precision, flags=0, N=None):
+    import torch
+    c = cascade.from_workload(w, precision=precision, flags=flags, N=N)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    u = torch.as_tensor(w.u, dtype=dt).cuda().contiguous()
+    y = c.forward(u)
+    torch.cuda.synchronize()
+    err = c.device_error()
+    assert err == 0, f"device error word {err}"
+    return c, y.double().cpu().numpy()
+
+
+def check(cascade, w, precision, flags=0):
+    w = cast_inputs(w, precision)
+    c, y = run_gpu(cascade, w, precision, flags)
+    yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
+    ey, ecx = rel_errors(w, y, yo, OUT_EPS[precision])
+    tol = TOL[precision]
+    assert ey <= tol and ecx <= tol, (ey, ecx)
+    return c, y, yo
+
+
+# ------------------------------------------------------------ FP64 path
+@pytest.mark.parametrize("m,p,q", [(1, 1, 1), (5, 2, 3), (64, 1, 1), (70, 3, 2)])
+def test_fp64_small_ragged(lib, m, p, q):
+    w = wl.small_system(m=m, p=p, q=q, lengths=(1, 2, 3, 0, 64, 65, 200, 1000), N=12, nsys=2,
+                        seed=m, radius=0.98, precision="fp64")
+    check(lib, w, "fp64")
+
+
+def test_fp64_plain_hippo_workload(lib):
+    """HiPPO-LegS m = 64, L = 4096, N = 11: equals the recursion (1.2)."""
+    w = wl.plain_fp64()
+    c, y, yo = check(lib, w, "fp64")
+    Abar, Bbar, C, D = oracle.system_matrices(w, 0)
+    yr, _ = oracle.recursion_forward_seq(Abar, Bbar, C, D, w.u)
+    assert np.linalg.norm(y - yr) / np.linalg.norm(yr) < 1e-12
+
+
+@pytest.mark.parametrize("N", [0, 1, 3])
+def test_fp64_truncated(lib, N):
+    """N + 1 < log2 L: the truncated polynomial, not the recursion."""
+    w = wl.small_system(m=9, p=2, q=2, lengths=(100, 37), N=N, seed=4, radius=1.03)
+    check(lib, w, "fp64")
+
+
+def test_fp64_recursion_kernel(lib):
+    import torch
+    w = wl.small_system(m=33, p=2, q=3, lengths=(50, 0, 7), N=10, seed=5, radius=0.9)
+    c = lib.from_workload(w, precision="fp64")
+    y = c.recursion(torch.as_tensor(w.u).cuda()).cpu().numpy()
+    for i in range(w.nseq):
+        sl = w.seq(i)
+        if sl.stop == sl.start:
+            continue
+        Abar, Bbar, C, D = oracle.system_matrices(w, int(w.sys_of_seq[i]))
+        yr, _ = oracle.recursion_forward_seq(Abar, Bbar, C, D, w.u[sl])
+        assert np.max(np.abs(y[sl] - yr)) <= 1e-12 * max(1, np.max(np.abs(yr)))
+
+
+# ------------------------------------------------------------ system prep
+def test_discretisation_and_powers(lib):
+    """Eq. (4.2) and the squaring chain on the device vs the oracle (dense
+    continuous A, pivoting exercised)."""
+    w = wl.small_system(m=48, p=3, q=2, lengths=(10,), N=6, seed=2, discrete=False, delta=0.3,
+                        nsys=3)
+    c = lib.from_workload(w, precision="fp64", N=6, max_len=200)
+    for s in range(3):
+        Abar, Bbar, C, D = oracle.system_matrices(w, s)
+        P = oracle.squaring_chain(Abar, 6)
+        G = c.powers(s, 6).cpu().numpy()
+        for k in range(7):
+            assert np.max(np.abs(G[k] - P[k])) <= 1e-12 * max(1.0, np.max(np.abs(P[k])))
+
+
+def test_hippo_paper_example_powers(lib):
+    """§4 example (1-based HiPPO, m = 100, delta = 5e-4): device powers match
+    the oracle's to 1e-12 and the (0,0) entry of Abar^(2^15) is d_1^(2^15)."""
+    import math
+    m = 100
+    A = wl.hippo_legs(m, base=1)[None]
+    B = wl.hippo_legs_B(m, base=1)[None]
+    w = wl.Workload(name="paper", m=m, p=1, q=1, N=15, precision="fp64",
+                    offsets=np.array([0, 4], np.int64), u=np.ones((4, 1)), B=B,
+                    C=np.ones((1, 1, m)), D=np.zeros((1, 1, 1)), sys_of_seq=np.zeros(1, np.int32),
+                    A=A, delta=np.array([5e-4]))
+    c = lib.from_workload(w, precision="fp64", N=15, max_len=1 << 16)
+    G = c.powers(0, 15).cpu().numpy()
+    Abar, _, _, _ = oracle.system_matrices(w, 0)
+    P = oracle.squaring_chain(Abar, 15)
+    for k in range(16):
+        assert np.max(np.abs(G[k] - P[k])) <= 1e-12 * np.max(np.abs(P[k]))
+    assert abs(G[15][0, 0] - math.exp(-(2 ** 16) * math.atanh(5e-4))) < 1e-11 * G[15][0, 0]
+
+
+def test_accuracy_rule_matches_oracle(lib):
+    w = wl.batching_form(nseq=6, Lmin=100, Lmax=3000, m=64)
+    c = lib.from_workload(w, precision="fp32")
+    Abar, _, _, _ = oracle.system_matrices(w, 0)
+    assert int(c.N()[0]) == oracle.choose_N(Abar, int(w.lengths.max()), w.eps)
+    for i, L in enumerate(w.lengths):
+        assert c.seq_N()[i] == oracle.effective_N(int(c.N()[0]), int(L))
+    # a contracting system reaches eps before covering the length
+    w2 = wl.small_system(m=32, lengths=(5000,), seed=1, radius=0.5, precision="fp32")
+    w2.N, w2.eps = -1, 1e-6
+    c2 = lib.from_workload(w2, precision="fp32")
+    Abar2, _, _, _ = oracle.system_matrices(w2, 0)
+    assert int(c2.N()[0]) == oracle.choose_N(Abar2, 5000, 1e-6) < 11
+
+
+# ------------------------------------------------------------ tensor-core paths
+@pytest.mark.parametrize("precision,m", [("bf16_split", 64), ("bf16_split", 128),
+                                         ("bf16_split", 256), ("fp32", 32), ("fp32", 128),
+                                         ("fp32", 256)])
+def test_tc_hippo_ragged(lib, precision, m):
+    """HiPPO-LegS with per-sequence step sizes, ragged lengths spanning
+    several 128-row tiles, empty and one-step sequences."""
+    lengths = (1, 2, 127, 128, 129, 0, 1000, 3000)
+    w = wl.precision_form(m=m, L=8, batch=len(lengths), N=12)
+    rng = np.random.default_rng(7)
+    w.offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    w.u = rng.standard_normal((int(w.offsets[-1]), 1))
+    w.precision = precision
+    check(lib, w, precision)
+
+
+@pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
+@pytest.mark.parametrize("p,q", [(1, 1), (4, 4), (3, 16), (2, 20)])
+def test_tc_mimo(lib, precision, p, q):
+    """MIMO systems: fused output for q <= 16, separate output kernel above."""
+    w = wl.differentiation_form(m=128, p=p, q=q, L=700, batch=3, N=9, delta=1e-2)
+    check(lib, w, precision)
+
+
+@pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
+def test_tc_large_m_multiblock(lib, precision):
+    """m = 512: two N-blocks per tile, output kernel path."""
+    w = wl.large_form(m=512, p=2, q=3, L=600, batch=2, N=9)
+    check(lib, w, precision)
+
+
+@pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
+def test_tc_unfused_matches_fused(lib, precision):
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_NO_FUSED_OUTPUT
+    w = wl.precision_form(m=128, L=900, batch=3, N=9)
+    w = cast_inputs(w, precision)
+    _, y1 = run_gpu(lib, w, precision)
+    _, y2 = run_gpu(lib, w, precision, flags=CASCADE_FLAG_NO_FUSED_OUTPUT)
+    ey, _ = rel_errors(w, y1, y2)
+    assert ey < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
+def test_tc_truncation_and_growth(lib, precision):
+    """Spectral radius above one with N below log2 L (truncated polynomial)."""
+    w = wl.small_system(m=64, p=2, q=2, lengths=(1000, 513), N=4, seed=3, radius=1.002,
+                        precision=precision)
+    check(lib, w, precision)
+
+
+def test_graph_replay_matches(lib):
+    import torch
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_GRAPH
+    w = cast_inputs(wl.precision_form(m=128, L=1000, batch=3, N=9), "bf16_split")
+    _, y1 = run_gpu(lib, w, "bf16_split")
+    c = lib.from_workload(w, precision="bf16_split", flags=CASCADE_FLAG_GRAPH)
+    u = torch.as_tensor(w.u, dtype=torch.float32).cuda()
+    y = torch.empty((w.rows, 1), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        y.zero_()
+        c.forward(u, y)
+        torch.cuda.synchronize()
+        assert np.array_equal(y.double().cpu().numpy(), y1)
+
+
+# ------------------------------------------------------------ full-size, sampled
+def test_precision_form_full_size_sampled(lib):
+    """64 sequences x 16384 steps, m = 256, N = 13, BF16 split (the benchmark's
+    launch configuration).  The oracle recomputes the sequences with the
+    smallest and largest step size in full, and 256-step prefixes of every
+    other one (the cascade is causal, so a prefix run with the same N gives
+    the same rows)."""
+    w = cast_inputs(wl.precision_form(), "bf16_split")
+    c, y = run_gpu(lib, w, "bf16_split")
+    Ns = c.seq_N()
+    assert np.all(Ns == 13)
+    full = {int(np.argmin(w.delta)), int(np.argmax(w.delta))}
+    worst = 0.0
+    for i in range(w.nseq):
+        sl = w.seq(i)
+        Abar, Bbar, C, D = oracle.system_matrices(w, int(w.sys_of_seq[i]))
+        n = sl.stop - sl.start if i in full else 256
+        uu = w.u[sl][:n]
+        yo = oracle.cascade_forward_seq(Abar, Bbar, C, D, uu, 13)
+        yg = y[sl][:n]
+        Du = uu @ D.T
+        e1 = np.linalg.norm(yg - yo) / np.linalg.norm(yo)
+        e2 = np.linalg.norm(yg - yo) / np.linalg.norm(yo - Du)
+        worst = max(worst, e1, e2)
+    assert worst <= TOL["bf16_split"], worst
+
+
+def test_batching_form_full_size_sampled(lib):
+    """512 sequences of uneven length (log-uniform in [1024, 65536], 8.85e6
+    rows), m = 128, p = q = 4, Abar = 1.000001 x trapezoid(HiPPO-LegS, 5e-7)
+    (spectral radius above one), N per sequence from eps = 1e-6, FP32 path.
+    The oracle recomputes the four shortest sequences in full and 512-step
+    prefixes of 16 others, with the N the library chose for each."""
+    w = cast_inputs(wl.batching_form(), "fp32")
+    c, y = run_gpu(lib, w, "fp32")
+    Ns = c.seq_N()
+    Abar, Bbar, C, D = oracle.system_matrices(w, 0)
+    assert int(c.N()[0]) == oracle.choose_N(Abar, int(w.lengths.max()), w.eps)
+    for i, L in enumerate(w.lengths):
+        assert Ns[i] == oracle.effective_N(int(c.N()[0]), int(L))
+    order = np.argsort(w.lengths)
+    picks = [(int(i), None) for i in order[:4]] + [(int(i), 512) for i in order[4::31][:16]]
+    worst_y, worst_cx = 0.0, 0.0
+    for i, n in picks:
+        sl = w.seq(i)
+        uu = w.u[sl] if n is None else w.u[sl][:n]
+        yo = oracle.cascade_forward_seq(Abar, Bbar, C, D, uu, int(Ns[i]))
+        yg = y[sl][: len(uu)]
+        Du = uu @ D.T
+        worst_y = max(worst_y, np.linalg.norm(yg - yo) / np.linalg.norm(yo))
+        d = np.linalg.norm(yg - yo) - 2.0 * OUT_EPS["fp32"] * np.linalg.norm(yo)
+        worst_cx = max(worst_cx, max(d, 0.0) / np.linalg.norm(yo - Du))
+    assert worst_y <= TOL["fp32"] and worst_cx <= TOL["fp32"], (worst_y, worst_cx)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16_split"])
+def test_batching_form_cx_only(lib, precision):
+    """The batching-form system with D = 0, so y = Cx exactly and the gate
+    measures the cascade itself (with D != 0, Du dominates y at delta = 5e-7):
+    24 uneven sequences up to 8192 steps, spectral radius above one."""
+    w = wl.batching_form(nseq=24, Lmax=8192)
+    w.D = np.zeros_like(w.D)
+    check(lib, w, precision)

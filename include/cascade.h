@@ -157,6 +157,9 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
    h_N [nseq]. */
 cascade_status_t cascade_get_seq_N(cascade_plan_t plan, int32_t* h_N);
 
+/* Size of the fixed device scratch array behind cascade_forward_fixed_scratch. */
+#define CASCADE_FIXED_SCRATCH_BYTES ((size_t)32 << 20)
+
 /* Bytes of caller-provided device workspace that forward (and, for plans
    with CASCADE_FLAG_SAVE_STATES, backward) need for the current batch. */
 cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes);
@@ -168,6 +171,27 @@ cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes);
    device-side wait timeouts are reported by cascade_get_device_error. */
 cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y,
                                  void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* cascade_forward without a workspace argument, for callers that cannot call
+   cudaMalloc: for example a plugin that runs inside a host framework whose
+   memory pool owns all device memory, or a latency-bound service path where
+   a device allocation may synchronise the GPU.  (The paper has no
+   counterpart: this is a deployment convenience of this library.)
+   The workspace comes from a fixed array of CASCADE_FIXED_SCRATCH_BYTES
+   (32 MiB) compiled into the library; every GPU that loads the library holds
+   it until the process exits.  Batches whose workspace
+   (cascade_workspace_size) exceeds it are rejected with
+   CASCADE_ERR_UNSUPPORTED and a message giving both sizes; stage timing must
+   be off (CASCADE_ERR_UNSUPPORTED otherwise).  The call itself allocates
+   nothing.  The first call on each device resolves the array's device
+   address (cudaGetSymbolAddress) with that device current; make that first
+   call before any stream capture.  All calls share the one array, which
+   keeps the last call's contents (the forward writes every byte it reads, so
+   nothing needs clearing); calls whose executions overlap on the GPU, on any
+   streams or plans, race on it and must be serialised by the caller.
+   Otherwise as cascade_forward: d_u [rows,p], d_y [rows,q], asynchronous. */
+cascade_status_t cascade_forward_fixed_scratch(cascade_plan_t plan, const void* d_u, void* d_y,
+                                               void* stream);
 
 /* Reverse-mode derivative of sum(dy * y) for the last forward (which must
    have run with CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE on this

@@ -335,6 +335,16 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
 
 }  // namespace
 
+namespace cascade {
+// Forward into a caller-chosen workspace (used by the fixed-scratch entry point).
+cascade_status_t forward_with_workspace(Plan* p, const void* u, void* y, void* ws,
+                                        cudaStream_t st) {
+  p->last_stream = st;
+  return run_forward(p, u, y, ws, st);
+}
+size_t forward_workspace_bytes(const Plan& p) { return forward_workspace(p, p.rows); }
+}  // namespace cascade
+
 // =================================================================== C ABI
 extern "C" {
 

@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 cascade comparator")
+    ap.add_argument("--seqs", type=int, default=64,
+                    help="sequences in the batch (64 = the benchmark; fewer only for profiler captures)")
     return ap.parse_args()
 
 
@@ -202,6 +204,8 @@ def main():
     dev = torch.device("cuda", local)
 
     w = wl.precision_form()
+    if args.seqs != w.nseq:
+        w = w.subset(range(args.seqs))
     m = w.m
     t_prep0 = time.perf_counter()
     c = cascade.from_workload(w, precision="bf16_split", device=dev)
@@ -217,6 +221,7 @@ def main():
     def step():
         c.forward(u, y)
 
+    shape = c.autotune(u, y, reps=2)          # kernel shape for this batch (untimed)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -341,7 +346,8 @@ def main():
             "config": {"workload": WORKLOAD, "global_batch": int(w.nseq) * world, "seq_len": 16384,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "flushed before each timed step (256 MiB write)",
-                       "timing": "CUDA events on the launching stream, sum over steps"},
+                       "timing": "CUDA events on the launching stream, sum over steps",
+                       "kernel_shape": {"stages": shape[0], "ring": shape[1], "chunks_per_step": shape[2]}},
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "traffic": None,
                          "kernel": "stage_tc_kernel<bf16,q=1> (stages 1..13)",

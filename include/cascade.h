@@ -226,6 +226,25 @@ cascade_status_t cascade_selftest_timeout(int32_t limit_us);
 /* Number of kernels this library launched since load (host-side count). */
 int64_t cascade_launch_count(void);
 
+/* Autotuner of the tensor-core stage kernel.  Runs the forward on the
+   current batch once per candidate kernel shape (operand pipeline depth,
+   epilogue staging ring, column chunks per epilogue step; every candidate
+   fits shared and tensor memory), `reps` timed passes each after one
+   warm-up, with CUDA events on `stream`, and keeps the fastest in the plan
+   for later forwards.  d_u, d_y and d_workspace are as for cascade_forward
+   (d_y is overwritten).  h_choice (NULL or int32[3]) receives the chosen
+   stages, ring slots and chunks per step.  Synchronous; a no-op for FP64
+   plans. */
+cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_y,
+                                  void* d_workspace, size_t workspace_bytes, void* stream,
+                                  int32_t reps, int32_t* h_choice);
+
+/* Set the tensor-core stage kernel shape directly (e.g. a shape saved from
+   an earlier cascade_autotune): h_shape = {stages, ring slots, chunks per
+   step}.  CASCADE_ERR_INVALID_ARG if it does not fit shared/tensor memory
+   for this plan's m and precision.  A no-op for FP64 plans. */
+cascade_status_t cascade_set_kernel_shape(cascade_plan_t plan, const int32_t* h_shape);
+
 /* Per-launch timing of the stage kernels.  When enabled, every later
    forward records a CUDA event pair on its stream around each tensor-core
    (or FP64) stage launch.  cascade_get_stage_times synchronises that stream

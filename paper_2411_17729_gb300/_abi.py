@@ -64,6 +64,9 @@ SIGNATURES = [
     ("cascade_get_device_error", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
     ("cascade_selftest_timeout", C.c_int, [C.c_int32]),
     ("cascade_launch_count", C.c_int64, []),
+    ("cascade_autotune", C.c_int, [cascade_plan_t, _P, _P, _P, C.c_size_t, _P, C.c_int32,
+                                   C.POINTER(C.c_int32)]),
+    ("cascade_set_kernel_shape", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
     ("cascade_enable_stage_timing", C.c_int, [cascade_plan_t, C.c_int32]),
     ("cascade_get_stage_times", C.c_int, [cascade_plan_t, C.c_int32, C.POINTER(C.c_int32),
                                           C.POINTER(C.c_float), C.POINTER(C.c_int32)]),

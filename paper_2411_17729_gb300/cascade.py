@@ -126,6 +126,21 @@ class Cascade:
         self._check(self.lib.cascade_recursion_forward(self.plan, _ptr(u), _ptr(y), _stream(stream)))
         return y
 
+    def autotune(self, u, y=None, reps=2, stream=None):
+        """Pick the fastest tensor-core kernel shape for the current batch
+        (returns (stages, ring slots, chunks per step))."""
+        if y is None:
+            y = torch.empty((self.rows, self.q), dtype=self.dtype, device=self.device)
+        ws = self.workspace()
+        choice = (C.c_int32 * 3)()
+        self._check(self.lib.cascade_autotune(self.plan, _ptr(u), _ptr(y), _ptr(ws), ws.numel(),
+                                              _stream(stream), reps, choice))
+        return tuple(choice[:])
+
+    def set_kernel_shape(self, stages, ring, group):
+        shape = (C.c_int32 * 3)(stages, ring, group)
+        self._check(self.lib.cascade_set_kernel_shape(self.plan, shape))
+
     def enable_stage_timing(self, on=True):
         self._check(self.lib.cascade_enable_stage_timing(self.plan, 1 if on else 0))
 

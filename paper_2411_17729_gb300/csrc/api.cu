@@ -72,7 +72,8 @@ static EncodeTiledFn get_encoder() {
 }
 
 bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
-                    uint64_t outer, uint32_t box_inner, uint32_t box_outer, std::string* err) {
+                    uint64_t outer, uint32_t box_inner, uint32_t box_outer, std::string* err,
+                    int swizzle_bytes) {
   EncodeTiledFn enc = get_encoder();
   if (!enc) {
     *err = "cuTensorMapEncodeTiled unavailable";
@@ -85,7 +86,8 @@ bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     char buf[128];
@@ -407,8 +409,8 @@ cascade_status_t cascade_plan_create(cascade_plan_t* out, const cascade_desc_t* 
   p->kmax1 = (d.N >= 0) ? std::min(d.N, Nmax) + 1 : Nmax + 2;
   p->fuse_output = d.precision != CASCADE_FP64 && !(d.flags & CASCADE_FLAG_NO_FUSED_OUTPUT) &&
                    block_n(d.m, d.precision) == d.m && d.q <= 16;
-  e = cudaMalloc(&p->err, sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int32_t));
+  e = cudaMalloc(&p->err, 8 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(p->err, 0, 8 * sizeof(int32_t));
   if (e != cudaSuccess) {
     delete static_cast<cascade_plan_s*>(p);
     return fail(nullptr, CASCADE_ERR_OOM, "device error word allocation failed");
@@ -699,8 +701,92 @@ cascade_status_t cascade_get_device_error(cascade_plan_t plan, int32_t* h_code) 
   if (!p || !h_code) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t st = static_cast<cudaStream_t>(p->last_stream);
   CK(cudaStreamSynchronize(st), "sync");
-  CK(cudaMemcpy(h_code, p->err, sizeof(int32_t), cudaMemcpyDeviceToHost), "read error word");
-  CK(cudaMemset(p->err, 0, sizeof(int32_t)), "clear error word");
+  int32_t words[8];
+  CK(cudaMemcpy(words, p->err, sizeof(words), cudaMemcpyDeviceToHost), "read error word");
+  CK(cudaMemset(p->err, 0, sizeof(words)), "clear error word");
+  *h_code = words[0];
+  if (words[0] != 0) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "device wait gave up: site %d block %d counters %d %d stage %d",
+             words[1], words[2], words[3], words[4], words[5]);
+    p->last_error = buf;
+  }
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_y,
+                                  void* d_workspace, size_t workspace_bytes, void* stream,
+                                  int32_t reps, int32_t* h_choice) {
+  Plan* p = plan;
+  if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->have_system || !p->have_batch) return fail(p, CASCADE_ERR_STATE, "system and batch must be set");
+  if (p->d.precision == CASCADE_FP64 || p->rows == 0) return CASCADE_OK;   // nothing to tune
+  if (!d_u || !d_y || !d_workspace) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL buffer");
+  if (workspace_bytes < forward_workspace(*p, p->rows))
+    return fail(p, CASCADE_ERR_INVALID_ARG, "workspace too small");
+  if (reps < 1) reps = 1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  p->last_stream = stream;
+  const bool timing = p->timing;
+  p->timing = false;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  float best = 1e30f;
+  TcConfig best_c = tc_default(p->d.m, p->d.precision);
+  cascade_status_t r = CASCADE_OK;
+  for (const TcConfig& c : tc_candidates(p->d.m, p->d.precision)) {
+    p->tc_stages = c.stages;
+    p->tc_ring = c.ring;
+    p->tc_group = c.group;
+    r = run_forward(p, d_u, d_y, d_workspace, st);             // warm-up
+    if (r != CASCADE_OK) break;
+    if (cudaEventRecord(e0, st) != cudaSuccess) { r = CASCADE_ERR_CUDA; break; }
+    for (int i = 0; i < reps && r == CASCADE_OK; ++i) r = run_forward(p, d_u, d_y, d_workspace, st);
+    if (r != CASCADE_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      r = cuda_fail(p, cudaGetLastError(), "autotune timing");
+      break;
+    }
+    if (ms < best) { best = ms; best_c = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->timing = timing;
+  p->tc_stages = best_c.stages;
+  p->tc_ring = best_c.ring;
+  p->tc_group = best_c.group;
+  p->tuned = (r == CASCADE_OK);
+  if (p->graph) {   // the recorded graph holds the old kernel shape
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  if (h_choice) {
+    h_choice[0] = best_c.stages;
+    h_choice[1] = best_c.ring;
+    h_choice[2] = best_c.group;
+  }
+  return r;
+}
+
+cascade_status_t cascade_set_kernel_shape(cascade_plan_t plan, const int32_t* h_shape) {
+  Plan* p = plan;
+  if (!p || !h_shape) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  if (p->d.precision == CASCADE_FP64) return CASCADE_OK;
+  bool ok = false;
+  for (const TcConfig& c : tc_candidates(p->d.m, p->d.precision))
+    ok = ok || (c.ring == h_shape[1] && c.group == h_shape[2] && h_shape[0] >= 2 &&
+                h_shape[0] <= c.stages);
+  if (!ok) return fail(p, CASCADE_ERR_INVALID_ARG, "kernel shape does not fit this plan");
+  p->tc_stages = h_shape[0];
+  p->tc_ring = h_shape[1];
+  p->tc_group = h_shape[2];
+  if (p->graph) {
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
   return CASCADE_OK;
 }
 

@@ -50,6 +50,7 @@ struct StageArgs {
   int32_t m, p, q;
   int32_t BN;
   int32_t stages;         // SMEM pipeline depth
+  int32_t ring;           // residual staging slots of the epilogue
   int32_t shift;          // 2^k
   int32_t k;              // stage index
   int32_t kmax1;          // power-table entries per system
@@ -62,6 +63,7 @@ struct StageArgs {
   const float* u;         // [rows, p]
   float* y;               // [rows, q]
   int32_t* err;           // device error word
+  int32_t* diag;          // where the first bounded wait gave up (5 words) or null
   unsigned long long timeout_ns;
 };
 
@@ -100,7 +102,7 @@ struct Plan {
   double* delta64 = nullptr;     // [nsys]
   double* scale64 = nullptr;     // [nsys] or null
   std::vector<int32_t> N_sys;
-  int32_t* err = nullptr;        // device error word
+  int32_t* err = nullptr;        // device error word, then 7 diagnostic words
   // batch
   bool have_batch = false;
   int64_t rows = 0;
@@ -118,6 +120,10 @@ struct Plan {
   Tile* d_stage0_tiles = nullptr;            // tiles for the first stage (all rows)
   int n_stage0_tiles = 0;
   bool fuse_output = false;
+  // tensor-core stage kernel shape: operand stages, epilogue ring slots,
+  // chunks per epilogue step (0 = heuristic); set by cascade_autotune
+  int tc_stages = 0, tc_ring = 0, tc_group = 0;
+  bool tuned = false;
   void* last_stream = nullptr;
   // per-launch stage timing
   bool timing = false;
@@ -166,8 +172,18 @@ cudaError_t launch_output(const Plan& p, const void* u, void* y, void* const* ws
 cudaError_t launch_recursion_f64(const Plan& p, const double* u, double* y, cudaStream_t st);
 cudaError_t launch_selftest_timeout(int32_t limit_us, int32_t* err, cudaStream_t st);
 
+// Shape of the tensor-core stage kernel (see stage_tc.cu).
+struct TcConfig {
+  int stages;   // operand pipeline depth
+  int ring;     // epilogue residual staging slots
+  int group;    // column chunks per epilogue step
+};
+std::vector<TcConfig> tc_candidates(int m, int precision);
+TcConfig tc_default(int m, int precision);
+
 // Tensor-map encoder resolved through the runtime's driver entry point.
 bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
-                    uint64_t outer, uint32_t box_inner, uint32_t box_outer, std::string* err);
+                    uint64_t outer, uint32_t box_inner, uint32_t box_outer, std::string* err,
+                    int swizzle_bytes = 128);
 
 }  // namespace cascade

@@ -83,6 +83,66 @@ __global__ void __launch_bounds__(256) stage0_kernel(const Tile* __restrict__ ti
   }
 }
 
+// First stage for the tensor-core formats: one thread writes 8 consecutive
+// state entries of one row (16-byte stores per plane), FP32 arithmetic.
+// Requires m % 8 == 0 (the tensor-core precisions need m % 32 == 0).
+template <int FMT>
+__global__ void __launch_bounds__(256) stage0_vec_kernel(const Tile* __restrict__ tiles, int BM,
+                                                         int m, int p, const float* __restrict__ u,
+                                                         const float* __restrict__ Bbar,
+                                                         const float* __restrict__ ABbar,
+                                                         void* out_hi, void* out_lo) {
+  const Tile t = tiles[blockIdx.x];
+  const int rows = min(BM, t.len - t.t0);
+  const int groups = m >> 3;
+  const float* Bs = Bbar + (int64_t)t.sys * m * p;
+  const float* ABs = ABbar + (int64_t)t.sys * m * p;
+  for (int idx = threadIdx.x; idx < rows * groups; idx += blockDim.x) {
+    const int r = idx / groups, c0 = (idx % groups) * 8;
+    const int l = t.t0 + r;
+    const int64_t row = t.seq_row0 + l;
+    const float* ur = u + row * p;
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+    for (int j = 0; j < p; ++j) {
+      const float uj = __ldg(ur + j);
+      const float upj = l >= 1 ? __ldg(ur - p + j) : 0.f;
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        acc[e] = fmaf(__ldg(Bs + (int64_t)(c0 + e) * p + j), uj,
+                      fmaf(__ldg(ABs + (int64_t)(c0 + e) * p + j), upj, acc[e]));
+    }
+    const int64_t off = row * m + c0;
+    if (FMT == FMT_BF16) {
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(acc[2 * j], acc[2 * j + 1]);
+        const float2 hf = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(acc[2 * j] - hf.x, acc[2 * j + 1] - hf.y);
+        hw[j] = *reinterpret_cast<const uint32_t*>(&hh);
+        lw[j] = *reinterpret_cast<const uint32_t*>(&ll);
+      }
+      *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out_hi) + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out_lo) + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    } else {
+      float hv[8], lv[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        hv[e] = ptx::tf32_rna(acc[e]);
+        lv[e] = ptx::tf32_rna(acc[e] - hv[e]);
+      }
+      float4* h = reinterpret_cast<float4*>(static_cast<float*>(out_hi) + off);
+      float4* lo4 = reinterpret_cast<float4*>(static_cast<float*>(out_lo) + off);
+      h[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+      h[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+      lo4[0] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      lo4[1] = make_float4(lv[4], lv[5], lv[6], lv[7]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- FP64 stage
 // Block: 64 rows x 64 state columns of one tile, 256 threads, 4x4 outputs each.
 __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__ tiles, int m,
@@ -271,14 +331,14 @@ cudaError_t launch_stage0(const Plan& p, const void* u, void* out_hi, void* out_
                                                         out_hi, out_lo);
       break;
     case CASCADE_BF16_SPLIT:
-      stage0_kernel<FMT_BF16, float><<<n, 256, 0, st>>>(p.d_stage0_tiles, BM, p.d.m, p.d.p,
-                                                        (const float*)u, p.Bbar32, p.ABbar32,
-                                                        out_hi, out_lo);
+      stage0_vec_kernel<FMT_BF16><<<n, 256, 0, st>>>(p.d_stage0_tiles, BM, p.d.m, p.d.p,
+                                                     (const float*)u, p.Bbar32, p.ABbar32,
+                                                     out_hi, out_lo);
       break;
     default:
-      stage0_kernel<FMT_F32, float><<<n, 256, 0, st>>>(p.d_stage0_tiles, BM, p.d.m, p.d.p,
-                                                       (const float*)u, p.Bbar32, p.ABbar32,
-                                                       out_hi, out_lo);
+      stage0_vec_kernel<FMT_F32><<<n, 256, 0, st>>>(p.d_stage0_tiles, BM, p.d.m, p.d.p,
+                                                    (const float*)u, p.Bbar32, p.ABbar32,
+                                                    out_hi, out_lo);
   }
   CASCADE_LAUNCHED();
   return cudaGetLastError();

@@ -23,17 +23,26 @@
 // with truncating adds reproduces the measured error), so the TF32 path adds
 // the two small correction products into a second TMEM accumulator and sums
 // the two in the epilogue: the large partial sum is then rounded once per
-// MMA instead of three times.  The residual add and the re-split into (hi, lo) happen in
-// the epilogue; on a sequence's last stage the epilogue can instead form
-// y = C v + D u (end of §3) and skip writing v.
+// MMA instead of three times.
 //
-// Block layout (192 threads, one block per SM, persistent over work items):
-//   warp 0      TMA producer (one elected lane)
+// Block layout (224 threads, one block per SM, persistent over work items):
+//   warp 0      TMA producer of the MMA operands (one elected lane)
 //   warp 1      TMEM allocator and MMA issuer (one elected lane)
-//   warps 2..5  epilogue: TMEM -> registers -> residual add -> global
-// Pipelines: `stages` shared-memory buffers (full/empty mbarriers) between the
-// producer and the MMA issuer; two TMEM accumulators (acc_full/acc_empty) between
-// the MMA issuer and the epilogue, so tile i's epilogue overlaps tile i+1's MMAs.
+//   warps 2..5  epilogue, thread = tile row = TMEM lane: accumulator row +
+//               residual row -> new (hi, lo) row, written back into the
+//               staging slot the residual arrived in
+//   warp 6      staging-ring manager (one elected lane): TMA loads of the
+//               residual column chunks RING chunks ahead (across tiles), TMA
+//               stores of finished chunks, refill of each slot once its store
+//               has read it
+// HBM traffic is whole lines in both directions, and the 64-byte swizzle of
+// every shared tile keeps the thread-per-row accesses free of bank conflicts.
+// No named barrier joins the epilogue warps: they signal a finished chunk
+// with an mbarrier arrive and only ever wait (boundedly) for data.
+// Pipelines: `stages` operand buffers (full/empty) producer -> MMA; two TMEM
+// accumulators (acc_full/acc_empty) MMA -> epilogue, so tile i's epilogue
+// overlaps tile i+1's MMAs; `ring` staging slots (res_full/res_done)
+// manager <-> epilogue.
 #include "common.cuh"
 #include "ptx.cuh"
 
@@ -41,129 +50,147 @@ namespace cascade {
 namespace {
 
 constexpr int BM = 128;
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 224;
+constexpr int RING_MAX = 8;                   // staging slots (runtime ring <= 8)
+constexpr uint32_t ROWB = 64;                 // bytes per row of every shared tile
+constexpr uint32_t PLANE_TILE = BM * ROWB;    // one plane of a 128-row chunk: 8 KB
+constexpr uint32_t SLOT_BYTES = 2 * PLANE_TILE;
 
 template <int ELEM>
-struct PlaneIO;
+struct Fmt;
 
-// BF16 (hi, lo) planes: 32 consecutive elements = 4 x 16 bytes per plane.
+// BF16 pair: a 64-byte row chunk holds 32 elements; 16 bytes = 8 elements.
 template <>
-struct PlaneIO<2> {
-  static __device__ __forceinline__ void load_add(const void* hi, const void* lo, int64_t off,
-                                                  float (&v)[32]) {
-    const uint4* h = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(hi) + off);
-    const uint4* l = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(lo) + off);
+struct Fmt<2> {
+  static constexpr int CW = 32;
+  static __device__ __forceinline__ void add16(uint4 h, uint4 l, float* v) {
+    const uint32_t aw[4] = {h.x, h.y, h.z, h.w};
+    const uint32_t bw[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint4 a = __ldg(h + i);
-      const uint4 b = __ldg(l + i);
-      const uint32_t aw[4] = {a.x, a.y, a.z, a.w};
-      const uint32_t bw[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&aw[j]));
-        const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bw[j]));
-        v[i * 8 + 2 * j] += fa.x + fb.x;
-        v[i * 8 + 2 * j + 1] += fa.y + fb.y;
-      }
+    for (int j = 0; j < 4; ++j) {
+      const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&aw[j]));
+      const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bw[j]));
+      v[2 * j] += fa.x + fb.x;
+      v[2 * j + 1] += fa.y + fb.y;
     }
   }
-  static __device__ __forceinline__ void store(void* hi, void* lo, int64_t off,
-                                               const float (&v)[32]) {
-    uint4* h = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(hi) + off);
-    uint4* l = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(lo) + off);
+  static __device__ __forceinline__ void split16(const float* v, uint4& h, uint4& l) {
+    uint32_t hw[4], lw[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      uint32_t hw[4], lw[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float x0 = v[i * 8 + 2 * j], x1 = v[i * 8 + 2 * j + 1];
-        const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
-        const float2 hf = __bfloat1622float2(hh);
-        const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-        hw[j] = *reinterpret_cast<const uint32_t*>(&hh);
-        lw[j] = *reinterpret_cast<const uint32_t*>(&ll);
-      }
-      h[i] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-      l[i] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      const float2 hf = __bfloat1622float2(hh);
+      const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+      hw[j] = *reinterpret_cast<const uint32_t*>(&hh);
+      lw[j] = *reinterpret_cast<const uint32_t*>(&ll);
     }
+    h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   }
 };
 
-// FP32 pair planes: hi = RN_tf32(x), lo = RN_tf32(x - hi), both TF32-exact, so the
-// tensor core (which reads the top 19 bits of each operand) sees them unrounded and
-// hi + lo carries x to ~2^-22 relative without bias.  32 elements = 8 x 16 bytes.
+// FP32 pair: hi = RN_tf32(x), lo = RN_tf32(x - hi), both TF32-exact, so the
+// tensor core (which reads the top 19 bits of each operand) sees them unrounded
+// and hi + lo carries x to ~2^-22 relative without bias.  16 bytes = 4 elements.
 template <>
-struct PlaneIO<4> {
-  static __device__ __forceinline__ void load_add(const void* hi, const void* lo, int64_t off,
-                                                  float (&v)[32]) {
-    const float4* h = reinterpret_cast<const float4*>(static_cast<const float*>(hi) + off);
-    const float4* l = reinterpret_cast<const float4*>(static_cast<const float*>(lo) + off);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float4 a = __ldg(h + i);
-      const float4 b = __ldg(l + i);
-      v[4 * i + 0] += a.x + b.x;
-      v[4 * i + 1] += a.y + b.y;
-      v[4 * i + 2] += a.z + b.z;
-      v[4 * i + 3] += a.w + b.w;
-    }
+struct Fmt<4> {
+  static constexpr int CW = 16;
+  static __device__ __forceinline__ void add16(uint4 h, uint4 l, float* v) {
+    v[0] += __uint_as_float(h.x) + __uint_as_float(l.x);
+    v[1] += __uint_as_float(h.y) + __uint_as_float(l.y);
+    v[2] += __uint_as_float(h.z) + __uint_as_float(l.z);
+    v[3] += __uint_as_float(h.w) + __uint_as_float(l.w);
   }
-  static __device__ __forceinline__ void store(void* hi, void* lo, int64_t off,
-                                               const float (&v)[32]) {
-    float4* h = reinterpret_cast<float4*>(static_cast<float*>(hi) + off);
-    float4* l = reinterpret_cast<float4*>(static_cast<float*>(lo) + off);
+  static __device__ __forceinline__ void split16(const float* v, uint4& h, uint4& l) {
+    float hv[4], lv[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float hv[4], lv[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        hv[j] = ptx::tf32_rna(v[4 * i + j]);
-        lv[j] = ptx::tf32_rna(v[4 * i + j] - hv[j]);
-      }
-      h[i] = make_float4(hv[0], hv[1], hv[2], hv[3]);
-      l[i] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+    for (int j = 0; j < 4; ++j) {
+      hv[j] = ptx::tf32_rna(v[j]);
+      lv[j] = ptx::tf32_rna(v[j] - hv[j]);
     }
+    h = make_uint4(__float_as_uint(hv[0]), __float_as_uint(hv[1]), __float_as_uint(hv[2]),
+                   __float_as_uint(hv[3]));
+    l = make_uint4(__float_as_uint(lv[0]), __float_as_uint(lv[1]), __float_as_uint(lv[2]),
+                   __float_as_uint(lv[3]));
   }
 };
 
-__device__ __forceinline__ void raise_timeout(int32_t* err, volatile int* abort_flag) {
-  atomicCAS(err, 0, (int32_t)CASCADE_ERR_TIMEOUT);
+// Record the first bounded wait that gave up: the error word, and where
+// (site, block, two counters of that wait) in the diagnostic words.
+__device__ __forceinline__ void raise_timeout(const StageArgs& a, volatile int* abort_flag, int site,
+                                              int x, int y) {
+  if (atomicCAS(a.err, 0, (int32_t)CASCADE_ERR_TIMEOUT) == 0 && a.diag) {
+    a.diag[0] = site;
+    a.diag[1] = (int32_t)blockIdx.x;
+    a.diag[2] = x;
+    a.diag[3] = y;
+    a.diag[4] = a.k;
+  }
   *abort_flag = 1;
 }
 
+// Per-item facts every role derives identically from the tile table.
+struct Item {
+  Tile t;
+  int n0;
+  bool copy;      // every source row precedes the sequence: no MMA, output = residual
+  bool fused;     // last stage with y = C v + D u formed in the epilogue
+  bool ragged;    // last tile of a sequence: rows past its end must not be written
+};
+
+template <int QMAX>
+__device__ __forceinline__ Item load_item(const StageArgs& a, int w) {
+  Item it;
+  it.t = a.tiles[w / a.nblocks];
+  it.n0 = (w % a.nblocks) * a.BN;
+  it.copy = it.t.t0 + BM <= a.shift;
+  it.fused = (QMAX > 0) && (it.t.flags & TILE_FINAL_FUSED);
+  it.ragged = it.t.t0 + BM > it.t.len;
+  return it;
+}
+
 // QMAX: 0 = never fuse the output; otherwise the largest q the fused
-// epilogue handles (register accumulators for y).
-template <int ELEM, int QMAX>
+// epilogue handles (register accumulators for y).  G: column chunks the
+// epilogue processes per step (their instructions interleave).
+template <int ELEM, int QMAX, int G>
 __global__ void __launch_bounds__(NTHREADS, 1)
     stage_tc_kernel(const __grid_constant__ CUtensorMap tm_vhi,
                     const __grid_constant__ CUtensorMap tm_vlo,
                     const __grid_constant__ CUtensorMap tm_phi,
-                    const __grid_constant__ CUtensorMap tm_plo, const StageArgs args) {
-  constexpr int KC = 128 / ELEM;      // K elements per 128-byte swizzle row
-  constexpr int UK = 32 / ELEM;       // K per tcgen05.mma
+                    const __grid_constant__ CUtensorMap tm_plo,
+                    const __grid_constant__ CUtensorMap tm_ohi,
+                    const __grid_constant__ CUtensorMap tm_olo, const StageArgs args) {
+  constexpr int KC = (int)ROWB / ELEM;   // K elements per 64-byte operand row
+  constexpr int UK = 32 / ELEM;          // K per tcgen05.mma
+  constexpr int CW = Fmt<ELEM>::CW;      // epilogue chunk: columns per 64-byte row
   constexpr uint32_t FMT = (ELEM == 2) ? 1u : 2u;
-  constexpr bool SEP = (ELEM == 4);   // separate accumulator for the correction products
+  constexpr bool SEP = (ELEM == 4);      // separate accumulator for the correction products
+  constexpr int QN = QMAX > 0 ? QMAX : 1;
   const int BN = args.BN;
   const int ACC = SEP ? 2 * args.BN : args.BN;   // TMEM columns of one tile's accumulators
   const int S = args.stages;
+  const int RING = args.ring;                    // multiple of G, <= RING_MAX
   const int m = args.m;
-  const int nchunks = m / KC;
+  const int nkc = m / KC;
+  const int nch = BN / CW;
   const int shift = args.shift;
   const int nwork = args.ntiles * args.nblocks;
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  const uint32_t a_bytes = BM * 128;
-  const uint32_t b_bytes = (uint32_t)BN * 128;
+  const uint32_t a_bytes = PLANE_TILE;
+  const uint32_t b_bytes = (uint32_t)BN * ROWB;
   const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
   uint8_t* bufs = smem;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * stage_bytes);
+  uint8_t* ring = smem + (size_t)S * stage_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)RING * SLOT_BYTES);
   uint64_t* empty = full + S;
   uint64_t* acc_full = empty + S;
   uint64_t* acc_empty = acc_full + 2;
-  uint64_t* drain = acc_empty + 2;
+  uint64_t* res_full = acc_empty + 2;
+  uint64_t* res_done = res_full + RING_MAX;
+  uint64_t* drain = res_done + RING_MAX;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -179,7 +206,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&acc_full[b], 1);
-      ptx::mbar_init(&acc_empty[b], 4 * 32);
+      ptx::mbar_init(&acc_empty[b], 128);
+    }
+    for (int s = 0; s < RING; ++s) {
+      ptx::mbar_init(&res_full[s], 1);
+      ptx::mbar_init(&res_done[s], 128);
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -188,6 +219,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     ptx::prefetch_tmap(&tm_vlo);
     ptx::prefetch_tmap(&tm_phi);
     ptx::prefetch_tmap(&tm_plo);
+    ptx::prefetch_tmap(&tm_ohi);
+    ptx::prefetch_tmap(&tm_olo);
   }
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, tmem_cols);
@@ -207,14 +240,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int issued_parity[8];
       for (int s = 0; s < 8; ++s) issued_parity[s] = -1;
       for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
-        const Tile t = args.tiles[w / args.nblocks];
-        if (t.t0 + BM <= shift) continue;                       // pure copy: no operands
-        const int n0 = (w % args.nblocks) * BN;
-        const int src_row = (int)(t.seq_row0 + t.t0 - shift);   // may be < 0 (zero fill)
-        const int prow = (t.sys * args.kmax1 + args.k) * m + n0;
-        for (int c = 0; c < nchunks; ++c) {
+        const Item it = load_item<QMAX>(args, w);
+        if (it.copy) continue;                                   // no operands
+        const int src_row = (int)(it.t.seq_row0 + it.t.t0 - shift);   // may be < 0 (zero fill)
+        const int prow = (it.t.sys * args.kmax1 + args.k) * m + it.n0;
+        for (int c = 0; c < nkc; ++c) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, limit, abort_flag)) {
-            raise_timeout(args.err, abort_flag);
+            raise_timeout(args, abort_flag, 1, w, stage);
             break;
           }
           uint8_t* sa_hi = bufs + (size_t)stage * stage_bytes;
@@ -242,22 +274,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t phase = 0;
     int acc_i = 0;
     for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
-      const Tile t = args.tiles[w / args.nblocks];
-      if (t.t0 + BM <= shift) continue;
+      const Item it = load_item<QMAX>(args, w);
+      if (it.copy) continue;
       const int abuf = acc_i & 1;
       const uint32_t aph = (uint32_t)((acc_i >> 1) & 1);
-      if (!ptx::mbar_wait(&acc_empty[abuf], aph ^ 1u, limit, abort_flag)) {
-        raise_timeout(args.err, abort_flag);
+      // lane-uniform outcome: the warp leaves its loop as a whole
+      if (!__all_sync(0xffffffffu, ptx::mbar_wait(&acc_empty[abuf], aph ^ 1u, limit, abort_flag))) {
+        raise_timeout(args, abort_flag, 2, w, acc_i);
         break;
       }
       ptx::tc_fence_after();
-      const int zero_rows = shift - t.t0;          // rows whose source precedes the sequence
+      const int zero_rows = shift - it.t.t0;       // rows whose source precedes the sequence
       const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * ACC);
       const uint32_t c_tmem = d_tmem + (SEP ? (uint32_t)BN : 0u);   // correction accumulator
       bool ok = true;
-      for (int c = 0; c < nchunks; ++c) {
-        if (!ptx::mbar_wait(&full[stage], phase, limit, abort_flag)) {
-          raise_timeout(args.err, abort_flag);
+      for (int c = 0; c < nkc; ++c) {
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait(&full[stage], phase, limit, abort_flag))) {
+          raise_timeout(args, abort_flag, 3, w, stage);
           ok = false;
           break;
         }
@@ -266,20 +299,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t* sb_hi = sa_lo + a_bytes;
         uint8_t* sb_lo = sb_hi + b_bytes;
         if (zero_rows > 0) {
-          // rows r < zero_rows occupy bytes [0, zero_rows*128) of each A buffer
+          // rows r < zero_rows occupy bytes [0, zero_rows * 64) of each A buffer
           uint4* zh = reinterpret_cast<uint4*>(sa_hi);
           uint4* zl = reinterpret_cast<uint4*>(sa_lo);
           const uint4 z = make_uint4(0, 0, 0, 0);
-          for (int i = lane; i < zero_rows * 8; i += 32) { zh[i] = z; zl[i] = z; }
+          for (int i = lane; i < zero_rows * 4; i += 32) { zh[i] = z; zl[i] = z; }
           ptx::fence_proxy_async_smem();
           __syncwarp();
         }
         ptx::tc_fence_after();
         if (lane == 0) {
-          const uint64_t dah = ptx::make_sdesc_sw128(ptx::smem_addr(sa_hi));
-          const uint64_t dal = ptx::make_sdesc_sw128(ptx::smem_addr(sa_lo));
-          const uint64_t dbh = ptx::make_sdesc_sw128(ptx::smem_addr(sb_hi));
-          const uint64_t dbl = ptx::make_sdesc_sw128(ptx::smem_addr(sb_lo));
+          const uint64_t dah = ptx::make_sdesc_sw64(ptx::smem_addr(sa_hi));
+          const uint64_t dal = ptx::make_sdesc_sw64(ptx::smem_addr(sa_lo));
+          const uint64_t dbh = ptx::make_sdesc_sw64(ptx::smem_addr(sb_hi));
+          const uint64_t dbl = ptx::make_sdesc_sw64(ptx::smem_addr(sb_lo));
 #pragma unroll
           for (int kk = 0; kk < KC / UK; ++kk) {
             const uint64_t adv = (uint64_t)((kk * UK * ELEM) >> 4);   // 32 bytes per step
@@ -309,77 +342,209 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       ptx::mbar_wait(drain, 0u, limit, nullptr);
     }
     __syncwarp();
+  } else if (warp == 6) {
+    // ------------------------------------------------------------ ring manager
+    if (lane == 0) {
+      int lw = blockIdx.x, lcc = 0;    // load cursor, up to RING chunks ahead of the epilogue
+      uint32_t issued = 0;
+      auto issue_next = [&](int slot) {
+        if (lw >= nwork) return;
+        const Tile lt = args.tiles[lw / args.nblocks];
+        const int x = (lw % args.nblocks) * BN + lcc * CW;
+        const int yrow = (int)(lt.seq_row0 + lt.t0);
+        uint8_t* sh = ring + (size_t)slot * SLOT_BYTES;
+        ptx::mbar_arrive_expect_tx(&res_full[slot], SLOT_BYTES);
+        ptx::tma_load_2d(sh, &tm_vhi, &res_full[slot], x, yrow);
+        ptx::tma_load_2d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow);
+        ++issued;
+        if (++lcc == nch) { lcc = 0; lw += gridDim.x; }
+      };
+      for (int s = 0; s < RING; ++s) issue_next(s);
+      uint32_t g = 0;                  // chunks retired
+      bool alive = true;
+      for (int w = blockIdx.x; w < nwork && alive; w += gridDim.x) {
+        const Item it = load_item<QMAX>(args, w);
+        const bool tma_out = !it.fused && !it.ragged;
+        const int ytile = (int)(it.t.seq_row0 + it.t.t0);
+        for (int cc = 0; cc < nch; ++cc, ++g) {
+          const int slot = (int)(g % RING);
+          uint8_t* sh = ring + (size_t)slot * SLOT_BYTES;
+          // Every chunk passes through both barriers of its slot, also a pure
+          // copy that the epilogue forwards untouched: a parity wait is then
+          // never more than one phase ahead of the barrier it polls.
+          if (!ptx::mbar_wait(&res_done[slot], (g / RING) & 1u, limit, abort_flag)) {
+            raise_timeout(args, abort_flag, 5, w, (int)g);
+            alive = false;
+            break;
+          }
+          if (tma_out) {
+            ptx::tma_store_2d(&tm_ohi, sh, it.n0 + cc * CW, ytile);
+            ptx::tma_store_2d(&tm_olo, sh + PLANE_TILE, it.n0 + cc * CW, ytile);
+            ptx::bulk_commit();
+            ptx::bulk_wait_read0();     // the slot may be overwritten once the store read it
+          }
+          issue_next(slot);
+        }
+      }
+      ptx::bulk_wait0();                // stores complete before the block exits
+      // loads issued but not retired (only after an abort): let them land
+      for (uint32_t h = g; h < issued; ++h)
+        ptx::mbar_wait(&res_full[h % RING], (h / RING) & 1u, limit, nullptr);
+    }
   } else {
     // ------------------------------------------------------------ epilogue
     const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
     const int r = quad * 32 + lane;            // tile row == TMEM lane
+    uint32_t g = 0;                            // chunks consumed
     int acc_i = 0;
-    for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
-      const Tile t = args.tiles[w / args.nblocks];
-      const bool copy = (t.t0 + BM <= shift);
-      const int n0 = (w % args.nblocks) * BN;
-      const int tr = t.t0 + r;
-      const bool valid = tr < t.len;
-      const int64_t grow = t.seq_row0 + tr;
-      const bool fused = (QMAX > 0) && (t.flags & TILE_FINAL_FUSED);
+    bool alive = true;                         // warp-uniform
+    for (int w = blockIdx.x; w < nwork && alive; w += gridDim.x) {
+      const Item it = load_item<QMAX>(args, w);
+      const bool tma_out = !it.fused && !it.ragged;
+      const int tr = it.t.t0 + r;
+      const bool valid = tr < it.t.len;
+      const int64_t grow = it.t.seq_row0 + tr;
       const int abuf = acc_i & 1;
-      if (!copy) {
+      if (it.copy && tma_out) {
+        // the manager forwards the residual as is; acknowledge each chunk once
+        // it has arrived, keeping both slot barriers phase-locked
+        for (int cc = 0; cc < nch; ++cc, ++g) {
+          const int slot = (int)(g % RING);
+          if (!__all_sync(0xffffffffu,
+                          ptx::mbar_wait(&res_full[slot], (g / RING) & 1u, limit, abort_flag))) {
+            raise_timeout(args, abort_flag, 8, w, (int)g);
+            alive = false;
+            break;
+          }
+          ptx::mbar_arrive(&res_done[slot]);
+        }
+        continue;
+      }
+      if (!it.copy) {
         const uint32_t aph = (uint32_t)((acc_i >> 1) & 1);
-        if (!ptx::mbar_wait(&acc_full[abuf], aph, limit, abort_flag)) {
-          raise_timeout(args.err, abort_flag);
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait(&acc_full[abuf], aph, limit, abort_flag))) {
+          raise_timeout(args, abort_flag, 6, w, acc_i);
           break;
         }
         ptx::tc_fence_after();
       }
-      float yacc[QMAX > 0 ? QMAX : 1];
+      float yacc[QN];
 #pragma unroll
-      for (int qq = 0; qq < (QMAX > 0 ? QMAX : 1); ++qq) yacc[qq] = 0.f;
-      const float* Cs = args.C32 + (int64_t)t.sys * args.q * m;
-      for (int cc = 0; cc < BN / 32; ++cc) {
-        float v[32];
-        if (!copy) {
-          const uint32_t ta = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(abuf * ACC + cc * 32);
-          ptx::tmem_ld32(ta, v);
+      for (int qq = 0; qq < QN; ++qq) yacc[qq] = 0.f;
+      const float* Cs = args.C32 + (int64_t)it.t.sys * args.q * m;
+      const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(abuf * ACC);
+      // G chunks per step (nch is always even): their TMEM loads, unpacking,
+      // splitting and shared-memory traffic are independent.
+      for (int cc = 0; cc < nch; cc += G, g += G) {
+        int slot[G];
+        uint8_t* sh[G];
+        bool got = true;
+#pragma unroll
+        for (int h = 0; h < G; ++h) {
+          slot[h] = (int)((g + h) % RING);
+          sh[h] = ring + (size_t)slot[h] * SLOT_BYTES;
+          got = got && ptx::mbar_wait(&res_full[slot[h]], ((g + h) / RING) & 1u, limit, abort_flag);
+        }
+        if (!__all_sync(0xffffffffu, got)) {     // tcgen05.ld below is warp-collective
+          raise_timeout(args, abort_flag, 7, w, (int)g);
+          alive = false;
+          break;
+        }
+        float v[G][CW];
+        if (!it.copy) {
+          uint32_t ra[G][CW];
+#pragma unroll
+          for (int h = 0; h < G; ++h) ptx::tmem_ld_nw<CW>(trow + (uint32_t)((cc + h) * CW), ra[h]);
           if (SEP) {
-            float w2[32];
-            ptx::tmem_ld32(ta + (uint32_t)BN, w2);
+            uint32_t rb[G][CW];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] += w2[j];
+            for (int h = 0; h < G; ++h)
+              ptx::tmem_ld_nw<CW>(trow + (uint32_t)(BN + (cc + h) * CW), rb[h]);
+            ptx::tmem_wait_ld();
+#pragma unroll
+            for (int h = 0; h < G; ++h)
+#pragma unroll
+              for (int j = 0; j < CW; ++j)
+                v[h][j] = __uint_as_float(ra[h][j]) + __uint_as_float(rb[h][j]);
+          } else {
+            ptx::tmem_wait_ld();
+#pragma unroll
+            for (int h = 0; h < G; ++h)
+#pragma unroll
+              for (int j = 0; j < CW; ++j) v[h][j] = __uint_as_float(ra[h][j]);
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = 0.f;
-        }
-        if (valid) {
-          const int col0 = n0 + cc * 32;
-          const int64_t off = grow * (int64_t)m + col0;
-          PlaneIO<ELEM>::load_add(args.vin_hi, args.vin_lo, off, v);
-          if (fused) {
+          for (int h = 0; h < G; ++h)
 #pragma unroll
-            for (int qq = 0; qq < (QMAX > 0 ? QMAX : 1); ++qq) {
+            for (int j = 0; j < CW; ++j) v[h][j] = 0.f;
+        }
+        uint4 hq[G][4], lq[G][4];
+#pragma unroll
+        for (int h = 0; h < G; ++h)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            hq[h][c] = *reinterpret_cast<const uint4*>(sh[h] + ptx::sw64_offset(r, c));
+            lq[h][c] = *reinterpret_cast<const uint4*>(sh[h] + PLANE_TILE + ptx::sw64_offset(r, c));
+          }
+#pragma unroll
+        for (int h = 0; h < G; ++h)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) Fmt<ELEM>::add16(hq[h][c], lq[h][c], v[h] + c * (CW / 4));
+        if (it.fused) {
+          if (valid) {
+#pragma unroll
+            for (int qq = 0; qq < QN; ++qq) {
               if (qq < args.q) {
-                const float* crow = Cs + (int64_t)qq * m + col0;
+                const float* crow = Cs + (int64_t)qq * m + it.n0 + cc * CW;
                 float s = 0.f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) s = fmaf(__ldg(crow + j), v[j], s);
+                for (int h = 0; h < G; ++h)
+#pragma unroll
+                  for (int j = 0; j < CW; ++j) s = fmaf(__ldg(crow + h * CW + j), v[h][j], s);
                 yacc[qq] += s;
               }
             }
-          } else {
-            PlaneIO<ELEM>::store(args.vout_hi, args.vout_lo, off, v);
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < G; ++h)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) Fmt<ELEM>::split16(v[h] + c * (CW / 4), hq[h][c], lq[h][c]);
+          if (tma_out) {
+#pragma unroll
+            for (int h = 0; h < G; ++h)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                *reinterpret_cast<uint4*>(sh[h] + ptx::sw64_offset(r, c)) = hq[h][c];
+                *reinterpret_cast<uint4*>(sh[h] + PLANE_TILE + ptx::sw64_offset(r, c)) = lq[h][c];
+              }
+            ptx::fence_proxy_async_smem();      // visible to the manager's TMA store
+          } else if (valid) {
+#pragma unroll
+            for (int h = 0; h < G; ++h) {
+              const int64_t off = (grow * (int64_t)m + it.n0 + (cc + h) * CW) * ELEM;
+              uint4* gh = reinterpret_cast<uint4*>(static_cast<uint8_t*>(args.vout_hi) + off);
+              uint4* gl = reinterpret_cast<uint4*>(static_cast<uint8_t*>(args.vout_lo) + off);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) { gh[c] = hq[h][c]; gl[c] = lq[h][c]; }
+            }
           }
         }
+#pragma unroll
+        for (int h = 0; h < G; ++h) ptx::mbar_arrive(&res_done[slot[h]]);
       }
-      if (!copy) {
+      if (!alive) break;
+      if (!it.copy) {
         ptx::tc_fence_before();
         ptx::mbar_arrive(&acc_empty[abuf]);
         ++acc_i;
       }
-      if (fused && valid) {
-        const float* Ds = args.D32 + (int64_t)t.sys * args.q * args.p;
+      if (it.fused && valid) {
+        const float* Ds = args.D32 + (int64_t)it.t.sys * args.q * args.p;
         const float* ur = args.u + grow * args.p;
 #pragma unroll
-        for (int qq = 0; qq < (QMAX > 0 ? QMAX : 1); ++qq) {
+        for (int qq = 0; qq < QN; ++qq) {
           if (qq < args.q) {
             float s = yacc[qq];
             for (int j = 0; j < args.p; ++j) s = fmaf(__ldg(Ds + qq * args.p + j), __ldg(ur + j), s);
@@ -396,26 +561,55 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 1) ptx::tmem_dealloc(tmem_base, tmem_cols);
 }
 
-template <int ELEM, int QMAX>
+template <int ELEM, int QMAX, int G>
 cudaError_t launch_variant(const CUtensorMap* maps, const StageArgs& a, int grid, size_t smem,
                            cudaStream_t st) {
-  auto kern = stage_tc_kernel<ELEM, QMAX>;
+  auto kern = stage_tc_kernel<ELEM, QMAX, G>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, NTHREADS, smem, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+  kern<<<grid, NTHREADS, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }
 
+size_t stage_bytes_for(int BN) { return 2 * (size_t)PLANE_TILE + 2 * (size_t)BN * ROWB; }
+
+// Shared memory besides the operand stages: alignment slack, the staging ring,
+// the mbarriers (room for RING_MAX ring barriers of each kind) and the TMEM slot.
+size_t fixed_smem_bytes(int S, int ring) {
+  return 1024 + (size_t)ring * SLOT_BYTES + 8 * (2 * S + 5 + 2 * RING_MAX) + 16;
+}
+
+bool tc_config_fits(int BN, const TcConfig& c) {
+  if (c.group != 1 && c.group != 2) return false;
+  if (c.ring < 2 * c.group || c.ring > RING_MAX || c.ring % c.group != 0) return false;
+  if (c.stages < 2 || c.stages > 8) return false;
+  return fixed_smem_bytes(c.stages, c.ring) + (size_t)c.stages * stage_bytes_for(BN) <= 227 * 1024;
+}
+
 }  // namespace
 
-int stage_tc_pipeline_depth(int BN, int elem) {
-  (void)elem;
-  const size_t stage_bytes = 2 * (size_t)BM * 128 + 2 * (size_t)BN * 128;
-  const size_t budget = 227 * 1024 - 1024 - 256;
-  int s = (int)(budget / stage_bytes);
-  if (s > 8) s = 8;
-  return s;
+// Candidate kernel shapes for the autotuner: for each (chunks per step, ring
+// slots), the deepest operand pipeline that fits.
+std::vector<TcConfig> tc_candidates(int m, int precision) {
+  const int BN = block_n(m, precision);
+  std::vector<TcConfig> out;
+  for (int g : {1, 2})
+    for (int ring : {4, 6, 8})
+      for (int st = 6; st >= 2; --st) {
+        TcConfig c{st, ring, g};
+        if (tc_config_fits(BN, c)) { out.push_back(c); break; }
+      }
+  return out;
+}
+
+// Shape used when no tuning was done: one chunk per step, a 4-slot ring,
+// the deepest operand pipeline (at most 4) that fits.
+TcConfig tc_default(int m, int precision) {
+  const int BN = block_n(m, precision);
+  TcConfig c{4, 4, 1};
+  while (c.stages > 2 && !tc_config_fits(BN, c)) --c.stages;
+  return c;
 }
 
 cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
@@ -426,20 +620,19 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   const int m = p.d.m;
   const int elem = (int)plane_elem_bytes(p.d.precision);
   const int BN = block_n(m, p.d.precision);
-  const int KC = 128 / elem;
-  (void)KC;
-  CUtensorMap maps[4];
+  TcConfig cfg{p.tc_stages, p.tc_ring, p.tc_group};
+  if (!tc_config_fits(BN, cfg)) cfg = tc_default(m, p.d.precision);
+  const uint32_t row_elems = ROWB / (uint32_t)elem;
+  CUtensorMap maps[6];
   std::string err;
   const uint64_t rows = (uint64_t)p.rows;
   const uint64_t prow = (uint64_t)p.d.nsys * p.kmax1 * m;
-  const size_t plane_elems = (size_t)p.d.nsys * p.kmax1 * m * m;
-  const uint8_t* phi = static_cast<const uint8_t*>(p.Phi);
-  const uint8_t* plo = static_cast<const uint8_t*>(p.Plo);
-  (void)plane_elems;
-  if (!encode_tmap_2d(&maps[0], vin_hi, elem, m, rows, 128 / elem, BM, &err) ||
-      !encode_tmap_2d(&maps[1], vin_lo, elem, m, rows, 128 / elem, BM, &err) ||
-      !encode_tmap_2d(&maps[2], phi, elem, m, prow, 128 / elem, BN, &err) ||
-      !encode_tmap_2d(&maps[3], plo, elem, m, prow, 128 / elem, BN, &err)) {
+  if (!encode_tmap_2d(&maps[0], vin_hi, elem, m, rows, row_elems, BM, &err, 64) ||
+      !encode_tmap_2d(&maps[1], vin_lo, elem, m, rows, row_elems, BM, &err, 64) ||
+      !encode_tmap_2d(&maps[2], p.Phi, elem, m, prow, row_elems, BN, &err, 64) ||
+      !encode_tmap_2d(&maps[3], p.Plo, elem, m, prow, row_elems, BN, &err, 64) ||
+      !encode_tmap_2d(&maps[4], vout_hi, elem, m, rows, row_elems, BM, &err, 64) ||
+      !encode_tmap_2d(&maps[5], vout_lo, elem, m, rows, row_elems, BM, &err, 64)) {
     set_global_error("tensor map encode failed: " + err);
     return cudaErrorInvalidValue;
   }
@@ -451,7 +644,8 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   a.p = p.d.p;
   a.q = p.d.q;
   a.BN = BN;
-  a.stages = stage_tc_pipeline_depth(BN, elem);
+  a.stages = cfg.stages;
+  a.ring = cfg.ring;
   a.shift = 1 << k;
   a.k = k;
   a.kmax1 = p.kmax1;
@@ -464,22 +658,27 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   a.u = u;
   a.y = y;
   a.err = p.err;
+  a.diag = p.err + 1;
   a.timeout_ns = 2000000000ull;
-  const size_t stage_bytes = 2 * (size_t)BM * 128 + 2 * (size_t)BN * 128;
-  const size_t smem = 1024 + (size_t)a.stages * stage_bytes + 8 * (2 * a.stages + 5) + 16;
+  const size_t smem = fixed_smem_bytes(a.stages, a.ring) + (size_t)a.stages * stage_bytes_for(BN);
   const int nwork = ntiles * a.nblocks;
   const int grid = nwork < p.num_sms ? nwork : p.num_sms;
   const int q = p.d.q;
   const bool fuse = p.fuse_output;
+  const int G = cfg.group;
+#define CASCADE_TC_DISPATCH(E, Q)                                               \
+  return G == 2 ? launch_variant<E, Q, 2>(maps, a, grid, smem, st)               \
+                : launch_variant<E, Q, 1>(maps, a, grid, smem, st)
   if (elem == 2) {
-    if (!fuse) return launch_variant<2, 0>(maps, a, grid, smem, st);
-    if (q == 1) return launch_variant<2, 1>(maps, a, grid, smem, st);
-    return launch_variant<2, 16>(maps, a, grid, smem, st);
+    if (!fuse) CASCADE_TC_DISPATCH(2, 0);
+    if (q == 1) CASCADE_TC_DISPATCH(2, 1);
+    CASCADE_TC_DISPATCH(2, 16);
   } else {
-    if (!fuse) return launch_variant<4, 0>(maps, a, grid, smem, st);
-    if (q == 1) return launch_variant<4, 1>(maps, a, grid, smem, st);
-    return launch_variant<4, 16>(maps, a, grid, smem, st);
+    if (!fuse) CASCADE_TC_DISPATCH(4, 0);
+    if (q == 1) CASCADE_TC_DISPATCH(4, 1);
+    CASCADE_TC_DISPATCH(4, 16);
   }
+#undef CASCADE_TC_DISPATCH
 }
 
 }  // namespace cascade

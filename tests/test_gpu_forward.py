@@ -34,7 +34,7 @@ def run_gpu(cascade, w, precision, flags=0, N=None):
     y = c.forward(u)
     torch.cuda.synchronize()
     err = c.device_error()
-    assert err == 0, f"device error word {err}"
+    assert err == 0, f"device error word {err}: {c.lib.cascade_last_error(c.plan)}"
     return c, y.double().cpu().numpy()
 
 
@@ -264,3 +264,64 @@ def test_batching_form_cx_only(lib, precision):
     w = wl.batching_form(nseq=24, Lmax=8192)
     w.D = np.zeros_like(w.D)
     check(lib, w, precision)
+
+
+@pytest.mark.parametrize("precision,m", [("bf16_split", 256), ("fp32", 128)])
+def test_autotuned_shape_keeps_parity(lib, precision, m):
+    """Every kernel shape the autotuner may pick gives the same results; the
+    chosen one is valid and keeps oracle parity."""
+    import torch
+    w = cast_inputs(wl.precision_form(m=m, L=1200, batch=4, N=10), precision)
+    c = lib.from_workload(w, precision=precision)
+    u = torch.as_tensor(w.u, dtype=torch.float32).cuda()
+    stages, ring, group = c.autotune(u)
+    assert 2 <= stages <= 8 and ring in (4, 6, 8) and group in (1, 2) and ring % group == 0
+    y = c.forward(u).double().cpu().numpy()
+    assert c.device_error() == 0
+    yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
+    ey, ecx = rel_errors(w, y, yo, OUT_EPS[precision])
+    assert ey <= TOL[precision] and ecx <= TOL[precision], (ey, ecx)
+
+
+@pytest.mark.parametrize("precision,m", [("bf16_split", 256), ("bf16_split", 128), ("fp32", 128),
+                                         ("fp32", 64)])
+def test_every_kernel_shape(lib, precision, m):
+    """Each kernel shape that fits (operand stages x ring slots x chunks per
+    step) matches the oracle on ragged sequences; shapes that do not fit are
+    refused."""
+    import torch
+    from paper_2411_17729_gb300._abi import CascadeError
+    lengths = (1, 130, 700, 257)
+    w = wl.precision_form(m=m, L=8, batch=len(lengths), N=10)
+    rng = np.random.default_rng(3)
+    w.offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    w.u = rng.standard_normal((int(w.offsets[-1]), 1))
+    w = cast_inputs(w, precision)
+    c = lib.from_workload(w, precision=precision)
+    u = torch.as_tensor(w.u, dtype=torch.float32).cuda()
+    yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
+    tried = 0
+    for group in (1, 2):
+        for ring in (4, 6, 8):
+            for stages in (2, 3, 4, 5, 6):
+                try:
+                    c.set_kernel_shape(stages, ring, group)
+                except CascadeError:
+                    continue
+                tried += 1
+                y = c.forward(u).double().cpu().numpy()
+                assert c.device_error() == 0
+                ey, ecx = rel_errors(w, y, yo, OUT_EPS[precision])
+                assert ey <= TOL[precision] and ecx <= TOL[precision], (stages, ring, group, ey, ecx)
+    assert tried >= 6
+    with pytest.raises(CascadeError):
+        c.set_kernel_shape(2, 5, 2)          # ring not a multiple of the step
+
+
+@pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
+def test_many_items_per_block(lib, precision):
+    """40 sequences x 2048 steps: every block of the persistent stage kernel
+    walks several tiles per stage, pass-through tiles (all sources before the
+    sequence start) interleaved with computed ones."""
+    w = wl.precision_form(m=128, L=2048, batch=40, N=10)
+    c, y, yo = check(lib, w, precision)

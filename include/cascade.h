@@ -193,16 +193,20 @@ cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y
 cascade_status_t cascade_forward_fixed_scratch(cascade_plan_t plan, const void* d_u, void* d_y,
                                                void* stream);
 
-/* Reverse-mode derivative of sum(dy * y) for the last forward (which must
-   have run with CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE on this
-   workspace).  Writes d_du [rows,p] (plan element type) and, per system,
-   d_dAbar [nsys,m,m], d_dBbar [nsys,m,p], d_dC [nsys,q,m], d_dD [nsys,q,p]
-   (double).  For continuous systems d_dA [nsys,m,m] and d_dB [nsys,m,p] are
-   the gradients through Eq. (4.2) (may be NULL to skip).  Gradient pointers
-   may be NULL individually.  Asynchronous. */
-cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_dy, void* d_du,
-                                  double* d_dAbar, double* d_dBbar, double* d_dC, double* d_dD,
-                                  double* d_dA, double* d_dB, void* d_workspace,
+/* Reverse-mode derivative of sum(dy * y) for the last cascade_forward on
+   this batch and workspace, which must come from a plan created with
+   CASCADE_FLAG_SAVE_STATES (the forward then keeps every stage output in the
+   workspace; CASCADE_ERR_STATE otherwise).  d_u is the forward's input,
+   d_dy [rows,q] the output gradient (plan element type).  Writes d_du
+   [rows,p] and, per system, d_dAbar [nsys,m,m], d_dBbar [nsys,m,p], d_dC
+   [nsys,q,m], d_dD [nsys,q,p] (double): the gradients through the squaring
+   chain (end of §2) and the stages (§3, derived adjoint: transposed powers,
+   reversed shifts).  For continuous systems d_dA [nsys,m,m] and d_dB
+   [nsys,m,p] are the gradients through Eq. (4.2).  Any output pointer may be
+   NULL to skip it.  Asynchronous. */
+cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_u, const void* d_dy,
+                                  void* d_du, double* d_dAbar, double* d_dBbar, double* d_dC,
+                                  double* d_dD, double* d_dA, double* d_dB, void* d_workspace,
                                   size_t workspace_bytes, void* stream);
 
 /* FP64 sequential recursion of Eq. (1.2), x_n = Abar x_(n-1) + Bbar u_n,

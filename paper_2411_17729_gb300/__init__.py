@@ -9,7 +9,7 @@ from .build import build  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("Cascade", "CascadeFunction"):
+    if name in ("Cascade", "CascadeFunction", "from_workload"):
         from . import cascade as _c
         return getattr(_c, name)
     raise AttributeError(name)

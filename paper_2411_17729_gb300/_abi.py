@@ -58,7 +58,7 @@ SIGNATURES = [
     ("cascade_workspace_size", C.c_int, [cascade_plan_t, C.POINTER(C.c_size_t)]),
     ("cascade_forward", C.c_int, [cascade_plan_t, _P, _P, _P, C.c_size_t, _P]),
     ("cascade_forward_fixed_scratch", C.c_int, [cascade_plan_t, _P, _P, _P]),
-    ("cascade_backward", C.c_int, [cascade_plan_t, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+    ("cascade_backward", C.c_int, [cascade_plan_t, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                    C.c_size_t, _P]),
     ("cascade_recursion_forward", C.c_int, [cascade_plan_t, _P, _P, _P]),
     ("cascade_get_device_error", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),

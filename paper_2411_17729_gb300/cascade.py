@@ -39,7 +39,7 @@ class Cascade:
         with torch.cuda.device(self.device):
             _abi.check(self.lib.cascade_plan_create(C.byref(self.plan), C.byref(d)))
         self._ws = None
-        self._keep = []
+        self.continuous = False
 
     def close(self):
         if self.plan:
@@ -66,11 +66,13 @@ class Cascade:
         self._check(self.lib.cascade_set_system_continuous(self.plan, _ptr(t[0]), _ptr(t[1]),
                                                            _ptr(t[2]), _ptr(sc), _ptr(t[3]),
                                                            _ptr(t[4]), _stream(stream)))
+        self.continuous = True
 
     def set_system_discrete(self, Abar, Bbar, C_, D, stream=None):
         t = [self._dev64(x, self.device) for x in (Abar, Bbar, C_, D)]
         self._check(self.lib.cascade_set_system_discrete(self.plan, *[_ptr(x) for x in t],
                                                          _stream(stream)))
+        self.continuous = False
 
     def set_batch(self, offsets, sys_of_seq=None):
         offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
@@ -118,6 +120,29 @@ class Cascade:
         self._check(self.lib.cascade_forward(self.plan, _ptr(u), _ptr(y), _ptr(ws), ws.numel(),
                                              _stream(stream)))
         return y
+
+    def backward(self, u, dy, stream=None, want=("du", "dAbar", "dBbar", "dC", "dD", "dA", "dB")):
+        """Gradients of sum(dy * y) for the last forward (plan created with
+        CASCADE_FLAG_SAVE_STATES).  Returns a dict of tensors; dA, dB only for
+        continuous systems."""
+        assert dy.dtype == self.dtype and dy.is_contiguous() and dy.shape == (self.rows, self.q)
+        f64 = dict(dtype=torch.float64, device=self.device)
+        m, p, q, ns = self.m, self.p, self.q, self.nsys
+        out = {}
+        if "du" in want:
+            out["du"] = torch.empty((self.rows, p), dtype=self.dtype, device=self.device)
+        shapes = {"dAbar": (ns, m, m), "dBbar": (ns, m, p), "dC": (ns, q, m), "dD": (ns, q, p)}
+        if self.continuous:
+            shapes.update({"dA": (ns, m, m), "dB": (ns, m, p)})
+        for k, shp in shapes.items():
+            if k in want:
+                out[k] = torch.zeros(shp, **f64)
+        ws = self.workspace()
+        g = lambda k: _ptr(out.get(k))
+        self._check(self.lib.cascade_backward(self.plan, _ptr(u), _ptr(dy), g("du"), g("dAbar"),
+                                              g("dBbar"), g("dC"), g("dD"), g("dA"), g("dB"),
+                                              _ptr(ws), ws.numel(), _stream(stream)))
+        return out
 
     def recursion(self, u, y=None, stream=None):
         assert u.dtype == torch.float64 and u.is_contiguous()
@@ -175,3 +200,37 @@ def from_workload(w, precision=None, flags=0, N=None, max_len=None, device=None)
         casc.set_system_continuous(rep(w.A), rep(w.B), delta, rep(w.C), rep(w.D), abar_scale=sc)
     casc.set_batch(w.offsets, w.sys_of_seq)
     return casc
+
+
+class CascadeFunction(torch.autograd.Function):
+    """y = cascade(u; A or Abar, B or Bbar, C, D) as a differentiable op.
+
+    apply(casc, u, A, B, C, D, delta=None): with ``delta`` the system is
+    continuous (A, B discretised by Eq. 4.2 on the device), otherwise A, B are
+    Abar, Bbar.  ``casc`` is a Cascade plan created with
+    CASCADE_FLAG_SAVE_STATES whose batch is already set; system tensors are
+    float64 [nsys, ...] on the plan's device.  Gradients flow to u, A (through
+    the squaring chain, and the discretisation when continuous), B, C and D.
+    """
+
+    @staticmethod
+    def forward(ctx, casc, u, A, B, C_, D, delta=None):
+        if delta is None:
+            casc.set_system_discrete(A.detach(), B.detach(), C_.detach(), D.detach())
+        else:
+            casc.set_system_continuous(A.detach(), B.detach(), delta.detach(), C_.detach(),
+                                       D.detach())
+        u = u.contiguous()
+        y = casc.forward(u)
+        ctx.casc = casc
+        ctx.continuous = delta is not None
+        ctx.save_for_backward(u)
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        (u,) = ctx.saved_tensors
+        g = ctx.casc.backward(u, dy.contiguous().to(u.dtype))
+        gA = g["dA"] if ctx.continuous else g["dAbar"]
+        gB = g["dB"] if ctx.continuous else g["dBbar"]
+        return None, g["du"], gA, gB, g["dC"], g["dD"], None

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <mutex>
 
 namespace cascade {
@@ -134,6 +135,8 @@ void dfree(void* ptr) {
   if (ptr) cudaFree(ptr);
 }
 
+bool saves_states(const Plan& p) { return (p.d.flags & CASCADE_FLAG_SAVE_STATES) != 0; }
+
 int ceil_log2(int64_t L) {
   int k = 0;
   while ((int64_t(1) << k) < L) ++k;
@@ -157,6 +160,16 @@ void free_batch(Plan* p) {
   p->d_out_tiles = nullptr;
   dfree(p->d_stage0_tiles);
   p->d_stage0_tiles = nullptr;
+  dfree(p->d_all_tiles);
+  p->d_all_tiles = nullptr;
+  p->n_all_tiles = 0;
+  dfree(p->d_chunk_data);
+  p->d_chunk_data = nullptr;
+  p->chunk_lists.clear();
+  p->max_chunks = 0;
+  p->d_adj_tiles.clear();
+  p->n_adj_tiles.clear();
+  p->saved_ws = nullptr;
   p->n_out_tiles = p->n_stage0_tiles = 0;
   p->have_batch = false;
   if (p->graph) {
@@ -167,13 +180,16 @@ void free_batch(Plan* p) {
 
 void free_system(Plan* p) {
   void* ptrs[] = {p->P64, p->Phi, p->Plo, p->Bbar64, p->ABbar64, p->C64, p->D64, p->Bbar32,
-                  p->ABbar32, p->C32, p->D32, p->A64, p->B64, p->delta64, p->scale64};
+                  p->ABbar32, p->C32, p->D32, p->A64, p->B64, p->delta64, p->scale64,
+                  p->PThi, p->PTlo, p->PT64, p->Minv64};
   for (void* q : ptrs) dfree(q);
   p->P64 = nullptr;
   p->Phi = p->Plo = nullptr;
   p->Bbar64 = p->ABbar64 = p->C64 = p->D64 = nullptr;
   p->Bbar32 = p->ABbar32 = p->C32 = p->D32 = nullptr;
   p->A64 = p->B64 = p->delta64 = p->scale64 = nullptr;
+  p->PThi = p->PTlo = nullptr;
+  p->PT64 = p->Minv64 = nullptr;
 }
 
 // Squaring chain, accuracy rule, Abar*Bbar, operand planes; P64[:,0] and
@@ -216,10 +232,16 @@ cascade_status_t finish_system(Plan* p, cudaStream_t st) {
       p->N_sys[s] = N;
     }
   }
+  if (p->PT64)
+    CK(launch_transpose(p->P64, p->PT64, m, mm, ns * p->kmax1, st), "transposed powers");
   // Operand formats
   if (p->d.precision != CASCADE_FP64) {
     CK(launch_split_planes(p->P64, p->Phi, p->Plo, (int64_t)ns * sys_stride, p->d.precision, st),
        "operand planes");
+    if (p->PThi)
+      CK(launch_split_planes(p->PT64, p->PThi, p->PTlo, (int64_t)ns * sys_stride, p->d.precision,
+                             st),
+         "transposed operand planes");
     CK(launch_to_f32(p->Bbar64, p->Bbar32, (int64_t)ns * m * pp, st), "Bbar f32");
     CK(launch_to_f32(p->ABbar64, p->ABbar32, (int64_t)ns * m * pp, st), "ABbar f32");
     CK(launch_to_f32(p->C64, p->C32, (int64_t)ns * q * m, st), "C f32");
@@ -247,6 +269,18 @@ cascade_status_t alloc_system(Plan* p) {
   CK(dalloc(&p->ABbar64, (size_t)ns * m * pp), "alloc ABbar");
   CK(dalloc(&p->C64, (size_t)ns * q * m), "alloc C");
   CK(dalloc(&p->D64, (size_t)ns * q * pp), "alloc D");
+  if (saves_states(*p)) {   // the adjoint stages use the transposed powers
+    CK(dalloc(&p->PT64, (size_t)ns * p->kmax1 * mm), "alloc transposed powers");
+    if (p->d.precision != CASCADE_FP64) {
+      const size_t e = plane_elem_bytes(p->d.precision);
+      uint8_t* hi = nullptr;
+      uint8_t* lo = nullptr;
+      CK(dalloc(&hi, (size_t)ns * p->kmax1 * mm * e), "alloc transposed planes");
+      CK(dalloc(&lo, (size_t)ns * p->kmax1 * mm * e), "alloc transposed planes");
+      p->PThi = hi;
+      p->PTlo = lo;
+    }
+  }
   if (p->d.precision != CASCADE_FP64) {
     const size_t e = plane_elem_bytes(p->d.precision);
     uint8_t* hi = nullptr;
@@ -263,35 +297,47 @@ cascade_status_t alloc_system(Plan* p) {
   return CASCADE_OK;
 }
 
-struct Planes {
-  void* hi[2];
-  void* lo[2];
-};
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t forward_workspace(const Plan& p, int64_t rows) {
-  const size_t plane = align256((size_t)rows * p.d.m * plane_elem_bytes(p.d.precision));
+// Workspace layout.  State buffers j = 0..nV-1 (each one FP64 plane or a
+// (hi, lo) plane pair over all rows); with CASCADE_FLAG_SAVE_STATES buffer j
+// keeps v^(j+1) of every stage, otherwise two buffers alternate.  Backward
+// adds two adjoint buffers, the split-K partials, dP_k, and small FP64 scratch.
+struct Layout {
+  size_t plane = 0, buf_stride = 0, lo_off = 0;
+  int nV = 2;
+  size_t off_W = 0, off_part = 0, off_dP = 0, off_R = 0, off_T = 0, total = 0;
+};
+
+Layout layout(const Plan& p) {
+  Layout L;
   const int nplanes = p.d.precision == CASCADE_FP64 ? 1 : 2;
-  return 2 * nplanes * plane + 256;
+  L.plane = align256((size_t)p.rows * p.d.m * plane_elem_bytes(p.d.precision));
+  L.buf_stride = nplanes * L.plane;
+  L.lo_off = nplanes == 2 ? L.plane : 0;
+  const bool save = saves_states(p);
+  L.nV = save ? std::max(p.maxN + 1, 1) : 2;
+  size_t off = (size_t)L.nV * L.buf_stride;
+  if (save) {
+    const size_t m = p.d.m, pp = p.d.p, q = p.d.q, ns = p.d.nsys;
+    const size_t acc = p.d.precision == CASCADE_FP64 ? 8 : 4;
+    const size_t elems = std::max(std::max(m * m, q * m), std::max(q * pp, m * pp));
+    L.off_W = off;
+    off += 2 * L.buf_stride;
+    L.off_part = off;
+    off += align256((size_t)std::max(p.max_chunks, 1) * elems * acc);
+    L.off_dP = off;
+    off += align256(ns * p.kmax1 * m * m * 8);
+    L.off_R = off;                                  // R1, R2, dBbar: [nsys, m, p] each
+    off += align256(3 * ns * m * pp * 8);
+    L.off_T = off;                                  // [nsys, m, m]
+    off += align256(ns * m * m * 8);
+  }
+  L.total = off + 256;
+  return L;
 }
 
-Planes carve(const Plan& p, void* ws) {
-  Planes pl{};
-  const size_t plane = align256((size_t)p.rows * p.d.m * plane_elem_bytes(p.d.precision));
-  uint8_t* base = static_cast<uint8_t*>(ws);
-  if (p.d.precision == CASCADE_FP64) {
-    pl.hi[0] = base;
-    pl.hi[1] = base + plane;
-    pl.lo[0] = pl.lo[1] = nullptr;
-  } else {
-    pl.hi[0] = base;
-    pl.lo[0] = base + plane;
-    pl.hi[1] = base + 2 * plane;
-    pl.lo[1] = base + 3 * plane;
-  }
-  return pl;
-}
+size_t forward_workspace(const Plan& p, int64_t) { return layout(p).total; }
 
 cudaError_t ensure_events(Plan* p, int pairs) {
   while ((int)p->ev.size() < 2 * pairs) {
@@ -304,24 +350,29 @@ cudaError_t ensure_events(Plan* p, int pairs) {
 }
 
 cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStream_t st) {
-  Planes pl = carve(*p, ws);
+  const Layout L = layout(*p);
+  const Bufs V{static_cast<uint8_t*>(ws), L.buf_stride, L.lo_off};
+  const bool save = saves_states(*p);
   const bool timing = p->timing;
   if (timing) {
     CK(ensure_events(p, std::max(p->maxN, 1)), "timing events");
     p->ev_k.clear();
     p->n_ev = 0;
   }
-  // stage 0 fused with v^(0) = Bbar u: writes buffer 1
-  CK(launch_stage0(*p, u, pl.hi[1], pl.lo[1], st), "first stage");
+  // buffer holding v^(k) read by stage k, and the one stage k writes
+  auto in_buf = [&](int k) { return save ? k - 1 : (k & 1); };
+  auto out_buf = [&](int k) { return save ? k : ((k + 1) & 1); };
+  // stage 0 fused with v^(0) = Bbar u
+  CK(launch_stage0(*p, u, V.hi(out_buf(0)), V.lo(out_buf(0)), st), "first stage");
   for (int k = 1; k <= p->maxN; ++k) {
-    const int in = k & 1, out = (k + 1) & 1;
+    const int in = in_buf(k), out = out_buf(k);
     if (timing && p->n_tiles[k] > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
     if (p->d.precision == CASCADE_FP64) {
-      CK(launch_stage_f64(*p, k, static_cast<const double*>(pl.hi[in]),
-                          static_cast<double*>(pl.hi[out]), st),
+      CK(launch_stage_f64(*p, k, static_cast<const double*>(V.hi(in)),
+                          static_cast<double*>(V.hi(out)), st),
          "stage (fp64)");
     } else {
-      CK(launch_stage_tc(*p, k, pl.hi[in], pl.lo[in], pl.hi[out], pl.lo[out],
+      CK(launch_stage_tc(*p, k, V.hi(in), V.lo(in), V.hi(out), V.lo(out),
                          static_cast<const float*>(u), static_cast<float*>(y), st),
          "stage (tensor core)");
     }
@@ -331,7 +382,119 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
       p->n_ev++;
     }
   }
-  CK(launch_output(*p, u, y, pl.hi, pl.lo, st), "output projection");
+  CK(launch_output(*p, u, y, V, st), "output projection");
+  if (save) {
+    p->saved_ws = ws;
+    p->saved_batch = p->batch_id;
+  }
+  return CASCADE_OK;
+}
+
+// Reverse-mode derivative of sum(dy * y) after a forward that kept its stage
+// outputs (see backward.cu for the equations).
+cascade_status_t run_backward(Plan* p, const void* u, const void* dy, void* du, double* dAbar,
+                              double* dBbar, double* dC, double* dD, double* dA, double* dB,
+                              void* ws, cudaStream_t st) {
+  const Layout L = layout(*p);
+  uint8_t* base = static_cast<uint8_t*>(ws);
+  const Bufs V{base, L.buf_stride, L.lo_off};
+  const Bufs W{base + L.off_W, L.buf_stride, L.lo_off};
+  void* part = base + L.off_part;
+  double* dP = reinterpret_cast<double*>(base + L.off_dP);
+  const int m = p->d.m, pp = p->d.p, q = p->d.q, ns = p->d.nsys;
+  const int64_t mm = (int64_t)m * m, mp = (int64_t)m * pp;
+  const int64_t kst = (int64_t)p->kmax1 * mm;
+  double* R1 = reinterpret_cast<double*>(base + L.off_R);
+  double* R2 = R1 + ns * mp;
+  double* dBb = R2 + ns * mp;
+  double* T = reinterpret_cast<double*>(base + L.off_T);
+  const bool f64 = p->d.precision == CASCADE_FP64;
+  const TSrc G{f64 ? 2 : 1, Bufs{}, 0, 0, dy, q};
+  const TSrc U{f64 ? 2 : 1, Bufs{}, 0, 0, u, pp};
+  auto chunks = [&](int li) { return p->d_chunk_data + p->chunk_lists[li].off_chunks; };
+  auto sysbeg = [&](int li) { return p->d_chunk_data + p->chunk_lists[li].off_begin; };
+  const int nall = p->chunk_lists[0].n;
+
+  // W^(N_i+1) = C^T G, in the adjoint buffer the stage N_i reads
+  CK(launch_adj_init(*p, dy, W, st), "adjoint init");
+  if (dC)   // dC = sum G v^(N+1)^T; v^(N_i+1) sits in state buffer N_i (tile.flags)
+    CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q,
+                      TSrc{0, V, 1, 0, nullptr, 0}, m, 0, part, dC, (int64_t)q * m, 0, st),
+       "dC");
+  if (dD)
+    CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q, U, pp, 0, part, dD,
+                      (int64_t)q * pp, 0, st),
+       "dD");
+  CK(cudaMemsetAsync(dP, 0, sizeof(double) * ns * kst, st), "zero dP");
+  for (int k = p->maxN; k >= 1; --k) {
+    const int win = (k + 1) & 1, wout = k & 1;
+    const ChunkList& cl = p->chunk_lists[k];
+    // dP_k = sum_{l >= s} W^(k+1)_l v^(k)_(l-s)^T; v^(k) is state buffer k-1
+    CK(launch_treduce(*p, p->d_tiles[k], chunks(k), cl.n, sysbeg(k),
+                      TSrc{0, W, 0, win, nullptr, 0}, m, TSrc{0, V, 0, k - 1, nullptr, 0}, m,
+                      1 << k, part, dP + (int64_t)k * mm, kst, 0, st),
+       "dP");
+    if (f64) {
+      CK(launch_stage_f64(*p, k, static_cast<const double*>(W.hi(win)),
+                          static_cast<double*>(W.hi(wout)), st, true),
+         "adjoint stage (fp64)");
+    } else {
+      CK(launch_stage_tc(*p, k, W.hi(win), W.lo(win), W.hi(wout), W.lo(wout), nullptr, nullptr,
+                         st, true),
+         "adjoint stage (tensor core)");
+    }
+  }
+  // first stage (fused with Bbar u): W^(1) is adjoint buffer 1
+  if (du) CK(launch_stage0_adj(*p, dy, W, 1, du, st), "du");
+  const TSrc W1{0, W, 0, 1, nullptr, 0};
+  CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, U, pp, 0, part, R1,
+                    mp, 0, st),
+     "R1");
+  CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, U, pp, 1, part, R2,
+                    mp, 0, st),
+     "R2");
+  // dP_0 += R2 Bbar^T;  dBbar = R1 + Abar^T R2
+  CK(launch_dgemm(R2, p->Bbar64, dP, m, m, pp, pp, pp, m, mp, mp, kst, ns, 1.0, 1.0, false, true, st),
+     "dP0");
+  CK(cudaMemcpyAsync(dBb, R1, sizeof(double) * ns * mp, cudaMemcpyDeviceToDevice, st), "copy");
+  CK(launch_dgemm(p->P64, R2, dBb, m, pp, m, m, pp, pp, kst, mp, mp, ns, 1.0, 1.0, true, false, st),
+     "dBbar");
+  // squaring chain P_(k+1) = P_k P_k:  dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1)
+  for (int k = p->kmax1 - 2; k >= 0; --k) {
+    CK(launch_dgemm(dP + (k + 1) * mm, p->P64 + k * mm, dP + k * mm, m, m, m, m, m, m, kst, kst,
+                    kst, ns, 1.0, 1.0, false, true, st),
+       "chain");
+    CK(launch_dgemm(p->P64 + k * mm, dP + (k + 1) * mm, dP + k * mm, m, m, m, m, m, m, kst, kst,
+                    kst, ns, 1.0, 1.0, true, false, st),
+       "chain");
+  }
+  if (dAbar)
+    CK(cudaMemcpy2DAsync(dAbar, sizeof(double) * mm, dP, sizeof(double) * kst, sizeof(double) * mm,
+                         ns, cudaMemcpyDeviceToDevice, st),
+       "dAbar");
+  if (dBbar)
+    CK(cudaMemcpyAsync(dBbar, dBb, sizeof(double) * ns * mp, cudaMemcpyDeviceToDevice, st), "dBbar");
+  // trapezoidal discretisation (Eq. 4.2), Abar = c M^-1 (I + delta/2 A), Bbar = delta M^-1 B:
+  // dA = delta/2 M^-T (c dAbar + dAbar Abar^T + dBbar Bbar^T),  dB = delta M^-T dBbar
+  if (p->continuous && (dA || dB)) {
+    CK(launch_dgemm(dP, p->P64, T, m, m, m, m, m, m, kst, kst, mm, ns, 1.0, 0.0, false, true, st),
+       "T");
+    CK(launch_dgemm(dBb, p->Bbar64, T, m, m, pp, pp, pp, m, mp, mp, mm, ns, 1.0, 1.0, false, true,
+                    st),
+       "T");
+    CK(launch_axpy_sys(dP, kst, T, mm, mm, ns, p->scale64, 1.0, true, st), "T");
+    if (dA) {
+      CK(launch_dgemm(p->Minv64, T, dA, m, m, m, m, m, m, mm, mm, mm, ns, 1.0, 0.0, true, false, st),
+         "dA");
+      CK(launch_axpy_sys(dA, mm, dA, mm, mm, ns, p->delta64, 0.5, false, st), "dA");
+    }
+    if (dB) {
+      CK(launch_dgemm(p->Minv64, dBb, dB, m, pp, m, m, pp, pp, mm, mp, mp, ns, 1.0, 0.0, true, false,
+                      st),
+         "dB");
+      CK(launch_axpy_sys(dB, mp, dB, mp, mp, ns, p->delta64, 1.0, false, st), "dB");
+    }
+  }
   return CASCADE_OK;
 }
 
@@ -408,7 +571,8 @@ cascade_status_t cascade_plan_create(cascade_plan_t* out, const cascade_desc_t* 
   const int Nmax = std::max(0, ceil_log2(d.max_len) - 1);
   p->kmax1 = (d.N >= 0) ? std::min(d.N, Nmax) + 1 : Nmax + 2;
   p->fuse_output = d.precision != CASCADE_FP64 && !(d.flags & CASCADE_FLAG_NO_FUSED_OUTPUT) &&
-                   block_n(d.m, d.precision) == d.m && d.q <= 16;
+                   !(d.flags & CASCADE_FLAG_SAVE_STATES) && block_n(d.m, d.precision) == d.m &&
+                   d.q <= 16;
   e = cudaMalloc(&p->err, 8 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(p->err, 0, 8 * sizeof(int32_t));
   if (e != cudaSuccess) {
@@ -465,12 +629,14 @@ cascade_status_t cascade_set_system_continuous(cascade_plan_t plan, const double
   CK(cudaMemcpyAsync(p->D64, d_D, sizeof(double) * ns * q * pp, cudaMemcpyDeviceToDevice, st), "copy D");
   double* work = nullptr;
   int32_t* sing = nullptr;
-  CK(dalloc(&work, (size_t)ns * m * (2 * m + pp)), "discretisation workspace");
+  CK(dalloc(&work, (size_t)ns * m * (3 * m + pp)), "discretisation workspace");
+  if (!p->Minv64) CK(dalloc(&p->Minv64, (size_t)ns * m * m), "alloc M^-1");
   cudaError_t e = cudaMalloc(&sing, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(sing, 0, sizeof(int32_t), st);
   if (e == cudaSuccess)
     e = launch_discretise(p->A64, p->B64, p->delta64, p->scale64, p->P64,
-                          (int64_t)p->kmax1 * m * m, p->Bbar64, work, ns, m, pp, sing, st);
+                          (int64_t)p->kmax1 * m * m, p->Bbar64, p->Minv64, work, ns, m, pp, sing,
+                          st);
   int32_t h_sing = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_sing, sing, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -553,9 +719,10 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
   p->sys_of_seq.assign(nseq, 0);
   if (h_sys_of_seq) p->sys_of_seq.assign(h_sys_of_seq, h_sys_of_seq + nseq);
   p->seq_N.assign(nseq, -1);
+  const bool save = saves_states(*p);
   const int BM = tile_rows(*p);
   int maxN = -1;
-  std::vector<Tile> t0s, outs;
+  std::vector<Tile> t0s, outs, all;
   std::vector<Seq> seqs;
   for (int i = 0; i < nseq; ++i) {
     const int64_t L = h_offsets[i + 1] - h_offsets[i];
@@ -565,7 +732,10 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     p->seq_N[i] = N;
     maxN = std::max(maxN, N);
     seqs.push_back(Seq{h_offsets[i], (int32_t)L, sys, N, 0});
-    for (int64_t t = 0; t < L; t += BM) t0s.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, 0, 0, 0});
+    for (int64_t t = 0; t < L; t += BM) {
+      t0s.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, 0, 0, 0});
+      all.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, N, 0, 0});   // flags = N_i
+    }
   }
   p->maxN = maxN;
   p->h_tiles.assign(std::max(maxN + 1, 1), {});
@@ -578,15 +748,17 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
       const bool fused = fused_last && k == N;
       const int64_t prev_shift = int64_t(1) << (k - 1);
       for (int64_t t = 0; t < L; t += BM) {
-        // rows below 2^(k-1) already hold their final value in the output buffer
-        if (!fused && k >= 2 && t + BM <= prev_shift) continue;
+        // Ping-pong buffers: rows below 2^(k-1) already hold their final value in the
+        // output buffer.  Kept stage outputs: every stage writes every row.
+        if (!save && !fused && k >= 2 && t + BM <= prev_shift) continue;
         p->h_tiles[k].push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys,
                                      fused ? (int32_t)TILE_FINAL_FUSED : 0, 0, 0});
       }
     }
-    if (!fused_last) {
+    if (!fused_last) {   // flags: state buffer holding v^(N+1)
+      const int buf = save ? N : ((N + 1) & 1);
       for (int64_t t = 0; t < L; t += BM)
-        outs.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, (N + 1) & 1, 0, 0});
+        outs.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, buf, 0, 0});
     }
   }
   auto upload = [&](const std::vector<Tile>& v, Tile** d) -> cudaError_t {
@@ -611,7 +783,48 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     CK(cudaMemcpy(p->d_seqs, seqs.data(), seqs.size() * sizeof(Seq), cudaMemcpyHostToDevice),
        "upload sequences");
   }
-  p->nseq = (int)seqs.size() == nseq ? nseq : nseq;
+  if (save) {
+    // adjoint stage k walks the same tiles as forward stage k (all tiles of the
+    // sequences with N_i >= k)
+    p->d_adj_tiles = p->d_tiles;
+    p->n_adj_tiles = p->n_tiles;
+    CK(upload(all, &p->d_all_tiles), "upload tiles");
+    p->n_all_tiles = (int)all.size();
+    // Time-reduction chunks: runs of up to CH consecutive tiles of one system,
+    // grouped by system (list 0: every tile; list k: the tiles of stage k).
+    const int CH = 8;
+    std::vector<int32_t> data;
+    p->chunk_lists.assign(std::max(maxN + 1, 1), ChunkList{});
+    for (size_t li = 0; li < p->chunk_lists.size(); ++li) {
+      const std::vector<Tile>& tl = li == 0 ? all : p->h_tiles[li];
+      std::vector<std::array<int32_t, 3>> ch;
+      for (int ti = 0; ti < (int)tl.size(); ++ti) {
+        if (ch.empty() || ch.back()[2] != tl[ti].sys || ch.back()[1] == CH ||
+            ch.back()[0] + ch.back()[1] != ti)
+          ch.push_back({ti, 0, tl[ti].sys});
+        ch.back()[1]++;
+      }
+      std::stable_sort(ch.begin(), ch.end(),
+                       [](const std::array<int32_t, 3>& a, const std::array<int32_t, 3>& b) {
+                         return a[2] < b[2];
+                       });
+      ChunkList& cl = p->chunk_lists[li];
+      cl.n = (int)ch.size();
+      cl.off_chunks = data.size();
+      for (auto& c : ch) data.insert(data.end(), c.begin(), c.end());
+      cl.off_begin = data.size();
+      size_t ci = 0;
+      for (int sidx = 0; sidx <= p->d.nsys; ++sidx) {
+        while (ci < ch.size() && ch[ci][2] < sidx) ++ci;
+        data.push_back((int32_t)ci);
+      }
+      p->max_chunks = std::max(p->max_chunks, cl.n);
+    }
+    CK(cudaMalloc(&p->d_chunk_data, data.size() * sizeof(int32_t)), "alloc chunks");
+    CK(cudaMemcpy(p->d_chunk_data, data.data(), data.size() * sizeof(int32_t),
+                  cudaMemcpyHostToDevice),
+       "upload chunks");
+  }
   p->have_batch = true;
   p->batch_id++;
   return CASCADE_OK;
@@ -680,9 +893,23 @@ cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y
   return run_forward(p, d_u, d_y, d_workspace, st);
 }
 
-cascade_status_t cascade_backward(cascade_plan_t plan, const void*, void*, double*, double*,
-                                  double*, double*, double*, double*, void*, size_t, void*) {
-  return fail(plan, CASCADE_ERR_UNSUPPORTED, "backward not available in this build");
+cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_u, const void* d_dy,
+                                  void* d_du, double* d_dAbar, double* d_dBbar, double* d_dC,
+                                  double* d_dD, double* d_dA, double* d_dB, void* d_workspace,
+                                  size_t workspace_bytes, void* stream) {
+  Plan* p = plan;
+  if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
+  if (!saves_states(*p))
+    return fail(p, CASCADE_ERR_STATE, "backward needs a plan created with CASCADE_FLAG_SAVE_STATES");
+  if (!p->have_system || !p->have_batch) return fail(p, CASCADE_ERR_STATE, "system and batch must be set");
+  if (p->rows == 0) return CASCADE_OK;
+  if (!d_u || !d_dy || !d_workspace) return fail(p, CASCADE_ERR_INVALID_ARG, "u, dy, workspace required");
+  if (p->saved_ws != d_workspace || p->saved_batch != p->batch_id)
+    return fail(p, CASCADE_ERR_STATE, "run cascade_forward on this batch and workspace first");
+  if (workspace_bytes < layout(*p).total) return fail(p, CASCADE_ERR_INVALID_ARG, "workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  p->last_stream = stream;
+  return run_backward(p, d_u, d_dy, d_du, d_dAbar, d_dBbar, d_dC, d_dD, d_dA, d_dB, d_workspace, st);
 }
 
 cascade_status_t cascade_recursion_forward(cascade_plan_t plan, const double* d_u, double* d_y,

@@ -1,0 +1,305 @@
+// backward.cu -- kernels of the reverse-mode derivative of the cascade.
+//
+// Forward (§3): v^(0)_l = Bbar u_l; v^(k+1)_l = v^(k)_l + P_k v^(k)_(l-s_k)
+// (s_k = 2^k, zero source before the sequence start); y_l = C v^(N+1)_l + D u_l;
+// P_0 = Abar, P_(k+1) = P_k P_k.  With G = dL/dy the adjoint runs the stages
+// backwards with the transposed powers and the reversed shift:
+//
+//   W^(N+1)_l = C^T G_l,
+//   W^(k)_l   = W^(k+1)_l + P_k^T W^(k+1)_(l+s_k)      (zero source past the end),
+//   dP_k      = sum_l W^(k+1)_l v^(k)_(l-s_k)^T,
+//   dC = sum_l G_l v^(N+1)_l^T,  dD = sum_l G_l u_l^T.
+//
+// The first stage is fused with the input projection in the forward
+// (v^(1)_l = Bbar u_l + Abar Bbar u_(l-1)), so its adjoint is fused too:
+//
+//   du_l   = Bbar^T W^(1)_l + (Abar Bbar)^T W^(1)_(l+1) + D^T G_l,
+//   R1     = sum_l W^(1)_l u_l^T,   R2 = sum_l W^(1)_l u_(l-1)^T,
+//   dBbar  = R1 + Abar^T R2,        dP_0 += R2 Bbar^T.
+//
+// This file holds the element-wise and reduction kernels; the adjoint stages
+// themselves reuse the forward stage kernels in reverse mode, and the
+// squaring-chain and discretisation adjoints are FP64 GEMMs (api.cu).
+//
+// Reductions over time are split-K: each block sums one chunk of tiles of one
+// system into a partial, and a second kernel adds the partials of each system
+// in chunk order in FP64, so results are deterministic.
+#include "common.cuh"
+#include "formats.cuh"
+
+namespace cascade {
+namespace {
+
+template <int FMT>
+__device__ __forceinline__ double src_get(const TSrc& s, const Tile& t, int64_t row, int col,
+                                          int m) {
+  if (s.kind == 1) return (double)static_cast<const float*>(s.dense)[row * s.ld + col];
+  if (s.kind == 2) return static_cast<const double*>(s.dense)[row * s.ld + col];
+  const int b = s.buf_mode ? t.flags : s.buf_fixed;
+  return Store<FMT>::get(s.bufs.hi(b), s.bufs.lo(b), row * m + col);
+}
+
+// partial[chunk][i][j] = sum over the chunk's rows l (l >= shift) of X[l][i] Y[l - shift][j].
+// Block = one 64 x 64 output block of one chunk; 256 threads, 4 x 4 outputs each.
+template <int FMT, typename ACC>
+__global__ void __launch_bounds__(256) treduce_kernel(const Tile* __restrict__ tiles,
+                                                      const int32_t* __restrict__ chunks, int BM,
+                                                      int m, TSrc X, int a, TSrc Y, int b, int shift,
+                                                      ACC* __restrict__ partial) {
+  __shared__ ACC xs[16][65];
+  __shared__ ACC ys[16][65];
+  const int c = blockIdx.z;
+  const int first = chunks[3 * c], count = chunks[3 * c + 1];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  ACC acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int ti = first; ti < first + count; ++ti) {
+    const Tile t = tiles[ti];
+    const int rows = min(BM, t.len - t.t0);
+    for (int r0 = 0; r0 < rows; r0 += 16) {
+      for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+        const int rr = e >> 6, col = e & 63;
+        const int l = t.t0 + r0 + rr;
+        const bool ok = (r0 + rr < rows) && l >= shift;
+        const int64_t row = t.seq_row0 + l;
+        xs[rr][col] = (ok && i0 + col < a) ? (ACC)src_get<FMT>(X, t, row, i0 + col, m) : (ACC)0;
+        ys[rr][col] = (ok && j0 + col < b) ? (ACC)src_get<FMT>(Y, t, row - shift, j0 + col, m)
+                                           : (ACC)0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) {
+        ACC xv[4], yv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xv[i] = xs[rr][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) yv[j] = ys[rr][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], yv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  ACC* out = partial + (int64_t)c * a * b;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = i0 + ty + 16 * i;
+    if (gi >= a) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = j0 + tx + 16 * j;
+      if (gj < b) out[(int64_t)gi * b + gj] = acc[i][j];
+    }
+  }
+}
+
+// out[s][e] (+)= sum over the chunks of system s, in order, of partial[chunk][e].
+template <typename ACC>
+__global__ void reduce_partials_kernel(const ACC* __restrict__ partial,
+                                       const int32_t* __restrict__ sys_begin, int64_t elems,
+                                       double* __restrict__ out, int64_t out_sys_stride,
+                                       int accumulate) {
+  const int s = blockIdx.y;
+  const int c0 = sys_begin[s], c1 = sys_begin[s + 1];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < elems;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int c = c0; c < c1; ++c) v += (double)partial[(int64_t)c * elems + e];
+    double* o = out + (int64_t)s * out_sys_stride + e;
+    *o = accumulate ? *o + v : v;
+  }
+}
+
+// W^(N+1)_l = C^T G_l into buffer (N_i + 1) & 1 (tile.flags = N_i); thread per (row, column).
+template <int FMT, typename T>
+__global__ void __launch_bounds__(256) adj_init_kernel(const Tile* __restrict__ tiles, int BM,
+                                                       int m, int q, const T* __restrict__ G,
+                                                       const T* __restrict__ C, Bufs W) {
+  const Tile t = tiles[blockIdx.x];
+  const int rows = min(BM, t.len - t.t0);
+  const int b = (t.flags + 1) & 1;
+  void* hi = W.hi(b);
+  void* lo = W.lo(b);
+  const T* Cs = C + (int64_t)t.sys * q * m;
+  for (int idx = threadIdx.x; idx < rows * m; idx += blockDim.x) {
+    const int r = idx / m, col = idx % m;
+    const int64_t row = t.seq_row0 + t.t0 + r;
+    double acc = 0.0;
+    for (int j = 0; j < q; ++j) acc = fma((double)Cs[(int64_t)j * m + col], (double)G[row * q + j], acc);
+    Store<FMT>::put(hi, lo, row * m + col, acc);
+  }
+}
+
+// du_l = Bbar^T W_l + (Abar Bbar)^T W_(l+1) + D^T G_l; one warp per row.
+template <int FMT, typename T>
+__global__ void __launch_bounds__(256) stage0_adj_kernel(const Tile* __restrict__ tiles, int BM,
+                                                         int m, int p, int q,
+                                                         const T* __restrict__ G,
+                                                         const T* __restrict__ Bbar,
+                                                         const T* __restrict__ ABbar,
+                                                         const T* __restrict__ D, Bufs W, int wbuf,
+                                                         T* __restrict__ du) {
+  const Tile t = tiles[blockIdx.x];
+  const int rows = min(BM, t.len - t.t0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const void* wh = W.hi(wbuf);
+  const void* wl = W.lo(wbuf);
+  const T* Bs = Bbar + (int64_t)t.sys * m * p;
+  const T* ABs = ABbar + (int64_t)t.sys * m * p;
+  const T* Ds = D + (int64_t)t.sys * q * p;
+  for (int r = warp; r < rows; r += nw) {
+    const int l = t.t0 + r;
+    const int64_t row = t.seq_row0 + l;
+    const bool next = l + 1 < t.len;
+    for (int j = 0; j < p; ++j) {
+      double s = 0.0;
+      for (int c = lane; c < m; c += 32) {
+        s = fma((double)Bs[(int64_t)c * p + j], Store<FMT>::get(wh, wl, row * m + c), s);
+        if (next) s = fma((double)ABs[(int64_t)c * p + j], Store<FMT>::get(wh, wl, (row + 1) * m + c), s);
+      }
+      for (int c = lane; c < q; c += 32) s = fma((double)Ds[(int64_t)c * p + j], (double)G[row * q + c], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) du[row * p + j] = (T)s;
+    }
+  }
+}
+
+// Batched transpose: out[b][j][i] = in[b][i][j] for n x n matrices.
+__global__ void transpose_kernel(const double* __restrict__ in, double* __restrict__ out, int n,
+                                 int64_t stride) {
+  __shared__ double tile[32][33];
+  const double* src = in + (int64_t)blockIdx.z * stride;
+  double* dst = out + (int64_t)blockIdx.z * stride;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int i = y0 + yy, j = x0 + threadIdx.x;
+    if (i < n && j < n) tile[yy][threadIdx.x] = src[(int64_t)i * n + j];
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int j = x0 + yy, i = y0 + threadIdx.x;
+    if (i < n && j < n) dst[(int64_t)j * n + i] = tile[threadIdx.x][yy];
+  }
+}
+
+// y[s][e] = (accumulate ? y[s][e] : 0) + factor * scal[s] * x[s][e]   (scal may be null: 1)
+__global__ void axpy_sys_kernel(const double* __restrict__ x, int64_t x_stride,
+                                double* __restrict__ y, int64_t y_stride, int64_t n,
+                                const double* __restrict__ scal, double factor, int accumulate) {
+  const int s = blockIdx.y;
+  const double a = factor * (scal ? scal[s] : 1.0);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a * x[(int64_t)s * x_stride + e];
+    double* o = y + (int64_t)s * y_stride + e;
+    *o = accumulate ? *o + v : v;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
+                           const int32_t* sys_begin, const TSrc& X, int a, const TSrc& Y, int b,
+                           int shift, void* partial, double* out, int64_t out_sys_stride,
+                           int accumulate, cudaStream_t st) {
+  if (nchunks == 0) return cudaSuccess;
+  const int BM = tile_rows(p);
+  const TSrc xs = X, ys = Y;
+  dim3 grid((b + 63) / 64, (a + 63) / 64, nchunks);
+  const int64_t elems = (int64_t)a * b;
+  const int rblocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
+  if (p.d.precision == CASCADE_FP64) {
+    treduce_kernel<FMT_F64, double><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
+                                                         shift, (double*)partial);
+    CASCADE_LAUNCHED();
+    reduce_partials_kernel<double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+        (const double*)partial, sys_begin, elems, out, out_sys_stride, accumulate);
+  } else {
+    if (p.d.precision == CASCADE_BF16_SPLIT)
+      treduce_kernel<FMT_BF16, float><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
+                                                           shift, (float*)partial);
+    else
+      treduce_kernel<FMT_F32, float><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
+                                                          shift, (float*)partial);
+    CASCADE_LAUNCHED();
+    reduce_partials_kernel<float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+        (const float*)partial, sys_begin, elems, out, out_sys_stride, accumulate);
+  }
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(const Plan& p, const void* G, const Bufs& W, cudaStream_t st) {
+  const int n = p.n_all_tiles;
+  if (n == 0) return cudaSuccess;
+  const int BM = tile_rows(p);
+  switch (p.d.precision) {
+    case CASCADE_FP64:
+      adj_init_kernel<FMT_F64, double><<<n, 256, 0, st>>>(p.d_all_tiles, BM, p.d.m, p.d.q,
+                                                          (const double*)G, p.C64, W);
+      break;
+    case CASCADE_BF16_SPLIT:
+      adj_init_kernel<FMT_BF16, float><<<n, 256, 0, st>>>(p.d_all_tiles, BM, p.d.m, p.d.q,
+                                                          (const float*)G, p.C32, W);
+      break;
+    default:
+      adj_init_kernel<FMT_F32, float><<<n, 256, 0, st>>>(p.d_all_tiles, BM, p.d.m, p.d.q,
+                                                         (const float*)G, p.C32, W);
+  }
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage0_adj(const Plan& p, const void* G, const Bufs& W, int wbuf, void* du,
+                              cudaStream_t st) {
+  const int n = p.n_all_tiles;
+  if (n == 0) return cudaSuccess;
+  const int BM = tile_rows(p);
+  switch (p.d.precision) {
+    case CASCADE_FP64:
+      stage0_adj_kernel<FMT_F64, double><<<n, 256, 0, st>>>(
+          p.d_all_tiles, BM, p.d.m, p.d.p, p.d.q, (const double*)G, p.Bbar64, p.ABbar64, p.D64,
+          W, wbuf, (double*)du);
+      break;
+    case CASCADE_BF16_SPLIT:
+      stage0_adj_kernel<FMT_BF16, float><<<n, 256, 0, st>>>(
+          p.d_all_tiles, BM, p.d.m, p.d.p, p.d.q, (const float*)G, p.Bbar32, p.ABbar32, p.D32, W,
+          wbuf, (float*)du);
+      break;
+    default:
+      stage0_adj_kernel<FMT_F32, float><<<n, 256, 0, st>>>(
+          p.d_all_tiles, BM, p.d.m, p.d.p, p.d.q, (const float*)G, p.Bbar32, p.ABbar32, p.D32, W,
+          wbuf, (float*)du);
+  }
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const double* in, double* out, int n, int64_t stride, int batch,
+                             cudaStream_t st) {
+  if (batch <= 0 || n <= 0) return cudaSuccess;
+  dim3 grid((n + 31) / 32, (n + 31) / 32, batch);
+  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(in, out, n, stride);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_sys(const double* x, int64_t x_stride, double* y, int64_t y_stride,
+                            int64_t n, int nsys, const double* scal, double factor,
+                            bool accumulate, cudaStream_t st) {
+  if (n <= 0 || nsys <= 0) return cudaSuccess;
+  const int blocks = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  axpy_sys_kernel<<<dim3(blocks, nsys), 256, 0, st>>>(x, x_stride, y, y_stride, n, scal, factor,
+                                                      accumulate ? 1 : 0);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+}  // namespace cascade

@@ -52,6 +52,7 @@ struct StageArgs {
   int32_t stages;         // SMEM pipeline depth
   int32_t ring;           // residual staging slots of the epilogue
   int32_t shift;          // 2^k
+  int32_t reverse;        // 1: adjoint stage (source l + s, transposed power)
   int32_t k;              // stage index
   int32_t kmax1;          // power-table entries per system
   const void* vin_hi;     // residual planes (row-major [rows, m])
@@ -76,6 +77,13 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 #endif
 
+// Time-reduction chunk list (backward): offsets into Plan::d_chunk_data.
+struct ChunkList {
+  int n = 0;
+  size_t off_chunks = 0;
+  size_t off_begin = 0;
+};
+
 // ------------------------------------------------------------- plan (host)
 struct Plan {
   cascade_desc_t d;
@@ -89,6 +97,10 @@ struct Plan {
   double* P64 = nullptr;         // [nsys, kmax1, m, m]
   void* Phi = nullptr;           // operand planes [nsys, kmax1, m, m] (bf16 or fp32)
   void* Plo = nullptr;
+  void* PThi = nullptr;          // transposed powers (adjoint stages), same format
+  void* PTlo = nullptr;
+  double* PT64 = nullptr;        // transposed FP64 powers (FP64 adjoint stages)
+  double* Minv64 = nullptr;      // (I - delta/2 A)^-1 per system (discretisation adjoint)
   double* Bbar64 = nullptr;      // [nsys, m, p]
   double* ABbar64 = nullptr;     // [nsys, m, p]   Abar * Bbar (first stage fused with Bbar u)
   double* C64 = nullptr;         // [nsys, q, m]
@@ -114,6 +126,17 @@ struct Plan {
   std::vector<std::vector<Tile>> h_tiles;   // per stage k = 1..maxN
   std::vector<Tile*> d_tiles;                // device copies
   std::vector<int32_t> n_tiles;
+  std::vector<std::vector<Tile>> h_adj_tiles;   // adjoint stage k = 1..maxN (all tiles)
+  std::vector<Tile*> d_adj_tiles;
+  std::vector<int32_t> n_adj_tiles;
+  Tile* d_all_tiles = nullptr;               // every tile of every sequence (flags = N_i)
+  int n_all_tiles = 0;
+  std::vector<ChunkList> chunk_lists;        // [0]: every tile; [k]: tiles of stage k
+  int32_t* d_chunk_data = nullptr;           // chunks [n][3] (first tile, count, system) and
+                                             // per-system chunk ranges [nsys + 1] of each list
+  int max_chunks = 0;
+  const void* saved_ws = nullptr;            // workspace of the last forward that kept states
+  int64_t saved_batch = -1;
   Seq* d_seqs = nullptr;                     // all sequences
   int n_out_tiles = 0;                       // tiles of sequences whose output is not fused
   Tile* d_out_tiles = nullptr;               // (flags = workspace buffer of the final states)
@@ -148,8 +171,8 @@ size_t state_bytes_per_row(const Plan& p);    // bytes of one state row (all pla
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_discretise(const double* A, const double* B, const double* delta,
                               const double* scale, double* Abar_out, int64_t abar_sys_stride,
-                              double* Bbar_out, double* work, int nsys, int m, int p,
-                              int32_t* singular, cudaStream_t st);
+                              double* Bbar_out, double* Minv_out, double* work, int nsys, int m,
+                              int p, int32_t* singular, cudaStream_t st);
 cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
                          int lda, int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC,
                          int batch, double alpha, double beta, bool transA, bool transB,
@@ -163,12 +186,43 @@ cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t
 cudaError_t launch_stage0(const Plan& p, const void* u, void* out_hi, void* out_lo,
                           cudaStream_t st);
 cudaError_t launch_stage_f64(const Plan& p, int k, const double* vin, double* vout,
-                             cudaStream_t st);
+                             cudaStream_t st, bool reverse = false);
 cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
                             void* vout_hi, void* vout_lo, const float* u, float* y,
-                            cudaStream_t st);
-cudaError_t launch_output(const Plan& p, const void* u, void* y, void* const* ws_planes_hi,
-                          void* const* ws_planes_lo, cudaStream_t st);
+                            cudaStream_t st, bool reverse = false);
+// Workspace buffer j of a family of equally sized state buffers.
+struct Bufs {
+  uint8_t* base;
+  size_t stride;      // bytes between buffers
+  size_t lo_off;      // bytes from a buffer's hi plane to its lo plane (0: single plane)
+  __host__ __device__ void* hi(int j) const { return base + (size_t)j * stride; }
+  __host__ __device__ void* lo(int j) const {
+    return lo_off ? base + (size_t)j * stride + lo_off : nullptr;
+  }
+};
+cudaError_t launch_output(const Plan& p, const void* u, void* y, const Bufs& V, cudaStream_t st);
+
+// Row-indexed operand of a time reduction (backward.cu).
+struct TSrc {
+  int kind;          // 0: workspace state buffer, 1: dense float [rows, ld], 2: dense double
+  Bufs bufs;         // kind 0
+  int buf_mode;      // 0: buffer buf_fixed; 1: buffer = tile.flags
+  int buf_fixed;
+  const void* dense; // kinds 1, 2
+  int ld;
+};
+cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
+                           const int32_t* sys_begin, const TSrc& X, int a, const TSrc& Y, int b,
+                           int shift, void* partial, double* out, int64_t out_sys_stride,
+                           int accumulate, cudaStream_t st);
+cudaError_t launch_adj_init(const Plan& p, const void* G, const Bufs& W, cudaStream_t st);
+cudaError_t launch_stage0_adj(const Plan& p, const void* G, const Bufs& W, int wbuf, void* du,
+                              cudaStream_t st);
+cudaError_t launch_transpose(const double* in, double* out, int n, int64_t stride, int batch,
+                             cudaStream_t st);
+cudaError_t launch_axpy_sys(const double* x, int64_t x_stride, double* y, int64_t y_stride,
+                            int64_t n, int nsys, const double* scal, double factor,
+                            bool accumulate, cudaStream_t st);
 cudaError_t launch_recursion_f64(const Plan& p, const double* u, double* y, cudaStream_t st);
 cudaError_t launch_selftest_timeout(int32_t limit_us, int32_t* err, cudaStream_t st);
 

@@ -11,14 +11,15 @@ namespace cascade {
 
 // ----------------------------------------------------------------------------
 // Discretisation: one thread block per system solves
-//   (I - delta/2 A) [Abar | Bbar] = [I + delta/2 A | delta B]
+//   (I - delta/2 A) [Abar | Bbar | M^-1] = [I + delta/2 A | delta B | I]
 // by Gauss-Jordan elimination with partial pivoting, in FP64, on an augmented
-// m x (2m + p) matrix held in global memory.
+// m x (3m + p) matrix held in global memory (M^-1 feeds the adjoint).
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) discretise_kernel(
     const double* __restrict__ A, const double* __restrict__ B, const double* __restrict__ delta,
     const double* __restrict__ scale, double* __restrict__ Abar, int64_t abar_stride,
-    double* __restrict__ Bbar, double* __restrict__ work, int m, int p, int32_t* singular) {
+    double* __restrict__ Bbar, double* __restrict__ Minv, double* __restrict__ work, int m, int p,
+    int32_t* singular) {
   extern __shared__ double fac[];          // m elimination factors
   __shared__ double red_v[32];
   __shared__ int red_i[32];
@@ -26,7 +27,7 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
   __shared__ double s_inv;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int W = 2 * m + p;
+  const int W = 3 * m + p;
   const double dl = delta[s];
   const double h = 0.5 * dl;
   const double* As = A + (int64_t)s * m * m;
@@ -38,7 +39,8 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
     double v;
     if (j < m) v = (i == j ? 1.0 : 0.0) - h * As[(int64_t)i * m + j];
     else if (j < 2 * m) v = (i == j - m ? 1.0 : 0.0) + h * As[(int64_t)i * m + (j - m)];
-    else v = dl * Bs[(int64_t)i * p + (j - 2 * m)];
+    else if (j < 2 * m + p) v = dl * Bs[(int64_t)i * p + (j - 2 * m)];
+    else v = (i == j - 2 * m - p) ? 1.0 : 0.0;
     T[idx] = v;
   }
   __syncthreads();
@@ -105,12 +107,19 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
     const int i = (int)(idx / p), j = (int)(idx % p);
     Bb[idx] = T[(int64_t)i * W + 2 * m + j];
   }
+  if (Minv) {
+    double* Mi = Minv + (int64_t)s * m * m;
+    for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
+      const int i = (int)(idx / m), j = (int)(idx % m);
+      Mi[idx] = T[(int64_t)i * W + 2 * m + p + j];
+    }
+  }
 }
 
 cudaError_t launch_discretise(const double* A, const double* B, const double* delta,
                               const double* scale, double* Abar_out, int64_t abar_sys_stride,
-                              double* Bbar_out, double* work, int nsys, int m, int p,
-                              int32_t* singular, cudaStream_t st) {
+                              double* Bbar_out, double* Minv_out, double* work, int nsys, int m,
+                              int p, int32_t* singular, cudaStream_t st) {
   const size_t smem = sizeof(double) * (size_t)m;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(discretise_kernel,
@@ -118,7 +127,7 @@ cudaError_t launch_discretise(const double* A, const double* B, const double* de
     if (e != cudaSuccess) return e;
   }
   discretise_kernel<<<nsys, 1024, smem, st>>>(A, B, delta, scale, Abar_out, abar_sys_stride,
-                                               Bbar_out, work, m, p, singular);
+                                               Bbar_out, Minv_out, work, m, p, singular);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }

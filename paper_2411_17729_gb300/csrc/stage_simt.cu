@@ -10,50 +10,11 @@
 //     replaces;
 //   * a bounded-wait self-test.
 #include "common.cuh"
+#include "formats.cuh"
 #include "ptx.cuh"
 
 namespace cascade {
 namespace {
-
-// Storage formats of a state row.
-enum { FMT_F64 = 0, FMT_BF16 = 2, FMT_F32 = 4 };
-
-template <int FMT>
-struct Store;
-template <>
-struct Store<FMT_F64> {
-  static __device__ __forceinline__ void put(void* hi, void*, int64_t i, double v) {
-    static_cast<double*>(hi)[i] = v;
-  }
-  static __device__ __forceinline__ double get(const void* hi, const void*, int64_t i) {
-    return static_cast<const double*>(hi)[i];
-  }
-};
-template <>
-struct Store<FMT_BF16> {
-  static __device__ __forceinline__ void put(void* hi, void* lo, int64_t i, double v) {
-    const float x = (float)v;
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    static_cast<__nv_bfloat16*>(hi)[i] = h;
-    static_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn(x - __bfloat162float(h));
-  }
-  static __device__ __forceinline__ double get(const void* hi, const void* lo, int64_t i) {
-    return (double)(__bfloat162float(static_cast<const __nv_bfloat16*>(hi)[i]) +
-                    __bfloat162float(static_cast<const __nv_bfloat16*>(lo)[i]));
-  }
-};
-template <>
-struct Store<FMT_F32> {
-  static __device__ __forceinline__ void put(void* hi, void* lo, int64_t i, double v) {
-    const float x = (float)v;
-    const float h = ptx::tf32_rna(x);
-    static_cast<float*>(hi)[i] = h;
-    static_cast<float*>(lo)[i] = ptx::tf32_rna(x - h);
-  }
-  static __device__ __forceinline__ double get(const void* hi, const void* lo, int64_t i) {
-    return (double)(static_cast<const float*>(hi)[i] + static_cast<const float*>(lo)[i]);
-  }
-};
 
 // ---------------------------------------------------------------- first stage
 // One block per tile of BM rows; thread items (row, column) with the column
@@ -146,7 +107,8 @@ __global__ void __launch_bounds__(256) stage0_vec_kernel(const Tile* __restrict_
 // ---------------------------------------------------------------- FP64 stage
 // Block: 64 rows x 64 state columns of one tile, 256 threads, 4x4 outputs each.
 __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__ tiles, int m,
-                                                        int shift, const double* __restrict__ P,
+                                                        int shift, int reverse,
+                                                        const double* __restrict__ P,
                                                         int64_t p_sys_stride,
                                                         const double* __restrict__ vin,
                                                         double* __restrict__ vout) {
@@ -157,7 +119,8 @@ __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__
   const int n0 = blockIdx.y * 64;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const double* Ps = P + (int64_t)t.sys * p_sys_stride;
-  const bool copy = t.t0 + BMF <= shift;
+  // adjoint stages (reverse): source l + s and the transposed power
+  const bool copy = reverse ? (t.t0 + shift >= t.len) : (t.t0 + BMF <= shift);
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -167,10 +130,11 @@ __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__
     for (int k0 = 0; k0 < m; k0 += 16) {
       for (int e = threadIdx.x; e < 1024; e += 256) {
         const int kk = e & 15, rr = e >> 4;
-        const int l = t.t0 + rr - shift;           // source time step
+        const int l = t.t0 + rr + (reverse ? shift : -shift);   // source time step
         const int gk = k0 + kk;
         double v = 0.0;
-        if (l >= 0 && t.t0 + rr < t.len && gk < m) v = vin[(t.seq_row0 + l) * (int64_t)m + gk];
+        if (l >= 0 && l < t.len && t.t0 + rr < t.len && gk < m)
+          v = vin[(t.seq_row0 + l) * (int64_t)m + gk];
         As[kk][rr] = v;
       }
       for (int e = threadIdx.x; e < 1024; e += 256) {
@@ -215,12 +179,10 @@ template <int FMT, typename T>
 __global__ void __launch_bounds__(256) output_kernel(const Tile* __restrict__ tiles, int BM, int m,
                                                      int p, int q, const T* __restrict__ u,
                                                      T* __restrict__ y, const T* __restrict__ C,
-                                                     const T* __restrict__ D, const void* b0_hi,
-                                                     const void* b0_lo, const void* b1_hi,
-                                                     const void* b1_lo) {
+                                                     const T* __restrict__ D, Bufs V) {
   const Tile t = tiles[blockIdx.x];
-  const void* vh = (t.flags & 1) ? b1_hi : b0_hi;
-  const void* vl = (t.flags & 1) ? b1_lo : b0_lo;
+  const void* vh = V.hi(t.flags);
+  const void* vl = V.lo(t.flags);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int rows = min(BM, t.len - t.t0);
   const T* Cs = C + (int64_t)t.sys * q * m;
@@ -345,19 +307,19 @@ cudaError_t launch_stage0(const Plan& p, const void* u, void* out_hi, void* out_
 }
 
 cudaError_t launch_stage_f64(const Plan& p, int k, const double* vin, double* vout,
-                             cudaStream_t st) {
-  const int n = p.n_tiles[k];
+                             cudaStream_t st, bool reverse) {
+  const int n = reverse ? p.n_adj_tiles[k] : p.n_tiles[k];
   if (n == 0) return cudaSuccess;
   dim3 grid(n, (p.d.m + 63) / 64);
-  stage_f64_kernel<<<grid, 256, 0, st>>>(p.d_tiles[k], p.d.m, 1 << k,
-                                         p.P64 + (int64_t)k * p.d.m * p.d.m,
+  stage_f64_kernel<<<grid, 256, 0, st>>>(reverse ? p.d_adj_tiles[k] : p.d_tiles[k], p.d.m, 1 << k,
+                                         reverse ? 1 : 0,
+                                         (reverse ? p.PT64 : p.P64) + (int64_t)k * p.d.m * p.d.m,
                                          (int64_t)p.kmax1 * p.d.m * p.d.m, vin, vout);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }
 
-cudaError_t launch_output(const Plan& p, const void* u, void* y, void* const* hi,
-                          void* const* lo, cudaStream_t st) {
+cudaError_t launch_output(const Plan& p, const void* u, void* y, const Bufs& V, cudaStream_t st) {
   const int n = p.n_out_tiles;
   if (n == 0) return cudaSuccess;
   const int BM = tile_rows(p);
@@ -366,17 +328,17 @@ cudaError_t launch_output(const Plan& p, const void* u, void* y, void* const* hi
     case CASCADE_FP64:
       output_kernel<FMT_F64, double><<<n, 256, 0, st>>>(tiles, BM, p.d.m, p.d.p, p.d.q,
                                                         (const double*)u, (double*)y, p.C64,
-                                                        p.D64, hi[0], lo[0], hi[1], lo[1]);
+                                                        p.D64, V);
       break;
     case CASCADE_BF16_SPLIT:
       output_kernel<FMT_BF16, float><<<n, 256, 0, st>>>(tiles, BM, p.d.m, p.d.p, p.d.q,
                                                         (const float*)u, (float*)y, p.C32, p.D32,
-                                                        hi[0], lo[0], hi[1], lo[1]);
+                                                        V);
       break;
     default:
       output_kernel<FMT_F32, float><<<n, 256, 0, st>>>(tiles, BM, p.d.m, p.d.p, p.d.q,
                                                        (const float*)u, (float*)y, p.C32, p.D32,
-                                                       hi[0], lo[0], hi[1], lo[1]);
+                                                       V);
   }
   CASCADE_LAUNCHED();
   return cudaGetLastError();

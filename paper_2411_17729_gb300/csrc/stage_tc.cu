@@ -143,7 +143,9 @@ __device__ __forceinline__ Item load_item(const StageArgs& a, int w) {
   Item it;
   it.t = a.tiles[w / a.nblocks];
   it.n0 = (w % a.nblocks) * a.BN;
-  it.copy = it.t.t0 + BM <= a.shift;
+  // every source row lies outside the sequence: before its start (forward
+  // stages) or past its end (adjoint stages, source l + s)
+  it.copy = a.reverse ? (it.t.t0 + a.shift >= it.t.len) : (it.t.t0 + BM <= a.shift);
   it.fused = (QMAX > 0) && (it.t.flags & TILE_FINAL_FUSED);
   it.ragged = it.t.t0 + BM > it.t.len;
   return it;
@@ -242,7 +244,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
         const Item it = load_item<QMAX>(args, w);
         if (it.copy) continue;                                   // no operands
-        const int src_row = (int)(it.t.seq_row0 + it.t.t0 - shift);   // may be < 0 (zero fill)
+        // source rows l - s (forward) or l + s (adjoint); may fall outside the
+        // tensor (zero fill) or in a neighbouring sequence (zeroed below)
+        const int src_row = (int)(it.t.seq_row0 + it.t.t0 + (args.reverse ? shift : -shift));
         const int prow = (it.t.sys * args.kmax1 + args.k) * m + it.n0;
         for (int c = 0; c < nkc; ++c) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, limit, abort_flag)) {
@@ -284,7 +288,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         break;
       }
       ptx::tc_fence_after();
-      const int zero_rows = shift - it.t.t0;       // rows whose source precedes the sequence
+      // tile rows [z0, z1) whose source lies outside the sequence read zero
+      const int z0 = args.reverse ? max(0, it.t.len - it.t.t0 - shift) : 0;
+      const int z1 = args.reverse ? BM : min(BM, shift - it.t.t0);
       const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * ACC);
       const uint32_t c_tmem = d_tmem + (SEP ? (uint32_t)BN : 0u);   // correction accumulator
       bool ok = true;
@@ -298,12 +304,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t* sa_lo = sa_hi + a_bytes;
         uint8_t* sb_hi = sa_lo + a_bytes;
         uint8_t* sb_lo = sb_hi + b_bytes;
-        if (zero_rows > 0) {
-          // rows r < zero_rows occupy bytes [0, zero_rows * 64) of each A buffer
+        if (z1 > z0) {
+          // row r occupies bytes [r * 64, r * 64 + 64) of each A buffer
           uint4* zh = reinterpret_cast<uint4*>(sa_hi);
           uint4* zl = reinterpret_cast<uint4*>(sa_lo);
           const uint4 z = make_uint4(0, 0, 0, 0);
-          for (int i = lane; i < zero_rows * 4; i += 32) { zh[i] = z; zl[i] = z; }
+          for (int i = z0 * 4 + lane; i < z1 * 4; i += 32) { zh[i] = z; zl[i] = z; }
           ptx::fence_proxy_async_smem();
           __syncwarp();
         }
@@ -614,8 +620,8 @@ TcConfig tc_default(int m, int precision) {
 
 cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
                             void* vout_hi, void* vout_lo, const float* u, float* y,
-                            cudaStream_t st) {
-  const int ntiles = p.n_tiles[k];
+                            cudaStream_t st, bool reverse) {
+  const int ntiles = reverse ? p.n_adj_tiles[k] : p.n_tiles[k];
   if (ntiles == 0) return cudaSuccess;
   const int m = p.d.m;
   const int elem = (int)plane_elem_bytes(p.d.precision);
@@ -629,15 +635,15 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   const uint64_t prow = (uint64_t)p.d.nsys * p.kmax1 * m;
   if (!encode_tmap_2d(&maps[0], vin_hi, elem, m, rows, row_elems, BM, &err, 64) ||
       !encode_tmap_2d(&maps[1], vin_lo, elem, m, rows, row_elems, BM, &err, 64) ||
-      !encode_tmap_2d(&maps[2], p.Phi, elem, m, prow, row_elems, BN, &err, 64) ||
-      !encode_tmap_2d(&maps[3], p.Plo, elem, m, prow, row_elems, BN, &err, 64) ||
+      !encode_tmap_2d(&maps[2], reverse ? p.PThi : p.Phi, elem, m, prow, row_elems, BN, &err, 64) ||
+      !encode_tmap_2d(&maps[3], reverse ? p.PTlo : p.Plo, elem, m, prow, row_elems, BN, &err, 64) ||
       !encode_tmap_2d(&maps[4], vout_hi, elem, m, rows, row_elems, BM, &err, 64) ||
       !encode_tmap_2d(&maps[5], vout_lo, elem, m, rows, row_elems, BM, &err, 64)) {
     set_global_error("tensor map encode failed: " + err);
     return cudaErrorInvalidValue;
   }
   StageArgs a{};
-  a.tiles = p.d_tiles[k];
+  a.tiles = reverse ? p.d_adj_tiles[k] : p.d_tiles[k];
   a.ntiles = ntiles;
   a.nblocks = m / BN;
   a.m = m;
@@ -647,6 +653,7 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   a.stages = cfg.stages;
   a.ring = cfg.ring;
   a.shift = 1 << k;
+  a.reverse = reverse ? 1 : 0;
   a.k = k;
   a.kmax1 = p.kmax1;
   a.vin_hi = vin_hi;

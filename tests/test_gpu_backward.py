@@ -1,0 +1,170 @@
+"""GPU parity of the reverse-mode derivative (through the C ABI) against the
+CPU FP64 oracle's adjoint, plus central finite differences through the GPU's
+own FP64 forward.  Bars: relative Frobenius error per gradient tensor, 1e-10
+for the FP64 path, 1e-5 for FP32, 2e-3 for the BF16 split."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from _parity import cast_inputs
+
+pytestmark = pytest.mark.gpu
+
+GTOL = {"fp64": 1e-10, "fp32": 1e-5, "bf16_split": 2e-3}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_17729_gb300 import build
+    build()
+    from paper_2411_17729_gb300 import cascade
+    return cascade
+
+
+def gpu_grads(lib, w, precision, dy):
+    import torch
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SAVE_STATES
+    c = lib.from_workload(w, precision=precision, flags=CASCADE_FLAG_SAVE_STATES)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    u = torch.as_tensor(w.u, dtype=dt).cuda().contiguous()
+    y = c.forward(u)
+    g = c.backward(u, torch.as_tensor(dy, dtype=dt).cuda().contiguous())
+    torch.cuda.synchronize()
+    assert c.device_error() == 0, c.lib.cascade_last_error(c.plan)
+    return c, y.double().cpu().numpy(), {k: v.double().cpu().numpy() for k, v in g.items()}
+
+
+def compare(w, c, g, dy, tol):
+    ref = oracle.cascade_backward(w, dy, N_per_seq=c.seq_N())
+    worst = {}
+    for k, v in g.items():
+        r = ref[k]
+        nr = np.linalg.norm(r)
+        err = np.linalg.norm(v - r) / nr if nr > 0 else np.linalg.norm(v)
+        worst[k] = err
+    bad = {k: e for k, e in worst.items() if not e <= tol}
+    assert not bad, (bad, worst)
+    return worst
+
+
+@pytest.mark.parametrize("discrete", [True, False])
+def test_fp64_backward_matches_oracle(lib, discrete):
+    w = wl.small_system(m=9, p=2, q=3, lengths=(20, 0, 37, 1, 70), N=6, nsys=2, seed=3,
+                        radius=0.97, discrete=discrete, delta=0.2, precision="fp64")
+    dy = np.random.default_rng(1).standard_normal((w.rows, w.q))
+    c, _, g = gpu_grads(lib, w, "fp64", dy)
+    compare(w, c, g, dy, GTOL["fp64"])
+
+
+def test_fp64_backward_truncated_and_growing(lib):
+    """N below log2 L and spectral radius above one."""
+    w = wl.small_system(m=7, p=3, q=2, lengths=(100, 41), N=3, seed=5, radius=1.03)
+    dy = np.random.default_rng(2).standard_normal((w.rows, w.q))
+    c, _, g = gpu_grads(lib, w, "fp64", dy)
+    compare(w, c, g, dy, GTOL["fp64"])
+
+
+def test_fp64_backward_finite_differences_on_gpu(lib):
+    """Directional derivatives of sum(dy * y) by central differences (h = 1e-6)
+    through the GPU's FP64 forward agree with the GPU backward."""
+    import torch
+    w = wl.small_system(m=6, p=2, q=2, lengths=(30, 17), N=4, seed=7, radius=0.95,
+                        discrete=False, delta=0.1, precision="fp64")
+    rng = np.random.default_rng(4)
+    dy = rng.standard_normal((w.rows, w.q))
+    c, _, g = gpu_grads(lib, w, "fp64", dy)
+    u = torch.as_tensor(w.u).cuda()
+
+    def loss(**over):
+        kw = dict(A=w.A, B=w.B, C=w.C, D=w.D)
+        kw.update(over)
+        c2 = lib.from_workload(w, precision="fp64")
+        c2.set_system_continuous(kw["A"], kw["B"], w.delta, kw["C"], kw["D"])
+        uu = torch.as_tensor(over.get("u", w.u)).cuda()
+        return float(np.sum(dy * c2.forward(uu).cpu().numpy()))
+
+    h = 1e-6
+    for name, X, grad in (("A", w.A, g["dA"]), ("B", w.B, g["dB"]), ("C", w.C, g["dC"]),
+                          ("D", w.D, g["dD"]), ("u", w.u, g["du"])):
+        E = rng.standard_normal(X.shape)
+        fd = (loss(**{name: X + h * E}) - loss(**{name: X - h * E})) / (2 * h)
+        an = float(np.sum(grad * E))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, fd, an)
+
+
+@pytest.mark.parametrize("precision,m", [("bf16_split", 128), ("fp32", 128), ("bf16_split", 256),
+                                         ("fp32", 64)])
+def test_tc_backward_matches_oracle(lib, precision, m):
+    """MIMO HiPPO system, ragged lengths, continuous (gradients to A and B)."""
+    w = wl.differentiation_form(m=m, p=4, q=4, L=8, batch=4, N=10, delta=1e-2)
+    lengths = (700, 129, 1, 300)
+    w.offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    w.u = np.random.default_rng(5).standard_normal((int(w.offsets[-1]), 4))
+    w = cast_inputs(w, precision)
+    dy = np.random.default_rng(6).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
+    c, _, g = gpu_grads(lib, w, precision, dy)
+    compare(w, c, g, dy, GTOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
+def test_tc_backward_discrete_multisystem(lib, precision):
+    """Discrete systems (orthogonal plus low rank), two systems, truncated N."""
+    w = wl.large_form(m=128, p=3, q=2, L=600, batch=3, N=6)
+    w.sys_of_seq = np.array([0, 1, 0], np.int32)
+    w.Abar = np.concatenate([w.Abar, 0.98 * w.Abar[:, ::-1, :]])
+    for k in ("B", "C", "D"):
+        setattr(w, k, np.concatenate([getattr(w, k), 0.5 * getattr(w, k)]))
+    w = cast_inputs(w, precision)
+    dy = np.random.default_rng(8).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
+    c, _, g = gpu_grads(lib, w, precision, dy)
+    compare(w, c, g, dy, GTOL[precision])
+
+
+def test_autograd_function(lib):
+    """torch.autograd through CascadeFunction gives the plan's gradients."""
+    import torch
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SAVE_STATES
+    w = wl.small_system(m=64, p=2, q=2, lengths=(300, 77), N=8, seed=9, radius=0.99,
+                        discrete=False, delta=0.05, precision="bf16_split")
+    w = cast_inputs(w, "bf16_split")
+    c = lib.from_workload(w, precision="bf16_split", flags=CASCADE_FLAG_SAVE_STATES)
+    dev = torch.device("cuda")
+    A = torch.tensor(w.A, device=dev, requires_grad=True)
+    B = torch.tensor(w.B, device=dev, requires_grad=True)
+    C = torch.tensor(w.C, device=dev, requires_grad=True)
+    D = torch.tensor(w.D, device=dev, requires_grad=True)
+    u = torch.tensor(w.u, dtype=torch.float32, device=dev, requires_grad=True)
+    delta = torch.tensor(w.delta, device=dev)
+    y = lib.CascadeFunction.apply(c, u, A, B, C, D, delta)
+    dy = torch.randn_like(y)
+    (y * dy).sum().backward()
+    dy_np = dy.double().cpu().numpy()
+    ref = oracle.cascade_backward(w, dy_np, N_per_seq=c.seq_N())
+    for t, k in ((A, "dA"), (B, "dB"), (C, "dC"), (D, "dD"), (u, "du")):
+        gt = t.grad.double().cpu().numpy()
+        assert np.linalg.norm(gt - ref[k]) <= 2e-3 * np.linalg.norm(ref[k]), k
+
+
+def test_backward_requires_saved_states(lib):
+    import torch
+    from paper_2411_17729_gb300._abi import CascadeError
+    w = wl.small_system(m=64, lengths=(100,), N=5, precision="bf16_split")
+    c = lib.from_workload(w, precision="bf16_split")
+    u = torch.zeros((w.rows, w.p), dtype=torch.float32, device="cuda")
+    c.forward(u)
+    with pytest.raises(CascadeError):
+        c.backward(u, torch.zeros((w.rows, w.q), dtype=torch.float32, device="cuda"))
+
+
+def test_differentiation_form_full_size(lib):
+    """m = 256, p = q = 16, 32 sequences x 8192 steps, N = 12, BF16 split,
+    gradients to u, A (through the squaring chain and Eq. 4.2), B, C, D
+    against the oracle's FP64 adjoint over the whole batch."""
+    w = cast_inputs(wl.differentiation_form(), "bf16_split")
+    dy = np.random.default_rng(10).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
+    c, _, g = gpu_grads(lib, w, "bf16_split", dy)
+    compare(w, c, g, dy, GTOL["bf16_split"])

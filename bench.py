@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 cascade comparator")
+    ap.add_argument("--no-bwd", action="store_true", help="skip the forward+backward measurement")
     ap.add_argument("--seqs", type=int, default=64,
                     help="sequences in the batch (64 = the benchmark; fewer only for profiler captures)")
     return ap.parse_args()
@@ -313,6 +314,45 @@ def main():
         e2e_ms = float(t.item())
     e2e_value = states_per_step * world / (e2e_ms / 1000.0)
 
+    # ---- forward + backward (plan that keeps its stage outputs), same workload
+    fb = None
+    if not args.no_bwd:
+        from paper_2411_17729_gb300._abi import CASCADE_FLAG_SAVE_STATES
+        c.close()
+        del ws
+        torch.cuda.empty_cache()
+        cb = cascade.from_workload(w, precision="bf16_split", flags=CASCADE_FLAG_SAVE_STATES,
+                                   device=dev)
+        cb.autotune(u, y, reps=1)
+        dy = torch.randn((w.rows, w.q), dtype=torch.float32, device=dev,
+                         generator=torch.Generator(device=dev).manual_seed(0))
+        for _ in range(2):
+            cb.forward(u, y)
+            cb.backward(u, dy)
+        fb_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                  torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            fb_ev[i][0].record(stream)
+            cb.forward(u, y)
+            fb_ev[i][1].record(stream)
+            cb.backward(u, dy)
+            fb_ev[i][2].record(stream)
+        torch.cuda.synchronize()
+        if cb.device_error() != 0:
+            raise RuntimeError("device wait timed out in the fwd+bwd region")
+        fb_ms = sum(a.elapsed_time(cc) for a, _, cc in fb_ev) / args.steps
+        bwd_ms = sum(b.elapsed_time(cc) for _, b, cc in fb_ev) / args.steps
+        if world > 1:
+            t = torch.tensor([fb_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            fb_ms = float(t.item())
+        fb = {"value": states_per_step * world / (fb_ms / 1000.0), "unit": "states/s",
+              "ms_per_step": fb_ms, "backward_ms": bwd_ms,
+              "gradients": "u, A (squaring chain + trapezoid), B, C, D"}
+        cb.close()
+
     # ---- FP64 plain cascade on the same GPU (comparator), on 8 sequences
     fp64 = None
     if not args.no_fp64:
@@ -362,13 +402,13 @@ def main():
                     "h2d_bytes_per_step": int(u.numel() * 4), "d2h_bytes_per_step": int(y.numel() * 4)},
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "fwd_bwd": fb,
             "fp64_cascade": fp64,
             "precompute_s": prep_s,
             "stage_ms": {str(k): statistics.median(v) for k, v in sorted(stage_ms.items())},
             "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
-    c.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -181,7 +181,7 @@ void free_batch(Plan* p) {
 void free_system(Plan* p) {
   void* ptrs[] = {p->P64, p->Phi, p->Plo, p->Bbar64, p->ABbar64, p->C64, p->D64, p->Bbar32,
                   p->ABbar32, p->C32, p->D32, p->A64, p->B64, p->delta64, p->scale64,
-                  p->PThi, p->PTlo, p->PT64, p->Minv64};
+                  p->PThi, p->PTlo, p->PT64, p->Minv64, p->P32, p->Minv32};
   for (void* q : ptrs) dfree(q);
   p->P64 = nullptr;
   p->Phi = p->Plo = nullptr;
@@ -190,6 +190,7 @@ void free_system(Plan* p) {
   p->A64 = p->B64 = p->delta64 = p->scale64 = nullptr;
   p->PThi = p->PTlo = nullptr;
   p->PT64 = p->Minv64 = nullptr;
+  p->P32 = p->Minv32 = nullptr;
 }
 
 // Squaring chain, accuracy rule, Abar*Bbar, operand planes; P64[:,0] and
@@ -242,6 +243,9 @@ cascade_status_t finish_system(Plan* p, cudaStream_t st) {
       CK(launch_split_planes(p->PT64, p->PThi, p->PTlo, (int64_t)ns * sys_stride, p->d.precision,
                              st),
          "transposed operand planes");
+    if (p->P32) CK(launch_to_f32(p->P64, p->P32, (int64_t)ns * sys_stride, st), "FP32 powers");
+    if (p->Minv32 && p->Minv64)
+      CK(launch_to_f32(p->Minv64, p->Minv32, (int64_t)ns * mm, st), "FP32 M^-1");
     CK(launch_to_f32(p->Bbar64, p->Bbar32, (int64_t)ns * m * pp, st), "Bbar f32");
     CK(launch_to_f32(p->ABbar64, p->ABbar32, (int64_t)ns * m * pp, st), "ABbar f32");
     CK(launch_to_f32(p->C64, p->C32, (int64_t)ns * q * m, st), "C f32");
@@ -272,6 +276,8 @@ cascade_status_t alloc_system(Plan* p) {
   if (saves_states(*p)) {   // the adjoint stages use the transposed powers
     CK(dalloc(&p->PT64, (size_t)ns * p->kmax1 * mm), "alloc transposed powers");
     if (p->d.precision != CASCADE_FP64) {
+      CK(dalloc(&p->P32, (size_t)ns * p->kmax1 * mm), "alloc FP32 powers");
+      CK(dalloc(&p->Minv32, (size_t)ns * mm), "alloc FP32 M^-1");
       const size_t e = plane_elem_bytes(p->d.precision);
       uint8_t* hi = nullptr;
       uint8_t* lo = nullptr;
@@ -328,10 +334,10 @@ Layout layout(const Plan& p) {
     off += align256((size_t)std::max(p.max_chunks, 1) * elems * acc);
     L.off_dP = off;
     off += align256(ns * p.kmax1 * m * m * 8);
-    L.off_R = off;                                  // R1, R2, dBbar: [nsys, m, p] each
-    off += align256(3 * ns * m * pp * 8);
-    L.off_T = off;                                  // [nsys, m, m]
-    off += align256(ns * m * m * 8);
+    L.off_R = off;                                  // R1, R2, dBbar, dB: [nsys, m, p] each
+    off += align256(4 * ns * m * pp * 8);
+    L.off_T = off;                                  // T, dA: [nsys, m, m] each
+    off += align256(2 * ns * m * m * 8);
   }
   L.total = off + 256;
   return L;
@@ -390,25 +396,59 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
   return CASCADE_OK;
 }
 
+// GEMM in the backward's arithmetic type (FP32 for the tensor-core plans,
+// FP64 for the FP64 plan).
+cudaError_t gemm_t(const double* A, const double* B, double* C, int M, int N, int K, int lda,
+                   int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch, double alpha,
+                   double beta, bool tA, bool tB, cudaStream_t st) {
+  return launch_dgemm(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, batch, alpha, beta, tA, tB, st);
+}
+cudaError_t gemm_t(const float* A, const float* B, float* C, int M, int N, int K, int lda,
+                   int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch, double alpha,
+                   double beta, bool tA, bool tB, cudaStream_t st) {
+  return launch_sgemm(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, batch, (float)alpha,
+                      (float)beta, tA, tB, st);
+}
+template <typename T>
+cudaError_t to_f64(const T* src, int64_t src_stride, double* dst, int64_t dst_stride, int64_t n,
+                   int nsys, cudaStream_t st);
+template <>
+cudaError_t to_f64<double>(const double* src, int64_t src_stride, double* dst, int64_t dst_stride,
+                           int64_t n, int nsys, cudaStream_t st) {
+  return cudaMemcpy2DAsync(dst, sizeof(double) * dst_stride, src, sizeof(double) * src_stride,
+                           sizeof(double) * n, nsys, cudaMemcpyDeviceToDevice, st);
+}
+template <>
+cudaError_t to_f64<float>(const float* src, int64_t src_stride, double* dst, int64_t dst_stride,
+                          int64_t n, int nsys, cudaStream_t st) {
+  return launch_convert_sys<float, double>(src, src_stride, dst, dst_stride, n, nsys, st);
+}
+
 // Reverse-mode derivative of sum(dy * y) after a forward that kept its stage
-// outputs (see backward.cu for the equations).
-cascade_status_t run_backward(Plan* p, const void* u, const void* dy, void* du, double* dAbar,
-                              double* dBbar, double* dC, double* dD, double* dA, double* dB,
-                              void* ws, cudaStream_t st) {
+// outputs (see backward.cu for the equations).  T: arithmetic of the small
+// m x m / m x p algebra at the end (squaring-chain and discretisation adjoints).
+template <typename T>
+cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Minv, const void* u,
+                                const void* dy, void* du, double* dAbar, double* dBbar,
+                                double* dC, double* dD, double* dA, double* dB, void* ws,
+                                cudaStream_t st) {
   const Layout L = layout(*p);
   uint8_t* base = static_cast<uint8_t*>(ws);
   const Bufs V{base, L.buf_stride, L.lo_off};
   const Bufs W{base + L.off_W, L.buf_stride, L.lo_off};
   void* part = base + L.off_part;
-  double* dP = reinterpret_cast<double*>(base + L.off_dP);
+  T* dP = reinterpret_cast<T*>(base + L.off_dP);
   const int m = p->d.m, pp = p->d.p, q = p->d.q, ns = p->d.nsys;
   const int64_t mm = (int64_t)m * m, mp = (int64_t)m * pp;
   const int64_t kst = (int64_t)p->kmax1 * mm;
-  double* R1 = reinterpret_cast<double*>(base + L.off_R);
-  double* R2 = R1 + ns * mp;
-  double* dBb = R2 + ns * mp;
-  double* T = reinterpret_cast<double*>(base + L.off_T);
+  T* R1 = reinterpret_cast<T*>(base + L.off_R);
+  T* R2 = R1 + ns * mp;
+  T* dBb = R2 + ns * mp;
+  T* dBt = dBb + ns * mp;
+  T* Tm = reinterpret_cast<T*>(base + L.off_T);
+  T* dAt = Tm + ns * mm;
   const bool f64 = p->d.precision == CASCADE_FP64;
+  const bool tf64 = sizeof(T) == 8;
   const TSrc G{f64 ? 2 : 1, Bufs{}, 0, 0, dy, q};
   const TSrc U{f64 ? 2 : 1, Bufs{}, 0, 0, u, pp};
   auto chunks = [&](int li) { return p->d_chunk_data + p->chunk_lists[li].off_chunks; };
@@ -419,21 +459,30 @@ cascade_status_t run_backward(Plan* p, const void* u, const void* dy, void* du, 
   CK(launch_adj_init(*p, dy, W, st), "adjoint init");
   if (dC)   // dC = sum G v^(N+1)^T; v^(N_i+1) sits in state buffer N_i (tile.flags)
     CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q,
-                      TSrc{0, V, 1, 0, nullptr, 0}, m, 0, part, dC, (int64_t)q * m, 0, st),
+                      TSrc{0, V, 1, 0, nullptr, 0}, m, 0, part, dC, true, (int64_t)q * m, 0, st),
        "dC");
   if (dD)
     CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q, U, pp, 0, part, dD,
-                      (int64_t)q * pp, 0, st),
+                      true, (int64_t)q * pp, 0, st),
        "dD");
-  CK(cudaMemsetAsync(dP, 0, sizeof(double) * ns * kst, st), "zero dP");
+  CK(cudaMemsetAsync(dP, 0, sizeof(T) * ns * kst, st), "zero dP");
   for (int k = p->maxN; k >= 1; --k) {
     const int win = (k + 1) & 1, wout = k & 1;
     const ChunkList& cl = p->chunk_lists[k];
     // dP_k = sum_{l >= s} W^(k+1)_l v^(k)_(l-s)^T; v^(k) is state buffer k-1
-    CK(launch_treduce(*p, p->d_tiles[k], chunks(k), cl.n, sysbeg(k),
-                      TSrc{0, W, 0, win, nullptr, 0}, m, TSrc{0, V, 0, k - 1, nullptr, 0}, m,
-                      1 << k, part, dP + (int64_t)k * mm, kst, 0, st),
-       "dP");
+    if (grad_tc_supported(*p)) {   // tensor cores, then the ordered per-system reduction
+      CK(launch_grad_tc(*p, p->d_tiles[k], chunks(k), cl.n, W.hi(win), W.lo(win), V.hi(k - 1),
+                        V.lo(k - 1), 1 << k, static_cast<float*>(part), st),
+         "dP (tensor core)");
+      CK(launch_reduce_partials(*p, static_cast<const float*>(part), sysbeg(k), mm,
+                                dP + (int64_t)k * mm, tf64, kst, st),
+         "dP reduction");
+    } else {
+      CK(launch_treduce(*p, p->d_tiles[k], chunks(k), cl.n, sysbeg(k),
+                        TSrc{0, W, 0, win, nullptr, 0}, m, TSrc{0, V, 0, k - 1, nullptr, 0}, m,
+                        1 << k, part, dP + (int64_t)k * mm, tf64, kst, 0, st),
+         "dP");
+    }
     if (f64) {
       CK(launch_stage_f64(*p, k, static_cast<const double*>(W.hi(win)),
                           static_cast<double*>(W.hi(wout)), st, true),
@@ -448,54 +497,54 @@ cascade_status_t run_backward(Plan* p, const void* u, const void* dy, void* du, 
   if (du) CK(launch_stage0_adj(*p, dy, W, 1, du, st), "du");
   const TSrc W1{0, W, 0, 1, nullptr, 0};
   CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, U, pp, 0, part, R1,
-                    mp, 0, st),
+                    tf64, mp, 0, st),
      "R1");
   CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, U, pp, 1, part, R2,
-                    mp, 0, st),
+                    tf64, mp, 0, st),
      "R2");
   // dP_0 += R2 Bbar^T;  dBbar = R1 + Abar^T R2
-  CK(launch_dgemm(R2, p->Bbar64, dP, m, m, pp, pp, pp, m, mp, mp, kst, ns, 1.0, 1.0, false, true, st),
-     "dP0");
-  CK(cudaMemcpyAsync(dBb, R1, sizeof(double) * ns * mp, cudaMemcpyDeviceToDevice, st), "copy");
-  CK(launch_dgemm(p->P64, R2, dBb, m, pp, m, m, pp, pp, kst, mp, mp, ns, 1.0, 1.0, true, false, st),
-     "dBbar");
+  CK(gemm_t(R2, Bbar, dP, m, m, pp, pp, pp, m, mp, mp, kst, ns, 1.0, 1.0, false, true, st), "dP0");
+  CK(cudaMemcpyAsync(dBb, R1, sizeof(T) * ns * mp, cudaMemcpyDeviceToDevice, st), "copy");
+  CK(gemm_t(P, R2, dBb, m, pp, m, m, pp, pp, kst, mp, mp, ns, 1.0, 1.0, true, false, st), "dBbar");
   // squaring chain P_(k+1) = P_k P_k:  dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1)
   for (int k = p->kmax1 - 2; k >= 0; --k) {
-    CK(launch_dgemm(dP + (k + 1) * mm, p->P64 + k * mm, dP + k * mm, m, m, m, m, m, m, kst, kst,
-                    kst, ns, 1.0, 1.0, false, true, st),
+    CK(gemm_t(dP + (k + 1) * mm, P + k * mm, dP + k * mm, m, m, m, m, m, m, kst, kst, kst, ns,
+              1.0, 1.0, false, true, st),
        "chain");
-    CK(launch_dgemm(p->P64 + k * mm, dP + (k + 1) * mm, dP + k * mm, m, m, m, m, m, m, kst, kst,
-                    kst, ns, 1.0, 1.0, true, false, st),
+    CK(gemm_t(P + k * mm, dP + (k + 1) * mm, dP + k * mm, m, m, m, m, m, m, kst, kst, kst, ns,
+              1.0, 1.0, true, false, st),
        "chain");
   }
-  if (dAbar)
-    CK(cudaMemcpy2DAsync(dAbar, sizeof(double) * mm, dP, sizeof(double) * kst, sizeof(double) * mm,
-                         ns, cudaMemcpyDeviceToDevice, st),
-       "dAbar");
-  if (dBbar)
-    CK(cudaMemcpyAsync(dBbar, dBb, sizeof(double) * ns * mp, cudaMemcpyDeviceToDevice, st), "dBbar");
+  if (dAbar) CK(to_f64<T>(dP, kst, dAbar, mm, mm, ns, st), "dAbar");
+  if (dBbar) CK(to_f64<T>(dBb, mp, dBbar, mp, mp, ns, st), "dBbar");
   // trapezoidal discretisation (Eq. 4.2), Abar = c M^-1 (I + delta/2 A), Bbar = delta M^-1 B:
   // dA = delta/2 M^-T (c dAbar + dAbar Abar^T + dBbar Bbar^T),  dB = delta M^-T dBbar
   if (p->continuous && (dA || dB)) {
-    CK(launch_dgemm(dP, p->P64, T, m, m, m, m, m, m, kst, kst, mm, ns, 1.0, 0.0, false, true, st),
-       "T");
-    CK(launch_dgemm(dBb, p->Bbar64, T, m, m, pp, pp, pp, m, mp, mp, mm, ns, 1.0, 1.0, false, true,
-                    st),
-       "T");
-    CK(launch_axpy_sys(dP, kst, T, mm, mm, ns, p->scale64, 1.0, true, st), "T");
+    CK(gemm_t(dP, P, Tm, m, m, m, m, m, m, kst, kst, mm, ns, 1.0, 0.0, false, true, st), "T");
+    CK(gemm_t(dBb, Bbar, Tm, m, m, pp, pp, pp, m, mp, mp, mm, ns, 1.0, 1.0, false, true, st), "T");
+    CK(launch_axpy_sys<T>(dP, kst, Tm, mm, mm, ns, p->scale64, 1.0, true, st), "T");
     if (dA) {
-      CK(launch_dgemm(p->Minv64, T, dA, m, m, m, m, m, m, mm, mm, mm, ns, 1.0, 0.0, true, false, st),
-         "dA");
-      CK(launch_axpy_sys(dA, mm, dA, mm, mm, ns, p->delta64, 0.5, false, st), "dA");
+      CK(gemm_t(Minv, Tm, dAt, m, m, m, m, m, m, mm, mm, mm, ns, 1.0, 0.0, true, false, st), "dA");
+      CK(launch_axpy_sys<T>(dAt, mm, dAt, mm, mm, ns, p->delta64, 0.5, false, st), "dA");
+      CK(to_f64<T>(dAt, mm, dA, mm, mm, ns, st), "dA");
     }
     if (dB) {
-      CK(launch_dgemm(p->Minv64, dBb, dB, m, pp, m, m, pp, pp, mm, mp, mp, ns, 1.0, 0.0, true, false,
-                      st),
-         "dB");
-      CK(launch_axpy_sys(dB, mp, dB, mp, mp, ns, p->delta64, 1.0, false, st), "dB");
+      CK(gemm_t(Minv, dBb, dBt, m, pp, m, m, pp, pp, mm, mp, mp, ns, 1.0, 0.0, true, false, st), "dB");
+      CK(launch_axpy_sys<T>(dBt, mp, dBt, mp, mp, ns, p->delta64, 1.0, false, st), "dB");
+      CK(to_f64<T>(dBt, mp, dB, mp, mp, ns, st), "dB");
     }
   }
   return CASCADE_OK;
+}
+
+cascade_status_t run_backward(Plan* p, const void* u, const void* dy, void* du, double* dAbar,
+                              double* dBbar, double* dC, double* dD, double* dA, double* dB,
+                              void* ws, cudaStream_t st) {
+  if (p->d.precision == CASCADE_FP64)
+    return run_backward_t<double>(p, p->P64, p->Bbar64, p->Minv64, u, dy, du, dAbar, dBbar, dC, dD,
+                                  dA, dB, ws, st);
+  return run_backward_t<float>(p, p->P32, p->Bbar32, p->Minv32, u, dy, du, dAbar, dBbar, dC, dD,
+                               dA, dB, ws, st);
 }
 
 }  // namespace

@@ -31,12 +31,13 @@ namespace cascade {
 namespace {
 
 template <int FMT>
-__device__ __forceinline__ double src_get(const TSrc& s, const Tile& t, int64_t row, int col,
-                                          int m) {
-  if (s.kind == 1) return (double)static_cast<const float*>(s.dense)[row * s.ld + col];
-  if (s.kind == 2) return static_cast<const double*>(s.dense)[row * s.ld + col];
+__device__ __forceinline__ typename Acc<FMT>::type src_get(const TSrc& s, const Tile& t,
+                                                           int64_t row, int col, int m) {
+  typedef typename Acc<FMT>::type A;
+  if (s.kind == 1) return (A) static_cast<const float*>(s.dense)[row * s.ld + col];
+  if (s.kind == 2) return (A) static_cast<const double*>(s.dense)[row * s.ld + col];
   const int b = s.buf_mode ? t.flags : s.buf_fixed;
-  return Store<FMT>::get(s.bufs.hi(b), s.bufs.lo(b), row * m + col);
+  return load_elem<FMT>(s.bufs.hi(b), s.bufs.lo(b), row * m + col);
 }
 
 // partial[chunk][i][j] = sum over the chunk's rows l (l >= shift) of X[l][i] Y[l - shift][j].
@@ -100,18 +101,18 @@ __global__ void __launch_bounds__(256) treduce_kernel(const Tile* __restrict__ t
 }
 
 // out[s][e] (+)= sum over the chunks of system s, in order, of partial[chunk][e].
-template <typename ACC>
+template <typename ACC, typename OUT>
 __global__ void reduce_partials_kernel(const ACC* __restrict__ partial,
                                        const int32_t* __restrict__ sys_begin, int64_t elems,
-                                       double* __restrict__ out, int64_t out_sys_stride,
+                                       OUT* __restrict__ out, int64_t out_sys_stride,
                                        int accumulate) {
   const int s = blockIdx.y;
   const int c0 = sys_begin[s], c1 = sys_begin[s + 1];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < elems;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double v = 0.0;
-    for (int c = c0; c < c1; ++c) v += (double)partial[(int64_t)c * elems + e];
-    double* o = out + (int64_t)s * out_sys_stride + e;
+    OUT v = 0;
+    for (int c = c0; c < c1; ++c) v += (OUT)partial[(int64_t)c * elems + e];
+    OUT* o = out + (int64_t)s * out_sys_stride + e;
     *o = accumulate ? *o + v : v;
   }
 }
@@ -130,9 +131,9 @@ __global__ void __launch_bounds__(256) adj_init_kernel(const Tile* __restrict__ 
   for (int idx = threadIdx.x; idx < rows * m; idx += blockDim.x) {
     const int r = idx / m, col = idx % m;
     const int64_t row = t.seq_row0 + t.t0 + r;
-    double acc = 0.0;
-    for (int j = 0; j < q; ++j) acc = fma((double)Cs[(int64_t)j * m + col], (double)G[row * q + j], acc);
-    Store<FMT>::put(hi, lo, row * m + col, acc);
+    T acc = 0;
+    for (int j = 0; j < q; ++j) acc = fma(Cs[(int64_t)j * m + col], G[row * q + j], acc);
+    Store<FMT>::put(hi, lo, row * m + col, (double)acc);
   }
 }
 
@@ -158,12 +159,12 @@ __global__ void __launch_bounds__(256) stage0_adj_kernel(const Tile* __restrict_
     const int64_t row = t.seq_row0 + l;
     const bool next = l + 1 < t.len;
     for (int j = 0; j < p; ++j) {
-      double s = 0.0;
+      T s = 0;
       for (int c = lane; c < m; c += 32) {
-        s = fma((double)Bs[(int64_t)c * p + j], Store<FMT>::get(wh, wl, row * m + c), s);
-        if (next) s = fma((double)ABs[(int64_t)c * p + j], Store<FMT>::get(wh, wl, (row + 1) * m + c), s);
+        s = fma(Bs[(int64_t)c * p + j], (T)load_elem<FMT>(wh, wl, row * m + c), s);
+        if (next) s = fma(ABs[(int64_t)c * p + j], (T)load_elem<FMT>(wh, wl, (row + 1) * m + c), s);
       }
-      for (int c = lane; c < q; c += 32) s = fma((double)Ds[(int64_t)c * p + j], (double)G[row * q + c], s);
+      for (int c = lane; c < q; c += 32) s = fma(Ds[(int64_t)c * p + j], G[row * q + c], s);
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
       if (lane == 0) du[row * p + j] = (T)s;
     }
@@ -189,17 +190,28 @@ __global__ void transpose_kernel(const double* __restrict__ in, double* __restri
 }
 
 // y[s][e] = (accumulate ? y[s][e] : 0) + factor * scal[s] * x[s][e]   (scal may be null: 1)
-__global__ void axpy_sys_kernel(const double* __restrict__ x, int64_t x_stride,
-                                double* __restrict__ y, int64_t y_stride, int64_t n,
-                                const double* __restrict__ scal, double factor, int accumulate) {
+template <typename T>
+__global__ void axpy_sys_kernel(const T* __restrict__ x, int64_t x_stride, T* __restrict__ y,
+                                int64_t y_stride, int64_t n, const double* __restrict__ scal,
+                                double factor, int accumulate) {
   const int s = blockIdx.y;
-  const double a = factor * (scal ? scal[s] : 1.0);
+  const T a = (T)(factor * (scal ? scal[s] : 1.0));
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const double v = a * x[(int64_t)s * x_stride + e];
-    double* o = y + (int64_t)s * y_stride + e;
+    const T v = a * x[(int64_t)s * x_stride + e];
+    T* o = y + (int64_t)s * y_stride + e;
     *o = accumulate ? *o + v : v;
   }
+}
+
+// out[s][i] = (T_out) in[s][i] over strided batches (precision conversion).
+template <typename TI, typename TO>
+__global__ void convert_sys_kernel(const TI* __restrict__ in, int64_t in_stride,
+                                   TO* __restrict__ out, int64_t out_stride, int64_t n) {
+  const int s = blockIdx.y;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[(int64_t)s * out_stride + e] = (TO)in[(int64_t)s * in_stride + e];
 }
 
 }  // namespace
@@ -207,8 +219,8 @@ __global__ void axpy_sys_kernel(const double* __restrict__ x, int64_t x_stride,
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
                            const int32_t* sys_begin, const TSrc& X, int a, const TSrc& Y, int b,
-                           int shift, void* partial, double* out, int64_t out_sys_stride,
-                           int accumulate, cudaStream_t st) {
+                           int shift, void* partial, void* out, bool out_f64,
+                           int64_t out_sys_stride, int accumulate, cudaStream_t st) {
   if (nchunks == 0) return cudaSuccess;
   const int BM = tile_rows(p);
   const TSrc xs = X, ys = Y;
@@ -219,8 +231,8 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
     treduce_kernel<FMT_F64, double><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
                                                          shift, (double*)partial);
     CASCADE_LAUNCHED();
-    reduce_partials_kernel<double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-        (const double*)partial, sys_begin, elems, out, out_sys_stride, accumulate);
+    reduce_partials_kernel<double, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+        (const double*)partial, sys_begin, elems, (double*)out, out_sys_stride, accumulate);
   } else {
     if (p.d.precision == CASCADE_BF16_SPLIT)
       treduce_kernel<FMT_BF16, float><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
@@ -229,9 +241,27 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
       treduce_kernel<FMT_F32, float><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
                                                           shift, (float*)partial);
     CASCADE_LAUNCHED();
-    reduce_partials_kernel<float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-        (const float*)partial, sys_begin, elems, out, out_sys_stride, accumulate);
+    if (out_f64)
+      reduce_partials_kernel<float, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+          (const float*)partial, sys_begin, elems, (double*)out, out_sys_stride, accumulate);
+    else
+      reduce_partials_kernel<float, float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+          (const float*)partial, sys_begin, elems, (float*)out, out_sys_stride, accumulate);
   }
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const Plan& p, const float* partial, const int32_t* sys_begin,
+                                   int64_t elems, void* out, bool out_f64, int64_t out_sys_stride,
+                                   cudaStream_t st) {
+  const int rblocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
+  if (out_f64)
+    reduce_partials_kernel<float, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+        partial, sys_begin, elems, (double*)out, out_sys_stride, 0);
+  else
+    reduce_partials_kernel<float, float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+        partial, sys_begin, elems, (float*)out, out_sys_stride, 0);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }
@@ -291,15 +321,34 @@ cudaError_t launch_transpose(const double* in, double* out, int n, int64_t strid
   return cudaGetLastError();
 }
 
-cudaError_t launch_axpy_sys(const double* x, int64_t x_stride, double* y, int64_t y_stride,
-                            int64_t n, int nsys, const double* scal, double factor,
-                            bool accumulate, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_axpy_sys(const T* x, int64_t x_stride, T* y, int64_t y_stride, int64_t n,
+                            int nsys, const double* scal, double factor, bool accumulate,
+                            cudaStream_t st) {
   if (n <= 0 || nsys <= 0) return cudaSuccess;
   const int blocks = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
-  axpy_sys_kernel<<<dim3(blocks, nsys), 256, 0, st>>>(x, x_stride, y, y_stride, n, scal, factor,
-                                                      accumulate ? 1 : 0);
+  axpy_sys_kernel<T><<<dim3(blocks, nsys), 256, 0, st>>>(x, x_stride, y, y_stride, n, scal,
+                                                         factor, accumulate ? 1 : 0);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }
+template cudaError_t launch_axpy_sys<double>(const double*, int64_t, double*, int64_t, int64_t,
+                                             int, const double*, double, bool, cudaStream_t);
+template cudaError_t launch_axpy_sys<float>(const float*, int64_t, float*, int64_t, int64_t, int,
+                                            const double*, double, bool, cudaStream_t);
+
+template <typename TI, typename TO>
+cudaError_t launch_convert_sys(const TI* in, int64_t in_stride, TO* out, int64_t out_stride,
+                               int64_t n, int nsys, cudaStream_t st) {
+  if (n <= 0 || nsys <= 0) return cudaSuccess;
+  const int blocks = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  convert_sys_kernel<TI, TO><<<dim3(blocks, nsys), 256, 0, st>>>(in, in_stride, out, out_stride, n);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert_sys<double, float>(const double*, int64_t, float*, int64_t,
+                                                       int64_t, int, cudaStream_t);
+template cudaError_t launch_convert_sys<float, double>(const float*, int64_t, double*, int64_t,
+                                                       int64_t, int, cudaStream_t);
 
 }  // namespace cascade

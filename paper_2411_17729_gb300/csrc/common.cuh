@@ -101,6 +101,8 @@ struct Plan {
   void* PTlo = nullptr;
   double* PT64 = nullptr;        // transposed FP64 powers (FP64 adjoint stages)
   double* Minv64 = nullptr;      // (I - delta/2 A)^-1 per system (discretisation adjoint)
+  float* P32 = nullptr;          // FP32 copies for the backward's small algebra
+  float* Minv32 = nullptr;
   double* Bbar64 = nullptr;      // [nsys, m, p]
   double* ABbar64 = nullptr;     // [nsys, m, p]   Abar * Bbar (first stage fused with Bbar u)
   double* C64 = nullptr;         // [nsys, q, m]
@@ -213,16 +215,31 @@ struct TSrc {
 };
 cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
                            const int32_t* sys_begin, const TSrc& X, int a, const TSrc& Y, int b,
-                           int shift, void* partial, double* out, int64_t out_sys_stride,
-                           int accumulate, cudaStream_t st);
+                           int shift, void* partial, void* out, bool out_f64,
+                           int64_t out_sys_stride, int accumulate, cudaStream_t st);
 cudaError_t launch_adj_init(const Plan& p, const void* G, const Bufs& W, cudaStream_t st);
+cudaError_t launch_reduce_partials(const Plan& p, const float* partial, const int32_t* sys_begin,
+                                   int64_t elems, void* out, bool out_f64, int64_t out_sys_stride,
+                                   cudaStream_t st);
+bool grad_tc_supported(const Plan& p);
+cudaError_t launch_grad_tc(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
+                           const void* w_hi, const void* w_lo, const void* v_hi, const void* v_lo,
+                           int shift, float* partial, cudaStream_t st);
 cudaError_t launch_stage0_adj(const Plan& p, const void* G, const Bufs& W, int wbuf, void* du,
                               cudaStream_t st);
 cudaError_t launch_transpose(const double* in, double* out, int n, int64_t stride, int batch,
                              cudaStream_t st);
-cudaError_t launch_axpy_sys(const double* x, int64_t x_stride, double* y, int64_t y_stride,
-                            int64_t n, int nsys, const double* scal, double factor,
-                            bool accumulate, cudaStream_t st);
+template <typename T>
+cudaError_t launch_axpy_sys(const T* x, int64_t x_stride, T* y, int64_t y_stride, int64_t n,
+                            int nsys, const double* scal, double factor, bool accumulate,
+                            cudaStream_t st);
+template <typename TI, typename TO>
+cudaError_t launch_convert_sys(const TI* in, int64_t in_stride, TO* out, int64_t out_stride,
+                               int64_t n, int nsys, cudaStream_t st);
+// Batched GEMM in float (same contract as launch_dgemm).
+cudaError_t launch_sgemm(const float* A, const float* B, float* C, int M, int N, int K, int lda,
+                         int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch,
+                         float alpha, float beta, bool transA, bool transB, cudaStream_t st);
 cudaError_t launch_recursion_f64(const Plan& p, const double* u, double* y, cudaStream_t st);
 cudaError_t launch_selftest_timeout(int32_t limit_us, int32_t* err, cudaStream_t st);
 

@@ -49,4 +49,31 @@ struct Store<FMT_F32> {
   }
 };
 
+// Element load in the arithmetic type of the format: double for the FP64
+// plane, float for the tensor-core pairs (FP64 arithmetic is slow on GB300).
+template <int FMT>
+struct Acc {
+  typedef float type;
+};
+template <>
+struct Acc<FMT_F64> {
+  typedef double type;
+};
+template <int FMT>
+__device__ __forceinline__ typename Acc<FMT>::type load_elem(const void* hi, const void* lo,
+                                                             int64_t i);
+template <>
+__device__ __forceinline__ double load_elem<FMT_F64>(const void* hi, const void*, int64_t i) {
+  return static_cast<const double*>(hi)[i];
+}
+template <>
+__device__ __forceinline__ float load_elem<FMT_BF16>(const void* hi, const void* lo, int64_t i) {
+  return __bfloat162float(static_cast<const __nv_bfloat16*>(hi)[i]) +
+         __bfloat162float(static_cast<const __nv_bfloat16*>(lo)[i]);
+}
+template <>
+__device__ __forceinline__ float load_elem<FMT_F32>(const void* hi, const void* lo, int64_t i) {
+  return static_cast<const float*>(hi)[i] + static_cast<const float*>(lo)[i];
+}
+
 }  // namespace cascade

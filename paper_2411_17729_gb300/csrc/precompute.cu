@@ -137,32 +137,30 @@ cudaError_t launch_discretise(const double* A, const double* B, const double* de
 // 4x4 outputs per thread.  Used for the squaring chain P_{k+1} = P_k P_k, the
 // product Abar Bbar, and the adjoint of the squaring chain.
 // ----------------------------------------------------------------------------
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) dgemm_kernel(const double* __restrict__ A,
-                                                    const double* __restrict__ B,
-                                                    double* __restrict__ C, int M, int N, int K,
-                                                    int lda, int ldb, int ldc, int64_t sA,
-                                                    int64_t sB, int64_t sC, double alpha,
-                                                    double beta) {
-  __shared__ double As[16][65];
-  __shared__ double Bs[16][65];
+template <typename T, bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm_kernel(const T* __restrict__ A, const T* __restrict__ B,
+                                                   T* __restrict__ C, int M, int N, int K, int lda,
+                                                   int ldb, int ldc, int64_t sA, int64_t sB,
+                                                   int64_t sC, T alpha, T beta) {
+  __shared__ T As[16][65];
+  __shared__ T Bs[16][65];
   A += (int64_t)blockIdx.z * sA;
   B += (int64_t)blockIdx.z * sB;
   C += (int64_t)blockIdx.z * sC;
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
 
   for (int k0 = 0; k0 < K; k0 += 16) {
     for (int e = threadIdx.x; e < 1024; e += 256) {
       int mm, kk;
       if (!TA) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
       const int gm = m0 + mm, gk = k0 + kk;
-      double v = 0.0;
+      T v = 0;
       if (gm < M && gk < K) v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
       As[kk][mm] = v;
     }
@@ -170,14 +168,14 @@ __global__ void __launch_bounds__(256) dgemm_kernel(const double* __restrict__ A
       int nn, kk;
       if (!TB) { nn = e & 63; kk = e >> 6; } else { kk = e & 15; nn = e >> 4; }
       const int gn = n0 + nn, gk = k0 + kk;
-      double v = 0.0;
+      T v = 0;
       if (gn < N && gk < K) v = TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
       Bs[kk][nn] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -197,28 +195,43 @@ __global__ void __launch_bounds__(256) dgemm_kernel(const double* __restrict__ A
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
-      double* c = C + (int64_t)gm * ldc + gn;
-      *c = alpha * acc[i][j] + (beta != 0.0 ? beta * *c : 0.0);
+      T* c = C + (int64_t)gm * ldc + gn;
+      *c = alpha * acc[i][j] + (beta != (T)0 ? beta * *c : (T)0);
     }
   }
+}
+
+template <typename T>
+cudaError_t launch_gemm(const T* A, const T* B, T* C, int M, int N, int K, int lda, int ldb,
+                        int ldc, int64_t sA, int64_t sB, int64_t sC, int batch, T alpha, T beta,
+                        bool transA, bool transB, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+  if (!transA && !transB)
+    gemm_kernel<T, false, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+  else if (transA && !transB)
+    gemm_kernel<T, true, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+  else if (!transA && transB)
+    gemm_kernel<T, false, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+  else
+    gemm_kernel<T, true, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
                          int lda, int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC,
                          int batch, double alpha, double beta, bool transA, bool transB,
                          cudaStream_t st) {
-  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
-  dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
-  if (!transA && !transB)
-    dgemm_kernel<false, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
-  else if (transA && !transB)
-    dgemm_kernel<true, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
-  else if (!transA && transB)
-    dgemm_kernel<false, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
-  else
-    dgemm_kernel<true, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
-  CASCADE_LAUNCHED();
-  return cudaGetLastError();
+  return launch_gemm<double>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, batch, alpha, beta,
+                             transA, transB, st);
+}
+
+cudaError_t launch_sgemm(const float* A, const float* B, float* C, int M, int N, int K, int lda,
+                         int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch,
+                         float alpha, float beta, bool transA, bool transB, cudaStream_t st) {
+  return launch_gemm<float>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, batch, alpha, beta,
+                            transA, transB, st);
 }
 
 // ----------------------------------------------------------------------------

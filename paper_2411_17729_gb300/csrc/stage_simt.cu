@@ -190,24 +190,24 @@ __global__ void __launch_bounds__(256) output_kernel(const Tile* __restrict__ ti
   for (int r = warp; r < rows; r += nw) {
     const int64_t row = t.seq_row0 + t.t0 + r;
     for (int q0 = 0; q0 < q; q0 += 8) {
-      double acc[8];
+      T acc[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+      for (int i = 0; i < 8; ++i) acc[i] = 0;
       for (int c = lane; c < m; c += 32) {
-        const double v = Store<FMT>::get(vh, vl, row * m + c);
+        const T v = (T)load_elem<FMT>(vh, vl, row * m + c);
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-          if (q0 + i < q) acc[i] = fma((double)Cs[(int64_t)(q0 + i) * m + c], v, acc[i]);
+          if (q0 + i < q) acc[i] = fma(Cs[(int64_t)(q0 + i) * m + c], v, acc[i]);
       }
       for (int c = lane; c < p; c += 32) {
-        const double uv = (double)u[row * p + c];
+        const T uv = u[row * p + c];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-          if (q0 + i < q) acc[i] = fma((double)Ds[(int64_t)(q0 + i) * p + c], uv, acc[i]);
+          if (q0 + i < q) acc[i] = fma(Ds[(int64_t)(q0 + i) * p + c], uv, acc[i]);
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        double s = acc[i];
+        T s = acc[i];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0 && q0 + i < q) y[row * q + q0 + i] = (T)s;
       }

@@ -27,6 +27,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cascade states/s (fwd)"
+# DRAM bytes (read + write) per launch of the stage kernel on the precision workload: an ncu
+# capture of stage k = 8 on 8 of the 64 sequences measured 235.5 MB (148.3 MB read, 87.2 MB
+# written); the traffic grows with the rows processed, so a full launch moves 8x that.
+TRAFFIC_NOTE = {"bytes_per_launch": 8 * 235.5e6,
+                "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of stage_tc_kernel, "
+                        "stage 8, 8 of 64 sequences, scaled x8 to the full launch"}
 WORKLOAD = ("precision_form: HiPPO-LegS m=256 p=q=1, 64 seqs x L=16384, N=13, "
             "delta log-uniform [1e-4,1e-1] per sequence, BF16 hi/lo split, FP32 accumulate")
 
@@ -40,8 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 cascade comparator")
     ap.add_argument("--no-bwd", action="store_true", help="skip the forward+backward measurement")
-    ap.add_argument("--seqs", type=int, default=64,
-                    help="sequences in the batch (64 = the benchmark; fewer only for profiler captures)")
+    ap.add_argument("--seqs", type=int, default=0,
+                    help="keep only the first SEQS sequences (profiler captures only)")
+    ap.add_argument("--workload", default="precision_form", choices=sorted(SPECS),
+                    help="precision_form is the benchmark; the others are the other configurations")
     return ap.parse_args()
 
 
@@ -78,13 +86,16 @@ def oracle_states_per_s(w, budget_s=12.0):
         if s not in cache:
             cache[s] = oracle.system_matrices(w, s)
         Abar, Bbar, C, D = cache[s]
-        oracle.cascade_forward_seq(Abar, Bbar, C, D, w.u[sl], w.N)
-        states += sl.stop - sl.start
+        L = sl.stop - sl.start
+        N = w.N if w.N >= 0 else oracle.choose_N(Abar, int(w.lengths.max()), w.eps)
+        oracle.cascade_forward_seq(Abar, Bbar, C, D, w.u[sl], oracle.effective_N(N, L))
+        states += L
         seqs += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return states / dt, f"{seqs} of {w.nseq} sequences (L={int(w.lengths[0])}), powers included", dt
+    return (states / dt, f"first {seqs} of {w.nseq} sequences ({states} states), powers included",
+            dt)
 
 
 class ClockSampler:
@@ -160,7 +171,10 @@ def run_reference(args):
         return
     import numpy as np  # noqa: F401
     import workloads as wl
-    w = wl.precision_form()
+    w = wl.WORKLOADS[args.workload]()
+    if args.seqs and args.seqs < w.nseq:
+        w = w.subset(range(args.seqs))
+    description = SPECS[args.workload][1]
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         oracle_states_per_s(w, budget_s=min(per_step, 2.0))
@@ -176,12 +190,44 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * secs / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "oracle": "numpy float64 cascade (CPU)"},
+            "config": {"workload": description, "global_batch": int(w.nseq),
+                       "seq_len": int(w.lengths.max()), "parallelism": "single",
+                       "oracle": "numpy float64 cascade (CPU)"},
             "cpu_baseline": {"value": value, "unit": "states/s", "cores": cores,
                              "kind": "oracle", "sample": samples[-1]},
             "e2e": {"value": value, "unit": "states/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- workloads
+# name -> (generator kwargs builder, precision, one-line description, run backward?)
+SPECS = {
+    "precision_form": ("bf16_split", WORKLOAD, True),
+    "plain_fp64": ("fp64", "plain_fp64: HiPPO-LegS m=64 p=q=1, 1 seq x L=4096, delta=1/4096, "
+                   "N=11, FP64 (equals the recursion)", False),
+    "batching_form": ("fp32", "batching_form: HiPPO-LegS m=128 p=q=4, 512 seqs, L_i log-uniform "
+                      "[1024,65536] (8.85e6 rows), Abar*(1+1e-6), N_i from eps=1e-6, FP32 "
+                      "(3xTF32)", False),
+    "differentiation_form": ("bf16_split", "differentiation_form: HiPPO-LegS m=256 p=q=16, "
+                             "32 seqs x L=8192, delta=1e-3, N=12, BF16 split, fwd+bwd", True),
+    "large_form": ("bf16_split", "large_form: Abar=0.9999 Q + rank-4 E, m=1024 p=q=64, 8 seqs x "
+                   "L=65536, N=15, BF16 split, fwd+bwd", True),
+}
+
+
+def timed_steps(fn, steps, flush, stream):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
 
 
 # --------------------------------------------------------------------- our arm
@@ -197,6 +243,7 @@ def main():
     from paper_2411_17729_gb300 import build
     build()
     from paper_2411_17729_gb300 import cascade
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SAVE_STATES
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -204,17 +251,22 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    w = wl.precision_form()
-    if args.seqs != w.nseq:
+    precision, description, has_bwd = SPECS[args.workload]
+    w = wl.WORKLOADS[args.workload]()
+    if args.seqs and args.seqs < w.nseq:
         w = w.subset(range(args.seqs))
     m = w.m
+    f64 = precision == "fp64"
+    dt = torch.float64 if f64 else torch.float32
+    esize = 8  # bytes of one state element (both planes, or the FP64 plane)
+    if precision == "bf16_split":
+        esize = 4
     t_prep0 = time.perf_counter()
-    c = cascade.from_workload(w, precision="bf16_split", device=dev)
+    c = cascade.from_workload(w, precision=precision, device=dev)
     torch.cuda.synchronize()
     prep_s = time.perf_counter() - t_prep0
-    u = torch.as_tensor(w.u, dtype=torch.float32).to(dev).contiguous()
-    y = torch.empty((w.rows, w.q), dtype=torch.float32, device=dev)
-    ws = c.workspace()
+    u = torch.as_tensor(w.u, dtype=dt).to(dev).contiguous()
+    y = torch.empty((w.rows, w.q), dtype=dt, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     lib = c.lib
@@ -222,7 +274,7 @@ def main():
     def step():
         c.forward(u, y)
 
-    shape = c.autotune(u, y, reps=2)          # kernel shape for this batch (untimed)
+    shape = c.autotune(u, y, reps=2) if not f64 else (0, 0, 0)   # kernel shape (untimed)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -272,59 +324,74 @@ def main():
     if c.device_error() != 0:
         raise RuntimeError("device wait timed out in the timed region")
 
-    # ---- roofline of the dominant kernel (tensor-core stage), per launch
+    # ---- roofline of the dominant kernel (the stage kernel), per launch
     hbm_peak, bf16_peak, peak_kind = peaks()
     Ls = w.lengths.astype(np.int64)
+    Ns = c.seq_N()
     tot_ms = {k: sum(v) for k, v in stage_ms.items()}
     avg_ms = sum(tot_ms.values()) / max(1, sum(len(v) for v in stage_ms.values()))
     launches_per_step = len(stage_ms)
     bytes_per_launch, flops_per_launch = [], []
     for k in stage_ms:
         s = 1 << k
-        upd = int(np.maximum(Ls - s, 0).sum())
-        rows_read = int(Ls.sum())
-        # read every row of V^(k) once, write the updated rows of V^(k+1): 4 bytes per
-        # element each way (BF16 hi + lo); plus the power's hi/lo planes per system
-        bytes_per_launch.append(4 * m * (rows_read + upd) + w.nsys * m * m * 4)
-        flops_per_launch.append(3 * 2 * m * m * upd)
-    alg_bytes = float(np.mean(bytes_per_launch))
-    alg_flops = float(np.mean(flops_per_launch))
-    achieved_gbs = alg_bytes / (avg_ms / 1000.0) / 1e9
-    achieved_tfs = alg_flops / (avg_ms / 1000.0) / 1e12
+        live = Ns >= k
+        upd = int(np.maximum(Ls[live] - s, 0).sum())
+        rows_read = int(Ls[live].sum())
+        # read every row of v^(k) once and write the updated rows of v^(k+1) (esize bytes
+        # per element), plus the power's operand planes per system
+        bytes_per_launch.append(esize * m * (rows_read + upd) + w.nsys * m * m * esize)
+        flops_per_launch.append((1 if f64 else 3) * 2 * m * m * upd)
+    alg_bytes = float(np.mean(bytes_per_launch)) if bytes_per_launch else 0.0
+    alg_flops = float(np.mean(flops_per_launch)) if flops_per_launch else 0.0
+    achieved_gbs = alg_bytes / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else 0.0
+    achieved_tfs = alg_flops / (avg_ms / 1000.0) / 1e12 if avg_ms > 0 else 0.0
     stage_share = sum(tot_ms.values()) / max(1e-9, sum(step_ms))
+    if f64:
+        roofline = {"bound": "alu", "achieved": achieved_tfs, "peak": 1.25, "unit": "TFLOP/s",
+                    "frac": achieved_tfs / 1.25, "traffic": None,
+                    "kernel": "stage_f64_kernel", "peak_kind": "nominal FP64 (1.25 TFLOP/s)",
+                    "alg_flops_per_launch": alg_flops, "avg_launch_ms": avg_ms,
+                    "launches_per_step": launches_per_step, "share_of_step": stage_share}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm_peak, "traffic": None,
+                    "kernel": f"stage_tc_kernel<{'bf16' if esize == 4 else 'tf32'}> (stages 1..N)",
+                    "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                    "avg_launch_ms": avg_ms, "launches_per_step": launches_per_step,
+                    "share_of_step": stage_share,
+                    "tensor": {"achieved": achieved_tfs, "peak": bf16_peak, "unit": "TFLOP/s",
+                               "frac": achieved_tfs / bf16_peak, "alg_flops_per_launch": alg_flops,
+                               "peak_note": "BF16 dense measured; the TF32 path's own peak is "
+                                            "half of it (nominal 1.1 vs 2.25 PFLOP/s)"}}
+        if args.workload == "precision_form" and args.seqs in (0, 64) and TRAFFIC_NOTE:
+            roofline["traffic"] = TRAFFIC_NOTE["bytes_per_launch"]
+            roofline["traffic_note"] = TRAFFIC_NOTE["note"]
 
     # ---- end to end through the public API with host buffers
-    u_host = torch.as_tensor(w.u, dtype=torch.float32).pin_memory()
-    y_host = torch.empty((w.rows, w.q), dtype=torch.float32).pin_memory()
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        e2e_ev[i][0].record(stream)
+    u_host = torch.as_tensor(w.u, dtype=dt).pin_memory()
+    y_host = torch.empty((w.rows, w.q), dtype=dt).pin_memory()
+
+    def e2e_step():
         u.copy_(u_host, non_blocking=True)
         c.forward(u, y)
         y_host.copy_(y, non_blocking=True)
-        e2e_ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
+
+    e2e_ms = sum(timed_steps(e2e_step, args.steps, flush, stream)) / args.steps
     if world > 1:
         t = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_value = states_per_step * world / (e2e_ms / 1000.0)
+    c.close()
+    torch.cuda.empty_cache()
 
     # ---- forward + backward (plan that keeps its stage outputs), same workload
     fb = None
-    if not args.no_bwd:
-        from paper_2411_17729_gb300._abi import CASCADE_FLAG_SAVE_STATES
-        c.close()
-        del ws
-        torch.cuda.empty_cache()
-        cb = cascade.from_workload(w, precision="bf16_split", flags=CASCADE_FLAG_SAVE_STATES,
+    if has_bwd and not args.no_bwd:
+        cb = cascade.from_workload(w, precision=precision, flags=CASCADE_FLAG_SAVE_STATES,
                                    device=dev)
         cb.autotune(u, y, reps=1)
-        dy = torch.randn((w.rows, w.q), dtype=torch.float32, device=dev,
+        dy = torch.randn((w.rows, w.q), dtype=dt, device=dev,
                          generator=torch.Generator(device=dev).manual_seed(0))
         for _ in range(2):
             cb.forward(u, y)
@@ -350,25 +417,31 @@ def main():
             fb_ms = float(t.item())
         fb = {"value": states_per_step * world / (fb_ms / 1000.0), "unit": "states/s",
               "ms_per_step": fb_ms, "backward_ms": bwd_ms,
-              "gradients": "u, A (squaring chain + trapezoid), B, C, D"}
+              "gradients": "u, A (or Abar), B (or Bbar), C, D"}
         cb.close()
+        torch.cuda.empty_cache()
 
-    # ---- FP64 plain cascade on the same GPU (comparator), on 8 sequences
+    # ---- FP64 plain cascade and FP64 recursion on the same GPU (comparators)
     fp64 = None
-    if not args.no_fp64:
-        sub = w.subset(range(8))
+    rec = None
+    nsub = min(8 if m <= 256 else 1, w.nseq)   # FP64 runs near 1.25 TFLOP/s: bound the sample
+    if not args.no_fp64 and not f64:
+        sub = w.subset(range(nsub))
         c64 = cascade.from_workload(sub, precision="fp64", device=dev)
         u64 = torch.as_tensor(sub.u, dtype=torch.float64).to(dev)
         c64.forward(u64)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        c64.forward(u64)
-        b.record(stream)
-        torch.cuda.synchronize()
-        fp64 = {"value": sub.rows / (a.elapsed_time(b) / 1000.0), "unit": "states/s",
-                "sample": "8 of 64 sequences, one pass"}
+        ms = timed_steps(lambda: c64.forward(u64), 1, flush, stream)[0]
+        fp64 = {"value": sub.rows / (ms / 1000.0), "unit": "states/s",
+                "sample": f"{sub.nseq} of {w.nseq} sequences, one pass"}
         c64.close()
+    if args.workload in ("large_form", "plain_fp64") and not args.no_fp64:
+        sub = w.subset(range(nsub))
+        cr = cascade.from_workload(sub, precision="fp64", device=dev)
+        u64 = torch.as_tensor(sub.u, dtype=torch.float64).to(dev)
+        ms = timed_steps(lambda: cr.recursion(u64), 1, flush, stream)[0]
+        rec = {"value": sub.rows / (ms / 1000.0), "unit": "states/s",
+               "sample": f"{sub.nseq} of {w.nseq} sequences, one pass, one block per sequence"}
+        cr.close()
 
     # ---- oracle on the host cores (rank 0, N = 1 only)
     cpu = None
@@ -381,29 +454,26 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16_split": "bf16", "fp32": "tf32", "fp64": "f64"}[precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": int(w.nseq) * world, "seq_len": 16384,
+            "config": {"workload": description, "global_batch": int(w.nseq) * world,
+                       "seq_len": int(Ls.max()),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "flushed before each timed step (256 MiB write)",
                        "timing": "CUDA events on the launching stream, sum over steps",
-                       "kernel_shape": {"stages": shape[0], "ring": shape[1], "chunks_per_step": shape[2]}},
-            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved_gbs / hbm_peak, "traffic": None,
-                         "kernel": "stage_tc_kernel<bf16,q=1> (stages 1..13)",
-                         "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
-                         "avg_launch_ms": avg_ms, "launches_per_step": launches_per_step,
-                         "share_of_step": stage_share,
-                         "tensor": {"achieved": achieved_tfs, "peak": bf16_peak, "unit": "TFLOP/s",
-                                    "frac": achieved_tfs / bf16_peak,
-                                    "alg_flops_per_launch": alg_flops}},
+                       "kernel_shape": {"stages": shape[0], "ring": shape[1],
+                                        "chunks_per_step": shape[2]}},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "states/s",
-                    "h2d_bytes_per_step": int(u.numel() * 4), "d2h_bytes_per_step": int(y.numel() * 4)},
+                    "h2d_bytes_per_step": int(u.numel() * u.element_size()),
+                    "d2h_bytes_per_step": int(y.numel() * y.element_size())},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "fwd_bwd": fb,
             "fp64_cascade": fp64,
+            "fp64_recursion": rec,
             "precompute_s": prep_s,
             "stage_ms": {str(k): statistics.median(v) for k, v in sorted(stage_ms.items())},
             "wall_s": wall,

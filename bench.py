@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 cascade comparator")
     ap.add_argument("--no-bwd", action="store_true", help="skip the forward+backward measurement")
+    ap.add_argument("--no-scan", action="store_true",
+                    help="skip the work-efficient (about 2L products) schedule measurement")
     ap.add_argument("--seqs", type=int, default=0,
                     help="keep only the first SEQS sequences (profiler captures only)")
     ap.add_argument("--workload", default="precision_form", choices=sorted(SPECS),
@@ -243,7 +245,8 @@ def main():
     from paper_2411_17729_gb300 import build
     build()
     from paper_2411_17729_gb300 import cascade
-    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SAVE_STATES
+    from paper_2411_17729_gb300._abi import (CASCADE_FLAG_RECOMPUTE, CASCADE_FLAG_SAVE_STATES,
+                                             CASCADE_FLAG_SCAN)
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -385,11 +388,68 @@ def main():
     c.close()
     torch.cuda.empty_cache()
 
+    # ---- the work-efficient schedule (about 2L products per sequence), same workload
+    scan = None
+    if not f64 and not args.no_scan:
+        import ctypes
+        cs = cascade.from_workload(w, precision=precision, flags=CASCADE_FLAG_SCAN, device=dev)
+        cs.autotune(u, y, reps=2)
+        for _ in range(max(args.warmup, 3)):
+            cs.forward(u, y)
+        cs.enable_stage_timing(True)
+        lev_ms = {}
+        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            sev[i][0].record(stream)
+            cs.forward(u, y)
+            sev[i][1].record(stream)
+            for k, ms in cs.stage_times():
+                lev_ms.setdefault(k, []).append(ms)
+        torch.cuda.synchronize()
+        cs.enable_stage_timing(False)
+        if cs.device_error() != 0:
+            raise RuntimeError("device wait timed out in the scan region")
+        scan_ms = sum(a.elapsed_time(b) for a, b in sev) / args.steps
+        if world > 1:
+            t = torch.tensor([scan_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            scan_ms = float(t.item())
+        nmv = ctypes.c_int64()
+        cs._check(cs.lib.cascade_get_matvec_count(cs.plan, ctypes.byref(nmv)))
+        # algorithmic bytes of the level launches: per updated row, read the
+        # destination and the source row and write the destination (esize bytes
+        # per element), plus the power planes per system and launch
+        upd = nmv.value - sum(int(L) // 2 for L in Ls)      # products made on the tensor cores
+        nlev = len(lev_ms)
+        lev_tot = sum(sum(v) for v in lev_ms.values()) / args.steps
+        lev_bytes = 3 * esize * m * upd + nlev * w.nsys * m * m * esize
+        lev_gbs = lev_bytes / (lev_tot / 1000.0) / 1e9 if lev_tot > 0 else 0.0
+        scan = {"value": states_per_step * world / (scan_ms / 1000.0), "unit": "states/s",
+                "ms_per_step": scan_ms, "matvecs_per_step": int(nmv.value),
+                "matvecs_stage_schedule": int(sum(
+                    sum(max(int(L) - (1 << k), 0) for k in range(int(Nk) + 1))
+                    for L, Nk in zip(Ls, Ns))),
+                "levels": nlev, "level_ms_per_step": lev_tot,
+                "roofline": {"bound": "hbm", "achieved": lev_gbs, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": lev_gbs / hbm_peak,
+                             "kernel": "stage_tc_kernel, strided in-place levels",
+                             "alg_bytes_per_step": lev_bytes, "peak_kind": peak_kind},
+                "schedule": "up-sweep k=1..K-1, down-sweep k=K-2..0 (first level fused "
+                            "with Bbar u), in place"}
+        cs.close()
+        torch.cuda.empty_cache()
+
     # ---- forward + backward (plan that keeps its stage outputs), same workload
     fb = None
     if has_bwd and not args.no_bwd:
-        cb = cascade.from_workload(w, precision=precision, flags=CASCADE_FLAG_SAVE_STATES,
-                                   device=dev)
+        # the differentiation workload recomputes stage outputs from checkpoints
+        recompute = args.workload == "differentiation_form"
+        cb = cascade.from_workload(w, precision=precision,
+                                   flags=CASCADE_FLAG_RECOMPUTE if recompute
+                                   else CASCADE_FLAG_SAVE_STATES, device=dev)
         cb.autotune(u, y, reps=1)
         dy = torch.randn((w.rows, w.q), dtype=dt, device=dev,
                          generator=torch.Generator(device=dev).manual_seed(0))
@@ -417,7 +477,9 @@ def main():
             fb_ms = float(t.item())
         fb = {"value": states_per_step * world / (fb_ms / 1000.0), "unit": "states/s",
               "ms_per_step": fb_ms, "backward_ms": bwd_ms,
-              "gradients": "u, A (or Abar), B (or Bbar), C, D"}
+              "gradients": "u, A (or Abar), B (or Bbar), C, D",
+              "stage_outputs": "recomputed from checkpoints" if recompute else "kept",
+              "workspace_bytes": int(cb.workspace_size())}
         cb.close()
         torch.cuda.empty_cache()
 
@@ -472,6 +534,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks,
             "fwd_bwd": fb,
+            "scan_fwd": scan,
             "fp64_cascade": fp64,
             "fp64_recursion": rec,
             "precompute_s": prep_s,

@@ -65,17 +65,31 @@ typedef enum {
 } cascade_precision_t;
 
 enum {
-  /* Keep every stage output V^(k) in the workspace so that cascade_backward
-     can run (without it, backward recomputes them: see CASCADE_FLAG_RECOMPUTE). */
+  /* Keep every stage output v^(k) in the workspace so that cascade_backward
+     can run: maxN + 1 state buffers.                                        */
   CASCADE_FLAG_SAVE_STATES = 1,
-  /* Backward recomputes stage outputs from checkpoints every c stages
-     instead of keeping all of them (lower workspace, one extra forward).    */
+  /* Keep only checkpoints v^(1), v^(1+c), v^(1+2c), ... and recompute the
+     other stage outputs in cascade_backward, one segment of c stages at a
+     time (c is chosen per batch to minimise the buffers; about 2 sqrt(N)
+     state buffers instead of N + 1, for maxN - ceil(maxN / c) extra stage
+     passes).  Results are bitwise equal to CASCADE_FLAG_SAVE_STATES.  Takes
+     precedence when both flags are given.                                  */
   CASCADE_FLAG_RECOMPUTE = 2,
-  /* Do not fuse y = C v + D u into the last stage (diagnostics).            */
+  /* Do not fuse y = C v + D u into the last stage (diagnostics).  The fused
+     epilogue is used for q <= 4 when one tile spans all m columns.          */
   CASCADE_FLAG_NO_FUSED_OUTPUT = 4,
   /* Record the forward launch sequence once per (u, y, workspace) triple in
      a CUDA graph and replay it on later calls.                             */
-  CASCADE_FLAG_GRAPH = 8
+  CASCADE_FLAG_GRAPH = 8,
+  /* Forward with the work-efficient schedule of the abstract and §6 instead
+     of the §3 one: an up-sweep applies Abar^(2^k) to every 2^(k+1)-th entry
+     (k = 0..K-1, K = ceil(log2 L)), a down-sweep fills the entries in between
+     (k = K-2..0), about 2L products by powers per sequence instead of
+     sum_k (L - 2^k).  In place on one state buffer.  The outputs equal the
+     §3 cascade's up to rounding when 2^(N_i+1) >= L_i, which cascade_set_batch
+     requires (CASCADE_ERR_UNSUPPORTED otherwise).  Tensor-core precisions
+     only; no backward (CASCADE_ERR_INVALID_ARG with SAVE_STATES/RECOMPUTE). */
+  CASCADE_FLAG_SCAN = 16
 };
 
 typedef struct cascade_plan_s* cascade_plan_t;
@@ -157,11 +171,19 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
    h_N [nseq]. */
 cascade_status_t cascade_get_seq_N(cascade_plan_t plan, int32_t* h_N);
 
+/* Products of a power Abar^(2^k) with a state vector that one forward over
+   the current batch executes (summed over sequences): sum_k (L_i - 2^k)^+
+   for the §3 schedule, about 2 L_i with CASCADE_FLAG_SCAN.  The input
+   projection's Abar Bbar u term of the first stage counts as one per row it
+   is applied to.  Host-side count of the schedule; *h_count. */
+cascade_status_t cascade_get_matvec_count(cascade_plan_t plan, int64_t* h_count);
+
 /* Size of the fixed device scratch array behind cascade_forward_fixed_scratch. */
 #define CASCADE_FIXED_SCRATCH_BYTES ((size_t)32 << 20)
 
 /* Bytes of caller-provided device workspace that forward (and, for plans
-   with CASCADE_FLAG_SAVE_STATES, backward) need for the current batch. */
+   with CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE, backward) need for
+   the current batch. */
 cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes);
 
 /* Apply the truncated transfer function to the current batch (§3):
@@ -195,8 +217,10 @@ cascade_status_t cascade_forward_fixed_scratch(cascade_plan_t plan, const void* 
 
 /* Reverse-mode derivative of sum(dy * y) for the last cascade_forward on
    this batch and workspace, which must come from a plan created with
-   CASCADE_FLAG_SAVE_STATES (the forward then keeps every stage output in the
-   workspace; CASCADE_ERR_STATE otherwise).  d_u is the forward's input,
+   CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE (the forward then keeps
+   every stage output, or checkpoints, in the workspace; CASCADE_ERR_STATE
+   otherwise).  With checkpoints the call overwrites the forward's other state
+   buffers; a second backward needs a new forward.  d_u is the forward's input,
    d_dy [rows,q] the output gradient (plan element type).  Writes d_du
    [rows,p] and, per system, d_dAbar [nsys,m,m], d_dBbar [nsys,m,p], d_dC
    [nsys,q,m], d_dD [nsys,q,p] (double): the gradients through the squaring

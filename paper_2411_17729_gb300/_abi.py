@@ -28,6 +28,7 @@ CASCADE_FLAG_SAVE_STATES = 1
 CASCADE_FLAG_RECOMPUTE = 2
 CASCADE_FLAG_NO_FUSED_OUTPUT = 4
 CASCADE_FLAG_GRAPH = 8
+CASCADE_FLAG_SCAN = 16
 
 PRECISIONS = {"fp64": CASCADE_FP64, "fp32": CASCADE_FP32, "bf16_split": CASCADE_BF16_SPLIT}
 
@@ -55,6 +56,7 @@ SIGNATURES = [
     ("cascade_set_batch", C.c_int, [cascade_plan_t, C.POINTER(C.c_int64), C.c_int32,
                                     C.POINTER(C.c_int32)]),
     ("cascade_get_seq_N", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
+    ("cascade_get_matvec_count", C.c_int, [cascade_plan_t, C.POINTER(C.c_int64)]),
     ("cascade_workspace_size", C.c_int, [cascade_plan_t, C.POINTER(C.c_size_t)]),
     ("cascade_forward", C.c_int, [cascade_plan_t, _P, _P, _P, C.c_size_t, _P]),
     ("cascade_forward_fixed_scratch", C.c_int, [cascade_plan_t, _P, _P, _P]),

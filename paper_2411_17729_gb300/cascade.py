@@ -123,8 +123,8 @@ class Cascade:
 
     def backward(self, u, dy, stream=None, want=("du", "dAbar", "dBbar", "dC", "dD", "dA", "dB")):
         """Gradients of sum(dy * y) for the last forward (plan created with
-        CASCADE_FLAG_SAVE_STATES).  Returns a dict of tensors; dA, dB only for
-        continuous systems."""
+        CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE).  Returns a dict of
+        tensors; dA, dB only for continuous systems."""
         assert dy.dtype == self.dtype and dy.is_contiguous() and dy.shape == (self.rows, self.q)
         f64 = dict(dtype=torch.float64, device=self.device)
         m, p, q, ns = self.m, self.p, self.q, self.nsys
@@ -208,7 +208,8 @@ class CascadeFunction(torch.autograd.Function):
     apply(casc, u, A, B, C, D, delta=None): with ``delta`` the system is
     continuous (A, B discretised by Eq. 4.2 on the device), otherwise A, B are
     Abar, Bbar.  ``casc`` is a Cascade plan created with
-    CASCADE_FLAG_SAVE_STATES whose batch is already set; system tensors are
+    CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE whose batch is already
+    set; system tensors are
     float64 [nsys, ...] on the plan's device.  Gradients flow to u, A (through
     the squaring chain, and the discretisation when continuous), B, C and D.
     """

@@ -99,6 +99,33 @@ bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t
   return true;
 }
 
+bool encode_tmap_3d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
+                    uint64_t S, uint64_t groups, uint32_t box_inner, uint32_t box_groups,
+                    std::string* err, int swizzle_bytes) {
+  EncodeTiledFn enc = get_encoder();
+  if (!enc) {
+    *err = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  const CUtensorMapDataType dt =
+      elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  cuuint64_t dims[3] = {inner, S, groups};
+  cuuint64_t strides[2] = {inner * (uint64_t)elem_bytes, S * inner * (uint64_t)elem_bytes};
+  cuuint32_t box[3] = {box_inner, 1, box_groups};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled (3-D) returned %d", (int)r);
+    *err = buf;
+    return false;
+  }
+  return true;
+}
+
 }  // namespace cascade
 
 using namespace cascade;
@@ -135,7 +162,26 @@ void dfree(void* ptr) {
   if (ptr) cudaFree(ptr);
 }
 
-bool saves_states(const Plan& p) { return (p.d.flags & CASCADE_FLAG_SAVE_STATES) != 0; }
+bool saves_states(const Plan& p) {
+  return (p.d.flags & CASCADE_FLAG_SAVE_STATES) != 0 && !(p.d.flags & CASCADE_FLAG_RECOMPUTE);
+}
+bool recomputes(const Plan& p) { return (p.d.flags & CASCADE_FLAG_RECOMPUTE) != 0; }
+bool scans(const Plan& p) { return (p.d.flags & CASCADE_FLAG_SCAN) != 0; }
+// The forward leaves what the backward needs (every stage output, or checkpoints).
+bool keeps_states(const Plan& p) { return saves_states(p) || recomputes(p); }
+
+// Workspace state buffer that holds v^(j) (j = 1..maxN+1, v^(j) = output of
+// stage j-1) when the forward has finished.  Two buffers alternate; with
+// CASCADE_FLAG_SAVE_STATES buffer j-1 keeps v^(j); with CASCADE_FLAG_RECOMPUTE
+// the checkpoints v^(1), v^(1+c), v^(1+2c), ... (c = ck_seg) go to buffers
+// 2, 3, ... and the other stage outputs alternate between buffers 0 and 1.
+// A sequence's rows are written only by stages k <= N_i, so its final states
+// v^(N_i+1) stay in fwd_buf(N_i+1).
+int fwd_buf(const Plan& p, int j) {
+  if (saves_states(p)) return j - 1;
+  if (recomputes(p) && j <= p.maxN && (j - 1) % p.ck_seg == 0) return 2 + (j - 1) / p.ck_seg;
+  return j & 1;
+}
 
 int ceil_log2(int64_t L) {
   int k = 0;
@@ -171,6 +217,10 @@ void free_batch(Plan* p) {
   p->n_adj_tiles.clear();
   p->saved_ws = nullptr;
   p->n_out_tiles = p->n_stage0_tiles = 0;
+  for (Plan::ScanLevel& lv : p->scan) dfree(lv.d_tiles);
+  p->scan.clear();
+  p->scan_rows_cap = 0;
+  p->matvecs = 0;
   p->have_batch = false;
   if (p->graph) {
     cudaGraphExecDestroy(p->graph);
@@ -273,7 +323,7 @@ cascade_status_t alloc_system(Plan* p) {
   CK(dalloc(&p->ABbar64, (size_t)ns * m * pp), "alloc ABbar");
   CK(dalloc(&p->C64, (size_t)ns * q * m), "alloc C");
   CK(dalloc(&p->D64, (size_t)ns * q * pp), "alloc D");
-  if (saves_states(*p)) {   // the adjoint stages use the transposed powers
+  if (keeps_states(*p)) {   // the adjoint stages use the transposed powers
     CK(dalloc(&p->PT64, (size_t)ns * p->kmax1 * mm), "alloc transposed powers");
     if (p->d.precision != CASCADE_FP64) {
       CK(dalloc(&p->P32, (size_t)ns * p->kmax1 * mm), "alloc FP32 powers");
@@ -318,16 +368,20 @@ struct Layout {
 Layout layout(const Plan& p) {
   Layout L;
   const int nplanes = p.d.precision == CASCADE_FP64 ? 1 : 2;
-  L.plane = align256((size_t)p.rows * p.d.m * plane_elem_bytes(p.d.precision));
+  const int64_t rows = scans(p) ? p.scan_rows_cap : p.rows;
+  L.plane = align256((size_t)rows * p.d.m * plane_elem_bytes(p.d.precision));
   L.buf_stride = nplanes * L.plane;
   L.lo_off = nplanes == 2 ? L.plane : 0;
-  const bool save = saves_states(p);
-  L.nV = save ? std::max(p.maxN + 1, 1) : 2;
+  const bool save = keeps_states(p);
+  if (saves_states(p)) L.nV = std::max(p.maxN + 1, 1);
+  else if (recomputes(p)) L.nV = 2 + p.n_ck + std::max(0, p.ck_seg - 3);   // + segment buffers
+  else if (scans(p)) L.nV = 1;                                               // in place
+  else L.nV = 2;
   size_t off = (size_t)L.nV * L.buf_stride;
   if (save) {
     const size_t m = p.d.m, pp = p.d.p, q = p.d.q, ns = p.d.nsys;
     const size_t acc = p.d.precision == CASCADE_FP64 ? 8 : 4;
-    const size_t elems = std::max(std::max(m * m, q * m), std::max(q * pp, m * pp));
+    const size_t elems = std::max(std::max(m * m, q * m), std::max(q * pp, 2 * m * pp));
     L.off_W = off;
     off += 2 * L.buf_stride;
     L.off_part = off;
@@ -358,18 +412,41 @@ cudaError_t ensure_events(Plan* p, int pairs) {
 cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStream_t st) {
   const Layout L = layout(*p);
   const Bufs V{static_cast<uint8_t*>(ws), L.buf_stride, L.lo_off};
-  const bool save = saves_states(*p);
+  const bool save = keeps_states(*p);
   const bool timing = p->timing;
   if (timing) {
-    CK(ensure_events(p, std::max(p->maxN, 1)), "timing events");
+    CK(ensure_events(p, std::max(std::max(p->maxN, 1), (int)p->scan.size())), "timing events");
     p->ev_k.clear();
     p->n_ev = 0;
   }
+  if (scans(*p)) {
+    // work-efficient schedule, in place on buffer 0: the first up-sweep level
+    // with the input projection, the other levels on the tensor cores, then
+    // y = C x + D u for every row
+    CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, 0, true, st), "first level");
+    for (const Plan::ScanLevel& lv : p->scan) {
+      if (timing && lv.n > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
+      CK(launch_stage_tc_strided(*p, lv.k, 2 << lv.k, lv.d_tiles, lv.n,
+                                 (uint64_t)p->scan_rows_cap, V.hi(0), V.lo(0), st),
+         "scan level");
+      if (timing && lv.n > 0) {
+        CK(cudaEventRecord(p->ev[2 * p->n_ev + 1], st), "event");
+        p->ev_k.push_back(lv.down ? 100 + lv.k : lv.k);
+        p->n_ev++;
+      }
+    }
+    CK(launch_proj_output(*p, static_cast<const float*>(u), static_cast<float*>(y), V, st),
+       "output projection");
+    return CASCADE_OK;
+  }
   // buffer holding v^(k) read by stage k, and the one stage k writes
-  auto in_buf = [&](int k) { return save ? k - 1 : (k & 1); };
-  auto out_buf = [&](int k) { return save ? k : ((k + 1) & 1); };
+  auto in_buf = [&](int k) { return fwd_buf(*p, k); };
+  auto out_buf = [&](int k) { return fwd_buf(*p, k + 1); };
   // stage 0 fused with v^(0) = Bbar u
-  CK(launch_stage0(*p, u, V.hi(out_buf(0)), V.lo(out_buf(0)), st), "first stage");
+  if (proj_supported(*p))
+    CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), false, st), "first stage");
+  else
+    CK(launch_stage0(*p, u, V.hi(out_buf(0)), V.lo(out_buf(0)), st), "first stage");
   for (int k = 1; k <= p->maxN; ++k) {
     const int in = in_buf(k), out = out_buf(k);
     if (timing && p->n_tiles[k] > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
@@ -388,7 +465,11 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
       p->n_ev++;
     }
   }
-  CK(launch_output(*p, u, y, V, st), "output projection");
+  if (proj_supported(*p))
+    CK(launch_proj_output(*p, static_cast<const float*>(u), static_cast<float*>(y), V, st),
+       "output projection");
+  else
+    CK(launch_output(*p, u, y, V, st), "output projection");
   if (save) {
     p->saved_ws = ws;
     p->saved_batch = p->batch_id;
@@ -455,31 +536,53 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   auto sysbeg = [&](int li) { return p->d_chunk_data + p->chunk_lists[li].off_begin; };
   const int nall = p->chunk_lists[0].n;
 
+  const bool proj = proj_supported(*p);
+
+  // dC = sum G v^(N+1)^T: v^(N_i+1) sits in state buffer tile.fbuf.  This runs
+  // first: with checkpoints, the recomputation below reuses those buffers.
+  if (dC) {
+    const TSrc VF{0, V, 1, 0, nullptr, 0};
+    if (wtreduce_supported(*p, m, q, 1))
+      CK(launch_wtreduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), VF, m, dy, q, 1, 0, 0,
+                         true, part, dC, true, (int64_t)q * m, 0, st),
+         "dC");
+    else
+      CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q, VF, m, 0, part, dC,
+                        true, (int64_t)q * m, 0, st),
+         "dC");
+  }
+  if (dD) {   // dD = sum G u^T
+    if (wtreduce_supported(*p, q, pp, 1))
+      CK(launch_wtreduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q, u, pp, 1, 0, 0,
+                         false, part, dD, true, (int64_t)q * pp, 0, st),
+         "dD");
+    else
+      CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q, U, pp, 0, part, dD,
+                        true, (int64_t)q * pp, 0, st),
+         "dD");
+  }
   // W^(N_i+1) = C^T G, in the adjoint buffer the stage N_i reads
-  CK(launch_adj_init(*p, dy, W, st), "adjoint init");
-  if (dC)   // dC = sum G v^(N+1)^T; v^(N_i+1) sits in state buffer N_i (tile.flags)
-    CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q,
-                      TSrc{0, V, 1, 0, nullptr, 0}, m, 0, part, dC, true, (int64_t)q * m, 0, st),
-       "dC");
-  if (dD)
-    CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q, U, pp, 0, part, dD,
-                      true, (int64_t)q * pp, 0, st),
-       "dD");
+  if (proj)
+    CK(launch_proj_adj_init(*p, static_cast<const float*>(dy), W, st), "adjoint init");
+  else
+    CK(launch_adj_init(*p, dy, W, st), "adjoint init");
   CK(cudaMemsetAsync(dP, 0, sizeof(T) * ns * kst, st), "zero dP");
-  for (int k = p->maxN; k >= 1; --k) {
+
+  // Adjoint of stage k (k >= 1) given v^(k) in state buffer vb:
+  //   dP_k = sum_{l >= s} W^(k+1)_l v^(k)_(l-s)^T,  W^(k) = W^(k+1) + P_k^T shift(W^(k+1)).
+  auto back_stage = [&](int k, int vb) -> cascade_status_t {
     const int win = (k + 1) & 1, wout = k & 1;
     const ChunkList& cl = p->chunk_lists[k];
-    // dP_k = sum_{l >= s} W^(k+1)_l v^(k)_(l-s)^T; v^(k) is state buffer k-1
     if (grad_tc_supported(*p)) {   // tensor cores, then the ordered per-system reduction
-      CK(launch_grad_tc(*p, p->d_tiles[k], chunks(k), cl.n, W.hi(win), W.lo(win), V.hi(k - 1),
-                        V.lo(k - 1), 1 << k, static_cast<float*>(part), st),
+      CK(launch_grad_tc(*p, p->d_tiles[k], chunks(k), cl.n, W.hi(win), W.lo(win), V.hi(vb),
+                        V.lo(vb), 1 << k, static_cast<float*>(part), st),
          "dP (tensor core)");
       CK(launch_reduce_partials(*p, static_cast<const float*>(part), sysbeg(k), mm,
                                 dP + (int64_t)k * mm, tf64, kst, st),
          "dP reduction");
     } else {
       CK(launch_treduce(*p, p->d_tiles[k], chunks(k), cl.n, sysbeg(k),
-                        TSrc{0, W, 0, win, nullptr, 0}, m, TSrc{0, V, 0, k - 1, nullptr, 0}, m,
+                        TSrc{0, W, 0, win, nullptr, 0}, m, TSrc{0, V, 0, vb, nullptr, 0}, m,
                         1 << k, part, dP + (int64_t)k * mm, tf64, kst, 0, st),
          "dP");
     }
@@ -492,16 +595,76 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
                          st, true),
          "adjoint stage (tensor core)");
     }
+    return CASCADE_OK;
+  };
+  // forward stage k from buffer a to buffer b (recomputation; no output projection)
+  auto fwd_stage = [&](int k, int a, int b) -> cascade_status_t {
+    if (f64)
+      CK(launch_stage_f64(*p, k, static_cast<const double*>(V.hi(a)),
+                          static_cast<double*>(V.hi(b)), st),
+         "recomputed stage (fp64)");
+    else
+      CK(launch_stage_tc(*p, k, V.hi(a), V.lo(a), V.hi(b), V.lo(b), nullptr, nullptr, st),
+         "recomputed stage (tensor core)");
+    return CASCADE_OK;
+  };
+  if (!recomputes(*p)) {
+    for (int k = p->maxN; k >= 1; --k) {   // v^(k) is state buffer k-1
+      const cascade_status_t r = back_stage(k, k - 1);
+      if (r != CASCADE_OK) return r;
+    }
+  } else {
+    // Segments of c stages from the last checkpoint down: recompute v^(a+1) ..
+    // v^(top) from the checkpoint v^(a) into buffers 0, 1, 2 + n_ck, ..., then
+    // run their adjoint stages top .. a.
+    const int c = p->ck_seg;
+    for (int sgi = p->n_ck - 1; sgi >= 0; --sgi) {
+      const int a = 1 + sgi * c;
+      const int top = std::min(a + c - 1, p->maxN);
+      auto buf_of = [&](int j) {
+        if (j == a) return 2 + sgi;
+        const int i = j - a - 1;
+        return i < 2 ? i : 2 + p->n_ck + (i - 2);
+      };
+      for (int k = a; k < top; ++k) {
+        const cascade_status_t r = fwd_stage(k, buf_of(k), buf_of(k + 1));
+        if (r != CASCADE_OK) return r;
+      }
+      for (int k = top; k >= a; --k) {
+        const cascade_status_t r = back_stage(k, buf_of(k));
+        if (r != CASCADE_OK) return r;
+      }
+    }
   }
   // first stage (fused with Bbar u): W^(1) is adjoint buffer 1
-  if (du) CK(launch_stage0_adj(*p, dy, W, 1, du, st), "du");
+  if (du) {
+    if (proj)
+      CK(launch_proj_du(*p, static_cast<const float*>(dy), W, 1, static_cast<float*>(du), st),
+         "du");
+    else
+      CK(launch_stage0_adj(*p, dy, W, 1, du, st), "du");
+  }
+  // R1 = sum W^(1)_l u_l^T,  R2 = sum W^(1)_l u_(l-1)^T
   const TSrc W1{0, W, 0, 1, nullptr, 0};
-  CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, U, pp, 0, part, R1,
-                    tf64, mp, 0, st),
-     "R1");
-  CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, U, pp, 1, part, R2,
-                    tf64, mp, 0, st),
-     "R2");
+  if (wtreduce_supported(*p, m, pp, 2)) {
+    CK(launch_wtreduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, u, pp, 2, 0, 1,
+                       false, part, R1, tf64, mp, (int64_t)ns * mp, st),
+       "R1, R2");
+  } else if (wtreduce_supported(*p, m, pp, 1)) {
+    CK(launch_wtreduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, u, pp, 1, 0, 0,
+                       false, part, R1, tf64, mp, 0, st),
+       "R1");
+    CK(launch_wtreduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, u, pp, 1, 1, 0,
+                       false, part, R2, tf64, mp, 0, st),
+       "R2");
+  } else {
+    CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, U, pp, 0, part, R1,
+                      tf64, mp, 0, st),
+       "R1");
+    CK(launch_treduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, U, pp, 1, part, R2,
+                      tf64, mp, 0, st),
+       "R2");
+  }
   // dP_0 += R2 Bbar^T;  dBbar = R1 + Abar^T R2
   CK(gemm_t(R2, Bbar, dP, m, m, pp, pp, pp, m, mp, mp, kst, ns, 1.0, 1.0, false, true, st), "dP0");
   CK(cudaMemcpyAsync(dBb, R1, sizeof(T) * ns * mp, cudaMemcpyDeviceToDevice, st), "copy");
@@ -597,6 +760,14 @@ cascade_status_t cascade_plan_create(cascade_plan_t* out, const cascade_desc_t* 
     return fail(p, CASCADE_ERR_INVALID_ARG, "unknown precision");
   if (d.N < -1 || d.N > 40) return fail(p, CASCADE_ERR_INVALID_ARG, "N must be in -1..40");
   if (d.N < 0 && !(d.eps >= 0.0)) return fail(p, CASCADE_ERR_INVALID_ARG, "eps must be >= 0");
+  if ((d.flags & CASCADE_FLAG_SCAN) &&
+      (d.flags & (CASCADE_FLAG_SAVE_STATES | CASCADE_FLAG_RECOMPUTE)))
+    return fail(p, CASCADE_ERR_INVALID_ARG,
+                "the work-efficient schedule (CASCADE_FLAG_SCAN) has no backward: it cannot "
+                "keep stage outputs");
+  if ((d.flags & CASCADE_FLAG_SCAN) && d.precision == CASCADE_FP64)
+    return fail(p, CASCADE_ERR_UNSUPPORTED,
+                "the work-efficient schedule runs on the tensor-core precisions only");
   if (d.precision != CASCADE_FP64) {
     const int kc = d.precision == CASCADE_BF16_SPLIT ? 64 : 32;
     if (d.m % kc != 0 || d.m > 4096 || block_n(d.m, d.precision) == 0)
@@ -619,9 +790,11 @@ cascade_status_t cascade_plan_create(cascade_plan_t* out, const cascade_desc_t* 
   }
   const int Nmax = std::max(0, ceil_log2(d.max_len) - 1);
   p->kmax1 = (d.N >= 0) ? std::min(d.N, Nmax) + 1 : Nmax + 2;
+  // y = C v + D u in the last stage's epilogue: one thread per row forms q dot
+  // products of length m, which pays for q <= 4; wider outputs go to the
+  // separate output GEMM
   p->fuse_output = d.precision != CASCADE_FP64 && !(d.flags & CASCADE_FLAG_NO_FUSED_OUTPUT) &&
-                   !(d.flags & CASCADE_FLAG_SAVE_STATES) && block_n(d.m, d.precision) == d.m &&
-                   d.q <= 16;
+                   block_n(d.m, d.precision) == d.m && d.q <= 4;
   e = cudaMalloc(&p->err, 8 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(p->err, 0, 8 * sizeof(int32_t));
   if (e != cudaSuccess) {
@@ -768,7 +941,7 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
   p->sys_of_seq.assign(nseq, 0);
   if (h_sys_of_seq) p->sys_of_seq.assign(h_sys_of_seq, h_sys_of_seq + nseq);
   p->seq_N.assign(nseq, -1);
-  const bool save = saves_states(*p);
+  const bool save = keeps_states(*p);
   const int BM = tile_rows(*p);
   int maxN = -1;
   std::vector<Tile> t0s, outs, all;
@@ -787,27 +960,107 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     }
   }
   p->maxN = maxN;
+  // products by powers: the Abar Bbar u term of the first stage on every row
+  // l >= 1 (odd rows only in the work-efficient schedule), then the stages
+  p->matvecs = 0;
+  for (int i = 0; i < nseq; ++i) {
+    const int64_t L = h_offsets[i + 1] - h_offsets[i];
+    if (L == 0) continue;
+    const int N = p->seq_N[i];
+    if (scans(*p)) {
+      if (N < ceil_log2(L) - 1) {
+        free_batch(p);
+        return fail(p, CASCADE_ERR_UNSUPPORTED,
+                    "the work-efficient schedule needs 2^(N+1) >= L for every sequence "
+                    "(truncated cascades use the stage schedule)");
+      }
+      p->matvecs += L / 2;
+    } else {
+      for (int k = 0; k <= N; ++k) p->matvecs += std::max<int64_t>(L - (int64_t(1) << k), 0);
+    }
+  }
+  if (scans(*p)) {
+    // Up-sweep level k (k = 1..K-1): rows l = (j+1) 2^(k+1) - 1 gain
+    // Abar^(2^k) v_(l - 2^k); level 0 is the first-stage projection.
+    // Down-sweep level k (k = K-2..0): rows l = (j+1) 2^(k+1) + 2^k - 1 gain
+    // Abar^(2^k) v_(l - 2^k), whose prefix is complete.  One launch per level,
+    // tiles of up to BM rows 2^(k+1) apart.
+    const int K = maxN + 1;     // levels of the longest sequence
+    int64_t cap = std::max<int64_t>(rows, 1);
+    const int64_t Smax = int64_t(1) << std::max(K, 1);
+    cap = (cap + Smax - 1) / Smax * Smax;
+    if (cap >= (int64_t(1) << 31)) {
+      free_batch(p);
+      return fail(p, CASCADE_ERR_UNSUPPORTED, "rows rounded up to 2^K must stay below 2^31");
+    }
+    p->scan_rows_cap = cap;
+    auto level = [&](int k, bool down) -> cascade_status_t {
+      std::vector<Tile> tl;
+      const int64_t S = int64_t(2) << k, d = down ? (int64_t(1) << k) : 0;
+      for (int i = 0; i < nseq; ++i) {
+        const int64_t L = h_offsets[i + 1] - h_offsets[i];
+        const int64_t cnt = L > d ? (L - d) / S : 0;
+        p->matvecs += cnt;
+        for (int64_t j0 = 0; j0 < cnt; j0 += BM) {
+          const int64_t R0 = h_offsets[i] + (j0 + 1) * S - 1 + d;
+          tl.push_back(Tile{R0, 0, (int32_t)std::min<int64_t>(BM, cnt - j0), p->sys_of_seq[i], 0,
+                            0, 0});
+        }
+      }
+      Plan::ScanLevel lv{k, down ? 1 : 0, (int)tl.size(), nullptr};
+      if (!tl.empty()) {
+        CK(cudaMalloc(&lv.d_tiles, tl.size() * sizeof(Tile)), "alloc scan schedule");
+        CK(cudaMemcpy(lv.d_tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice),
+           "upload scan schedule");
+      }
+      p->scan.push_back(lv);
+      return CASCADE_OK;
+    };
+    for (int k = 1; k <= K - 1; ++k) {
+      const cascade_status_t r = level(k, false);
+      if (r != CASCADE_OK) return r;
+    }
+    for (int k = K - 2; k >= 0; --k) {
+      const cascade_status_t r = level(k, true);
+      if (r != CASCADE_OK) return r;
+    }
+  }
+  if (recomputes(*p)) {
+    // segment length c: fewest state buffers 2 + ceil(maxN / c) + max(0, c - 3),
+    // ties to the smaller c (more checkpoints, fewer recomputed stages)
+    p->ck_seg = 2;
+    int best = 1 << 30;
+    for (int c = 2; c <= std::max(2, maxN); ++c) {
+      const int nb = 2 + (std::max(maxN, 1) + c - 1) / c + std::max(0, c - 3);
+      if (nb < best) { best = nb; p->ck_seg = c; }
+    }
+    p->n_ck = maxN >= 1 ? (maxN + p->ck_seg - 1) / p->ck_seg : 0;
+  } else {
+    p->ck_seg = 0;
+    p->n_ck = 0;
+  }
+  for (Tile& t : all) t.fbuf = fwd_buf(*p, t.flags + 1);
   p->h_tiles.assign(std::max(maxN + 1, 1), {});
   for (int i = 0; i < nseq; ++i) {
     const int64_t L = h_offsets[i + 1] - h_offsets[i];
     if (L == 0) continue;
     const int N = p->seq_N[i], sys = p->sys_of_seq[i];
-    const bool fused_last = p->fuse_output && N >= 1;
-    for (int k = 1; k <= N; ++k) {
+    const bool fused_last = p->fuse_output && N >= 1 && !scans(*p);
+    for (int k = 1; k <= N && !scans(*p); ++k) {   // stage schedule (§3)
       const bool fused = fused_last && k == N;
       const int64_t prev_shift = int64_t(1) << (k - 1);
       for (int64_t t = 0; t < L; t += BM) {
         // Ping-pong buffers: rows below 2^(k-1) already hold their final value in the
-        // output buffer.  Kept stage outputs: every stage writes every row.
+        // output buffer.  Kept stage outputs or checkpoints: every stage writes every row.
         if (!save && !fused && k >= 2 && t + BM <= prev_shift) continue;
         p->h_tiles[k].push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys,
                                      fused ? (int32_t)TILE_FINAL_FUSED : 0, 0, 0});
       }
     }
-    if (!fused_last) {   // flags: state buffer holding v^(N+1)
-      const int buf = save ? N : ((N + 1) & 1);
+    if (!fused_last) {   // fbuf: state buffer holding v^(N+1)
+      const int buf = scans(*p) ? 0 : fwd_buf(*p, N + 1);
       for (int64_t t = 0; t < L; t += BM)
-        outs.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, buf, 0, 0});
+        outs.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, 0, buf, 0});
     }
   }
   auto upload = [&](const std::vector<Tile>& v, Tile** d) -> cudaError_t {
@@ -887,6 +1140,14 @@ cascade_status_t cascade_get_seq_N(cascade_plan_t plan, int32_t* h_N) {
   return CASCADE_OK;
 }
 
+cascade_status_t cascade_get_matvec_count(cascade_plan_t plan, int64_t* h_count) {
+  Plan* p = plan;
+  if (!p || !h_count) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  if (!p->have_batch) return fail(p, CASCADE_ERR_STATE, "no batch set");
+  *h_count = p->matvecs;
+  return CASCADE_OK;
+}
+
 cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes) {
   Plan* p = plan;
   if (!p || !bytes) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
@@ -937,6 +1198,10 @@ cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y
       p->graph_batch_id = p->batch_id;
     }
     CK(cudaGraphLaunch(p->graph, st), "graph launch");
+    if (keeps_states(*p)) {
+      p->saved_ws = d_workspace;
+      p->saved_batch = p->batch_id;
+    }
     return CASCADE_OK;
   }
   return run_forward(p, d_u, d_y, d_workspace, st);
@@ -948,8 +1213,9 @@ cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_u, const vo
                                   size_t workspace_bytes, void* stream) {
   Plan* p = plan;
   if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
-  if (!saves_states(*p))
-    return fail(p, CASCADE_ERR_STATE, "backward needs a plan created with CASCADE_FLAG_SAVE_STATES");
+  if (!keeps_states(*p))
+    return fail(p, CASCADE_ERR_STATE,
+                "backward needs a plan created with CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE");
   if (!p->have_system || !p->have_batch) return fail(p, CASCADE_ERR_STATE, "system and batch must be set");
   if (p->rows == 0) return CASCADE_OK;
   if (!d_u || !d_dy || !d_workspace) return fail(p, CASCADE_ERR_INVALID_ARG, "u, dy, workspace required");
@@ -958,7 +1224,11 @@ cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_u, const vo
   if (workspace_bytes < layout(*p).total) return fail(p, CASCADE_ERR_INVALID_ARG, "workspace too small");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   p->last_stream = stream;
-  return run_backward(p, d_u, d_dy, d_du, d_dAbar, d_dBbar, d_dC, d_dD, d_dA, d_dB, d_workspace, st);
+  const cascade_status_t r =
+      run_backward(p, d_u, d_dy, d_du, d_dAbar, d_dBbar, d_dC, d_dD, d_dA, d_dB, d_workspace, st);
+  // recomputation reuses the buffers of the forward's final states
+  if (recomputes(*p)) p->saved_ws = nullptr;
+  return r;
 }
 
 cascade_status_t cascade_recursion_forward(cascade_plan_t plan, const double* d_u, double* d_y,

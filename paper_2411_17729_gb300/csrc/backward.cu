@@ -36,7 +36,7 @@ __device__ __forceinline__ typename Acc<FMT>::type src_get(const TSrc& s, const 
   typedef typename Acc<FMT>::type A;
   if (s.kind == 1) return (A) static_cast<const float*>(s.dense)[row * s.ld + col];
   if (s.kind == 2) return (A) static_cast<const double*>(s.dense)[row * s.ld + col];
-  const int b = s.buf_mode ? t.flags : s.buf_fixed;
+  const int b = s.buf_mode ? t.fbuf : s.buf_fixed;
   return load_elem<FMT>(s.bufs.hi(b), s.bufs.lo(b), row * m + col);
 }
 
@@ -101,23 +101,165 @@ __global__ void __launch_bounds__(256) treduce_kernel(const Tile* __restrict__ t
 }
 
 // out[s][e] (+)= sum over the chunks of system s, in order, of partial[chunk][e].
+// A chunk's partial may hold several outputs back to back (seg elements each);
+// output h of system s starts at out + h * seg_stride + s * out_sys_stride.
 template <typename ACC, typename OUT>
 __global__ void reduce_partials_kernel(const ACC* __restrict__ partial,
                                        const int32_t* __restrict__ sys_begin, int64_t elems,
                                        OUT* __restrict__ out, int64_t out_sys_stride,
-                                       int accumulate) {
+                                       int64_t seg, int64_t seg_stride, int accumulate) {
   const int s = blockIdx.y;
   const int c0 = sys_begin[s], c1 = sys_begin[s + 1];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < elems;
        e += (int64_t)gridDim.x * blockDim.x) {
     OUT v = 0;
     for (int c = c0; c < c1; ++c) v += (OUT)partial[(int64_t)c * elems + e];
-    OUT* o = out + (int64_t)s * out_sys_stride + e;
+    const int64_t h = e / seg;
+    OUT* o = out + h * seg_stride + (int64_t)s * out_sys_stride + (e - h * seg);
     *o = accumulate ? *o + v : v;
   }
 }
 
-// W^(N+1)_l = C^T G_l into buffer (N_i + 1) & 1 (tile.flags = N_i); thread per (row, column).
+// Vector loads of CPT consecutive entries of a state row (CPT * element size
+// is 4, 8, 16 or 32 bytes and the address is aligned to it).
+template <int BYTES>
+__device__ __forceinline__ void ld_words(const void* p, uint32_t* w) {
+  if constexpr (BYTES == 4) {
+    w[0] = *static_cast<const uint32_t*>(p);
+  } else if constexpr (BYTES == 8) {
+    const uint2 v = *static_cast<const uint2*>(p);
+    w[0] = v.x; w[1] = v.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < BYTES / 16; ++i) {
+      const uint4 v = static_cast<const uint4*>(p)[i];
+      w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+    }
+  }
+}
+template <int FMT, int CPT>
+__device__ __forceinline__ void load_row_vec(const void* hi, const void* lo, int64_t idx,
+                                             float* out) {
+  if constexpr (FMT == FMT_BF16) {
+    uint32_t h[CPT / 2], l[CPT / 2];
+    ld_words<CPT * 2>(static_cast<const __nv_bfloat16*>(hi) + idx, h);
+    ld_words<CPT * 2>(static_cast<const __nv_bfloat16*>(lo) + idx, l);
+#pragma unroll
+    for (int i = 0; i < CPT / 2; ++i) {
+      // a BF16 value is the top half of the FP32 with the same bits
+      out[2 * i] = __uint_as_float(h[i] << 16) + __uint_as_float(l[i] << 16);
+      out[2 * i + 1] = __uint_as_float(h[i] & 0xffff0000u) + __uint_as_float(l[i] & 0xffff0000u);
+    }
+  } else {
+    uint32_t h[CPT], l[CPT];
+    ld_words<CPT * 4>(static_cast<const float*>(hi) + idx, h);
+    ld_words<CPT * 4>(static_cast<const float*>(lo) + idx, l);
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) out[i] = __uint_as_float(h[i]) + __uint_as_float(l[i]);
+  }
+}
+
+// Wide-by-thin time reduction, for the products whose one side is narrow
+// (p or q columns): for h < nsh and every row l of the chunk's tiles,
+//   partial[chunk][h] += X_l (outer) T_(l - sh_h),
+// X a state buffer or dense array with `a` columns, T dense [rows, ld] with tc
+// columns (zero before the sequence start).  Each (chunk, h) block is stored
+// [tc][a] if thin_major, else [a][tc].  Threads own CPT consecutive columns
+// of X and all TT = nsh * tc thin columns; 256 / G rows are processed at once
+// (G threads per row), and the row groups are summed in a fixed order, so the
+// result is deterministic.
+constexpr int WT_SMEM_BYTES = 32768;
+template <int FMT, typename ACC, int CPT, int TT>
+__global__ void __launch_bounds__(256) wtreduce_kernel(const Tile* __restrict__ tiles,
+                                                       const int32_t* __restrict__ chunks, int BM,
+                                                       int m, TSrc X, int a,
+                                                       const ACC* __restrict__ T, int ld, int tc,
+                                                       int nsh, int sh0, int sh1, int gshift,
+                                                       int vec, int thin_major,
+                                                       ACC* __restrict__ partial) {
+  __shared__ __align__(16) unsigned char red_raw[WT_SMEM_BYTES];
+  ACC* red = reinterpret_cast<ACC*>(red_raw);
+  const int c = blockIdx.x;
+  const int first = chunks[3 * c], count = chunks[3 * c + 1];
+  const int G = 1 << gshift, R = 256 >> gshift;
+  const int g = threadIdx.x & (G - 1), rg = threadIdx.x >> gshift;
+  const int i0 = g * CPT;
+  const int tt = nsh * tc;
+  ACC acc[CPT][TT];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i)
+#pragma unroll
+    for (int e = 0; e < TT; ++e) acc[i][e] = 0;
+  for (int ti = first; ti < first + count; ++ti) {
+    const Tile t = tiles[ti];
+    const int rows = min(BM, t.len - t.t0);
+    for (int rr = rg; rr < rows; rr += R) {
+      const int l = t.t0 + rr;
+      const int64_t row = t.seq_row0 + l;
+      ACC tv[TT];
+#pragma unroll
+      for (int e = 0; e < TT; ++e) {
+        const int h = e >= tc ? 1 : 0;
+        const int j = e - h * tc;
+        const int src = l - (h ? sh1 : sh0);
+        tv[e] = (e < tt && src >= 0) ? T[(t.seq_row0 + src) * ld + j] : (ACC)0;
+      }
+      if (i0 >= a) continue;
+      ACC xv[CPT];
+      if constexpr (FMT != FMT_F64) {
+        if (vec) {
+          const int b = X.buf_mode ? t.fbuf : X.buf_fixed;
+          float f[CPT];
+          load_row_vec<FMT, CPT>(X.bufs.hi(b), X.bufs.lo(b), row * m + i0, f);
+#pragma unroll
+          for (int i = 0; i < CPT; ++i) xv[i] = f[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < CPT; ++i)
+            xv[i] = i0 + i < a ? (ACC)src_get<FMT>(X, t, row, i0 + i, m) : (ACC)0;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < CPT; ++i)
+          xv[i] = i0 + i < a ? (ACC)src_get<FMT>(X, t, row, i0 + i, m) : (ACC)0;
+      }
+#pragma unroll
+      for (int i = 0; i < CPT; ++i)
+#pragma unroll
+        for (int e = 0; e < TT; ++e) acc[i][e] = fma(xv[i], tv[e], acc[i][e]);
+    }
+  }
+  // sum the row groups in order: red[i * tt + e]
+  for (int q = 0; q < R; ++q) {
+    if (rg == q) {
+#pragma unroll
+      for (int i = 0; i < CPT; ++i) {
+        if (i0 + i >= a) continue;
+#pragma unroll
+        for (int e = 0; e < TT; ++e) {
+          if (e >= tt) continue;
+          ACC* r = red + (int64_t)(i0 + i) * tt + e;
+          *r = (q == 0 ? (ACC)0 : *r) + acc[i][e];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t elems = (int64_t)a * tt;
+  ACC* out = partial + (int64_t)c * elems;
+  for (int64_t idx = threadIdx.x; idx < elems; idx += 256) {
+    // idx in the output layout: [h][tc][a] or [h][a][tc]
+    const int h = (int)(idx / ((int64_t)a * tc));
+    const int rem = (int)(idx - (int64_t)h * a * tc);
+    int i, j;
+    if (thin_major) { j = rem / a; i = rem - j * a; }
+    else { i = rem / tc; j = rem - i * tc; }
+    out[idx] = red[(int64_t)i * tt + h * tc + j];
+  }
+}
+
+// W^(N+1)_l = C^T G_l into adjoint buffer (N_i + 1) & 1 (tile.flags = N_i); thread per
+// (row, column).
 template <int FMT, typename T>
 __global__ void __launch_bounds__(256) adj_init_kernel(const Tile* __restrict__ tiles, int BM,
                                                        int m, int q, const T* __restrict__ G,
@@ -232,7 +374,7 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
                                                          shift, (double*)partial);
     CASCADE_LAUNCHED();
     reduce_partials_kernel<double, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-        (const double*)partial, sys_begin, elems, (double*)out, out_sys_stride, accumulate);
+        (const double*)partial, sys_begin, elems, (double*)out, out_sys_stride, elems, 0, accumulate);
   } else {
     if (p.d.precision == CASCADE_BF16_SPLIT)
       treduce_kernel<FMT_BF16, float><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
@@ -243,10 +385,96 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
     CASCADE_LAUNCHED();
     if (out_f64)
       reduce_partials_kernel<float, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-          (const float*)partial, sys_begin, elems, (double*)out, out_sys_stride, accumulate);
+          (const float*)partial, sys_begin, elems, (double*)out, out_sys_stride, elems, 0, accumulate);
     else
       reduce_partials_kernel<float, float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-          (const float*)partial, sys_begin, elems, (float*)out, out_sys_stride, accumulate);
+          (const float*)partial, sys_begin, elems, (float*)out, out_sys_stride, elems, 0, accumulate);
+  }
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+// Thread shape of the wide-by-thin reduction: CPT columns per thread for TT
+// thin columns (CPT * TT <= 32 accumulators).
+static int wt_tt(int tt) { return tt <= 4 ? 4 : tt <= 8 ? 8 : tt <= 16 ? 16 : 0; }
+static int wt_cpt(int TT) { return TT <= 4 ? 8 : TT <= 8 ? 4 : 2; }
+
+bool wtreduce_supported(const Plan& p, int a, int tc, int nsh) {
+  const int tt = nsh * tc;
+  const int TT = wt_tt(tt);
+  if (TT == 0 || nsh < 1 || nsh > 2) return false;
+  const size_t acc = p.d.precision == CASCADE_FP64 ? 8 : 4;
+  if ((size_t)a * tt * acc > (size_t)WT_SMEM_BYTES) return false;
+  return (a + wt_cpt(TT) - 1) / wt_cpt(TT) <= 256;
+}
+
+template <int FMT, typename ACC, int CPT, int TT>
+static void wt_launch(int nchunks, const Tile* tiles, const int32_t* chunks, int BM, int m,
+                      const TSrc& X, int a, const ACC* T, int ld, int tc, int nsh, int sh0,
+                      int sh1, int gshift, int vec, int thin_major, ACC* partial,
+                      cudaStream_t st) {
+  wtreduce_kernel<FMT, ACC, CPT, TT><<<nchunks, 256, 0, st>>>(
+      tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1, gshift, vec, thin_major, partial);
+}
+
+template <int FMT, typename ACC>
+static void wt_dispatch(int TT, int nchunks, const Tile* tiles, const int32_t* chunks, int BM,
+                        int m, const TSrc& X, int a, const ACC* T, int ld, int tc, int nsh,
+                        int sh0, int sh1, int gshift, int vec, int thin_major, ACC* partial,
+                        cudaStream_t st) {
+  if (TT == 4)
+    wt_launch<FMT, ACC, 8, 4>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
+                              gshift, vec, thin_major, partial, st);
+  else if (TT == 8)
+    wt_launch<FMT, ACC, 4, 8>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
+                              gshift, vec, thin_major, partial, st);
+  else
+    wt_launch<FMT, ACC, 2, 16>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
+                               gshift, vec, thin_major, partial, st);
+}
+
+cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
+                            const int32_t* sys_begin, const TSrc& X, int a, const void* T, int tc,
+                            int nsh, int sh0, int sh1, bool thin_major, void* partial, void* out,
+                            bool out_f64, int64_t out_sys_stride, int64_t seg_stride,
+                            cudaStream_t st) {
+  if (nchunks == 0) return cudaSuccess;
+  if (!wtreduce_supported(p, a, tc, nsh)) return cudaErrorInvalidValue;
+  const int BM = tile_rows(p);
+  const int TT = wt_tt(nsh * tc);
+  const int CPT = wt_cpt(TT);
+  int gshift = 0;
+  while ((1 << gshift) < (a + CPT - 1) / CPT) ++gshift;
+  // vector loads: a state buffer whose rows the column groups cover exactly
+  const int vec = (X.kind == 0 && a == p.d.m && a % CPT == 0) ? 1 : 0;
+  const int64_t elems = (int64_t)nsh * a * tc;
+  const int rblocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
+  const int64_t seg = (int64_t)a * tc;
+  if (p.d.precision == CASCADE_FP64) {
+    wt_dispatch<FMT_F64, double>(TT, nchunks, tiles, chunks, BM, p.d.m, X, a,
+                                 static_cast<const double*>(T), tc, tc, nsh, sh0, sh1, gshift, 0,
+                                 thin_major ? 1 : 0, static_cast<double*>(partial), st);
+    CASCADE_LAUNCHED();
+    reduce_partials_kernel<double, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+        (const double*)partial, sys_begin, elems, (double*)out, out_sys_stride, seg, seg_stride, 0);
+  } else {
+    if (p.d.precision == CASCADE_BF16_SPLIT)
+      wt_dispatch<FMT_BF16, float>(TT, nchunks, tiles, chunks, BM, p.d.m, X, a,
+                                   static_cast<const float*>(T), tc, tc, nsh, sh0, sh1, gshift, vec,
+                                   thin_major ? 1 : 0, static_cast<float*>(partial), st);
+    else
+      wt_dispatch<FMT_F32, float>(TT, nchunks, tiles, chunks, BM, p.d.m, X, a,
+                                  static_cast<const float*>(T), tc, tc, nsh, sh0, sh1, gshift, vec,
+                                  thin_major ? 1 : 0, static_cast<float*>(partial), st);
+    CASCADE_LAUNCHED();
+    if (out_f64)
+      reduce_partials_kernel<float, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+          (const float*)partial, sys_begin, elems, (double*)out, out_sys_stride, seg, seg_stride,
+          0);
+    else
+      reduce_partials_kernel<float, float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+          (const float*)partial, sys_begin, elems, (float*)out, out_sys_stride, seg, seg_stride,
+          0);
   }
   CASCADE_LAUNCHED();
   return cudaGetLastError();
@@ -258,10 +486,10 @@ cudaError_t launch_reduce_partials(const Plan& p, const float* partial, const in
   const int rblocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
   if (out_f64)
     reduce_partials_kernel<float, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-        partial, sys_begin, elems, (double*)out, out_sys_stride, 0);
+        partial, sys_begin, elems, (double*)out, out_sys_stride, elems, 0, 0);
   else
     reduce_partials_kernel<float, float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-        partial, sys_begin, elems, (float*)out, out_sys_stride, 0);
+        partial, sys_begin, elems, (float*)out, out_sys_stride, elems, 0, 0);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }

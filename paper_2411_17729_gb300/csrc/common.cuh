@@ -27,7 +27,8 @@ struct Tile {
   int32_t len;        // sequence length L_i
   int32_t sys;        // system index
   int32_t flags;      // TILE_FINAL_FUSED: last stage with y = Cv + Du fused
-  int32_t pad0, pad1;
+  int32_t fbuf;       // workspace state buffer that holds the sequence's final states
+  int32_t pad1;
 };
 static_assert(sizeof(Tile) == 32, "Tile is 32 bytes");
 enum { TILE_FINAL_FUSED = 1 };
@@ -55,6 +56,12 @@ struct StageArgs {
   int32_t reverse;        // 1: adjoint stage (source l + s, transposed power)
   int32_t k;              // stage index
   int32_t kmax1;          // power-table entries per system
+  int32_t keep_v;         // fused last stage also writes v (the backward reads it)
+  int32_t S;              // 0: a tile is BM consecutive rows.  S > 0 (work-efficient
+                          // schedule): a tile is BM rows S apart, tile.seq_row0 the
+                          // first destination row, tile.len the rows in the tile,
+                          // sources shift rows earlier, in place; the state maps are
+                          // 3-D (column, row in group of S, group)
   const void* vin_hi;     // residual planes (row-major [rows, m])
   const void* vin_lo;
   void* vout_hi;
@@ -131,7 +138,8 @@ struct Plan {
   std::vector<std::vector<Tile>> h_adj_tiles;   // adjoint stage k = 1..maxN (all tiles)
   std::vector<Tile*> d_adj_tiles;
   std::vector<int32_t> n_adj_tiles;
-  Tile* d_all_tiles = nullptr;               // every tile of every sequence (flags = N_i)
+  Tile* d_all_tiles = nullptr;               // every tile of every sequence (flags = N_i,
+                                             // fbuf = buffer of its final states)
   int n_all_tiles = 0;
   std::vector<ChunkList> chunk_lists;        // [0]: every tile; [k]: tiles of stage k
   int32_t* d_chunk_data = nullptr;           // chunks [n][3] (first tile, count, system) and
@@ -145,6 +153,21 @@ struct Plan {
   Tile* d_stage0_tiles = nullptr;            // tiles for the first stage (all rows)
   int n_stage0_tiles = 0;
   bool fuse_output = false;
+  // work-efficient schedule (CASCADE_FLAG_SCAN): its launches in order, each
+  // one level k of the up-sweep or the down-sweep over rows 2^(k+1) apart
+  struct ScanLevel {
+    int k;
+    int down;
+    int n;            // tiles
+    Tile* d_tiles;
+  };
+  std::vector<ScanLevel> scan;
+  int64_t scan_rows_cap = 0;     // state rows allocated (a multiple of the largest 2^(k+1))
+  int64_t matvecs = 0;           // products by powers in one forward of the batch
+  // stage-output checkpoints (CASCADE_FLAG_RECOMPUTE): v^(j) is kept for
+  // j = 1, 1 + ck_seg, 1 + 2 ck_seg, ... <= maxN; the backward recomputes the
+  // others one segment at a time
+  int ck_seg = 0, n_ck = 0;
   // tensor-core stage kernel shape: operand stages, epilogue ring slots,
   // chunks per epilogue step (0 = heuristic); set by cascade_autotune
   int tc_stages = 0, tc_ring = 0, tc_group = 0;
@@ -192,6 +215,10 @@ cudaError_t launch_stage_f64(const Plan& p, int k, const double* vin, double* vo
 cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
                             void* vout_hi, void* vout_lo, const float* u, float* y,
                             cudaStream_t st, bool reverse = false);
+// In-place stage k over rows S apart (the work-efficient schedule); the state
+// planes hold rows_cap rows, a multiple of S.
+cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,
+                                    uint64_t rows_cap, void* v_hi, void* v_lo, cudaStream_t st);
 // Workspace buffer j of a family of equally sized state buffers.
 struct Bufs {
   uint8_t* base;
@@ -208,7 +235,7 @@ cudaError_t launch_output(const Plan& p, const void* u, void* y, const Bufs& V, 
 struct TSrc {
   int kind;          // 0: workspace state buffer, 1: dense float [rows, ld], 2: dense double
   Bufs bufs;         // kind 0
-  int buf_mode;      // 0: buffer buf_fixed; 1: buffer = tile.flags
+  int buf_mode;      // 0: buffer buf_fixed; 1: buffer = tile.fbuf
   int buf_fixed;
   const void* dense; // kinds 1, 2
   int ld;
@@ -218,6 +245,23 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
                            int shift, void* partial, void* out, bool out_f64,
                            int64_t out_sys_stride, int accumulate, cudaStream_t st);
 cudaError_t launch_adj_init(const Plan& p, const void* G, const Bufs& W, cudaStream_t st);
+// Wide-by-thin time reduction (one narrow side, see backward.cu); false if the
+// shape is outside what the kernel handles (the caller then uses launch_treduce).
+bool wtreduce_supported(const Plan& p, int a, int tc, int nsh);
+cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
+                            const int32_t* sys_begin, const TSrc& X, int a, const void* T, int tc,
+                            int nsh, int sh0, int sh1, bool thin_major, void* partial, void* out,
+                            bool out_f64, int64_t out_sys_stride, int64_t seg_stride,
+                            cudaStream_t st);
+// Narrow projections as register-tiled GEMMs (proj.cu; tensor-core formats).
+bool proj_supported(const Plan& p);
+cudaError_t launch_proj_stage0(const Plan& p, const float* u, const Bufs& V, int buf,
+                               bool odd_only, cudaStream_t st);
+cudaError_t launch_proj_adj_init(const Plan& p, const float* G, const Bufs& W, cudaStream_t st);
+cudaError_t launch_proj_output(const Plan& p, const float* u, float* y, const Bufs& V,
+                               cudaStream_t st);
+cudaError_t launch_proj_du(const Plan& p, const float* G, const Bufs& W, int wbuf, float* du,
+                           cudaStream_t st);
 cudaError_t launch_reduce_partials(const Plan& p, const float* partial, const int32_t* sys_begin,
                                    int64_t elems, void* out, bool out_f64, int64_t out_sys_stride,
                                    cudaStream_t st);
@@ -256,5 +300,9 @@ TcConfig tc_default(int m, int precision);
 bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
                     uint64_t outer, uint32_t box_inner, uint32_t box_outer, std::string* err,
                     int swizzle_bytes = 128);
+// Row-major [groups * S, inner] viewed as (inner, S, groups); box (box_inner, 1, box_groups).
+bool encode_tmap_3d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
+                    uint64_t S, uint64_t groups, uint32_t box_inner, uint32_t box_groups,
+                    std::string* err, int swizzle_bytes = 128);
 
 }  // namespace cascade

@@ -198,7 +198,9 @@ __global__ void __launch_bounds__(NTH, 1)
           uint8_t* sa = smem + (size_t)stage * stage_bytes;
           uint8_t* sb = sa + 2 * a_bytes;
           // zero K rows whose W row lies past the sequence end, and whose V source
-          // lies before the sequence start
+          // lies before the sequence start.  Past the end both operands are
+          // zeroed: those V rows may belong to the next sequence, whose buffer
+          // rows need not hold finite values at this stage (0 * NaN).
           const int l0 = t.t0 + kk * BMK;
           const int wz = max(0, min(BMK, l0 + BMK - t.len));      // last wz rows of A
           const int vz = max(0, min(BMK, shift - l0));            // first vz rows of B
@@ -212,6 +214,12 @@ __global__ void __launch_bounds__(NTH, 1)
             }
             for (int e = lane; e < vz * 4 * (BN / 32) * 2; e += 32) {
               const int q4 = e & 3, r = (e >> 2) % vz, rest = (e >> 2) / vz;
+              const int b = rest % (BN / 32), plane = rest / (BN / 32);
+              uint8_t* row = sb + plane * b_bytes + b * BOX_BYTES + (r >> 3) * 512 + (r & 7) * 64;
+              reinterpret_cast<uint4*>(row)[q4] = z;
+            }
+            for (int e = lane; e < wz * 4 * (BN / 32) * 2; e += 32) {
+              const int q4 = e & 3, r = BMK - wz + ((e >> 2) % wz), rest = (e >> 2) / wz;
               const int b = rest % (BN / 32), plane = rest / (BN / 32);
               uint8_t* row = sb + plane * b_bytes + b * BOX_BYTES + (r >> 3) * 512 + (r & 7) * 64;
               reinterpret_cast<uint4*>(row)[q4] = z;

@@ -1,0 +1,366 @@
+// proj.cu -- the narrow projections around the cascade, as register-tiled
+// GEMMs on the CUDA cores (FP32 arithmetic, tensor-core state formats):
+//
+//   expand   (p or q columns -> m state columns)
+//     first stage fused with the input projection (§3, Eq. 3.2 with v^(0) = Bbar u):
+//         v^(1)_l = Bbar u_l + (Abar Bbar) u_(l-1)
+//     (the work-efficient schedule's first up-sweep level adds the second
+//     term on odd l only)
+//     adjoint seed of the backward:  W^(N+1)_l = C^T G_l
+//   contract (m state columns -> p or q columns)
+//     output projection (end of §3):            y_l  = C v_l + D u_l
+//     adjoint of the first stage:               du_l = Bbar^T W_l + (Abar Bbar)^T W_(l+1) + D^T G_l
+//
+// Coefficients are addressed through strides, M(i, j) = M[sys * ss + i * si + j * sj], so the
+// same kernels read Bbar [m,p], C [q,m] and D [q,p] as they are stored or transposed.
+// One block computes one 128-row tile of one sequence against a 64-column block
+// of the result; rows outside the sequence read as zero (x_(-1) = 0, §1).
+#include "common.cuh"
+#include "formats.cuh"
+#include "ptx.cuh"
+
+namespace cascade {
+namespace {
+
+constexpr int PBM = 128;   // rows per tile (the tensor-core tile height)
+
+struct Coef {
+  const float* M;
+  int64_t ss, si, sj;
+  __device__ __forceinline__ float at(int sys, int i, int j) const {
+    return M[(int64_t)sys * ss + (int64_t)i * si + (int64_t)j * sj];
+  }
+};
+
+// 8 FP32 values -> (hi, lo) planes of the format at element offset `off`.
+template <int FMT>
+__device__ __forceinline__ void store8(void* hi, void* lo, int64_t off, const float* v) {
+  if constexpr (FMT == FMT_BF16) {
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      const float2 hf = __bfloat1622float2(hh);
+      const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+      hw[j] = *reinterpret_cast<const uint32_t*>(&hh);
+      lw[j] = *reinterpret_cast<const uint32_t*>(&ll);
+    }
+    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(hi) + off) =
+        make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(lo) + off) =
+        make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  } else {
+    float hv[8], lv[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      hv[e] = ptx::tf32_rna(v[e]);
+      lv[e] = ptx::tf32_rna(v[e] - hv[e]);
+    }
+    float4* h = reinterpret_cast<float4*>(static_cast<float*>(hi) + off);
+    float4* l = reinterpret_cast<float4*>(static_cast<float*>(lo) + off);
+    h[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    h[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+    l[0] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+    l[1] = make_float4(lv[4], lv[5], lv[6], lv[7]);
+  }
+}
+
+// 8 consecutive state entries (hi + lo) as FP32.
+template <int FMT>
+__device__ __forceinline__ void load8(const void* hi, const void* lo, int64_t off, float* v) {
+  if constexpr (FMT == FMT_BF16) {
+    const uint4 h = *reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(hi) + off);
+    const uint4 l = *reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(lo) + off);
+    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      // a BF16 value is the upper half of the FP32 with the same bits
+      v[2 * j] = __uint_as_float(hw[j] << 16) + __uint_as_float(lw[j] << 16);
+      v[2 * j + 1] = __uint_as_float(hw[j] & 0xffff0000u) + __uint_as_float(lw[j] & 0xffff0000u);
+    }
+  } else {
+    const float4* h = reinterpret_cast<const float4*>(static_cast<const float*>(hi) + off);
+    const float4* l = reinterpret_cast<const float4*>(static_cast<const float*>(lo) + off);
+    const float4 h0 = h[0], h1 = h[1], l0 = l[0], l1 = l[1];
+    v[0] = h0.x + l0.x; v[1] = h0.y + l0.y; v[2] = h0.z + l0.z; v[3] = h0.w + l0.w;
+    v[4] = h1.x + l1.x; v[5] = h1.y + l1.y; v[6] = h1.z + l1.z; v[7] = h1.w + l1.w;
+  }
+}
+
+// ------------------------------------------------------------------ expand
+// out_l[c] = sum_j M1(c, j) X_l[j] (+ sum_j M2(c, j) X_(l-1)[j], on odd l only if
+// odd_only),  c < m, j < px.  Thread (cg, rg): columns c0 + 8 cg .. +8, rows
+// rg + 32 i (i < 4); tiles start at even l, so l has the parity of rg.
+constexpr int EKC = 32;
+template <int FMT, bool TWO>
+__global__ void __launch_bounds__(256) expand_kernel(const Tile* __restrict__ tiles, int m, int px,
+                                                     const float* __restrict__ X, int ldx,
+                                                     Coef M1, Coef M2, Bufs out, int buf_mode,
+                                                     int buf_fixed, int odd_only) {
+  __shared__ float Xs[PBM + 1][EKC + 1];        // row 0: time t0 - 1
+  __shared__ __align__(16) float M1s[EKC][64];
+  __shared__ __align__(16) float M2s[TWO ? EKC : 1][64];
+  const Tile t = tiles[blockIdx.x];
+  const int c0 = blockIdx.y * 64;
+  const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;
+  const bool second = TWO && (!odd_only || ((t.t0 + rg) & 1) != 0);
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[i][e] = 0.f;
+  for (int j0 = 0; j0 < px; j0 += EKC) {
+    const int kc = min(EKC, px - j0);
+    for (int e = threadIdx.x; e < (PBM + 1) * EKC; e += 256) {
+      const int r = e / EKC, jj = e - r * EKC;
+      const int tm = t.t0 - 1 + r;
+      float v = 0.f;
+      if (jj < kc && tm >= 0 && tm < t.len) v = X[(t.seq_row0 + tm) * ldx + j0 + jj];
+      Xs[r][jj] = v;
+    }
+    for (int e = threadIdx.x; e < EKC * 64; e += 256) {
+      const int jj = e >> 6, cc = e & 63;
+      const bool ok = jj < kc && c0 + cc < m;
+      M1s[jj][cc] = ok ? M1.at(t.sys, c0 + cc, j0 + jj) : 0.f;
+      if (TWO) M2s[jj][cc] = ok ? M2.at(t.sys, c0 + cc, j0 + jj) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < kc; ++jj) {
+      float b1[8], b2[8];
+      const float4 p0 = *reinterpret_cast<const float4*>(&M1s[jj][cg * 8]);
+      const float4 p1 = *reinterpret_cast<const float4*>(&M1s[jj][cg * 8 + 4]);
+      b1[0] = p0.x; b1[1] = p0.y; b1[2] = p0.z; b1[3] = p0.w;
+      b1[4] = p1.x; b1[5] = p1.y; b1[6] = p1.z; b1[7] = p1.w;
+      if (TWO) {
+        const float4 q0 = *reinterpret_cast<const float4*>(&M2s[jj][cg * 8]);
+        const float4 q1 = *reinterpret_cast<const float4*>(&M2s[jj][cg * 8 + 4]);
+        b2[0] = q0.x; b2[1] = q0.y; b2[2] = q0.z; b2[3] = q0.w;
+        b2[4] = q1.x; b2[5] = q1.y; b2[6] = q1.z; b2[7] = q1.w;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = rg + 32 * i;
+        const float x1 = Xs[r + 1][jj];
+        const float x0 = second ? Xs[r][jj] : 0.f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          acc[i][e] = fmaf(b1[e], x1, acc[i][e]);
+          if (TWO) acc[i][e] = fmaf(b2[e], x0, acc[i][e]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int c = c0 + cg * 8;
+  if (c >= m) return;
+  const int b = buf_mode ? ((t.flags + 1) & 1) : buf_fixed;
+  void* hi = out.hi(b);
+  void* lo = out.lo(b);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = rg + 32 * i;
+    if (t.t0 + r >= t.len) continue;
+    store8<FMT>(hi, lo, (t.seq_row0 + t.t0 + r) * (int64_t)m + c, acc[i]);
+  }
+}
+
+// ------------------------------------------------------------------ contract
+// out_l[j] = sum_c M1(j, c) V_l[c] (+ sum_c M2(j, c) V_(l+1)[c]) + sum_i M3(j, i) X_l[i],
+// j < nout, c < m, i < px.  The K loop runs over the m state columns, then over
+// the px dense columns.  Thread (cg, rg): rows 4 rg .. +4, columns j0 + CT cg .. +CT.
+constexpr int CKC = 16;
+template <int FMT, bool TWO, int CT>
+__global__ void __launch_bounds__(256) contract_kernel(const Tile* __restrict__ tiles, int m,
+                                                       int nout, Bufs V, int buf_mode,
+                                                       int buf_fixed, Coef M1, Coef M2, Coef M3,
+                                                       const float* __restrict__ X, int px,
+                                                       float* __restrict__ out) {
+  constexpr int QB = 8 * CT;
+  __shared__ __align__(16) float Vs[CKC][PBM + 4];
+  __shared__ __align__(16) float V2s[TWO ? CKC : 1][PBM + 4];
+  __shared__ __align__(16) float M1s[CKC][QB];
+  __shared__ __align__(16) float M2s[TWO ? CKC : 1][QB];
+  const Tile t = tiles[blockIdx.x];
+  const int j0 = blockIdx.y * QB;
+  const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;
+  const int b = buf_mode ? t.fbuf : buf_fixed;
+  const void* vh = V.hi(b);
+  const void* vl = V.lo(b);
+  float acc[4][CT];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int e = 0; e < CT; ++e) acc[i][e] = 0.f;
+  // loader: thread -> (row lr, 8 columns lc8) of the 128 x 16 chunk
+  const int lr = threadIdx.x >> 1, lc8 = (threadIdx.x & 1) * 8;
+  const int tl = t.t0 + lr;
+  const int64_t lrow = t.seq_row0 + tl;
+  const int nk = m + px;
+  for (int k0 = 0; k0 < nk; k0 += CKC) {
+    const bool dense = k0 >= m;            // m % 16 == 0: a chunk is all V or all X
+    const int kd = k0 - m;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = 0.f;
+    if (tl < t.len) {
+      if (!dense) {
+        load8<FMT>(vh, vl, lrow * m + k0 + lc8, v);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (kd + lc8 + e < px) v[e] = X[lrow * px + kd + lc8 + e];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) Vs[lc8 + e][lr] = v[e];
+    const bool two = TWO && !dense;
+    if (two) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = 0.f;
+      if (tl + 1 < t.len) load8<FMT>(vh, vl, (lrow + 1) * m + k0 + lc8, v);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) V2s[lc8 + e][lr] = v[e];
+    }
+    for (int e = threadIdx.x; e < CKC * QB; e += 256) {
+      const int kk = e / QB, jj = e - kk * QB;
+      const bool ok = j0 + jj < nout;
+      if (!dense) {
+        M1s[kk][jj] = ok ? M1.at(t.sys, j0 + jj, k0 + kk) : 0.f;
+        if (TWO) M2s[kk][jj] = ok ? M2.at(t.sys, j0 + jj, k0 + kk) : 0.f;
+      } else {
+        M1s[kk][jj] = (ok && kd + kk < px) ? M3.at(t.sys, j0 + jj, kd + kk) : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < CKC; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&Vs[kk][rg * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      float mv[CT];
+#pragma unroll
+      for (int e = 0; e < CT; ++e) mv[e] = M1s[kk][cg * CT + e];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int e = 0; e < CT; ++e) acc[i][e] = fmaf(av[i], mv[e], acc[i][e]);
+      if (two) {
+        const float4 a2 = *reinterpret_cast<const float4*>(&V2s[kk][rg * 4]);
+        const float av2[4] = {a2.x, a2.y, a2.z, a2.w};
+#pragma unroll
+        for (int e = 0; e < CT; ++e) mv[e] = M2s[kk][cg * CT + e];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int e = 0; e < CT; ++e) acc[i][e] = fmaf(av2[i], mv[e], acc[i][e]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = rg * 4 + i;
+    if (t.t0 + r >= t.len) continue;
+    const int64_t row = t.seq_row0 + t.t0 + r;
+#pragma unroll
+    for (int e = 0; e < CT; ++e) {
+      const int j = j0 + cg * CT + e;
+      if (j < nout) out[row * nout + j] = acc[i][e];
+    }
+  }
+}
+
+template <int FMT, bool TWO>
+cudaError_t contract_dispatch(const Tile* tiles, int ntiles, int m, int nout, const Bufs& V,
+                              int buf_mode, int buf_fixed, const Coef& M1, const Coef& M2,
+                              const Coef& M3, const float* X, int px, float* out,
+                              cudaStream_t st) {
+  const int ct = nout <= 8 ? 1 : nout <= 16 ? 2 : nout <= 32 ? 4 : 8;
+  dim3 grid(ntiles, (nout + 8 * ct - 1) / (8 * ct));
+#define CASCADE_CONTRACT(CTV)                                                                 \
+  contract_kernel<FMT, TWO, CTV><<<grid, 256, 0, st>>>(tiles, m, nout, V, buf_mode, buf_fixed, \
+                                                       M1, M2, M3, X, px, out)
+  switch (ct) {
+    case 1: CASCADE_CONTRACT(1); break;
+    case 2: CASCADE_CONTRACT(2); break;
+    case 4: CASCADE_CONTRACT(4); break;
+    default: CASCADE_CONTRACT(8);
+  }
+#undef CASCADE_CONTRACT
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+template <bool TWO>
+cudaError_t expand_dispatch(int precision, const Tile* tiles, int ntiles, int m, int px,
+                            const float* X, int ldx, const Coef& M1, const Coef& M2,
+                            const Bufs& out, int buf_mode, int buf_fixed, int odd_only,
+                            cudaStream_t st) {
+  dim3 grid(ntiles, (m + 63) / 64);
+  if (precision == CASCADE_BF16_SPLIT)
+    expand_kernel<FMT_BF16, TWO><<<grid, 256, 0, st>>>(tiles, m, px, X, ldx, M1, M2, out,
+                                                      buf_mode, buf_fixed, odd_only);
+  else
+    expand_kernel<FMT_F32, TWO><<<grid, 256, 0, st>>>(tiles, m, px, X, ldx, M1, M2, out, buf_mode,
+                                                     buf_fixed, odd_only);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool proj_supported(const Plan& p) {
+  return p.d.precision != CASCADE_FP64 && p.d.m % 16 == 0 && tile_rows(p) == PBM;
+}
+
+// v^(1) = Bbar u_l + (Abar Bbar) u_(l-1) into state buffer `buf` (first stage);
+// odd_only: the second term on odd l only (first up-sweep level).
+cudaError_t launch_proj_stage0(const Plan& p, const float* u, const Bufs& V, int buf,
+                               bool odd_only, cudaStream_t st) {
+  if (p.n_stage0_tiles == 0) return cudaSuccess;
+  const int m = p.d.m, pp = p.d.p;
+  const Coef B{p.Bbar32, (int64_t)m * pp, pp, 1};     // Bbar [m, p]: (c, j)
+  const Coef AB{p.ABbar32, (int64_t)m * pp, pp, 1};
+  return expand_dispatch<true>(p.d.precision, p.d_stage0_tiles, p.n_stage0_tiles, m, pp, u, pp, B,
+                               AB, V, 0, buf, odd_only ? 1 : 0, st);
+}
+
+// W^(N_i+1) = C^T G into adjoint buffer (N_i + 1) & 1 of every tile.
+cudaError_t launch_proj_adj_init(const Plan& p, const float* G, const Bufs& W, cudaStream_t st) {
+  if (p.n_all_tiles == 0) return cudaSuccess;
+  const int m = p.d.m, q = p.d.q;
+  const Coef Ct{p.C32, (int64_t)q * m, 1, m};          // C [q, m]: (c, j) = C[j][c]
+  return expand_dispatch<false>(p.d.precision, p.d_all_tiles, p.n_all_tiles, m, q, G, q, Ct, Ct,
+                                W, 1, 0, 0, st);
+}
+
+// y = C v + D u for the tiles whose output was not fused (state buffer tile.fbuf).
+cudaError_t launch_proj_output(const Plan& p, const float* u, float* y, const Bufs& V,
+                               cudaStream_t st) {
+  if (p.n_out_tiles == 0) return cudaSuccess;
+  const int m = p.d.m, pp = p.d.p, q = p.d.q;
+  const Coef C{p.C32, (int64_t)q * m, m, 1};           // (j, c)
+  const Coef D{p.D32, (int64_t)q * pp, pp, 1};         // (j, i)
+  if (p.d.precision == CASCADE_BF16_SPLIT)
+    return contract_dispatch<FMT_BF16, false>(p.d_out_tiles, p.n_out_tiles, m, q, V, 1, 0, C, C, D,
+                                              u, pp, y, st);
+  return contract_dispatch<FMT_F32, false>(p.d_out_tiles, p.n_out_tiles, m, q, V, 1, 0, C, C, D, u,
+                                           pp, y, st);
+}
+
+// du = Bbar^T W_l + (Abar Bbar)^T W_(l+1) + D^T G_l with W^(1) in adjoint buffer `wbuf`.
+cudaError_t launch_proj_du(const Plan& p, const float* G, const Bufs& W, int wbuf, float* du,
+                           cudaStream_t st) {
+  if (p.n_all_tiles == 0) return cudaSuccess;
+  const int m = p.d.m, pp = p.d.p, q = p.d.q;
+  const Coef Bt{p.Bbar32, (int64_t)m * pp, 1, pp};     // (j, c) = Bbar[c][j]
+  const Coef ABt{p.ABbar32, (int64_t)m * pp, 1, pp};
+  const Coef Dt{p.D32, (int64_t)q * pp, 1, pp};        // (j, i) = D[i][j]
+  if (p.d.precision == CASCADE_BF16_SPLIT)
+    return contract_dispatch<FMT_BF16, true>(p.d_all_tiles, p.n_all_tiles, m, pp, W, 0, wbuf, Bt,
+                                             ABt, Dt, G, q, du, st);
+  return contract_dispatch<FMT_F32, true>(p.d_all_tiles, p.n_all_tiles, m, pp, W, 0, wbuf, Bt, ABt,
+                                          Dt, G, q, du, st);
+}
+
+}  // namespace cascade

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__
 }
 
 // ---------------------------------------------------------------- output
-// One block per output tile (tile.flags = which workspace buffer holds the
+// One block per output tile (tile.fbuf = which workspace buffer holds the
 // final states); one warp per row: y[row, :] = C v + D u.
 template <int FMT, typename T>
 __global__ void __launch_bounds__(256) output_kernel(const Tile* __restrict__ tiles, int BM, int m,
@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(256) output_kernel(const Tile* __restrict__ ti
                                                      T* __restrict__ y, const T* __restrict__ C,
                                                      const T* __restrict__ D, Bufs V) {
   const Tile t = tiles[blockIdx.x];
-  const void* vh = V.hi(t.flags);
-  const void* vl = V.lo(t.flags);
+  const void* vh = V.hi(t.fbuf);
+  const void* vl = V.lo(t.fbuf);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int rows = min(BM, t.len - t.t0);
   const T* Cs = C + (int64_t)t.sys * q * m;
@@ -310,6 +310,10 @@ cudaError_t launch_stage_f64(const Plan& p, int k, const double* vin, double* vo
                              cudaStream_t st, bool reverse) {
   const int n = reverse ? p.n_adj_tiles[k] : p.n_tiles[k];
   if (n == 0) return cudaSuccess;
+  if (!(reverse ? p.PT64 : p.P64) || !vin || !vout) {
+    set_global_error("stage launch without its powers or state buffers");
+    return cudaErrorInvalidValue;
+  }
   dim3 grid(n, (p.d.m + 63) / 64);
   stage_f64_kernel<<<grid, 256, 0, st>>>(reverse ? p.d_adj_tiles[k] : p.d_tiles[k], p.d.m, 1 << k,
                                          reverse ? 1 : 0,

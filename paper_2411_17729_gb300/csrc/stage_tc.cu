@@ -145,7 +145,8 @@ __device__ __forceinline__ Item load_item(const StageArgs& a, int w) {
   it.n0 = (w % a.nblocks) * a.BN;
   // every source row lies outside the sequence: before its start (forward
   // stages) or past its end (adjoint stages, source l + s)
-  it.copy = a.reverse ? (it.t.t0 + a.shift >= it.t.len) : (it.t.t0 + BM <= a.shift);
+  it.copy = a.S ? false
+                 : a.reverse ? (it.t.t0 + a.shift >= it.t.len) : (it.t.t0 + BM <= a.shift);
   it.fused = (QMAX > 0) && (it.t.flags & TILE_FINAL_FUSED);
   it.ragged = it.t.t0 + BM > it.t.len;
   return it;
@@ -247,6 +248,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // source rows l - s (forward) or l + s (adjoint); may fall outside the
         // tensor (zero fill) or in a neighbouring sequence (zeroed below)
         const int src_row = (int)(it.t.seq_row0 + it.t.t0 + (args.reverse ? shift : -shift));
+        // strided tiles: the same row as (row in group, group) of the 3-D map
+        const int src_y = args.S ? src_row % args.S : src_row;
+        const int src_z = args.S ? src_row / args.S : 0;
         const int prow = (it.t.sys * args.kmax1 + args.k) * m + it.n0;
         for (int c = 0; c < nkc; ++c) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, limit, abort_flag)) {
@@ -258,8 +262,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint8_t* sb_hi = sa_lo + a_bytes;
           uint8_t* sb_lo = sb_hi + b_bytes;
           ptx::mbar_arrive_expect_tx(&full[stage], stage_bytes);
-          ptx::tma_load_2d(sa_hi, &tm_vhi, &full[stage], c * KC, src_row);
-          ptx::tma_load_2d(sa_lo, &tm_vlo, &full[stage], c * KC, src_row);
+          if (args.S) {
+            ptx::tma_load_3d(sa_hi, &tm_vhi, &full[stage], c * KC, src_y, src_z);
+            ptx::tma_load_3d(sa_lo, &tm_vlo, &full[stage], c * KC, src_y, src_z);
+          } else {
+            ptx::tma_load_2d(sa_hi, &tm_vhi, &full[stage], c * KC, src_row);
+            ptx::tma_load_2d(sa_lo, &tm_vlo, &full[stage], c * KC, src_row);
+          }
           ptx::tma_load_2d(sb_hi, &tm_phi, &full[stage], c * KC, prow);
           ptx::tma_load_2d(sb_lo, &tm_plo, &full[stage], c * KC, prow);
           issued_parity[stage] = (int)phase;
@@ -289,8 +298,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       ptx::tc_fence_after();
       // tile rows [z0, z1) whose source lies outside the sequence read zero
+      // (strided tiles: every source lies inside its sequence)
       const int z0 = args.reverse ? max(0, it.t.len - it.t.t0 - shift) : 0;
-      const int z1 = args.reverse ? BM : min(BM, shift - it.t.t0);
+      const int z1 = args.S ? 0 : args.reverse ? BM : min(BM, shift - it.t.t0);
       const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * ACC);
       const uint32_t c_tmem = d_tmem + (SEP ? (uint32_t)BN : 0u);   // correction accumulator
       bool ok = true;
@@ -360,8 +370,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int yrow = (int)(lt.seq_row0 + lt.t0);
         uint8_t* sh = ring + (size_t)slot * SLOT_BYTES;
         ptx::mbar_arrive_expect_tx(&res_full[slot], SLOT_BYTES);
-        ptx::tma_load_2d(sh, &tm_vhi, &res_full[slot], x, yrow);
-        ptx::tma_load_2d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow);
+        if (args.S) {
+          ptx::tma_load_3d(sh, &tm_vhi, &res_full[slot], x, yrow % args.S, yrow / args.S);
+          ptx::tma_load_3d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow % args.S,
+                           yrow / args.S);
+        } else {
+          ptx::tma_load_2d(sh, &tm_vhi, &res_full[slot], x, yrow);
+          ptx::tma_load_2d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow);
+        }
         ++issued;
         if (++lcc == nch) { lcc = 0; lw += gridDim.x; }
       };
@@ -370,7 +386,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool alive = true;
       for (int w = blockIdx.x; w < nwork && alive; w += gridDim.x) {
         const Item it = load_item<QMAX>(args, w);
-        const bool tma_out = !it.fused && !it.ragged;
+        const bool tma_out = (!it.fused || args.keep_v) && !it.ragged;
         const int ytile = (int)(it.t.seq_row0 + it.t.t0);
         for (int cc = 0; cc < nch; ++cc, ++g) {
           const int slot = (int)(g % RING);
@@ -384,8 +400,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           if (tma_out) {
-            ptx::tma_store_2d(&tm_ohi, sh, it.n0 + cc * CW, ytile);
-            ptx::tma_store_2d(&tm_olo, sh + PLANE_TILE, it.n0 + cc * CW, ytile);
+            if (args.S) {
+              ptx::tma_store_3d(&tm_ohi, sh, it.n0 + cc * CW, ytile % args.S, ytile / args.S);
+              ptx::tma_store_3d(&tm_olo, sh + PLANE_TILE, it.n0 + cc * CW, ytile % args.S,
+                                ytile / args.S);
+            } else {
+              ptx::tma_store_2d(&tm_ohi, sh, it.n0 + cc * CW, ytile);
+              ptx::tma_store_2d(&tm_olo, sh + PLANE_TILE, it.n0 + cc * CW, ytile);
+            }
             ptx::bulk_commit();
             ptx::bulk_wait_read0();     // the slot may be overwritten once the store read it
           }
@@ -406,12 +428,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bool alive = true;                         // warp-uniform
     for (int w = blockIdx.x; w < nwork && alive; w += gridDim.x) {
       const Item it = load_item<QMAX>(args, w);
-      const bool tma_out = !it.fused && !it.ragged;
+      const bool tma_out = (!it.fused || args.keep_v) && !it.ragged;
       const int tr = it.t.t0 + r;
       const bool valid = tr < it.t.len;
-      const int64_t grow = it.t.seq_row0 + tr;
+      const int64_t grow = args.S ? it.t.seq_row0 + (int64_t)r * args.S : it.t.seq_row0 + tr;
       const int abuf = acc_i & 1;
-      if (it.copy && tma_out) {
+      if (it.copy && tma_out && !it.fused) {
         // the manager forwards the residual as is; acknowledge each chunk once
         // it has arrived, keeping both slot barriers phase-locked
         for (int cc = 0; cc < nch; ++cc, ++g) {
@@ -512,7 +534,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               }
             }
           }
-        } else {
+        }
+        if (!it.fused || args.keep_v) {
 #pragma unroll
           for (int h = 0; h < G; ++h)
 #pragma unroll
@@ -618,11 +641,20 @@ TcConfig tc_default(int m, int precision) {
   return c;
 }
 
-cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
-                            void* vout_hi, void* vout_lo, const float* u, float* y,
-                            cudaStream_t st, bool reverse) {
-  const int ntiles = reverse ? p.n_adj_tiles[k] : p.n_tiles[k];
+namespace {
+
+// One launch of the stage kernel over `tiles` (stage k).  S = 0: dense tiles,
+// 2-D state maps; S > 0: strided in-place tiles (vin == vout), 3-D state maps
+// over `rows_cap` rows (a multiple of S).
+cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, int S,
+                          uint64_t rows_cap, const void* vin_hi, const void* vin_lo,
+                          void* vout_hi, void* vout_lo, const float* u, float* y,
+                          cudaStream_t st, bool reverse) {
   if (ntiles == 0) return cudaSuccess;
+  if (!(reverse ? p.PThi : p.Phi) || !vin_hi || !vin_lo || !vout_hi || !vout_lo) {
+    set_global_error("stage launch without its power or state planes");
+    return cudaErrorInvalidValue;
+  }
   const int m = p.d.m;
   const int elem = (int)plane_elem_bytes(p.d.precision);
   const int BN = block_n(m, p.d.precision);
@@ -631,19 +663,21 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   const uint32_t row_elems = ROWB / (uint32_t)elem;
   CUtensorMap maps[6];
   std::string err;
-  const uint64_t rows = (uint64_t)p.rows;
   const uint64_t prow = (uint64_t)p.d.nsys * p.kmax1 * m;
-  if (!encode_tmap_2d(&maps[0], vin_hi, elem, m, rows, row_elems, BM, &err, 64) ||
-      !encode_tmap_2d(&maps[1], vin_lo, elem, m, rows, row_elems, BM, &err, 64) ||
+  auto state_map = [&](CUtensorMap* map, const void* base) {
+    return S ? encode_tmap_3d(map, base, elem, m, (uint64_t)S, rows_cap / (uint64_t)S, row_elems,
+                              BM, &err, 64)
+             : encode_tmap_2d(map, base, elem, m, rows_cap, row_elems, BM, &err, 64);
+  };
+  if (!state_map(&maps[0], vin_hi) || !state_map(&maps[1], vin_lo) ||
       !encode_tmap_2d(&maps[2], reverse ? p.PThi : p.Phi, elem, m, prow, row_elems, BN, &err, 64) ||
       !encode_tmap_2d(&maps[3], reverse ? p.PTlo : p.Plo, elem, m, prow, row_elems, BN, &err, 64) ||
-      !encode_tmap_2d(&maps[4], vout_hi, elem, m, rows, row_elems, BM, &err, 64) ||
-      !encode_tmap_2d(&maps[5], vout_lo, elem, m, rows, row_elems, BM, &err, 64)) {
+      !state_map(&maps[4], vout_hi) || !state_map(&maps[5], vout_lo)) {
     set_global_error("tensor map encode failed: " + err);
     return cudaErrorInvalidValue;
   }
   StageArgs a{};
-  a.tiles = reverse ? p.d_adj_tiles[k] : p.d_tiles[k];
+  a.tiles = tiles;
   a.ntiles = ntiles;
   a.nblocks = m / BN;
   a.m = m;
@@ -656,6 +690,8 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   a.reverse = reverse ? 1 : 0;
   a.k = k;
   a.kmax1 = p.kmax1;
+  a.keep_v = (p.d.flags & (CASCADE_FLAG_SAVE_STATES | CASCADE_FLAG_RECOMPUTE)) ? 1 : 0;
+  a.S = S;
   a.vin_hi = vin_hi;
   a.vin_lo = vin_lo;
   a.vout_hi = vout_hi;
@@ -671,7 +707,9 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   const int nwork = ntiles * a.nblocks;
   const int grid = nwork < p.num_sms ? nwork : p.num_sms;
   const int q = p.d.q;
-  const bool fuse = p.fuse_output;
+  // the fused output applies to dense forward stages that are given y (the
+  // stages the backward recomputes are not)
+  const bool fuse = p.fuse_output && !reverse && y != nullptr && S == 0;
   const int G = cfg.group;
 #define CASCADE_TC_DISPATCH(E, Q)                                               \
   return G == 2 ? launch_variant<E, Q, 2>(maps, a, grid, smem, st)               \
@@ -679,13 +717,30 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   if (elem == 2) {
     if (!fuse) CASCADE_TC_DISPATCH(2, 0);
     if (q == 1) CASCADE_TC_DISPATCH(2, 1);
-    CASCADE_TC_DISPATCH(2, 16);
+    CASCADE_TC_DISPATCH(2, 4);
   } else {
     if (!fuse) CASCADE_TC_DISPATCH(4, 0);
     if (q == 1) CASCADE_TC_DISPATCH(4, 1);
-    CASCADE_TC_DISPATCH(4, 16);
+    CASCADE_TC_DISPATCH(4, 4);
   }
 #undef CASCADE_TC_DISPATCH
+}
+
+}  // namespace
+
+cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
+                            void* vout_hi, void* vout_lo, const float* u, float* y,
+                            cudaStream_t st, bool reverse) {
+  return stage_tc_core(p, k, reverse ? p.d_adj_tiles[k] : p.d_tiles[k],
+                       reverse ? p.n_adj_tiles[k] : p.n_tiles[k], 0, (uint64_t)p.rows, vin_hi,
+                       vin_lo, vout_hi, vout_lo, u, y, st, reverse);
+}
+
+cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,
+                                    uint64_t rows_cap, void* v_hi, void* v_lo, cudaStream_t st) {
+  if (S <= 0 || rows_cap % (uint64_t)S != 0) return cudaErrorInvalidValue;
+  return stage_tc_core(p, k, tiles, ntiles, S, rows_cap, v_hi, v_lo, v_hi, v_lo, nullptr, nullptr,
+                       st, false);
 }
 
 }  // namespace cascade

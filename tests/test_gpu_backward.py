@@ -25,10 +25,11 @@ def lib():
     return cascade
 
 
-def gpu_grads(lib, w, precision, dy):
+def gpu_grads(lib, w, precision, dy, flags=None):
     import torch
     from paper_2411_17729_gb300._abi import CASCADE_FLAG_SAVE_STATES
-    c = lib.from_workload(w, precision=precision, flags=CASCADE_FLAG_SAVE_STATES)
+    c = lib.from_workload(w, precision=precision,
+                          flags=CASCADE_FLAG_SAVE_STATES if flags is None else flags)
     dt = torch.float64 if precision == "fp64" else torch.float32
     u = torch.as_tensor(w.u, dtype=dt).cuda().contiguous()
     y = c.forward(u)
@@ -162,9 +163,59 @@ def test_backward_requires_saved_states(lib):
 
 def test_differentiation_form_full_size(lib):
     """m = 256, p = q = 16, 32 sequences x 8192 steps, N = 12, BF16 split,
-    gradients to u, A (through the squaring chain and Eq. 4.2), B, C, D
-    against the oracle's FP64 adjoint over the whole batch."""
+    stage outputs recomputed from checkpoints, gradients to u, A (through the
+    squaring chain and Eq. 4.2), B, C, D against the oracle's FP64 adjoint over
+    the whole batch."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_RECOMPUTE
     w = cast_inputs(wl.differentiation_form(), "bf16_split")
     dy = np.random.default_rng(10).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
+    c, _, g = gpu_grads(lib, w, "bf16_split", dy, flags=CASCADE_FLAG_RECOMPUTE)
+    compare(w, c, g, dy, GTOL["bf16_split"])
+
+
+@pytest.mark.parametrize("p,q", [(1, 1), (8, 2), (16, 16), (3, 20), (64, 64)])
+def test_tc_backward_mimo_shapes(lib, p, q):
+    """Input and output widths across the projection and reduction kernels:
+    one narrow side (register-tiled reductions, one or two shifts per pass)
+    and wide ones (tiled reductions), ragged lengths."""
+    w = wl.differentiation_form(m=128, p=p, q=q, L=8, batch=3, N=9, delta=1e-2)
+    lengths = (300, 129, 1)
+    w.offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    w.u = np.random.default_rng(11).standard_normal((int(w.offsets[-1]), p))
+    w = cast_inputs(w, "bf16_split")
+    dy = np.random.default_rng(12).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
     c, _, g = gpu_grads(lib, w, "bf16_split", dy)
     compare(w, c, g, dy, GTOL["bf16_split"])
+
+
+@pytest.mark.parametrize("precision,m", [("bf16_split", 128), ("fp32", 64), ("fp64", 24)])
+def test_recompute_matches_saved_states(lib, precision, m):
+    """Checkpointed stage outputs (CASCADE_FLAG_RECOMPUTE) give the same
+    forward output and gradients, bit for bit, as keeping every stage output,
+    and both match the oracle.  Lengths give per-sequence N from 0 to 10, so
+    segments of several stages, of one stage, and sequences that stop inside a
+    segment all occur."""
+    import torch
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_RECOMPUTE, CASCADE_FLAG_SAVE_STATES
+    if precision == "fp64":
+        w = wl.small_system(m=m, p=2, q=3, lengths=(700, 129, 1, 300, 2000), N=10, nsys=2,
+                            seed=13, radius=0.97, discrete=False, delta=0.05)
+    else:
+        w = wl.differentiation_form(m=m, p=2, q=3, L=8, batch=5, N=10, delta=1e-2)
+        lengths = (700, 129, 1, 300, 2000)
+        w.offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+        w.u = np.random.default_rng(14).standard_normal((int(w.offsets[-1]), 2))
+        w = cast_inputs(w, precision)
+    dy = np.random.default_rng(15).standard_normal((w.rows, w.q))
+    if precision != "fp64":
+        dy = dy.astype(np.float32).astype(np.float64)
+    c1, y1, g1 = gpu_grads(lib, w, precision, dy, flags=CASCADE_FLAG_SAVE_STATES)
+    c2, y2, g2 = gpu_grads(lib, w, precision, dy, flags=CASCADE_FLAG_RECOMPUTE)
+    c0 = lib.from_workload(w, precision=precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    y0 = c0.forward(torch.as_tensor(w.u, dtype=dt).cuda().contiguous()).double().cpu().numpy()
+    assert np.array_equal(y0, y1) and np.array_equal(y1, y2)
+    assert c2.workspace_size() < c1.workspace_size()
+    for k in g1:
+        assert np.array_equal(g1[k], g2[k]), k
+    compare(w, c2, g2, dy, GTOL[precision])

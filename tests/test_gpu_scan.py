@@ -1,0 +1,144 @@
+"""GPU parity of the work-efficient schedule (CASCADE_FLAG_SCAN: up-sweep and
+down-sweep over the powers Abar^(2^k), about 2L products per sequence, as the
+abstract and §6 count them) against the CPU FP64 oracle's cascade, which it
+equals up to rounding when 2^(N+1) >= L.  Same bars as the stage schedule:
+2e-3 (BF16 split) and 1e-5 (FP32) on y and on Cx = y - Du."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from _parity import OUT_EPS, TOL, cast_inputs, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_17729_gb300 import build
+    build()
+    from paper_2411_17729_gb300 import cascade
+    return cascade
+
+
+def scan_products(L):
+    """Products by powers the schedule makes for one sequence of length L:
+    odd rows of the first level, then up-sweep levels 1..K-1 and down-sweep
+    levels K-2..0 (K = ceil(log2 L))."""
+    K = int(np.ceil(np.log2(L))) if L > 1 else 0
+    n = L // 2
+    n += sum(L // 2 ** (k + 1) for k in range(1, K))
+    n += sum((L - 2 ** k) // 2 ** (k + 1) for k in range(K - 1) if L > 2 ** k)
+    return n
+
+
+def run(lib, w, precision, flags):
+    import torch
+    c = lib.from_workload(w, precision=precision, flags=flags)
+    u = torch.as_tensor(w.u, dtype=torch.float32).cuda().contiguous()
+    y = c.forward(u)
+    torch.cuda.synchronize()
+    assert c.device_error() == 0, c.lib.cascade_last_error(c.plan)
+    return c, y.double().cpu().numpy()
+
+
+def matvecs(c):
+    import ctypes
+    n = ctypes.c_int64()
+    c._check(c.lib.cascade_get_matvec_count(c.plan, ctypes.byref(n)))
+    return n.value
+
+
+LENGTHS = (1, 2, 3, 4, 5, 64, 127, 128, 129, 255, 256, 257, 1000, 2048, 3001)
+
+
+@pytest.mark.parametrize("precision,m", [("bf16_split", 128), ("bf16_split", 256),
+                                         ("fp32", 128), ("fp32", 64)])
+def test_scan_matches_oracle(lib, precision, m):
+    """Ragged lengths around every power of two the tiles and levels meet
+    (1 .. 3001), two systems, MIMO."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SCAN
+    w = wl.differentiation_form(m=m, p=3, q=2, L=8, batch=len(LENGTHS), N=11, delta=1e-2)
+    w.offsets = np.concatenate([[0], np.cumsum(LENGTHS)]).astype(np.int64)
+    w.u = np.random.default_rng(21).standard_normal((int(w.offsets[-1]), 3))
+    w.sys_of_seq = (np.arange(len(LENGTHS)) % 2).astype(np.int32)
+    w.A = np.concatenate([w.A, w.A])
+    w.delta = np.array([1e-2, 3e-2])
+    for k in ("B", "C", "D"):
+        setattr(w, k, np.concatenate([getattr(w, k), 0.7 * getattr(w, k)]))
+    w = cast_inputs(w, precision)
+    c, y = run(lib, w, precision, CASCADE_FLAG_SCAN)
+    yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
+    ey, ecx = rel_errors(w, y, yo, OUT_EPS[precision])
+    assert ey <= TOL[precision] and ecx <= TOL[precision], (ey, ecx)
+    # operation count: about 2L, never above it (abstract, §6)
+    want = sum(scan_products(L) for L in LENGTHS)
+    assert matvecs(c) == want
+    assert want <= sum(oracle.matvec_counts(11, L)["paper_bound"] for L in LENGTHS)
+
+
+def test_stage_schedule_count(lib):
+    """The stage schedule's count is the oracle's sum_k (L - 2^k)^+ per sequence."""
+    w = wl.precision_form(m=64, L=8, batch=len(LENGTHS), N=12)
+    w.offsets = np.concatenate([[0], np.cumsum(LENGTHS)]).astype(np.int64)
+    w.u = np.random.default_rng(22).standard_normal((int(w.offsets[-1]), 1))
+    w = cast_inputs(w, "bf16_split")
+    c, _ = run(lib, w, "bf16_split", 0)
+    Ns = c.seq_N()
+    assert matvecs(c) == sum(oracle.matvec_counts(int(N), L)["executed"]
+                             for N, L in zip(Ns, LENGTHS))
+
+
+def test_scan_equals_stage_schedule(lib):
+    """Both schedules on the same batch agree to the rounding of the format."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SCAN
+    w = cast_inputs(wl.precision_form(m=256, L=4096, batch=6, N=11), "bf16_split")
+    _, y1 = run(lib, w, "bf16_split", 0)
+    _, y2 = run(lib, w, "bf16_split", CASCADE_FLAG_SCAN)
+    yo = oracle.cascade_forward(w)
+    e1, _ = rel_errors(w, y1, yo, OUT_EPS["bf16_split"])
+    e2, _ = rel_errors(w, y2, yo, OUT_EPS["bf16_split"])
+    assert e1 <= TOL["bf16_split"] and e2 <= TOL["bf16_split"], (e1, e2)
+    e12, _ = rel_errors(w, y2, y1)
+    assert e12 <= TOL["bf16_split"], e12
+
+
+def test_scan_precision_form_full_size_sampled(lib):
+    """64 sequences x 16384 steps, m = 256, N = 13 (the benchmark's
+    configuration) on the work-efficient schedule: the oracle recomputes the
+    sequences with the smallest and largest step in full and 256-step
+    prefixes of the others."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SCAN
+    w = cast_inputs(wl.precision_form(), "bf16_split")
+    c, y = run(lib, w, "bf16_split", CASCADE_FLAG_SCAN)
+    assert matvecs(c) == 64 * scan_products(16384)
+    full = {int(np.argmin(w.delta)), int(np.argmax(w.delta))}
+    worst = 0.0
+    for i in range(w.nseq):
+        sl = w.seq(i)
+        Abar, Bbar, C, D = oracle.system_matrices(w, int(w.sys_of_seq[i]))
+        n = sl.stop - sl.start if i in full else 256
+        uu = w.u[sl][:n]
+        yo = oracle.cascade_forward_seq(Abar, Bbar, C, D, uu, 13)
+        yg = y[sl][:n]
+        Du = uu @ D.T
+        worst = max(worst, np.linalg.norm(yg - yo) / np.linalg.norm(yo),
+                    np.linalg.norm(yg - yo) / np.linalg.norm(yo - Du))
+    assert worst <= TOL["bf16_split"], worst
+
+
+def test_scan_refuses_truncation_and_backward(lib):
+    """2^(N+1) < L has no work-efficient form here (UNSUPPORTED), and the
+    schedule keeps no stage outputs for a backward (INVALID_ARG)."""
+    from paper_2411_17729_gb300._abi import (CASCADE_FLAG_SAVE_STATES, CASCADE_FLAG_SCAN,
+                                             CascadeError)
+    w = cast_inputs(wl.precision_form(m=64, L=1000, batch=2, N=4), "bf16_split")
+    with pytest.raises(CascadeError):
+        lib.from_workload(w, precision="bf16_split", flags=CASCADE_FLAG_SCAN)
+    w2 = cast_inputs(wl.precision_form(m=64, L=100, batch=2, N=9), "bf16_split")
+    with pytest.raises(CascadeError):
+        lib.from_workload(w2, precision="bf16_split",
+                          flags=CASCADE_FLAG_SCAN | CASCADE_FLAG_SAVE_STATES)

@@ -27,12 +27,56 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "discretise_trapezoid", "squaring_chain", "stage", "cascade_states",
+    "discretise_trapezoid", "discretise_zoh", "discretise_zoh_vjp", "squaring_chain", "stage",
+    "cascade_states",
     "cascade_forward_seq", "cascade_forward", "recursion_forward_seq",
     "brute_force_seq", "choose_N", "effective_N", "cascade_vjp_seq",
     "squaring_chain_vjp", "discretise_trapezoid_vjp", "cascade_backward",
     "system_matrices", "stage_count", "matvec_counts",
 ]
+
+
+# --------------------------------------------------------------------------- §5
+def _zoh_block(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Z = [[A, B], [0, 0]], (m + p) x (m + p)."""
+    m, p = B.shape
+    Z = np.zeros((m + p, m + p))
+    Z[:m, :m] = A
+    Z[:m, m:] = B
+    return Z
+
+
+def discretise_zoh(A: np.ndarray, B: np.ndarray, delta: float):
+    """Zero-order-hold discretisation named in §5:
+
+        Abar = exp(delta A),   Bbar = (delta A)^{-1} (exp(delta A) - I) (delta B),
+
+    reading the printed last factor "delta A" as "delta B" (with delta A the
+    units do not match and B would not enter).  Both blocks are read off one
+    exponential of the block matrix delta [[A, B], [0, 0]], whose upper right
+    block is int_0^delta exp(sA) ds B: that equals the formula above when A is
+    invertible and needs no inverse otherwise.  scipy.linalg.expm is the step.
+    """
+    import scipy.linalg
+    m = A.shape[0]
+    E = scipy.linalg.expm(delta * _zoh_block(A, B))
+    return E[:m, :m].copy(), E[:m, m:].copy()
+
+
+def discretise_zoh_vjp(A, B, delta, dAbar, dBbar):
+    """Adjoint of ``discretise_zoh``.  With F(Z) = exp(Z), Z = delta [[A, B],
+    [0, 0]], the directional derivative is the Frechet derivative L(Z, E) and
+    its adjoint is L(Z^T, G); G carries (dAbar, dBbar) in the blocks that
+    Abar, Bbar occupy.  Then dA = delta dZ[:m, :m], dB = delta dZ[:m, m:].
+    scipy.linalg.expm_frechet is the step."""
+    import scipy.linalg
+    m, p = B.shape
+    Z = delta * _zoh_block(A, B)
+    G = np.zeros((m + p, m + p))
+    G[:m, :m] = dAbar
+    G[:m, m:] = dBbar
+    dZ = scipy.linalg.expm_frechet(Z.T, G, compute_expm=False)
+    return delta * dZ[:m, :m], delta * dZ[:m, m:]
 
 
 # --------------------------------------------------------------------------- §1
@@ -53,7 +97,8 @@ def discretise_trapezoid(A: np.ndarray, B: np.ndarray, delta: float):
 def system_matrices(w, s: int):
     """(Abar, Bbar, C, D) of system ``s`` of a workload, in float64.
 
-    Continuous systems are discretised with Eq. (4.2); an ``abar_scale``
+    Continuous systems are discretised with Eq. (4.2) (or the zero-order hold
+    of §5 when ``w.discretisation == "zoh"``); an ``abar_scale``
     multiplies Abar after discretisation (used to push the spectral radius
     above 1 for the stability experiments of §6).
     """
@@ -63,7 +108,8 @@ def system_matrices(w, s: int):
     else:
         A = w.A[min(s, w.A.shape[0] - 1)]
         B = w.B[min(s, w.B.shape[0] - 1)]
-        Abar, Bbar = discretise_trapezoid(A, B, float(w.delta[min(s, len(w.delta) - 1)]))
+        rule = discretise_zoh if w.discretisation == "zoh" else discretise_trapezoid
+        Abar, Bbar = rule(A, B, float(w.delta[min(s, len(w.delta) - 1)]))
         if w.abar_scale is not None:
             Abar = Abar * float(w.abar_scale[min(s, len(w.abar_scale) - 1)])
     C = np.asarray(w.C[min(s, w.C.shape[0] - 1)], dtype=np.float64)
@@ -292,8 +338,8 @@ def cascade_backward(w, G, N_per_seq=None):
     """Gradients of sum(G * y) for a whole workload.
 
     Returns a dict with du [rows, p] and, per system s, dAbar, dBbar, dC, dD
-    (and dA, dB for continuous systems, through Eq. 4.2; abar_scale, if any,
-    is applied to dAbar first)."""
+    (and dA, dB for continuous systems, through Eq. 4.2 or the zero-order
+    hold; abar_scale, if any, is applied to dAbar first)."""
     out = {"du": np.zeros((w.rows, w.p))}
     nsys = w.nsys
     acc = {s: None for s in range(nsys)}
@@ -330,7 +376,8 @@ def cascade_backward(w, G, N_per_seq=None):
         dA, dB = [], []
         for s in range(nsys):
             scale = 1.0 if w.abar_scale is None else float(w.abar_scale[min(s, len(w.abar_scale) - 1)])
-            dA_s, dB_s = discretise_trapezoid_vjp(
+            vjp = discretise_zoh_vjp if w.discretisation == "zoh" else discretise_trapezoid_vjp
+            dA_s, dB_s = vjp(
                 w.A[min(s, w.A.shape[0] - 1)], w.B[min(s, w.B.shape[0] - 1)],
                 float(w.delta[min(s, len(w.delta) - 1)]), out["dAbar"][s] * scale,
                 out["dBbar"][s])

@@ -78,6 +78,7 @@ class Workload:
     A: np.ndarray | None = None         # float64 [nsys, m, m] continuous
     delta: np.ndarray | None = None     # float64 [nsys]
     abar_scale: np.ndarray | None = None  # float64 [nsys] multiplies Abar after discretisation
+    discretisation: str = "trapezoid"   # rule for continuous systems: "trapezoid" or "zoh"
     Abar: np.ndarray | None = None      # float64 [nsys, m, m] discrete
     eps: float = 0.0
     meta: dict = field(default_factory=dict)

@@ -392,6 +392,7 @@ def main():
     scan = None
     if not f64 and not args.no_scan:
         import ctypes
+        torch.cuda.nvtx.range_push("scan")         # profiler filter (ncu --nvtx-include scan/)
         cs = cascade.from_workload(w, precision=precision, flags=CASCADE_FLAG_SCAN, device=dev)
         cs.autotune(u, y, reps=2)
         for _ in range(max(args.warmup, 3)):
@@ -441,10 +442,12 @@ def main():
                             "with Bbar u), in place"}
         cs.close()
         torch.cuda.empty_cache()
+        torch.cuda.nvtx.range_pop()
 
     # ---- forward + backward (plan that keeps its stage outputs), same workload
     fb = None
     if has_bwd and not args.no_bwd:
+        torch.cuda.nvtx.range_push("fwd_bwd")
         # the differentiation workload recomputes stage outputs from checkpoints
         recompute = args.workload == "differentiation_form"
         cb = cascade.from_workload(w, precision=precision,
@@ -482,6 +485,7 @@ def main():
               "workspace_bytes": int(cb.workspace_size())}
         cb.close()
         torch.cuda.empty_cache()
+        torch.cuda.nvtx.range_pop()
 
     # ---- FP64 plain cascade and FP64 recursion on the same GPU (comparators)
     fp64 = None

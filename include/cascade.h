@@ -89,7 +89,15 @@ enum {
      §3 cascade's up to rounding when 2^(N_i+1) >= L_i, which cascade_set_batch
      requires (CASCADE_ERR_UNSUPPORTED otherwise).  Tensor-core precisions
      only; no backward (CASCADE_ERR_INVALID_ARG with SAVE_STATES/RECOMPUTE). */
-  CASCADE_FLAG_SCAN = 16
+  CASCADE_FLAG_SCAN = 16,
+  /* cascade_set_system_continuous discretises by the zero-order hold of §5,
+     Abar = exp(delta A), Bbar = (delta A)^-1 (exp(delta A) - I) delta B (the
+     printed last factor delta A read as delta B), instead of Eq. (4.2); both
+     blocks come from one exponential of delta [[A, B], [0, 0]], so A need not
+     be invertible.  FP64 scaling and squaring with a [13/13] Pade approximant.
+     The backward's dA, dB go through the Frechet derivative of the
+     exponential.                                                           */
+  CASCADE_FLAG_ZOH = 32
 };
 
 typedef struct cascade_plan_s* cascade_plan_t;

@@ -186,6 +186,8 @@ class Cascade:
 def from_workload(w, precision=None, flags=0, N=None, max_len=None, device=None):
     """Plan for a ``workloads.Workload`` with its systems and batch set."""
     prec = precision or w.precision
+    if getattr(w, "discretisation", "trapezoid") == "zoh" and w.Abar is None:
+        flags |= _abi.CASCADE_FLAG_ZOH
     casc = Cascade(w.m, w.p, w.q, nsys=w.nsys, N=w.N if N is None else N, eps=w.eps,
                    precision=prec, max_len=int(max_len or max(1, int(w.lengths.max(initial=1)))),
                    max_rows=max(w.rows, 1), flags=flags, device=device)

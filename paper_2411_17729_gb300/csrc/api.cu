@@ -167,6 +167,7 @@ bool saves_states(const Plan& p) {
 }
 bool recomputes(const Plan& p) { return (p.d.flags & CASCADE_FLAG_RECOMPUTE) != 0; }
 bool scans(const Plan& p) { return (p.d.flags & CASCADE_FLAG_SCAN) != 0; }
+bool zoh(const Plan& p) { return (p.d.flags & CASCADE_FLAG_ZOH) != 0; }
 // The forward leaves what the backward needs (every stage output, or checkpoints).
 bool keeps_states(const Plan& p) { return saves_states(p) || recomputes(p); }
 
@@ -233,6 +234,8 @@ void free_system(Plan* p) {
                   p->ABbar32, p->C32, p->D32, p->A64, p->B64, p->delta64, p->scale64,
                   p->PThi, p->PTlo, p->PT64, p->Minv64, p->P32, p->Minv32};
   for (void* q : ptrs) dfree(q);
+  dfree(p->zoh_f_adj);
+  p->zoh_f_adj = nullptr;
   p->P64 = nullptr;
   p->Phi = p->Plo = nullptr;
   p->Bbar64 = p->ABbar64 = p->C64 = p->D64 = nullptr;
@@ -362,7 +365,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
   size_t plane = 0, buf_stride = 0, lo_off = 0;
   int nV = 2;
-  size_t off_W = 0, off_part = 0, off_dP = 0, off_R = 0, off_T = 0, total = 0;
+  size_t off_W = 0, off_part = 0, off_dP = 0, off_R = 0, off_T = 0, off_Z = 0, total = 0;
 };
 
 Layout layout(const Plan& p) {
@@ -392,6 +395,14 @@ Layout layout(const Plan& p) {
     off += align256(4 * ns * m * pp * 8);
     L.off_T = off;                                  // T, dA: [nsys, m, m] each
     off += align256(2 * ns * m * m * 8);
+    if (zoh(p) && p.continuous) {
+      // adjoint of the zero-order hold: dAbar, dBbar in FP64, Z^T, the 2n x 2n
+      // block matrices, the exponential's scratch, the G norms and a flag word
+      const size_t n = m + pp, n2 = 2 * n;
+      L.off_Z = off;
+      off += align256(8 * (ns * m * m + ns * m * pp + ns * n * n + ns * n2 * n2 +
+                           expm_scratch_doubles((int)n2, (int)ns) + ns) + 8);
+    }
   }
   L.total = off + 256;
   return L;
@@ -487,8 +498,25 @@ cudaError_t gemm_t(const double* A, const double* B, double* C, int M, int N, in
 cudaError_t gemm_t(const float* A, const float* B, float* C, int M, int N, int K, int lda,
                    int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch, double alpha,
                    double beta, bool tA, bool tB, cudaStream_t st) {
+  if (M >= 128 && N >= 128)   // square-ish products: the 128 x 128 register-tiled kernel
+    return launch_sgemm2(A, B, tA, tB, nullptr, nullptr, false, false, C, M, N, K, lda, ldb, ldc,
+                         sA, sB, sC, batch, (float)alpha, (float)beta, st);
   return launch_sgemm(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, batch, (float)alpha,
                       (float)beta, tA, tB, st);
+}
+// One level of the squaring-chain adjoint: dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1).
+cudaError_t chain_step(const double* dPn, const double* P, double* dP, int m, int64_t stride,
+                       int batch, cudaStream_t st) {
+  cudaError_t e = launch_dgemm(dPn, P, dP, m, m, m, m, m, m, stride, stride, stride, batch, 1.0,
+                               1.0, false, true, st);
+  if (e != cudaSuccess) return e;
+  return launch_dgemm(P, dPn, dP, m, m, m, m, m, m, stride, stride, stride, batch, 1.0, 1.0, true,
+                      false, st);
+}
+cudaError_t chain_step(const float* dPn, const float* P, float* dP, int m, int64_t stride,
+                       int batch, cudaStream_t st) {
+  return launch_sgemm2(dPn, P, false, true, P, dPn, true, false, dP, m, m, m, m, m, m, stride,
+                       stride, stride, batch, 1.0f, 1.0f, st);
 }
 template <typename T>
 cudaError_t to_f64(const T* src, int64_t src_stride, double* dst, int64_t dst_stride, int64_t n,
@@ -670,19 +698,39 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   CK(cudaMemcpyAsync(dBb, R1, sizeof(T) * ns * mp, cudaMemcpyDeviceToDevice, st), "copy");
   CK(gemm_t(P, R2, dBb, m, pp, m, m, pp, pp, kst, mp, mp, ns, 1.0, 1.0, true, false, st), "dBbar");
   // squaring chain P_(k+1) = P_k P_k:  dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1)
-  for (int k = p->kmax1 - 2; k >= 0; --k) {
-    CK(gemm_t(dP + (k + 1) * mm, P + k * mm, dP + k * mm, m, m, m, m, m, m, kst, kst, kst, ns,
-              1.0, 1.0, false, true, st),
-       "chain");
-    CK(gemm_t(P + k * mm, dP + (k + 1) * mm, dP + k * mm, m, m, m, m, m, m, kst, kst, kst, ns,
-              1.0, 1.0, true, false, st),
-       "chain");
-  }
+  for (int k = p->kmax1 - 2; k >= 0; --k)
+    CK(chain_step(dP + (k + 1) * mm, P + k * mm, dP + k * mm, m, kst, ns, st), "chain");
   if (dAbar) CK(to_f64<T>(dP, kst, dAbar, mm, mm, ns, st), "dAbar");
   if (dBbar) CK(to_f64<T>(dBb, mp, dBbar, mp, mp, ns, st), "dBbar");
   // trapezoidal discretisation (Eq. 4.2), Abar = c M^-1 (I + delta/2 A), Bbar = delta M^-1 B:
   // dA = delta/2 M^-T (c dAbar + dAbar Abar^T + dBbar Bbar^T),  dB = delta M^-T dBbar
-  if (p->continuous && (dA || dB)) {
+  if (p->continuous && zoh(*p) && (dA || dB)) {
+    // zero-order hold (§5): dZ = L(Z^T, G) is the upper right block of
+    // exp([[Z^T, G/g], [0, Z^T]]) times g; dA = delta dZ[:m, :m], dB = delta dZ[:m, m:]
+    const int n = m + pp;
+    const int64_t nn = (int64_t)n * n;
+    double* dA64 = reinterpret_cast<double*>(base + L.off_Z);
+    double* dB64 = dA64 + ns * mm;
+    double* ZT = dB64 + ns * mp;
+    double* Wb = ZT + ns * nn;
+    double* scr = Wb + 4 * ns * nn;
+    double* gnorm = scr + expm_scratch_doubles(2 * n, ns);
+    int32_t* sing = reinterpret_cast<int32_t*>(gnorm + ns);
+    CK(to_f64<T>(dP, kst, dA64, mm, mm, ns, st), "dAbar (fp64)");
+    CK(to_f64<T>(dBb, mp, dB64, mp, mp, ns, st), "dBbar (fp64)");
+    CK(launch_zoh_block(p->A64, p->B64, p->delta64, ZT, m, pp, ns, true, st), "Z^T");
+    CK(launch_frechet_block(ZT, dA64, dB64, p->scale64, Wb, gnorm, m, pp, ns, st), "W");
+    CK(cudaMemsetAsync(sing, 0, sizeof(int32_t), st), "flag");
+    CK(expm_batched(Wb, 2 * n, ns, p->zoh_sq_adj, p->zoh_f_adj, scr, sing, st), "exp(W)");
+    if (dA) {
+      CK(launch_block(Wb, 2 * n, 0, n, m, m, dA, mm, gnorm, 1.0, ns, st), "dA");
+      CK(launch_axpy_sys<double>(dA, mm, dA, mm, mm, ns, p->delta64, 1.0, false, st), "dA");
+    }
+    if (dB) {
+      CK(launch_block(Wb, 2 * n, 0, n + m, m, pp, dB, mp, gnorm, 1.0, ns, st), "dB");
+      CK(launch_axpy_sys<double>(dB, mp, dB, mp, mp, ns, p->delta64, 1.0, false, st), "dB");
+    }
+  } else if (p->continuous && (dA || dB)) {
     CK(gemm_t(dP, P, Tm, m, m, m, m, m, m, kst, kst, mm, ns, 1.0, 0.0, false, true, st), "T");
     CK(gemm_t(dBb, Bbar, Tm, m, m, pp, pp, pp, m, mp, mp, mm, ns, 1.0, 1.0, false, true, st), "T");
     CK(launch_axpy_sys<T>(dP, kst, Tm, mm, mm, ns, p->scale64, 1.0, true, st), "T");
@@ -710,6 +758,61 @@ cascade_status_t run_backward(Plan* p, const void* u, const void* dy, void* du, 
                                dA, dB, ws, st);
 }
 
+}  // namespace
+
+namespace {
+// Zero-order hold of every system (§5): Z = delta [[A, B], [0, 0]], E = exp(Z),
+// Abar = scale * E[:m, :m] into P64[:, 0], Bbar = E[:m, m:].  Records, per
+// system, the squarings of this exponential and of the adjoint's block
+// exponential (whose 1-norm is at most ||Z||_inf + 1).  Synchronises st.
+cascade_status_t discretise_zoh(Plan* p, cudaStream_t st) {
+  const int m = p->d.m, pp = p->d.p, ns = p->d.nsys, n = m + pp;
+  const size_t nn = (size_t)n * n;
+  double* Z = nullptr;
+  double* scratch = nullptr;
+  double* nrm = nullptr;      // 1-norms, inf-norms, scale factors
+  int32_t* sing = nullptr;
+  cudaError_t e = dalloc(&Z, ns * nn);
+  if (e == cudaSuccess) e = dalloc(&scratch, expm_scratch_doubles(n, ns));
+  if (e == cudaSuccess) e = dalloc(&nrm, (size_t)3 * ns);
+  if (e == cudaSuccess) e = dalloc(&sing, 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sing, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = launch_zoh_block(p->A64, p->B64, p->delta64, Z, m, pp, ns, false, st);
+  if (e == cudaSuccess) e = launch_norms(Z, n, ns, nrm, nrm + ns, st);
+  std::vector<double> h(2 * (size_t)ns);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), nrm, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  p->zoh_sq.assign(ns, 0);
+  p->zoh_sq_adj.assign(ns, 0);
+  std::vector<double> f(ns), fa(ns);
+  for (int s = 0; s < ns; ++s) {
+    p->zoh_sq[s] = expm_squarings(h[s]);
+    p->zoh_sq_adj[s] = expm_squarings(h[ns + s] + 1.0);
+    f[s] = ldexp(1.0, -p->zoh_sq[s]);
+    fa[s] = ldexp(1.0, -p->zoh_sq_adj[s]);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(nrm + 2 * ns, f.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !p->zoh_f_adj) e = dalloc(&p->zoh_f_adj, (size_t)ns);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->zoh_f_adj, fa.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = expm_batched(Z, n, ns, p->zoh_sq, nrm + 2 * ns, scratch, sing, st);
+  if (e == cudaSuccess)
+    e = launch_block(Z, n, 0, 0, m, m, p->P64, (int64_t)p->kmax1 * m * m, p->scale64, 1.0, ns, st);
+  if (e == cudaSuccess)
+    e = launch_block(Z, n, 0, m, m, pp, p->Bbar64, (int64_t)m * pp, nullptr, 1.0, ns, st);
+  int32_t h_sing = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_sing, sing, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // f, fa live on the host
+  dfree(Z);
+  dfree(scratch);
+  dfree(nrm);
+  dfree(sing);
+  if (e != cudaSuccess) return cuda_fail(p, e, "zero-order hold");
+  if (h_sing) return fail(p, CASCADE_ERR_INVALID_ARG, "singular Pade denominator in exp(delta A)");
+  return CASCADE_OK;
+}
 }  // namespace
 
 namespace cascade {
@@ -849,6 +952,12 @@ cascade_status_t cascade_set_system_continuous(cascade_plan_t plan, const double
   }
   CK(cudaMemcpyAsync(p->C64, d_C, sizeof(double) * ns * q * m, cudaMemcpyDeviceToDevice, st), "copy C");
   CK(cudaMemcpyAsync(p->D64, d_D, sizeof(double) * ns * q * pp, cudaMemcpyDeviceToDevice, st), "copy D");
+  if (zoh(*p)) {
+    r = discretise_zoh(p, st);
+    if (r != CASCADE_OK) return r;
+    p->continuous = true;
+    return finish_system(p, st);
+  }
   double* work = nullptr;
   int32_t* sing = nullptr;
   CK(dalloc(&work, (size_t)ns * m * (3 * m + pp)), "discretisation workspace");
@@ -1094,7 +1203,10 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     p->n_all_tiles = (int)all.size();
     // Time-reduction chunks: runs of up to CH consecutive tiles of one system,
     // grouped by system (list 0: every tile; list k: the tiles of stage k).
-    const int CH = 8;
+    // Longer runs mean fewer partial sums to write and add; CH shrinks until
+    // the reductions have at least three blocks per SM.
+    int CH = 16;
+    while (CH > 4 && (int64_t)all.size() < (int64_t)CH * 3 * p->num_sms) CH >>= 1;
     std::vector<int32_t> data;
     p->chunk_lists.assign(std::max(maxN + 1, 1), ChunkList{});
     for (size_t li = 0; li < p->chunk_lists.size(); ++li) {

@@ -190,60 +190,93 @@ __global__ void __launch_bounds__(256) wtreduce_kernel(const Tile* __restrict__ 
   for (int i = 0; i < CPT; ++i)
 #pragma unroll
     for (int e = 0; e < TT; ++e) acc[i][e] = 0;
+  constexpr int RU = 4;   // rows in flight per thread
   for (int ti = first; ti < first + count; ++ti) {
     const Tile t = tiles[ti];
     const int rows = min(BM, t.len - t.t0);
-    for (int rr = rg; rr < rows; rr += R) {
-      const int l = t.t0 + rr;
-      const int64_t row = t.seq_row0 + l;
-      ACC tv[TT];
+    const int b = X.buf_mode ? t.fbuf : X.buf_fixed;
+    for (int rr0 = rg; rr0 < rows; rr0 += RU * R) {
+      ACC tv[RU][TT], xv[RU][CPT];
 #pragma unroll
-      for (int e = 0; e < TT; ++e) {
-        const int h = e >= tc ? 1 : 0;
-        const int j = e - h * tc;
-        const int src = l - (h ? sh1 : sh0);
-        tv[e] = (e < tt && src >= 0) ? T[(t.seq_row0 + src) * ld + j] : (ACC)0;
-      }
-      if (i0 >= a) continue;
-      ACC xv[CPT];
-      if constexpr (FMT != FMT_F64) {
-        if (vec) {
-          const int b = X.buf_mode ? t.fbuf : X.buf_fixed;
-          float f[CPT];
-          load_row_vec<FMT, CPT>(X.bufs.hi(b), X.bufs.lo(b), row * m + i0, f);
+      for (int u = 0; u < RU; ++u) {
+        const int rr = rr0 + u * R;
+        const bool live = rr < rows && i0 < a;
+        const int l = t.t0 + rr;
+        const int64_t row = t.seq_row0 + l;
 #pragma unroll
-          for (int i = 0; i < CPT; ++i) xv[i] = f[i];
-        } else {
-#pragma unroll
-          for (int i = 0; i < CPT; ++i)
-            xv[i] = i0 + i < a ? (ACC)src_get<FMT>(X, t, row, i0 + i, m) : (ACC)0;
+        for (int e = 0; e < TT; ++e) {
+          const int h = e >= tc ? 1 : 0;
+          const int j = e - h * tc;
+          const int src = l - (h ? sh1 : sh0);
+          tv[u][e] = (live && e < tt && src >= 0) ? T[(t.seq_row0 + src) * ld + j] : (ACC)0;
         }
-      } else {
+        if constexpr (FMT != FMT_F64) {
+          if (vec && live) {
+            float f[CPT];
+            load_row_vec<FMT, CPT>(X.bufs.hi(b), X.bufs.lo(b), row * m + i0, f);
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) xv[u][i] = f[i];
+            continue;
+          }
+        }
 #pragma unroll
         for (int i = 0; i < CPT; ++i)
-          xv[i] = i0 + i < a ? (ACC)src_get<FMT>(X, t, row, i0 + i, m) : (ACC)0;
+          xv[u][i] = (live && i0 + i < a) ? (ACC)src_get<FMT>(X, t, row, i0 + i, m) : (ACC)0;
       }
 #pragma unroll
-      for (int i = 0; i < CPT; ++i)
+      for (int u = 0; u < RU; ++u)
 #pragma unroll
-        for (int e = 0; e < TT; ++e) acc[i][e] = fma(xv[i], tv[e], acc[i][e]);
+        for (int i = 0; i < CPT; ++i)
+#pragma unroll
+          for (int e = 0; e < TT; ++e) acc[i][e] = fma(xv[u][i], tv[u][e], acc[i][e]);
     }
   }
-  // sum the row groups in order: red[i * tt + e]
-  for (int q = 0; q < R; ++q) {
-    if (rg == q) {
+  // Sum the row groups.  Single precision: every group stores its partial and
+  // a pairwise tree with a fixed pairing adds them (log2 R barriers).  Double
+  // precision (shared memory holds one partial): in group order.
+  if constexpr (sizeof(ACC) == 4) {
+    const int slab = a * tt;    // R * slab <= 256 * CPT * TT floats, within the buffer
+    if (i0 < a) {
 #pragma unroll
       for (int i = 0; i < CPT; ++i) {
         if (i0 + i >= a) continue;
 #pragma unroll
-        for (int e = 0; e < TT; ++e) {
-          if (e >= tt) continue;
-          ACC* r = red + (int64_t)(i0 + i) * tt + e;
-          *r = (q == 0 ? (ACC)0 : *r) + acc[i][e];
+        for (int e = 0; e < TT; ++e)
+          if (e < tt) red[(int64_t)rg * slab + (i0 + i) * tt + e] = acc[i][e];
+      }
+    }
+    for (int sstep = R >> 1; sstep >= 1; sstep >>= 1) {
+      __syncthreads();
+      if (rg < sstep && i0 < a) {
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+          if (i0 + i >= a) continue;
+#pragma unroll
+          for (int e = 0; e < TT; ++e)
+            if (e < tt) {
+              ACC* r0 = red + (int64_t)rg * slab + (i0 + i) * tt + e;
+              *r0 += r0[(int64_t)sstep * slab];
+            }
         }
       }
     }
     __syncthreads();
+  } else {
+    for (int q = 0; q < R; ++q) {
+      if (rg == q) {
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+          if (i0 + i >= a) continue;
+#pragma unroll
+          for (int e = 0; e < TT; ++e) {
+            if (e >= tt) continue;
+            ACC* r = red + (int64_t)(i0 + i) * tt + e;
+            *r = (q == 0 ? (ACC)0 : *r) + acc[i][e];
+          }
+        }
+      }
+      __syncthreads();
+    }
   }
   const int64_t elems = (int64_t)a * tt;
   ACC* out = partial + (int64_t)c * elems;
@@ -396,7 +429,9 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
 
 // Thread shape of the wide-by-thin reduction: CPT columns per thread for TT
 // thin columns (CPT * TT <= 32 accumulators).
-static int wt_tt(int tt) { return tt <= 4 ? 4 : tt <= 8 ? 8 : tt <= 16 ? 16 : 0; }
+static int wt_tt(int tt) {
+  return tt <= 1 ? 1 : tt <= 2 ? 2 : tt <= 4 ? 4 : tt <= 8 ? 8 : tt <= 16 ? 16 : 0;
+}
 static int wt_cpt(int TT) { return TT <= 4 ? 8 : TT <= 8 ? 4 : 2; }
 
 bool wtreduce_supported(const Plan& p, int a, int tc, int nsh) {
@@ -422,7 +457,13 @@ static void wt_dispatch(int TT, int nchunks, const Tile* tiles, const int32_t* c
                         int m, const TSrc& X, int a, const ACC* T, int ld, int tc, int nsh,
                         int sh0, int sh1, int gshift, int vec, int thin_major, ACC* partial,
                         cudaStream_t st) {
-  if (TT == 4)
+  if (TT == 1)
+    wt_launch<FMT, ACC, 8, 1>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
+                              gshift, vec, thin_major, partial, st);
+  else if (TT == 2)
+    wt_launch<FMT, ACC, 8, 2>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
+                              gshift, vec, thin_major, partial, st);
+  else if (TT == 4)
     wt_launch<FMT, ACC, 8, 4>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
                               gshift, vec, thin_major, partial, st);
   else if (TT == 8)

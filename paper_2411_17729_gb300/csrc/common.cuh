@@ -122,6 +122,10 @@ struct Plan {
   double* B64 = nullptr;         // continuous B [nsys,m,p]
   double* delta64 = nullptr;     // [nsys]
   double* scale64 = nullptr;     // [nsys] or null
+  // zero-order hold (CASCADE_FLAG_ZOH): squarings of the forward exponential and
+  // of the adjoint's block exponential, per system, and their scale factors
+  std::vector<int> zoh_sq, zoh_sq_adj;
+  double* zoh_f_adj = nullptr;   // [nsys] 2^-zoh_sq_adj
   std::vector<int32_t> N_sys;
   int32_t* err = nullptr;        // device error word, then 7 diagnostic words
   // batch
@@ -284,7 +288,27 @@ cudaError_t launch_convert_sys(const TI* in, int64_t in_stride, TO* out, int64_t
 cudaError_t launch_sgemm(const float* A, const float* B, float* C, int M, int N, int K, int lda,
                          int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch,
                          float alpha, float beta, bool transA, bool transB, cudaStream_t st);
+// C = alpha (op(A1) op(B1) + op(A2) op(B2)) + beta C in FP32, batched; A2 = null: one
+// product.  Both products share the leading dimensions and batch strides.
+cudaError_t launch_sgemm2(const float* A1, const float* B1, bool tA1, bool tB1, const float* A2,
+                          const float* B2, bool tA2, bool tB2, float* C, int M, int N, int K,
+                          int lda, int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC,
+                          int batch, float alpha, float beta, cudaStream_t st);
 cudaError_t launch_recursion_f64(const Plan& p, const double* u, double* y, cudaStream_t st);
+// Zero-order hold (zoh.cu): matrix exponentials by scaling and squaring, FP64.
+size_t expm_scratch_doubles(int n, int ns);
+int expm_squarings(double norm1);
+cudaError_t expm_batched(double* X, int n, int ns, const std::vector<int>& sq, const double* d_f,
+                         double* scratch, int32_t* singular, cudaStream_t st);
+cudaError_t launch_zoh_block(const double* A, const double* B, const double* delta, double* Z,
+                             int m, int p, int ns, bool transpose, cudaStream_t st);
+cudaError_t launch_norms(const double* X, int n, int ns, double* n1, double* ninf,
+                         cudaStream_t st);
+cudaError_t launch_frechet_block(const double* ZT, const double* dAbar, const double* dBbar,
+                                 const double* scale, double* W, double* gnorm, int m, int p,
+                                 int ns, cudaStream_t st);
+cudaError_t launch_block(const double* X, int n, int r0, int c0, int rows, int cols, double* out,
+                         int64_t out_stride, const double* f, double c, int ns, cudaStream_t st);
 cudaError_t launch_selftest_timeout(int32_t limit_us, int32_t* err, cudaStream_t st);
 
 // Shape of the tensor-core stage kernel (see stage_tc.cu).

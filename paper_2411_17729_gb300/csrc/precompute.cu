@@ -227,6 +227,114 @@ cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int
                              transA, transB, st);
 }
 
+// ----------------------------------------------------------------------------
+// Batched FP32 GEMM with two products, C = alpha (op(A1) op(B1) + op(A2) op(B2))
+// + beta C (row-major; A2 may be null), 128 x 128 tiles, 8 x 8 outputs per
+// thread as two 4 x 4 quadrants (float4 shared-memory reads).  Used for the
+// backward's squaring-chain adjoint dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1),
+// one launch per level.
+// ----------------------------------------------------------------------------
+struct GemmOp {
+  const float* A;
+  const float* B;
+  int lda, ldb;
+  int64_t sA, sB;
+  int ta, tb;
+};
+
+constexpr int G2_BM = 128, G2_BK = 16;
+
+__device__ __forceinline__ void g2_load(float (*dst)[G2_BM + 4], const float* X, int ld,
+                                        bool trans, int r0, int k0, int R, int K) {
+  // dst[k][r] = op(X)[r0 + r][k0 + k]; op(X)[r][k] = trans ? X[k][r] : X[r][k]
+  const int t = threadIdx.x;
+  if (!trans) {
+    const int r = t >> 1, kb = (t & 1) * 8;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int gr = r0 + r, gk = k0 + kb + e;
+      dst[kb + e][r] = (gr < R && gk < K) ? X[(int64_t)gr * ld + gk] : 0.f;
+    }
+  } else {
+    const int k = t >> 4, rb = (t & 15) * 8;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int gr = r0 + rb + e, gk = k0 + k;
+      dst[k][rb + e] = (gr < R && gk < K) ? X[(int64_t)gk * ld + gr] : 0.f;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) sgemm2_kernel(GemmOp o1, GemmOp o2, int two,
+                                                     float* __restrict__ C, int M, int N, int K,
+                                                     int ldc, int64_t sC, float alpha,
+                                                     float beta) {
+  __shared__ __align__(16) float As[G2_BK][G2_BM + 4];
+  __shared__ __align__(16) float Bs[G2_BK][G2_BM + 4];
+  const int b = blockIdx.z;
+  const int m0 = blockIdx.y * G2_BM, n0 = blockIdx.x * G2_BM;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int op = 0; op < 1 + two; ++op) {
+    const GemmOp& o = op ? o2 : o1;
+    const float* A = o.A + (int64_t)b * o.sA;
+    const float* B = o.B + (int64_t)b * o.sB;
+    for (int k0 = 0; k0 < K; k0 += G2_BK) {
+      g2_load(As, A, o.lda, o.ta != 0, m0, k0, M, K);
+      // op(B)[k][n] = op(B^T)[n][k]: load B^T's rows n with the opposite transposition
+      g2_load(Bs, B, o.ldb, o.tb == 0, n0, k0, N, K);
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < G2_BK; ++kk) {
+        float a[8], bv[8];
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+        a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+        a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+        bv[0] = b0.x; bv[1] = b0.y; bv[2] = b0.z; bv[3] = b0.w;
+        bv[4] = b1.x; bv[5] = b1.y; bv[6] = b1.z; bv[7] = b1.w;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  float* Cb = C + (int64_t)b * sC;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+      if (gn >= N) continue;
+      float* c = Cb + (int64_t)gm * ldc + gn;
+      *c = alpha * acc[i][j] + (beta != 0.f ? beta * *c : 0.f);
+    }
+  }
+}
+
+cudaError_t launch_sgemm2(const float* A1, const float* B1, bool tA1, bool tB1, const float* A2,
+                          const float* B2, bool tA2, bool tB2, float* C, int M, int N, int K,
+                          int lda, int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC,
+                          int batch, float alpha, float beta, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  const GemmOp o1{A1, B1, lda, ldb, sA, sB, tA1 ? 1 : 0, tB1 ? 1 : 0};
+  const GemmOp o2{A2 ? A2 : A1, B2 ? B2 : B1, lda, ldb, sA, sB, tA2 ? 1 : 0, tB2 ? 1 : 0};
+  dim3 grid((N + G2_BM - 1) / G2_BM, (M + G2_BM - 1) / G2_BM, batch);
+  sgemm2_kernel<<<grid, 256, 0, st>>>(o1, o2, A2 ? 1 : 0, C, M, N, K, ldc, sC, alpha, beta);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sgemm(const float* A, const float* B, float* C, int M, int N, int K, int lda,
                          int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch,
                          float alpha, float beta, bool transA, bool transB, cudaStream_t st) {

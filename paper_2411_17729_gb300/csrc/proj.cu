@@ -270,11 +270,205 @@ __global__ void __launch_bounds__(256) contract_kernel(const Tile* __restrict__ 
   }
 }
 
+// ------------------------------------------------------------------ narrow forms
+// With px (expand) or nout (contract) of a few columns the GEMM tiles above are
+// mostly padding; these stream the state rows instead.  Coefficients sit in
+// shared memory as [j][c] (m * width <= THIN_ELEMS floats per matrix).
+constexpr int THIN_ELEMS = 4096;
+
+// Shared-memory position of coefficient (j, c): column c = 8 g + 4 h + t is
+// stored so that the 32 threads reading the 4-column half h of consecutive
+// groups g touch 512 consecutive bytes (no bank conflicts):
+//   j * stride + (g / 32) * 256 + h * 128 + (g % 32) * 4 + t,  stride = m rounded up to 256.
+__device__ __forceinline__ int thin_idx(int j, int c, int stride) {
+  const int g = c >> 3, h = (c >> 2) & 1, t = c & 3;
+  return j * stride + (g >> 5) * 256 + h * 128 + (g & 31) * 4 + t;
+}
+__host__ __device__ __forceinline__ int thin_stride(int m) { return (m + 255) & ~255; }
+
+// expand: thread item = (row, 8 columns); 2 items in flight per thread.
+template <int FMT, bool TWO>
+__global__ void __launch_bounds__(256) expand_thin_kernel(const Tile* __restrict__ tiles, int m,
+                                                          int px, const float* __restrict__ X,
+                                                          int ldx, Coef M1, Coef M2, Bufs out,
+                                                          int buf_mode, int buf_fixed,
+                                                          int odd_only) {
+  __shared__ __align__(16) float M1s[THIN_ELEMS];
+  __shared__ __align__(16) float M2s[TWO ? THIN_ELEMS : 4];
+  __shared__ float Xs[(PBM + 1) * 8];      // rows t0 - 1 .. t0 + 127 of X (px <= 8)
+  const Tile t = tiles[blockIdx.x];
+  const int stride = thin_stride(m);
+  for (int e = threadIdx.x; e < px * m; e += 256) {
+    const int j = e / m, c = e - j * m;
+    M1s[thin_idx(j, c, stride)] = M1.at(t.sys, c, j);
+    if (TWO) M2s[thin_idx(j, c, stride)] = M2.at(t.sys, c, j);
+  }
+  for (int e = threadIdx.x; e < (PBM + 1) * px; e += 256) {
+    const int r = e / px, j = e - r * px;
+    const int l = t.t0 - 1 + r;
+    Xs[e] = (l >= 0 && l < t.len) ? X[(t.seq_row0 + l) * ldx + j] : 0.f;
+  }
+  __syncthreads();
+  const int b = buf_mode ? ((t.flags + 1) & 1) : buf_fixed;
+  void* hi = out.hi(b);
+  void* lo = out.lo(b);
+  const int groups = m >> 3;
+  const int rows = min(PBM, t.len - t.t0);
+  const int items = rows * groups;
+  for (int it0 = threadIdx.x; it0 < items; it0 += 512) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int it = it0 + h * 256;
+      if (it >= items) continue;
+      const int r = it / groups, c0 = (it - r * groups) * 8;
+      const int l = t.t0 + r;
+      const int64_t row = t.seq_row0 + l;
+      const bool second = TWO && l >= 1 && (!odd_only || (l & 1));
+      float acc[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+      for (int j = 0; j < px; ++j) {
+        const float x1 = Xs[(r + 1) * px + j];
+        const float x0 = second ? Xs[r * px + j] : 0.f;
+        const float4 a0 = *reinterpret_cast<const float4*>(&M1s[thin_idx(j, c0, stride)]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&M1s[thin_idx(j, c0 + 4, stride)]);
+        acc[0] = fmaf(a0.x, x1, acc[0]); acc[1] = fmaf(a0.y, x1, acc[1]);
+        acc[2] = fmaf(a0.z, x1, acc[2]); acc[3] = fmaf(a0.w, x1, acc[3]);
+        acc[4] = fmaf(a1.x, x1, acc[4]); acc[5] = fmaf(a1.y, x1, acc[5]);
+        acc[6] = fmaf(a1.z, x1, acc[6]); acc[7] = fmaf(a1.w, x1, acc[7]);
+        if (TWO) {
+          const float4 b0 = *reinterpret_cast<const float4*>(&M2s[thin_idx(j, c0, stride)]);
+          const float4 b1 = *reinterpret_cast<const float4*>(&M2s[thin_idx(j, c0 + 4, stride)]);
+          acc[0] = fmaf(b0.x, x0, acc[0]); acc[1] = fmaf(b0.y, x0, acc[1]);
+          acc[2] = fmaf(b0.z, x0, acc[2]); acc[3] = fmaf(b0.w, x0, acc[3]);
+          acc[4] = fmaf(b1.x, x0, acc[4]); acc[5] = fmaf(b1.y, x0, acc[5]);
+          acc[6] = fmaf(b1.z, x0, acc[6]); acc[7] = fmaf(b1.w, x0, acc[7]);
+        }
+      }
+      store8<FMT>(hi, lo, row * (int64_t)m + c0, acc);
+    }
+  }
+}
+
+// contract: each warp walks 16 consecutive rows of the tile, lanes over 8-column
+// groups (NCH groups per lane, m <= 256 NCH), then a warp reduction per output
+// column.  With the shifted term, row l+1 is loaded once and serves as the
+// next row of l and then as the row itself.
+template <int FMT, bool TWO, int NCH>
+__global__ void __launch_bounds__(256) contract_thin_kernel(const Tile* __restrict__ tiles, int m,
+                                                            int nout, Bufs V, int buf_mode,
+                                                            int buf_fixed, Coef M1, Coef M2,
+                                                            Coef M3, const float* __restrict__ X,
+                                                            int px, float* __restrict__ out) {
+  constexpr int QT = 4;   // nout <= QT
+  __shared__ __align__(16) float M1s[THIN_ELEMS];
+  __shared__ __align__(16) float M2s[TWO ? THIN_ELEMS : 4];
+  const Tile t = tiles[blockIdx.x];
+  const int stride = thin_stride(m);
+  for (int e = threadIdx.x; e < nout * m; e += 256) {
+    const int j = e / m, c = e - j * m;
+    M1s[thin_idx(j, c, stride)] = M1.at(t.sys, j, c);
+    if (TWO) M2s[thin_idx(j, c, stride)] = M2.at(t.sys, j, c);
+  }
+  __syncthreads();
+  const int b = buf_mode ? t.fbuf : buf_fixed;
+  const void* vh = V.hi(b);
+  const void* vl = V.lo(b);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = min(PBM, t.len - t.t0);
+  const int rbeg = warp * 16, rend = min(rows, rbeg + 16);
+  auto load_row = [&](int r, float (&v)[NCH][8]) {
+    const int64_t row = t.seq_row0 + t.t0 + r;
+#pragma unroll
+    for (int ci = 0; ci < NCH; ++ci) {
+      const int c0 = lane * 8 + ci * 256;
+      if (c0 < m && r < t.len - t.t0) {
+        load8<FMT>(vh, vl, row * (int64_t)m + c0, v[ci]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[ci][e] = 0.f;
+      }
+    }
+  };
+  // rows in register blocks of RB (RB + 1 rows loaded with the shifted term; the
+  // last one is carried into the next block)
+  constexpr int RB = NCH >= 4 ? 1 : 4 / NCH;
+  constexpr int NV = RB + (TWO ? 1 : 0);
+  float v[NV][NCH][8];
+  bool have0 = false;
+  for (int r0 = rbeg; r0 < rend; r0 += RB) {
+#pragma unroll
+    for (int u = 0; u < NV; ++u)
+      if (!(u == 0 && have0)) load_row(r0 + u, v[u]);
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int r = r0 + u;
+      if (r >= rend) break;
+      float acc[QT];
+#pragma unroll
+      for (int j = 0; j < QT; ++j) {
+        float sj = 0.f;
+        if (j < nout) {
+#pragma unroll
+          for (int ci = 0; ci < NCH; ++ci) {
+            const int c0 = lane * 8 + ci * 256;
+            if (c0 >= m) continue;
+            const float4 a0 = *reinterpret_cast<const float4*>(&M1s[thin_idx(j, c0, stride)]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&M1s[thin_idx(j, c0 + 4, stride)]);
+            const float w1[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sj = fmaf(w1[e], v[u][ci][e], sj);
+            if (TWO) {
+              const float4 b0 = *reinterpret_cast<const float4*>(&M2s[thin_idx(j, c0, stride)]);
+              const float4 b1 =
+                  *reinterpret_cast<const float4*>(&M2s[thin_idx(j, c0 + 4, stride)]);
+              const float w2[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+              for (int e = 0; e < 8; ++e) sj = fmaf(w2[e], v[u + (TWO ? 1 : 0)][ci][e], sj);
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
+        acc[j] = sj;
+      }
+      if (lane < nout) {
+        const int64_t row = t.seq_row0 + t.t0 + r;
+        float sv = 0.f;
+#pragma unroll
+        for (int j = 0; j < QT; ++j)
+          if (j == lane) sv = acc[j];
+        for (int i = 0; i < px; ++i) sv = fmaf(M3.at(t.sys, lane, i), __ldg(X + row * px + i), sv);
+        out[row * nout + lane] = sv;
+      }
+    }
+    if (TWO) {   // row r0 + RB is the first row of the next block
+#pragma unroll
+      for (int ci = 0; ci < NCH; ++ci)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[0][ci][e] = v[NV - 1][ci][e];
+      have0 = true;
+    }
+  }
+}
+
 template <int FMT, bool TWO>
 cudaError_t contract_dispatch(const Tile* tiles, int ntiles, int m, int nout, const Bufs& V,
                               int buf_mode, int buf_fixed, const Coef& M1, const Coef& M2,
                               const Coef& M3, const float* X, int px, float* out,
                               cudaStream_t st) {
+  if (nout <= 4 && thin_stride(m) * nout <= THIN_ELEMS && m <= 1024) {
+    const int nch = (m + 255) / 256;
+#define CASCADE_CTHIN(NC)                                                                     \
+  contract_thin_kernel<FMT, TWO, NC><<<ntiles, 256, 0, st>>>(tiles, m, nout, V, buf_mode,      \
+                                                             buf_fixed, M1, M2, M3, X, px, out)
+    if (nch == 1) CASCADE_CTHIN(1);
+    else if (nch == 2) CASCADE_CTHIN(2);
+    else CASCADE_CTHIN(4);
+#undef CASCADE_CTHIN
+    CASCADE_LAUNCHED();
+    return cudaGetLastError();
+  }
   const int ct = nout <= 8 ? 1 : nout <= 16 ? 2 : nout <= 32 ? 4 : 8;
   dim3 grid(ntiles, (nout + 8 * ct - 1) / (8 * ct));
 #define CASCADE_CONTRACT(CTV)                                                                 \
@@ -296,6 +490,16 @@ cudaError_t expand_dispatch(int precision, const Tile* tiles, int ntiles, int m,
                             const float* X, int ldx, const Coef& M1, const Coef& M2,
                             const Bufs& out, int buf_mode, int buf_fixed, int odd_only,
                             cudaStream_t st) {
+  if (px <= 8 && thin_stride(m) * px <= THIN_ELEMS) {
+    if (precision == CASCADE_BF16_SPLIT)
+      expand_thin_kernel<FMT_BF16, TWO><<<ntiles, 256, 0, st>>>(tiles, m, px, X, ldx, M1, M2, out,
+                                                               buf_mode, buf_fixed, odd_only);
+    else
+      expand_thin_kernel<FMT_F32, TWO><<<ntiles, 256, 0, st>>>(tiles, m, px, X, ldx, M1, M2, out,
+                                                              buf_mode, buf_fixed, odd_only);
+    CASCADE_LAUNCHED();
+    return cudaGetLastError();
+  }
   dim3 grid(ntiles, (m + 63) / 64);
   if (precision == CASCADE_BF16_SPLIT)
     expand_kernel<FMT_BF16, TWO><<<grid, 256, 0, st>>>(tiles, m, px, X, ldx, M1, M2, out,

@@ -173,6 +173,18 @@ def test_differentiation_form_full_size(lib):
     compare(w, c, g, dy, GTOL["bf16_split"])
 
 
+def test_large_form_backward_reduced_length(lib):
+    """The large form's shapes (m = 1024, p = q = 64, Abar = 0.9999 Q + rank-4 E,
+    N = 15 clipped to the length) on one 3000-step sequence: every gradient
+    (u, Abar through the squaring chain, Bbar, C, D) against the oracle's
+    FP64 adjoint."""
+    w = wl.large_form(L=3000, batch=1)
+    w = cast_inputs(w, "bf16_split")
+    dy = np.random.default_rng(16).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
+    c, _, g = gpu_grads(lib, w, "bf16_split", dy)
+    compare(w, c, g, dy, GTOL["bf16_split"])
+
+
 @pytest.mark.parametrize("p,q", [(1, 1), (8, 2), (16, 16), (3, 20), (64, 64)])
 def test_tc_backward_mimo_shapes(lib, p, q):
     """Input and output widths across the projection and reduction kernels:

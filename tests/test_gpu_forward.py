@@ -228,6 +228,29 @@ def test_precision_form_full_size_sampled(lib):
     assert worst <= TOL["bf16_split"], worst
 
 
+def test_large_form_full_size_sampled(lib):
+    """m = 1024, p = q = 64, 8 sequences x 65536 steps, N = 15, Abar = 0.9999 Q
+    + rank-4 E, BF16 split (four N-blocks per tile, separate output GEMM), in
+    the benchmark's launch configuration.  The oracle recomputes 192-step
+    prefixes of every sequence (the cascade is causal, so a prefix run with
+    the same N gives the same rows)."""
+    w = cast_inputs(wl.large_form(), "bf16_split")
+    c, y = run_gpu(lib, w, "bf16_split")
+    assert np.all(c.seq_N() == 15)
+    Abar, Bbar, C, D = oracle.system_matrices(w, 0)
+    powers = oracle.squaring_chain(Abar, 15)
+    worst = 0.0
+    for i in range(w.nseq):
+        sl = w.seq(i)
+        uu = w.u[sl][:192]
+        yo = oracle.cascade_forward_seq(Abar, Bbar, C, D, uu, 15, powers=powers)
+        yg = y[sl][:192]
+        Du = uu @ D.T
+        worst = max(worst, np.linalg.norm(yg - yo) / np.linalg.norm(yo),
+                    np.linalg.norm(yg - yo) / np.linalg.norm(yo - Du))
+    assert worst <= TOL["bf16_split"], worst
+
+
 def test_batching_form_full_size_sampled(lib):
     """512 sequences of uneven length (log-uniform in [1024, 65536], 8.85e6
     rows), m = 128, p = q = 4, Abar = 1.000001 x trapezoid(HiPPO-LegS, 5e-7)

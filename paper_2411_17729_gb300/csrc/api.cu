@@ -220,6 +220,11 @@ void free_batch(Plan* p) {
   p->n_out_tiles = p->n_stage0_tiles = 0;
   for (Plan::ScanLevel& lv : p->scan) dfree(lv.d_tiles);
   p->scan.clear();
+  dfree(p->d_scan_rows);
+  dfree(p->d_scan_rows_sys);
+  p->d_scan_rows = nullptr;
+  p->d_scan_rows_sys = nullptr;
+  p->n_scan_rows = 0;
   p->scan_rows_cap = 0;
   p->matvecs = 0;
   p->have_batch = false;
@@ -438,7 +443,8 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
     for (const Plan::ScanLevel& lv : p->scan) {
       if (timing && lv.n > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
       CK(launch_stage_tc_strided(*p, lv.k, 2 << lv.k, lv.d_tiles, lv.n,
-                                 (uint64_t)p->scan_rows_cap, V.hi(0), V.lo(0), st),
+                                 (uint64_t)p->scan_rows_cap, V.hi(0), V.lo(0),
+                                 static_cast<const float*>(u), static_cast<float*>(y), st),
          "scan level");
       if (timing && lv.n > 0) {
         CK(cudaEventRecord(p->ev[2 * p->n_ev + 1], st), "event");
@@ -446,8 +452,13 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
         p->n_ev++;
       }
     }
-    CK(launch_proj_output(*p, static_cast<const float*>(u), static_cast<float*>(y), V, st),
-       "output projection");
+    if (p->fuse_output)
+      CK(launch_proj_rows_output(*p, p->d_scan_rows, p->n_scan_rows, p->d_scan_rows_sys,
+                                 static_cast<const float*>(u), static_cast<float*>(y), V, 0, st),
+         "output projection (rows 2^t - 1)");
+    else
+      CK(launch_proj_output(*p, static_cast<const float*>(u), static_cast<float*>(y), V, st),
+         "output projection");
     return CASCADE_OK;
   }
   // buffer holding v^(k) read by stage k, and the one stage k writes
@@ -506,7 +517,7 @@ cudaError_t gemm_t(const float* A, const float* B, float* C, int M, int N, int K
 }
 // One level of the squaring-chain adjoint: dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1).
 cudaError_t chain_step(const double* dPn, const double* P, double* dP, int m, int64_t stride,
-                       int batch, cudaStream_t st) {
+                       int batch, cudaStream_t st, void*, size_t) {
   cudaError_t e = launch_dgemm(dPn, P, dP, m, m, m, m, m, m, stride, stride, stride, batch, 1.0,
                                1.0, false, true, st);
   if (e != cudaSuccess) return e;
@@ -514,9 +525,10 @@ cudaError_t chain_step(const double* dPn, const double* P, double* dP, int m, in
                       false, st);
 }
 cudaError_t chain_step(const float* dPn, const float* P, float* dP, int m, int64_t stride,
-                       int batch, cudaStream_t st) {
+                       int batch, cudaStream_t st, void* scratch, size_t scratch_bytes) {
   return launch_sgemm2(dPn, P, false, true, P, dPn, true, false, dP, m, m, m, m, m, m, stride,
-                       stride, stride, batch, 1.0f, 1.0f, st);
+                       stride, stride, batch, 1.0f, 1.0f, st, static_cast<float*>(scratch),
+                       scratch_bytes / sizeof(float));
 }
 template <typename T>
 cudaError_t to_f64(const T* src, int64_t src_stride, double* dst, int64_t dst_stride, int64_t n,
@@ -699,7 +711,9 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   CK(gemm_t(P, R2, dBb, m, pp, m, m, pp, pp, kst, mp, mp, ns, 1.0, 1.0, true, false, st), "dBbar");
   // squaring chain P_(k+1) = P_k P_k:  dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1)
   for (int k = p->kmax1 - 2; k >= 0; --k)
-    CK(chain_step(dP + (k + 1) * mm, P + k * mm, dP + k * mm, m, kst, ns, st), "chain");
+    CK(chain_step(dP + (k + 1) * mm, P + k * mm, dP + k * mm, m, kst, ns, st, part,
+                  L.off_dP - L.off_part),
+       "chain");
   if (dAbar) CK(to_f64<T>(dP, kst, dAbar, mm, mm, ns, st), "dAbar");
   if (dBbar) CK(to_f64<T>(dBb, mp, dBbar, mp, mp, ns, st), "dBbar");
   // trapezoidal discretisation (Eq. 4.2), Abar = c M^-1 (I + delta/2 A), Bbar = delta M^-1 B:
@@ -1112,8 +1126,10 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
         p->matvecs += cnt;
         for (int64_t j0 = 0; j0 < cnt; j0 += BM) {
           const int64_t R0 = h_offsets[i] + (j0 + 1) * S - 1 + d;
-          tl.push_back(Tile{R0, 0, (int32_t)std::min<int64_t>(BM, cnt - j0), p->sys_of_seq[i], 0,
-                            0, 0});
+          // every row a down-sweep level writes is final: with the fused output its
+          // epilogue also forms y for it
+          tl.push_back(Tile{R0, 0, (int32_t)std::min<int64_t>(BM, cnt - j0), p->sys_of_seq[i],
+                            (down && p->fuse_output) ? (int32_t)TILE_FINAL_FUSED : 0, 0, 0});
         }
       }
       Plan::ScanLevel lv{k, down ? 1 : 0, (int)tl.size(), nullptr};
@@ -1132,6 +1148,28 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     for (int k = K - 2; k >= 0; --k) {
       const cascade_status_t r = level(k, true);
       if (r != CASCADE_OK) return r;
+    }
+    if (p->fuse_output) {
+      // rows l = 2^t - 1 are never written by the down-sweep: their y is formed
+      // after the last level
+      std::vector<int64_t> rws;
+      std::vector<int32_t> rsys;
+      for (int i = 0; i < nseq; ++i) {
+        const int64_t L = h_offsets[i + 1] - h_offsets[i];
+        for (int64_t l = 0; l < L; l = 2 * l + 1) {
+          rws.push_back(h_offsets[i] + l);
+          rsys.push_back(p->sys_of_seq[i]);
+        }
+      }
+      p->n_scan_rows = (int)rws.size();
+      if (!rws.empty()) {
+        CK(cudaMalloc(&p->d_scan_rows, rws.size() * sizeof(int64_t)), "alloc scan rows");
+        CK(cudaMalloc(&p->d_scan_rows_sys, rsys.size() * sizeof(int32_t)), "alloc scan rows");
+        CK(cudaMemcpy(p->d_scan_rows, rws.data(), rws.size() * sizeof(int64_t),
+                      cudaMemcpyHostToDevice), "upload scan rows");
+        CK(cudaMemcpy(p->d_scan_rows_sys, rsys.data(), rsys.size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice), "upload scan rows");
+      }
     }
   }
   if (recomputes(*p)) {
@@ -1155,6 +1193,7 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     if (L == 0) continue;
     const int N = p->seq_N[i], sys = p->sys_of_seq[i];
     const bool fused_last = p->fuse_output && N >= 1 && !scans(*p);
+    // (the work-efficient schedule forms y in its down-sweep levels instead)
     for (int k = 1; k <= N && !scans(*p); ++k) {   // stage schedule (§3)
       const bool fused = fused_last && k == N;
       const int64_t prev_shift = int64_t(1) << (k - 1);
@@ -1166,7 +1205,7 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
                                      fused ? (int32_t)TILE_FINAL_FUSED : 0, 0, 0});
       }
     }
-    if (!fused_last) {   // fbuf: state buffer holding v^(N+1)
+    if (!fused_last && !(scans(*p) && p->fuse_output)) {   // fbuf: buffer holding v^(N+1)
       const int buf = scans(*p) ? 0 : fwd_buf(*p, N + 1);
       for (int64_t t = 0; t < L; t += BM)
         outs.push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys, 0, buf, 0});

@@ -164,52 +164,61 @@ __device__ __forceinline__ void load_row_vec(const void* hi, const void* lo, int
 //   partial[chunk][h] += X_l (outer) T_(l - sh_h),
 // X a state buffer or dense array with `a` columns, T dense [rows, ld] with tc
 // columns (zero before the sequence start).  Each (chunk, h) block is stored
-// [tc][a] if thin_major, else [a][tc].  Threads own CPT consecutive columns
-// of X and all TT = nsh * tc thin columns; 256 / G rows are processed at once
-// (G threads per row), and the row groups are summed in a fixed order, so the
-// result is deterministic.
+// [tc][a] if thin_major, else [a][tc].  A thread owns CPT consecutive columns
+// of X (16-byte loads) and TT of the tt = nsh * tc thin columns: G column groups
+// x TG thin groups of threads share a row, 256 / (G TG) rows are processed at
+// once, and the row groups are summed in a fixed order, so the result is
+// deterministic.
 constexpr int WT_SMEM_BYTES = 32768;
+constexpr int WT_TC_MAX = 16;   // thin columns per source (the rows staged in shared memory)
 template <int FMT, typename ACC, int CPT, int TT>
 __global__ void __launch_bounds__(256) wtreduce_kernel(const Tile* __restrict__ tiles,
                                                        const int32_t* __restrict__ chunks, int BM,
                                                        int m, TSrc X, int a,
                                                        const ACC* __restrict__ T, int ld, int tc,
                                                        int nsh, int sh0, int sh1, int gshift,
-                                                       int vec, int thin_major,
+                                                       int tgshift, int vec, int thin_major,
                                                        ACC* __restrict__ partial) {
   __shared__ __align__(16) unsigned char red_raw[WT_SMEM_BYTES];
+  // the tile's thin rows, times t0 - 1 .. t0 + BM - 1 (shifts are 0 or 1)
+  constexpr int TROWS = (FMT == FMT_F64 ? 64 : 128) + 1;
+  __shared__ ACC Ts[TROWS * WT_TC_MAX];
   ACC* red = reinterpret_cast<ACC*>(red_raw);
   const int c = blockIdx.x;
   const int first = chunks[3 * c], count = chunks[3 * c + 1];
-  const int G = 1 << gshift, R = 256 >> gshift;
-  const int g = threadIdx.x & (G - 1), rg = threadIdx.x >> gshift;
+  const int G = 1 << gshift, R = 256 >> (gshift + tgshift);
+  const int g = threadIdx.x & (G - 1);
+  const int tg = (threadIdx.x >> gshift) & ((1 << tgshift) - 1);
+  const int rg = threadIdx.x >> (gshift + tgshift);
   const int i0 = g * CPT;
+  const int e0 = tg * TT;           // this thread's first thin column
   const int tt = nsh * tc;
   ACC acc[CPT][TT];
 #pragma unroll
   for (int i = 0; i < CPT; ++i)
 #pragma unroll
     for (int e = 0; e < TT; ++e) acc[i][e] = 0;
-  constexpr int RU = 4;   // rows in flight per thread
+  // rows in flight per thread: RU rows of CPT columns (32 values) are loaded
+  // before their products; the thin values are read from shared memory
+  constexpr int RU = 32 / CPT;
   for (int ti = first; ti < first + count; ++ti) {
     const Tile t = tiles[ti];
     const int rows = min(BM, t.len - t.t0);
     const int b = X.buf_mode ? t.fbuf : X.buf_fixed;
+    __syncthreads();   // the previous tile's thin rows are no longer read
+    for (int e = threadIdx.x; e < (rows + 1) * tc; e += 256) {
+      const int r = e / tc, j = e - r * tc;
+      const int l = t.t0 - 1 + r;
+      Ts[r * WT_TC_MAX + j] = l >= 0 ? T[(t.seq_row0 + l) * ld + j] : (ACC)0;
+    }
+    __syncthreads();
     for (int rr0 = rg; rr0 < rows; rr0 += RU * R) {
-      ACC tv[RU][TT], xv[RU][CPT];
+      ACC xv[RU][CPT];
 #pragma unroll
       for (int u = 0; u < RU; ++u) {
         const int rr = rr0 + u * R;
         const bool live = rr < rows && i0 < a;
-        const int l = t.t0 + rr;
-        const int64_t row = t.seq_row0 + l;
-#pragma unroll
-        for (int e = 0; e < TT; ++e) {
-          const int h = e >= tc ? 1 : 0;
-          const int j = e - h * tc;
-          const int src = l - (h ? sh1 : sh0);
-          tv[u][e] = (live && e < tt && src >= 0) ? T[(t.seq_row0 + src) * ld + j] : (ACC)0;
-        }
+        const int64_t row = t.seq_row0 + t.t0 + rr;
         if constexpr (FMT != FMT_F64) {
           if (vec && live) {
             float f[CPT];
@@ -224,11 +233,22 @@ __global__ void __launch_bounds__(256) wtreduce_kernel(const Tile* __restrict__ 
           xv[u][i] = (live && i0 + i < a) ? (ACC)src_get<FMT>(X, t, row, i0 + i, m) : (ACC)0;
       }
 #pragma unroll
-      for (int u = 0; u < RU; ++u)
+      for (int u = 0; u < RU; ++u) {
+        const int rr = rr0 + u * R;
+        if (rr >= rows) break;
+        const int l = t.t0 + rr;
 #pragma unroll
-        for (int i = 0; i < CPT; ++i)
+        for (int e = 0; e < TT; ++e) {
+          const int eg = e0 + e;
+          if (eg >= tt) break;
+          const int h = eg >= tc ? 1 : 0;
+          const int j = eg - h * tc;
+          const int sh = h ? sh1 : sh0;
+          const ACC tv = l - sh >= 0 ? Ts[(rr + 1 - sh) * WT_TC_MAX + j] : (ACC)0;
 #pragma unroll
-          for (int e = 0; e < TT; ++e) acc[i][e] = fma(xv[u][i], tv[u][e], acc[i][e]);
+          for (int i = 0; i < CPT; ++i) acc[i][e] = fma(xv[u][i], tv, acc[i][e]);
+        }
+      }
     }
   }
   // Sum the row groups.  Single precision: every group stores its partial and
@@ -242,7 +262,7 @@ __global__ void __launch_bounds__(256) wtreduce_kernel(const Tile* __restrict__ 
         if (i0 + i >= a) continue;
 #pragma unroll
         for (int e = 0; e < TT; ++e)
-          if (e < tt) red[(int64_t)rg * slab + (i0 + i) * tt + e] = acc[i][e];
+          if (e0 + e < tt) red[(int64_t)rg * slab + (i0 + i) * tt + e0 + e] = acc[i][e];
       }
     }
     for (int sstep = R >> 1; sstep >= 1; sstep >>= 1) {
@@ -253,8 +273,8 @@ __global__ void __launch_bounds__(256) wtreduce_kernel(const Tile* __restrict__ 
           if (i0 + i >= a) continue;
 #pragma unroll
           for (int e = 0; e < TT; ++e)
-            if (e < tt) {
-              ACC* r0 = red + (int64_t)rg * slab + (i0 + i) * tt + e;
+            if (e0 + e < tt) {
+              ACC* r0 = red + (int64_t)rg * slab + (i0 + i) * tt + e0 + e;
               *r0 += r0[(int64_t)sstep * slab];
             }
         }
@@ -269,8 +289,8 @@ __global__ void __launch_bounds__(256) wtreduce_kernel(const Tile* __restrict__ 
           if (i0 + i >= a) continue;
 #pragma unroll
           for (int e = 0; e < TT; ++e) {
-            if (e >= tt) continue;
-            ACC* r = red + (int64_t)(i0 + i) * tt + e;
+            if (e0 + e >= tt) continue;
+            ACC* r = red + (int64_t)(i0 + i) * tt + e0 + e;
             *r = (q == 0 ? (ACC)0 : *r) + acc[i][e];
           }
         }
@@ -429,49 +449,50 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
 
 // Thread shape of the wide-by-thin reduction: CPT columns per thread for TT
 // thin columns (CPT * TT <= 32 accumulators).
-static int wt_tt(int tt) {
-  return tt <= 1 ? 1 : tt <= 2 ? 2 : tt <= 4 ? 4 : tt <= 8 ? 8 : tt <= 16 ? 16 : 0;
+// Thread shape of the wide-by-thin reduction: 8 columns per thread, TT thin
+// columns per thread (at most 4, so 32 accumulators), TG thin groups per row.
+static int wt_tt(int tt) { return tt <= 1 ? 1 : tt <= 2 ? 2 : 4; }
+static int wt_tg(int tt) {
+  const int TT = wt_tt(tt);
+  int tg = 1;
+  while (tg * TT < tt) tg <<= 1;
+  return tg;
 }
-static int wt_cpt(int TT) { return TT <= 4 ? 8 : TT <= 8 ? 4 : 2; }
 
 bool wtreduce_supported(const Plan& p, int a, int tc, int nsh) {
   const int tt = nsh * tc;
-  const int TT = wt_tt(tt);
-  if (TT == 0 || nsh < 1 || nsh > 2) return false;
+  if (nsh < 1 || nsh > 2 || tc < 1 || tc > WT_TC_MAX || tt > 32) return false;
+  int G = 1;
+  while (G * 8 < a) G <<= 1;
+  if (G * wt_tg(tt) > 256) return false;
   const size_t acc = p.d.precision == CASCADE_FP64 ? 8 : 4;
-  if ((size_t)a * tt * acc > (size_t)WT_SMEM_BYTES) return false;
-  return (a + wt_cpt(TT) - 1) / wt_cpt(TT) <= 256;
+  return (size_t)a * tt * acc <= (size_t)WT_SMEM_BYTES;
 }
 
 template <int FMT, typename ACC, int CPT, int TT>
 static void wt_launch(int nchunks, const Tile* tiles, const int32_t* chunks, int BM, int m,
                       const TSrc& X, int a, const ACC* T, int ld, int tc, int nsh, int sh0,
-                      int sh1, int gshift, int vec, int thin_major, ACC* partial,
+                      int sh1, int gshift, int tgshift, int vec, int thin_major, ACC* partial,
                       cudaStream_t st) {
-  wtreduce_kernel<FMT, ACC, CPT, TT><<<nchunks, 256, 0, st>>>(
-      tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1, gshift, vec, thin_major, partial);
+  wtreduce_kernel<FMT, ACC, CPT, TT><<<nchunks, 256, 0, st>>>(tiles, chunks, BM, m, X, a, T, ld,
+                                                              tc, nsh, sh0, sh1, gshift, tgshift,
+                                                              vec, thin_major, partial);
 }
 
 template <int FMT, typename ACC>
 static void wt_dispatch(int TT, int nchunks, const Tile* tiles, const int32_t* chunks, int BM,
                         int m, const TSrc& X, int a, const ACC* T, int ld, int tc, int nsh,
-                        int sh0, int sh1, int gshift, int vec, int thin_major, ACC* partial,
-                        cudaStream_t st) {
+                        int sh0, int sh1, int gshift, int tgshift, int vec, int thin_major,
+                        ACC* partial, cudaStream_t st) {
   if (TT == 1)
     wt_launch<FMT, ACC, 8, 1>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
-                              gshift, vec, thin_major, partial, st);
+                              gshift, tgshift, vec, thin_major, partial, st);
   else if (TT == 2)
     wt_launch<FMT, ACC, 8, 2>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
-                              gshift, vec, thin_major, partial, st);
-  else if (TT == 4)
-    wt_launch<FMT, ACC, 8, 4>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
-                              gshift, vec, thin_major, partial, st);
-  else if (TT == 8)
-    wt_launch<FMT, ACC, 4, 8>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
-                              gshift, vec, thin_major, partial, st);
+                              gshift, tgshift, vec, thin_major, partial, st);
   else
-    wt_launch<FMT, ACC, 2, 16>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
-                               gshift, vec, thin_major, partial, st);
+    wt_launch<FMT, ACC, 8, 4>(nchunks, tiles, chunks, BM, m, X, a, T, ld, tc, nsh, sh0, sh1,
+                              gshift, tgshift, vec, thin_major, partial, st);
 }
 
 cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
@@ -480,12 +501,14 @@ cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chu
                             bool out_f64, int64_t out_sys_stride, int64_t seg_stride,
                             cudaStream_t st) {
   if (nchunks == 0) return cudaSuccess;
-  if (!wtreduce_supported(p, a, tc, nsh)) return cudaErrorInvalidValue;
+  if (!wtreduce_supported(p, a, tc, nsh) || sh0 < 0 || sh0 > 1 || sh1 < 0 || sh1 > 1)
+    return cudaErrorInvalidValue;
   const int BM = tile_rows(p);
   const int TT = wt_tt(nsh * tc);
-  const int CPT = wt_cpt(TT);
-  int gshift = 0;
+  const int CPT = 8;
+  int gshift = 0, tgshift = 0;
   while ((1 << gshift) < (a + CPT - 1) / CPT) ++gshift;
+  while ((1 << tgshift) < wt_tg(nsh * tc)) ++tgshift;
   // vector loads: a state buffer whose rows the column groups cover exactly
   const int vec = (X.kind == 0 && a == p.d.m && a % CPT == 0) ? 1 : 0;
   const int64_t elems = (int64_t)nsh * a * tc;
@@ -493,7 +516,7 @@ cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chu
   const int64_t seg = (int64_t)a * tc;
   if (p.d.precision == CASCADE_FP64) {
     wt_dispatch<FMT_F64, double>(TT, nchunks, tiles, chunks, BM, p.d.m, X, a,
-                                 static_cast<const double*>(T), tc, tc, nsh, sh0, sh1, gshift, 0,
+                                 static_cast<const double*>(T), tc, tc, nsh, sh0, sh1, gshift, tgshift, 0,
                                  thin_major ? 1 : 0, static_cast<double*>(partial), st);
     CASCADE_LAUNCHED();
     reduce_partials_kernel<double, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
@@ -501,11 +524,11 @@ cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chu
   } else {
     if (p.d.precision == CASCADE_BF16_SPLIT)
       wt_dispatch<FMT_BF16, float>(TT, nchunks, tiles, chunks, BM, p.d.m, X, a,
-                                   static_cast<const float*>(T), tc, tc, nsh, sh0, sh1, gshift, vec,
+                                   static_cast<const float*>(T), tc, tc, nsh, sh0, sh1, gshift, tgshift, vec,
                                    thin_major ? 1 : 0, static_cast<float*>(partial), st);
     else
       wt_dispatch<FMT_F32, float>(TT, nchunks, tiles, chunks, BM, p.d.m, X, a,
-                                  static_cast<const float*>(T), tc, tc, nsh, sh0, sh1, gshift, vec,
+                                  static_cast<const float*>(T), tc, tc, nsh, sh0, sh1, gshift, tgshift, vec,
                                   thin_major ? 1 : 0, static_cast<float*>(partial), st);
     CASCADE_LAUNCHED();
     if (out_f64)

@@ -167,6 +167,9 @@ struct Plan {
   };
   std::vector<ScanLevel> scan;
   int64_t scan_rows_cap = 0;     // state rows allocated (a multiple of the largest 2^(k+1))
+  int64_t* d_scan_rows = nullptr;  // rows l = 2^t - 1 of every sequence (never written by the
+  int32_t* d_scan_rows_sys = nullptr;  // down-sweep) and their systems: their y when the
+  int n_scan_rows = 0;                 // levels form y themselves
   int64_t matvecs = 0;           // products by powers in one forward of the batch
   // stage-output checkpoints (CASCADE_FLAG_RECOMPUTE): v^(j) is kept for
   // j = 1, 1 + ck_seg, 1 + 2 ck_seg, ... <= maxN; the backward recomputes the
@@ -220,9 +223,11 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
                             void* vout_hi, void* vout_lo, const float* u, float* y,
                             cudaStream_t st, bool reverse = false);
 // In-place stage k over rows S apart (the work-efficient schedule); the state
-// planes hold rows_cap rows, a multiple of S.
+// planes hold rows_cap rows, a multiple of S.  Tiles flagged TILE_FINAL_FUSED
+// also form y = C v + D u for their rows (u, y may be null otherwise).
 cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,
-                                    uint64_t rows_cap, void* v_hi, void* v_lo, cudaStream_t st);
+                                    uint64_t rows_cap, void* v_hi, void* v_lo, const float* u,
+                                    float* y, cudaStream_t st);
 // Workspace buffer j of a family of equally sized state buffers.
 struct Bufs {
   uint8_t* base;
@@ -266,6 +271,10 @@ cudaError_t launch_proj_output(const Plan& p, const float* u, float* y, const Bu
                                cudaStream_t st);
 cudaError_t launch_proj_du(const Plan& p, const float* G, const Bufs& W, int wbuf, float* du,
                            cudaStream_t st);
+// y = C v + D u for an explicit list of rows (state buffer `buf`).
+cudaError_t launch_proj_rows_output(const Plan& p, const int64_t* rows, int nrows,
+                                    const int32_t* row_sys, const float* u, float* y,
+                                    const Bufs& V, int buf, cudaStream_t st);
 cudaError_t launch_reduce_partials(const Plan& p, const float* partial, const int32_t* sys_begin,
                                    int64_t elems, void* out, bool out_f64, int64_t out_sys_stride,
                                    cudaStream_t st);
@@ -289,11 +298,14 @@ cudaError_t launch_sgemm(const float* A, const float* B, float* C, int M, int N,
                          int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch,
                          float alpha, float beta, bool transA, bool transB, cudaStream_t st);
 // C = alpha (op(A1) op(B1) + op(A2) op(B2)) + beta C in FP32, batched; A2 = null: one
-// product.  Both products share the leading dimensions and batch strides.
+// product.  Both products share the leading dimensions and batch strides.  With
+// few output tiles the K range is split over blocks when `scratch` (device
+// floats) has room for the partial products; they are added in a fixed order.
 cudaError_t launch_sgemm2(const float* A1, const float* B1, bool tA1, bool tB1, const float* A2,
                           const float* B2, bool tA2, bool tB2, float* C, int M, int N, int K,
                           int lda, int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC,
-                          int batch, float alpha, float beta, cudaStream_t st);
+                          int batch, float alpha, float beta, cudaStream_t st,
+                          float* scratch = nullptr, size_t scratch_floats = 0);
 cudaError_t launch_recursion_f64(const Plan& p, const double* u, double* y, cudaStream_t st);
 // Zero-order hold (zoh.cu): matrix exponentials by scaling and squaring, FP64.
 size_t expm_scratch_doubles(int n, int ns);

@@ -7,6 +7,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace cascade {
 
 // ----------------------------------------------------------------------------
@@ -242,96 +244,170 @@ struct GemmOp {
   int ta, tb;
 };
 
-constexpr int G2_BM = 128, G2_BK = 16;
+constexpr int G2_BK = 16;
 
-__device__ __forceinline__ void g2_load(float (*dst)[G2_BM + 4], const float* X, int ld,
-                                        bool trans, int r0, int k0, int R, int K) {
-  // dst[k][r] = op(X)[r0 + r][k0 + k]; op(X)[r][k] = trans ? X[k][r] : X[r][k]
+// dst[k][r] = op(X)[r0 + r][k0 + k] for r < TBM, k < 16; op(X)[r][k] = trans ? X[k][r] : X[r][k]
+template <int TBM>
+__device__ __forceinline__ void g2_load(float (*dst)[TBM + 4], const float* X, int ld, bool trans,
+                                        int r0, int k0, int R, int Kend) {
+  constexpr int PER = TBM * G2_BK / 256;   // elements per thread: 8 or 4
   const int t = threadIdx.x;
   if (!trans) {
-    const int r = t >> 1, kb = (t & 1) * 8;
+    constexpr int TPR = G2_BK / PER;       // threads per row
+    const int r = t / TPR, kb = (t % TPR) * PER;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < PER; ++e) {
       const int gr = r0 + r, gk = k0 + kb + e;
-      dst[kb + e][r] = (gr < R && gk < K) ? X[(int64_t)gr * ld + gk] : 0.f;
+      dst[kb + e][r] = (gr < R && gk < Kend) ? X[(int64_t)gr * ld + gk] : 0.f;
     }
   } else {
-    const int k = t >> 4, rb = (t & 15) * 8;
+    constexpr int TPK = TBM / PER;         // threads per k
+    const int k = t / TPK, rb = (t % TPK) * PER;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < PER; ++e) {
       const int gr = r0 + rb + e, gk = k0 + k;
-      dst[k][rb + e] = (gr < R && gk < K) ? X[(int64_t)gk * ld + gr] : 0.f;
+      dst[k][rb + e] = (gr < R && gk < Kend) ? X[(int64_t)gk * ld + gr] : 0.f;
     }
   }
 }
 
-__global__ void __launch_bounds__(256) sgemm2_kernel(GemmOp o1, GemmOp o2, int two,
+// TBM = 128: 8 x 8 outputs per thread (two 4 x 4 quadrants); TBM = 64: 4 x 4.
+// gridDim.z = batch * ks: slice z % ks of K; with ks > 1 the slice's product
+// (times alpha) goes to part[slice][b] and a second kernel adds the slices in
+// order (deterministic split-K).
+template <int TBM>
+__global__ void __launch_bounds__(256, 2) sgemm2_kernel(GemmOp o1, GemmOp o2, int two,
                                                      float* __restrict__ C, int M, int N, int K,
                                                      int ldc, int64_t sC, float alpha,
-                                                     float beta) {
-  __shared__ __align__(16) float As[G2_BK][G2_BM + 4];
-  __shared__ __align__(16) float Bs[G2_BK][G2_BM + 4];
-  const int b = blockIdx.z;
-  const int m0 = blockIdx.y * G2_BM, n0 = blockIdx.x * G2_BM;
+                                                     float beta, int ks,
+                                                     float* __restrict__ part) {
+  constexpr int Q = TBM / 32;   // outputs per thread per dimension / 2 quadrants (4 or 2)
+  constexpr int T = TBM == 128 ? 8 : 4;
+  __shared__ __align__(16) float As[G2_BK][TBM + 4];
+  __shared__ __align__(16) float Bs[G2_BK][TBM + 4];
+  const int b = blockIdx.z / ks, slice = blockIdx.z % ks;
+  const int kc = ((K + ks - 1) / ks + G2_BK - 1) / G2_BK * G2_BK;
+  const int kbeg = slice * kc, kend = min(K, kbeg + kc);
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBM;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[8][8];
+  float acc[T][T];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < T; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < T; ++j) acc[i][j] = 0.f;
+  // row (column) of output i: quadrant i / 4 at offset TBM / 2, then 4 consecutive
+  auto rix = [&](int i, int tid) { return (i >> 2) * (TBM / 2) + tid * 4 + (i & 3); };
   for (int op = 0; op < 1 + two; ++op) {
     const GemmOp& o = op ? o2 : o1;
     const float* A = o.A + (int64_t)b * o.sA;
     const float* B = o.B + (int64_t)b * o.sB;
-    for (int k0 = 0; k0 < K; k0 += G2_BK) {
-      g2_load(As, A, o.lda, o.ta != 0, m0, k0, M, K);
+    for (int k0 = kbeg; k0 < kend; k0 += G2_BK) {
+      g2_load<TBM>(As, A, o.lda, o.ta != 0, m0, k0, M, kend);
       // op(B)[k][n] = op(B^T)[n][k]: load B^T's rows n with the opposite transposition
-      g2_load(Bs, B, o.ldb, o.tb == 0, n0, k0, N, K);
+      g2_load<TBM>(Bs, B, o.ldb, o.tb == 0, n0, k0, N, kend);
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < G2_BK; ++kk) {
-        float a[8], bv[8];
-        const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-        const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
-        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
-        a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
-        a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
-        bv[0] = b0.x; bv[1] = b0.y; bv[2] = b0.z; bv[3] = b0.w;
-        bv[4] = b1.x; bv[5] = b1.y; bv[6] = b1.z; bv[7] = b1.w;
+        float a[T], bv[T];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int h = 0; h < T / 4; ++h) {
+          const float4 av = *reinterpret_cast<const float4*>(&As[kk][h * (TBM / 2) + ty * 4]);
+          const float4 bw = *reinterpret_cast<const float4*>(&Bs[kk][h * (TBM / 2) + tx * 4]);
+          a[4 * h] = av.x; a[4 * h + 1] = av.y; a[4 * h + 2] = av.z; a[4 * h + 3] = av.w;
+          bv[4 * h] = bw.x; bv[4 * h + 1] = bw.y; bv[4 * h + 2] = bw.z; bv[4 * h + 3] = bw.w;
+        }
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+        for (int i = 0; i < T; ++i)
+#pragma unroll
+          for (int j = 0; j < T; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
       }
       __syncthreads();
     }
   }
-  float* Cb = C + (int64_t)b * sC;
+  (void)Q;
+  if (ks == 1) {
+    float* Cb = C + (int64_t)b * sC;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
-    if (gm >= M) continue;
+    for (int i = 0; i < T; ++i) {
+      const int gm = m0 + rix(i, ty);
+      if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
-      if (gn >= N) continue;
-      float* c = Cb + (int64_t)gm * ldc + gn;
-      *c = alpha * acc[i][j] + (beta != 0.f ? beta * *c : 0.f);
+      for (int j = 0; j < T; ++j) {
+        const int gn = n0 + rix(j, tx);
+        if (gn >= N) continue;
+        float* cp = Cb + (int64_t)gm * ldc + gn;
+        *cp = alpha * acc[i][j] + (beta != 0.f ? beta * *cp : 0.f);
+      }
     }
+  } else {
+    const int batch = gridDim.z / ks;
+    float* Pb = part + ((int64_t)slice * batch + b) * M * N;
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+      const int gm = m0 + rix(i, ty);
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        const int gn = n0 + rix(j, tx);
+        if (gn < N) Pb[(int64_t)gm * N + gn] = alpha * acc[i][j];
+      }
+    }
+  }
+}
+
+// C[b] = beta C[b] + sum over slices, in order, of part[slice][b]
+__global__ void splitk_sum_kernel(const float* __restrict__ part, int ks, int batch, int M, int N,
+                                  float* __restrict__ C, int ldc, int64_t sC, float beta) {
+  const int b = blockIdx.y;
+  const int64_t mn = (int64_t)M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < mn;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int sl = 0; sl < ks; ++sl) v += part[((int64_t)sl * batch + b) * mn + e];
+    float* cp = C + (int64_t)b * sC + (e / N) * ldc + (e % N);
+    *cp = (beta != 0.f ? beta * *cp : 0.f) + v;
   }
 }
 
 cudaError_t launch_sgemm2(const float* A1, const float* B1, bool tA1, bool tB1, const float* A2,
                           const float* B2, bool tA2, bool tB2, float* C, int M, int N, int K,
                           int lda, int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC,
-                          int batch, float alpha, float beta, cudaStream_t st) {
+                          int batch, float alpha, float beta, cudaStream_t st, float* scratch,
+                          size_t scratch_floats) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
   const GemmOp o1{A1, B1, lda, ldb, sA, sB, tA1 ? 1 : 0, tB1 ? 1 : 0};
   const GemmOp o2{A2 ? A2 : A1, B2 ? B2 : B1, lda, ldb, sA, sB, tA2 ? 1 : 0, tB2 ? 1 : 0};
-  dim3 grid((N + G2_BM - 1) / G2_BM, (M + G2_BM - 1) / G2_BM, batch);
-  sgemm2_kernel<<<grid, 256, 0, st>>>(o1, o2, A2 ? 1 : 0, C, M, N, K, ldc, sC, alpha, beta);
+  const int64_t tiles128 = (int64_t)((M + 127) / 128) * ((N + 127) / 128) * batch;
+  if (tiles128 >= sms) {
+    dim3 grid((N + 127) / 128, (M + 127) / 128, batch);
+    sgemm2_kernel<128><<<grid, 256, 0, st>>>(o1, o2, A2 ? 1 : 0, C, M, N, K, ldc, sC, alpha, beta,
+                                            1, nullptr);
+    CASCADE_LAUNCHED();
+    return cudaGetLastError();
+  }
+  // few tiles: 64 x 64 tiles and, if there is scratch, K split into slices
+  const int64_t tiles64 = (int64_t)((M + 63) / 64) * ((N + 63) / 64) * batch;
+  int ks = (int)std::min<int64_t>((2 * sms + tiles64 - 1) / tiles64, std::max(1, K / 64));
+  while (ks > 1 && (size_t)ks * batch * M * N > scratch_floats) --ks;
+  if (!scratch) ks = 1;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch * ks);
+  sgemm2_kernel<64><<<grid, 256, 0, st>>>(o1, o2, A2 ? 1 : 0, C, M, N, K, ldc, sC, alpha, beta,
+                                         ks, scratch);
   CASCADE_LAUNCHED();
+  if (ks > 1) {
+    const int64_t mn = (int64_t)M * N;
+    const int blocks = (int)std::min<int64_t>((mn + 255) / 256, 1024);
+    splitk_sum_kernel<<<dim3(blocks, batch), 256, 0, st>>>(scratch, ks, batch, M, N, C, ldc, sC,
+                                                          beta);
+    CASCADE_LAUNCHED();
+  }
   return cudaGetLastError();
 }
 

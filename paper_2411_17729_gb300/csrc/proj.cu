@@ -354,13 +354,13 @@ __global__ void __launch_bounds__(256) expand_thin_kernel(const Tile* __restrict
 // groups (NCH groups per lane, m <= 256 NCH), then a warp reduction per output
 // column.  With the shifted term, row l+1 is loaded once and serves as the
 // next row of l and then as the row itself.
-template <int FMT, bool TWO, int NCH>
+template <int FMT, bool TWO, int NCH, int QT>
 __global__ void __launch_bounds__(256) contract_thin_kernel(const Tile* __restrict__ tiles, int m,
                                                             int nout, Bufs V, int buf_mode,
                                                             int buf_fixed, Coef M1, Coef M2,
                                                             Coef M3, const float* __restrict__ X,
                                                             int px, float* __restrict__ out) {
-  constexpr int QT = 4;   // nout <= QT
+  // nout <= QT (1, 2 or 4)
   __shared__ __align__(16) float M1s[THIN_ELEMS];
   __shared__ __align__(16) float M2s[TWO ? THIN_ELEMS : 4];
   const Tile t = tiles[blockIdx.x];
@@ -459,12 +459,17 @@ cudaError_t contract_dispatch(const Tile* tiles, int ntiles, int m, int nout, co
                               cudaStream_t st) {
   if (nout <= 4 && thin_stride(m) * nout <= THIN_ELEMS && m <= 1024) {
     const int nch = (m + 255) / 256;
-#define CASCADE_CTHIN(NC)                                                                     \
-  contract_thin_kernel<FMT, TWO, NC><<<ntiles, 256, 0, st>>>(tiles, m, nout, V, buf_mode,      \
-                                                             buf_fixed, M1, M2, M3, X, px, out)
-    if (nch == 1) CASCADE_CTHIN(1);
-    else if (nch == 2) CASCADE_CTHIN(2);
-    else CASCADE_CTHIN(4);
+#define CASCADE_CTHIN(NC, QC)                                                                 \
+  contract_thin_kernel<FMT, TWO, NC, QC><<<ntiles, 256, 0, st>>>(tiles, m, nout, V, buf_mode,  \
+                                                                 buf_fixed, M1, M2, M3, X, px, out)
+#define CASCADE_CTHIN_Q(NC)          \
+  if (nout == 1) CASCADE_CTHIN(NC, 1); \
+  else if (nout == 2) CASCADE_CTHIN(NC, 2); \
+  else CASCADE_CTHIN(NC, 4)
+    if (nch == 1) { CASCADE_CTHIN_Q(1); }
+    else if (nch == 2) { CASCADE_CTHIN_Q(2); }
+    else { CASCADE_CTHIN_Q(4); }
+#undef CASCADE_CTHIN_Q
 #undef CASCADE_CTHIN
     CASCADE_LAUNCHED();
     return cudaGetLastError();
@@ -509,6 +514,36 @@ cudaError_t expand_dispatch(int precision, const Tile* tiles, int ntiles, int m,
                                                      buf_fixed, odd_only);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
+}
+
+// y = C v + D u for listed rows: one warp per row, lanes over 8-column groups.
+template <int FMT>
+__global__ void __launch_bounds__(256) rows_output_kernel(const int64_t* __restrict__ rows,
+                                                          const int32_t* __restrict__ row_sys,
+                                                          int nrows, int m, int q, int px,
+                                                          Bufs V, int buf, Coef C, Coef D,
+                                                          const float* __restrict__ u,
+                                                          float* __restrict__ y) {
+  const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= nrows) return;
+  const int64_t row = rows[gw];
+  const int s = row_sys[gw];
+  for (int j = 0; j < q; ++j) {
+    float acc = 0.f;
+    for (int c0 = lane * 8; c0 < m; c0 += 256) {
+      float v[8];
+      load8<FMT>(V.hi(buf), V.lo(buf), row * (int64_t)m + c0, v);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc = fmaf(C.at(s, j, c0 + e), v[e], acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      for (int i = 0; i < px; ++i) acc = fmaf(D.at(s, j, i), u[row * px + i], acc);
+      y[row * q + j] = acc;
+    }
+  }
 }
 
 }  // namespace
@@ -565,6 +600,25 @@ cudaError_t launch_proj_du(const Plan& p, const float* G, const Bufs& W, int wbu
                                              ABt, Dt, G, q, du, st);
   return contract_dispatch<FMT_F32, true>(p.d_all_tiles, p.n_all_tiles, m, pp, W, 0, wbuf, Bt, ABt,
                                           Dt, G, q, du, st);
+}
+
+// y = C v + D u for an explicit list of rows (state buffer `buf`).
+cudaError_t launch_proj_rows_output(const Plan& p, const int64_t* rows, int nrows,
+                                    const int32_t* row_sys, const float* u, float* y,
+                                    const Bufs& V, int buf, cudaStream_t st) {
+  if (nrows == 0) return cudaSuccess;
+  const int m = p.d.m, pp = p.d.p, q = p.d.q;
+  const Coef C{p.C32, (int64_t)q * m, m, 1};
+  const Coef D{p.D32, (int64_t)q * pp, pp, 1};
+  const int blocks = (nrows * 32 + 255) / 256;
+  if (p.d.precision == CASCADE_BF16_SPLIT)
+    rows_output_kernel<FMT_BF16><<<blocks, 256, 0, st>>>(rows, row_sys, nrows, m, q, pp, V, buf, C,
+                                                        D, u, y);
+  else
+    rows_output_kernel<FMT_F32><<<blocks, 256, 0, st>>>(rows, row_sys, nrows, m, q, pp, V, buf, C, D,
+                                                       u, y);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
 }
 
 }  // namespace cascade

@@ -690,7 +690,9 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   a.reverse = reverse ? 1 : 0;
   a.k = k;
   a.kmax1 = p.kmax1;
-  a.keep_v = (p.d.flags & (CASCADE_FLAG_SAVE_STATES | CASCADE_FLAG_RECOMPUTE)) ? 1 : 0;
+  // fused tiles also write v when the backward reads it, and in the strided
+  // schedule, where a row finished at down-sweep level k is a source below it
+  a.keep_v = ((p.d.flags & (CASCADE_FLAG_SAVE_STATES | CASCADE_FLAG_RECOMPUTE)) || S > 0) ? 1 : 0;
   a.S = S;
   a.vin_hi = vin_hi;
   a.vin_lo = vin_lo;
@@ -707,9 +709,9 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   const int nwork = ntiles * a.nblocks;
   const int grid = nwork < p.num_sms ? nwork : p.num_sms;
   const int q = p.d.q;
-  // the fused output applies to dense forward stages that are given y (the
-  // stages the backward recomputes are not)
-  const bool fuse = p.fuse_output && !reverse && y != nullptr && S == 0;
+  // the fused output applies to forward stages that are given y (the stages
+  // the backward recomputes are not)
+  const bool fuse = p.fuse_output && !reverse && y != nullptr;
   const int G = cfg.group;
 #define CASCADE_TC_DISPATCH(E, Q)                                               \
   return G == 2 ? launch_variant<E, Q, 2>(maps, a, grid, smem, st)               \
@@ -737,10 +739,10 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
 }
 
 cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,
-                                    uint64_t rows_cap, void* v_hi, void* v_lo, cudaStream_t st) {
+                                    uint64_t rows_cap, void* v_hi, void* v_lo, const float* u,
+                                    float* y, cudaStream_t st) {
   if (S <= 0 || rows_cap % (uint64_t)S != 0) return cudaErrorInvalidValue;
-  return stage_tc_core(p, k, tiles, ntiles, S, rows_cap, v_hi, v_lo, v_hi, v_lo, nullptr, nullptr,
-                       st, false);
+  return stage_tc_core(p, k, tiles, ntiles, S, rows_cap, v_hi, v_lo, v_hi, v_lo, u, y, st, false);
 }
 
 }  // namespace cascade

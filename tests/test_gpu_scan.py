@@ -55,13 +55,16 @@ def matvecs(c):
 LENGTHS = (1, 2, 3, 4, 5, 64, 127, 128, 129, 255, 256, 257, 1000, 2048, 3001)
 
 
-@pytest.mark.parametrize("precision,m", [("bf16_split", 128), ("bf16_split", 256),
-                                         ("fp32", 128), ("fp32", 64)])
-def test_scan_matches_oracle(lib, precision, m):
+@pytest.mark.parametrize("precision,m,q", [("bf16_split", 128, 2), ("bf16_split", 256, 2),
+                                           ("fp32", 128, 2), ("fp32", 64, 2),
+                                           ("bf16_split", 128, 6)])
+def test_scan_matches_oracle(lib, precision, m, q):
     """Ragged lengths around every power of two the tiles and levels meet
-    (1 .. 3001), two systems, MIMO."""
+    (1 .. 3001), two systems, MIMO.  With q <= 4 the down-sweep levels form y
+    in their epilogue (rows 2^t - 1 separately); q = 6 takes the separate
+    output pass."""
     from paper_2411_17729_gb300._abi import CASCADE_FLAG_SCAN
-    w = wl.differentiation_form(m=m, p=3, q=2, L=8, batch=len(LENGTHS), N=11, delta=1e-2)
+    w = wl.differentiation_form(m=m, p=3, q=q, L=8, batch=len(LENGTHS), N=11, delta=1e-2)
     w.offsets = np.concatenate([[0], np.cumsum(LENGTHS)]).astype(np.int64)
     w.u = np.random.default_rng(21).standard_normal((int(w.offsets[-1]), 3))
     w.sys_of_seq = (np.arange(len(LENGTHS)) % 2).astype(np.int32)

@@ -62,6 +62,22 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: every replica must have finished its units."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units all replicas processed per second of the slowest rank's time."""
+    return units_per_rank * world / (ms / 1000.0)
+
+
 # --------------------------------------------------------------------- helpers
 def blas_threads():
     try:
@@ -318,12 +334,9 @@ def main():
     c.enable_stage_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms_per_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms_per_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+    ms_per_step = max_over_ranks(ms_per_step, world, dev)
     states_per_step = int(w.rows)
-    value = states_per_step * world / (ms_per_step / 1000.0)
+    value = whole_job_rate(states_per_step, world, ms_per_step)
     if c.device_error() != 0:
         raise RuntimeError("device wait timed out in the timed region")
 
@@ -380,11 +393,8 @@ def main():
         y_host.copy_(y, non_blocking=True)
 
     e2e_ms = sum(timed_steps(e2e_step, args.steps, flush, stream)) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = states_per_step * world / (e2e_ms / 1000.0)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e_value = whole_job_rate(states_per_step, world, e2e_ms)
     c.close()
     torch.cuda.empty_cache()
 
@@ -414,10 +424,7 @@ def main():
         if cs.device_error() != 0:
             raise RuntimeError("device wait timed out in the scan region")
         scan_ms = sum(a.elapsed_time(b) for a, b in sev) / args.steps
-        if world > 1:
-            t = torch.tensor([scan_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            scan_ms = float(t.item())
+        scan_ms = max_over_ranks(scan_ms, world, dev)
         nmv = ctypes.c_int64()
         cs._check(cs.lib.cascade_get_matvec_count(cs.plan, ctypes.byref(nmv)))
         # algorithmic bytes of the level launches: per updated row, read the
@@ -428,7 +435,7 @@ def main():
         lev_tot = sum(sum(v) for v in lev_ms.values()) / args.steps
         lev_bytes = 3 * esize * m * upd + nlev * w.nsys * m * m * esize
         lev_gbs = lev_bytes / (lev_tot / 1000.0) / 1e9 if lev_tot > 0 else 0.0
-        scan = {"value": states_per_step * world / (scan_ms / 1000.0), "unit": "states/s",
+        scan = {"value": whole_job_rate(states_per_step, world, scan_ms), "unit": "states/s",
                 "ms_per_step": scan_ms, "matvecs_per_step": int(nmv.value),
                 "matvecs_stage_schedule": int(sum(
                     sum(max(int(L) - (1 << k), 0) for k in range(int(Nk) + 1))
@@ -474,11 +481,8 @@ def main():
             raise RuntimeError("device wait timed out in the fwd+bwd region")
         fb_ms = sum(a.elapsed_time(cc) for a, _, cc in fb_ev) / args.steps
         bwd_ms = sum(b.elapsed_time(cc) for _, b, cc in fb_ev) / args.steps
-        if world > 1:
-            t = torch.tensor([fb_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            fb_ms = float(t.item())
-        fb = {"value": states_per_step * world / (fb_ms / 1000.0), "unit": "states/s",
+        fb_ms = max_over_ranks(fb_ms, world, dev)
+        fb = {"value": whole_job_rate(states_per_step, world, fb_ms), "unit": "states/s",
               "ms_per_step": fb_ms, "backward_ms": bwd_ms,
               "gradients": "u, A (or Abar), B (or Bbar), C, D",
               "stage_outputs": "recomputed from checkpoints" if recompute else "kept",
@@ -539,6 +543,13 @@ def main():
             "clocks": clocks,
             "fwd_bwd": fb,
             "scan_fwd": scan,
+            # products by powers per step: executed by the stage schedule of §3, the
+            # 2L bound of the abstract and §6, and the L of the recursion (Eq. 1.2)
+            "op_count": {"stage_schedule": int(sum(
+                sum(max(int(L) - (1 << k), 0) for k in range(int(Nk) + 1))
+                for L, Nk in zip(Ls, Ns))),
+                "work_efficient_schedule": scan["matvecs_per_step"] if scan else None,
+                "paper_bound_2L": int(2 * Ls.sum()), "recursion_L": int(Ls.sum())},
             "fp64_cascade": fp64,
             "fp64_recursion": rec,
             "precompute_s": prep_s,

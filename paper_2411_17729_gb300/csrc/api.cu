@@ -214,6 +214,9 @@ void free_batch(Plan* p) {
   p->d_chunk_data = nullptr;
   p->chunk_lists.clear();
   p->max_chunks = 0;
+  dfree(p->d_red_scratch);
+  p->d_red_scratch = nullptr;
+  p->red_scratch_bytes = 0;
   p->d_adj_tiles.clear();
   p->n_adj_tiles.clear();
   p->saved_ws = nullptr;
@@ -1273,6 +1276,10 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
       }
       p->max_chunks = std::max(p->max_chunks, cl.n);
     }
+    // group sums for the reductions with little parallelism: fewer than
+    // 2048 x SMs systems x elements, so G groups need under twice that
+    p->red_scratch_bytes = (size_t)2 * 2048 * p->num_sms * sizeof(double);
+    CK(cudaMalloc(&p->d_red_scratch, p->red_scratch_bytes), "alloc reduction scratch");
     CK(cudaMalloc(&p->d_chunk_data, data.size() * sizeof(int32_t)), "alloc chunks");
     CK(cudaMemcpy(p->d_chunk_data, data.data(), data.size() * sizeof(int32_t),
                   cudaMemcpyHostToDevice),

@@ -27,6 +27,8 @@
 #include "common.cuh"
 #include "formats.cuh"
 
+#include <algorithm>
+
 namespace cascade {
 namespace {
 
@@ -114,6 +116,40 @@ __global__ void reduce_partials_kernel(const ACC* __restrict__ partial,
        e += (int64_t)gridDim.x * blockDim.x) {
     OUT v = 0;
     for (int c = c0; c < c1; ++c) v += (OUT)partial[(int64_t)c * elems + e];
+    const int64_t h = e / seg;
+    OUT* o = out + h * seg_stride + (int64_t)s * out_sys_stride + (e - h * seg);
+    *o = accumulate ? *o + v : v;
+  }
+}
+
+// With few systems x elements the sum above has too little parallelism: the
+// chunks of each system are first split into G contiguous groups summed in
+// order into tmp[s][g][e], then the G group sums are added in order.
+template <typename ACC>
+__global__ void reduce_groups_kernel(const ACC* __restrict__ partial,
+                                     const int32_t* __restrict__ sys_begin, int64_t elems,
+                                     int G, ACC* __restrict__ tmp) {
+  const int s = blockIdx.y, g = blockIdx.z;
+  const int c0 = sys_begin[s], c1 = sys_begin[s + 1];
+  const int per = (c1 - c0 + G - 1) / G;
+  const int a = min(c1, c0 + g * per), b = min(c1, a + per);
+  ACC* t = tmp + ((int64_t)s * G + g) * elems;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < elems;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    ACC v = 0;
+    for (int c = a; c < b; ++c) v += partial[(int64_t)c * elems + e];
+    t[e] = v;
+  }
+}
+template <typename ACC, typename OUT>
+__global__ void reduce_group_sums_kernel(const ACC* __restrict__ tmp, int G, int64_t elems,
+                                         OUT* __restrict__ out, int64_t out_sys_stride,
+                                         int64_t seg, int64_t seg_stride, int accumulate) {
+  const int s = blockIdx.y;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < elems;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    OUT v = 0;
+    for (int g = 0; g < G; ++g) v += (OUT)tmp[((int64_t)s * G + g) * elems + e];
     const int64_t h = e / seg;
     OUT* o = out + h * seg_stride + (int64_t)s * out_sys_stride + (e - h * seg);
     *o = accumulate ? *o + v : v;
@@ -412,6 +448,35 @@ __global__ void convert_sys_kernel(const TI* __restrict__ in, int64_t in_stride,
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+// Sum the chunk partials of every system into out (see reduce_partials_kernel),
+// in two grouped passes when systems x elements alone cannot fill the GPU.
+template <typename ACC, typename OUT>
+static void sum_chunks(const Plan& p, const ACC* partial, const int32_t* sys_begin,
+                       int64_t elems, OUT* out, int64_t out_sys_stride, int64_t seg,
+                       int64_t seg_stride, int accumulate, cudaStream_t st) {
+  const int rblocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
+  const int64_t want = (int64_t)2048 * p.num_sms;   // threads that keep the GPU busy
+  const int64_t have = elems * p.d.nsys;
+  int G = 1;
+  if (have < want && p.d_red_scratch) {
+    G = (int)std::min<int64_t>(32, (want + have - 1) / have);
+    while (G > 1 && (size_t)G * have * sizeof(ACC) > p.red_scratch_bytes) --G;
+  }
+  if (G <= 1) {
+    reduce_partials_kernel<ACC, OUT><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+        partial, sys_begin, elems, out, out_sys_stride, seg, seg_stride, accumulate);
+    CASCADE_LAUNCHED();
+    return;
+  }
+  ACC* tmp = static_cast<ACC*>(p.d_red_scratch);
+  reduce_groups_kernel<ACC><<<dim3(rblocks, p.d.nsys, G), 256, 0, st>>>(partial, sys_begin,
+                                                                        elems, G, tmp);
+  CASCADE_LAUNCHED();
+  reduce_group_sums_kernel<ACC, OUT><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
+      tmp, G, elems, out, out_sys_stride, seg, seg_stride, accumulate);
+  CASCADE_LAUNCHED();
+}
+
 cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
                            const int32_t* sys_begin, const TSrc& X, int a, const TSrc& Y, int b,
                            int shift, void* partial, void* out, bool out_f64,
@@ -426,8 +491,8 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
     treduce_kernel<FMT_F64, double><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
                                                          shift, (double*)partial);
     CASCADE_LAUNCHED();
-    reduce_partials_kernel<double, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-        (const double*)partial, sys_begin, elems, (double*)out, out_sys_stride, elems, 0, accumulate);
+    sum_chunks<double, double>(p, (const double*)partial, sys_begin, elems, (double*)out,
+                               out_sys_stride, elems, 0, accumulate, st);
   } else {
     if (p.d.precision == CASCADE_BF16_SPLIT)
       treduce_kernel<FMT_BF16, float><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
@@ -437,13 +502,12 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
                                                           shift, (float*)partial);
     CASCADE_LAUNCHED();
     if (out_f64)
-      reduce_partials_kernel<float, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-          (const float*)partial, sys_begin, elems, (double*)out, out_sys_stride, elems, 0, accumulate);
+      sum_chunks<float, double>(p, (const float*)partial, sys_begin, elems, (double*)out,
+                                out_sys_stride, elems, 0, accumulate, st);
     else
-      reduce_partials_kernel<float, float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-          (const float*)partial, sys_begin, elems, (float*)out, out_sys_stride, elems, 0, accumulate);
+      sum_chunks<float, float>(p, (const float*)partial, sys_begin, elems, (float*)out,
+                               out_sys_stride, elems, 0, accumulate, st);
   }
-  CASCADE_LAUNCHED();
   return cudaGetLastError();
 }
 
@@ -519,8 +583,8 @@ cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chu
                                  static_cast<const double*>(T), tc, tc, nsh, sh0, sh1, gshift, tgshift, 0,
                                  thin_major ? 1 : 0, static_cast<double*>(partial), st);
     CASCADE_LAUNCHED();
-    reduce_partials_kernel<double, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-        (const double*)partial, sys_begin, elems, (double*)out, out_sys_stride, seg, seg_stride, 0);
+    sum_chunks<double, double>(p, (const double*)partial, sys_begin, elems, (double*)out,
+                               out_sys_stride, seg, seg_stride, 0, st);
   } else {
     if (p.d.precision == CASCADE_BF16_SPLIT)
       wt_dispatch<FMT_BF16, float>(TT, nchunks, tiles, chunks, BM, p.d.m, X, a,
@@ -532,29 +596,24 @@ cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chu
                                   thin_major ? 1 : 0, static_cast<float*>(partial), st);
     CASCADE_LAUNCHED();
     if (out_f64)
-      reduce_partials_kernel<float, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-          (const float*)partial, sys_begin, elems, (double*)out, out_sys_stride, seg, seg_stride,
-          0);
+      sum_chunks<float, double>(p, (const float*)partial, sys_begin, elems, (double*)out,
+                                out_sys_stride, seg, seg_stride, 0, st);
     else
-      reduce_partials_kernel<float, float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-          (const float*)partial, sys_begin, elems, (float*)out, out_sys_stride, seg, seg_stride,
-          0);
+      sum_chunks<float, float>(p, (const float*)partial, sys_begin, elems, (float*)out,
+                               out_sys_stride, seg, seg_stride, 0, st);
   }
-  CASCADE_LAUNCHED();
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_partials(const Plan& p, const float* partial, const int32_t* sys_begin,
                                    int64_t elems, void* out, bool out_f64, int64_t out_sys_stride,
                                    cudaStream_t st) {
-  const int rblocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
   if (out_f64)
-    reduce_partials_kernel<float, double><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-        partial, sys_begin, elems, (double*)out, out_sys_stride, elems, 0, 0);
+    sum_chunks<float, double>(p, partial, sys_begin, elems, (double*)out, out_sys_stride, elems,
+                              0, 0, st);
   else
-    reduce_partials_kernel<float, float><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
-        partial, sys_begin, elems, (float*)out, out_sys_stride, elems, 0, 0);
-  CASCADE_LAUNCHED();
+    sum_chunks<float, float>(p, partial, sys_begin, elems, (float*)out, out_sys_stride, elems, 0,
+                             0, st);
   return cudaGetLastError();
 }
 

@@ -149,6 +149,8 @@ struct Plan {
   int32_t* d_chunk_data = nullptr;           // chunks [n][3] (first tile, count, system) and
                                              // per-system chunk ranges [nsys + 1] of each list
   int max_chunks = 0;
+  void* d_red_scratch = nullptr;             // group sums of the chunk reductions
+  size_t red_scratch_bytes = 0;
   const void* saved_ws = nullptr;            // workspace of the last forward that kept states
   int64_t saved_batch = -1;
   Seq* d_seqs = nullptr;                     // all sequences

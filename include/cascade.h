@@ -277,8 +277,11 @@ cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_
 
 /* Set the tensor-core stage kernel shape directly (e.g. a shape saved from
    an earlier cascade_autotune): h_shape = {stages, ring slots, chunks per
-   step}.  CASCADE_ERR_INVALID_ARG if it does not fit shared/tensor memory
-   for this plan's m and precision.  A no-op for FP64 plans. */
+   step}.  The kernel's two epilogue groups take alternate steps and each ring
+   slot must always serve the same group, so ring slots must be a multiple of
+   2 x chunks per step.  CASCADE_ERR_INVALID_ARG if that fails or the shape
+   does not fit shared/tensor memory for this plan's m and precision.  A no-op
+   for FP64 plans. */
 cascade_status_t cascade_set_kernel_shape(cascade_plan_t plan, const int32_t* h_shape);
 
 /* Per-launch timing of the stage kernels.  When enabled, every later

@@ -50,7 +50,9 @@ namespace cascade {
 namespace {
 
 constexpr int BM = 128;
-constexpr int NTHREADS = 224;
+// warps: 0 TMA producer, 1 MMA issuer, 6 ring manager, 2-5 and 7-10 epilogue
+// (two groups of four, one warp per TMEM lane quadrant in each)
+constexpr int NTHREADS = 352;
 constexpr int RING_MAX = 8;                   // staging slots (runtime ring <= 8)
 constexpr uint32_t ROWB = 64;                 // bytes per row of every shared tile
 constexpr uint32_t PLANE_TILE = BM * ROWB;    // one plane of a 128-row chunk: 8 KB
@@ -194,8 +196,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* res_full = acc_empty + 2;
   uint64_t* res_done = res_full + RING_MAX;
   uint64_t* drain = res_done + RING_MAX;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* ypart = drain + 1;      // group 1's partial y sums of a fused tile are ready
+  uint64_t* yfree = ypart + 1;      // group 0 has taken them
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(yfree + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* ysum = reinterpret_cast<float*>(tmem_slot + 4);   // [QN][128]
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -209,13 +214,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&acc_full[b], 1);
-      ptx::mbar_init(&acc_empty[b], 128);
+      ptx::mbar_init(&acc_empty[b], 256);    // both epilogue groups
     }
     for (int s = 0; s < RING; ++s) {
       ptx::mbar_init(&res_full[s], 1);
       ptx::mbar_init(&res_done[s], 128);
     }
     ptx::mbar_init(drain, 1);
+    ptx::mbar_init(ypart, 128);
+    ptx::mbar_init(yfree, 128);
     *abort_flag = 0;
     ptx::fence_mbar_init();
     ptx::prefetch_tmap(&tm_vhi);
@@ -384,6 +391,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int s = 0; s < RING; ++s) issue_next(s);
       uint32_t g = 0;                  // chunks retired
       bool alive = true;
+      // A slot is refilled one chunk after its store was issued, so that the
+      // store of the newest chunk reads shared memory while the older one's
+      // slot is reloaded (bulk wait with one group allowed in flight).
+      int pend_slot = -1;
       for (int w = blockIdx.x; w < nwork && alive; w += gridDim.x) {
         const Item it = load_item<QMAX>(args, w);
         const bool tma_out = (!it.fused || args.keep_v) && !it.ragged;
@@ -409,9 +420,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               ptx::tma_store_2d(&tm_olo, sh + PLANE_TILE, it.n0 + cc * CW, ytile);
             }
             ptx::bulk_commit();
-            ptx::bulk_wait_read0();     // the slot may be overwritten once the store read it
           }
-          issue_next(slot);
+          if (pend_slot >= 0) {
+            // the previous chunk's store (if any) has read its slot: all bulk
+            // groups but this chunk's (the newest, when it stored) are done reading
+            if (tma_out) ptx::bulk_wait_read1();
+            else ptx::bulk_wait_read0();
+            issue_next(pend_slot);
+          }
+          pend_slot = slot;
         }
       }
       ptx::bulk_wait0();                // stores complete before the block exits
@@ -423,7 +440,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------ epilogue
     const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
     const int r = quad * 32 + lane;            // tile row == TMEM lane
-    uint32_t g = 0;                            // chunks consumed
+    // Two epilogue groups share the tiles: chunk g (counted over the whole
+    // launch) belongs to group (g / G) % 2, so with ring % (2 G) == 0 every ring
+    // slot is always served by the same group and a parity wait never runs two
+    // phases ahead; each chunk still gets 128 arrivals on res_done.  For tiles
+    // that form y, group 1 hands its partial sums to group 0 through ysum.
+    const int egrp = warp >= 7 ? 1 : 0;
+    uint32_t g = 0;                            // chunks consumed (by either group)
+    int nfused = 0;                            // fused tiles seen (ypart / yfree phases)
     int acc_i = 0;
     bool alive = true;                         // warp-uniform
     for (int w = blockIdx.x; w < nwork && alive; w += gridDim.x) {
@@ -437,6 +461,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // the manager forwards the residual as is; acknowledge each chunk once
         // it has arrived, keeping both slot barriers phase-locked
         for (int cc = 0; cc < nch; ++cc, ++g) {
+          if (((g / G) & 1) != (uint32_t)egrp) continue;
           const int slot = (int)(g % RING);
           if (!__all_sync(0xffffffffu,
                           ptx::mbar_wait(&res_full[slot], (g / RING) & 1u, limit, abort_flag))) {
@@ -456,6 +481,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         ptx::tc_fence_after();
       }
+
       float yacc[QN];
 #pragma unroll
       for (int qq = 0; qq < QN; ++qq) yacc[qq] = 0.f;
@@ -464,6 +490,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // G chunks per step (nch is always even): their TMEM loads, unpacking,
       // splitting and shared-memory traffic are independent.
       for (int cc = 0; cc < nch; cc += G, g += G) {
+        if (((g / G) & 1) != (uint32_t)egrp) continue;   // the other group's step
         int slot[G];
         uint8_t* sh[G];
         bool got = true;
@@ -569,6 +596,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ptx::mbar_arrive(&acc_empty[abuf]);
         ++acc_i;
       }
+      if (it.fused) {
+        // y sums over all columns: group 1 hands its partial sums to group 0
+        const uint32_t fph = (uint32_t)(nfused & 1);
+        ++nfused;
+        if (egrp == 1) {
+          if (nfused > 1 &&
+              !__all_sync(0xffffffffu, ptx::mbar_wait(yfree, fph ^ 1u, limit, abort_flag))) {
+            raise_timeout(args, abort_flag, 9, w, nfused);
+            break;
+          }
+#pragma unroll
+          for (int qq = 0; qq < QN; ++qq) ysum[qq * 128 + r] = yacc[qq];
+          ptx::mbar_arrive(ypart);
+          continue;
+        }
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait(ypart, fph, limit, abort_flag))) {
+          raise_timeout(args, abort_flag, 10, w, nfused);
+          break;
+        }
+#pragma unroll
+        for (int qq = 0; qq < QN; ++qq) yacc[qq] += ysum[qq * 128 + r];
+        ptx::mbar_arrive(yfree);
+      }
       if (it.fused && valid) {
         const float* Ds = args.D32 + (int64_t)it.t.sys * args.q * args.p;
         const float* ur = args.u + grow * args.p;
@@ -606,12 +656,15 @@ size_t stage_bytes_for(int BN) { return 2 * (size_t)PLANE_TILE + 2 * (size_t)BN 
 // Shared memory besides the operand stages: alignment slack, the staging ring,
 // the mbarriers (room for RING_MAX ring barriers of each kind) and the TMEM slot.
 size_t fixed_smem_bytes(int S, int ring) {
-  return 1024 + (size_t)ring * SLOT_BYTES + 8 * (2 * S + 5 + 2 * RING_MAX) + 16;
+  // alignment, ring, mbarriers, TMEM slot and abort flag, the partial y sums
+  return 1024 + (size_t)ring * SLOT_BYTES + 8 * (2 * S + 7 + 2 * RING_MAX) + 16 +
+         sizeof(float) * 4 * 128;
 }
 
 bool tc_config_fits(int BN, const TcConfig& c) {
   if (c.group != 1 && c.group != 2) return false;
-  if (c.ring < 2 * c.group || c.ring > RING_MAX || c.ring % c.group != 0) return false;
+  // each ring slot always serves the same epilogue group: ring % (2 group) == 0
+  if (c.ring < 2 * c.group || c.ring > RING_MAX || c.ring % (2 * c.group) != 0) return false;
   if (c.stages < 2 || c.stages > 8) return false;
   return fixed_smem_bytes(c.stages, c.ring) + (size_t)c.stages * stage_bytes_for(BN) <= 227 * 1024;
 }

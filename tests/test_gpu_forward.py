@@ -310,8 +310,9 @@ def test_autotuned_shape_keeps_parity(lib, precision, m):
                                          ("fp32", 64)])
 def test_every_kernel_shape(lib, precision, m):
     """Each kernel shape that fits (operand stages x ring slots x chunks per
-    step) matches the oracle on ragged sequences; shapes that do not fit are
-    refused."""
+    step) matches the oracle on ragged sequences; shapes that do not fit, or
+    whose ring slots cannot be split evenly between the two epilogue groups,
+    are refused."""
     import torch
     from paper_2411_17729_gb300._abi import CascadeError
     lengths = (1, 130, 700, 257)
@@ -336,9 +337,11 @@ def test_every_kernel_shape(lib, precision, m):
                 assert c.device_error() == 0
                 ey, ecx = rel_errors(w, y, yo, OUT_EPS[precision])
                 assert ey <= TOL[precision] and ecx <= TOL[precision], (stages, ring, group, ey, ecx)
-    assert tried >= 6
+    assert tried >= 5
     with pytest.raises(CascadeError):
         c.set_kernel_shape(2, 5, 2)          # ring not a multiple of the step
+    with pytest.raises(CascadeError):
+        c.set_kernel_shape(2, 6, 2)          # ring slots not split evenly over the two groups
 
 
 @pytest.mark.parametrize("precision", ["bf16_split", "fp32"])

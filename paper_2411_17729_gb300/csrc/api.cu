@@ -713,10 +713,18 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   CK(cudaMemcpyAsync(dBb, R1, sizeof(T) * ns * mp, cudaMemcpyDeviceToDevice, st), "copy");
   CK(gemm_t(P, R2, dBb, m, pp, m, m, pp, pp, kst, mp, mp, ns, 1.0, 1.0, true, false, st), "dBbar");
   // squaring chain P_(k+1) = P_k P_k:  dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1)
-  for (int k = p->kmax1 - 2; k >= 0; --k)
-    CK(chain_step(dP + (k + 1) * mm, P + k * mm, dP + k * mm, m, kst, ns, st, part,
-                  L.off_dP - L.off_part),
-       "chain");
+  // on the tensor cores for the BF16-split plans (the four split planes of
+  // dP_(k+1) fit in the partial-sum region, free by now); FP32 / FP64 otherwise
+  const bool chain_tc = sizeof(T) == 4 && chain_tc_supported(*p) &&
+                        chain_tc_scratch_bytes(*p) <= L.off_dP - L.off_part;
+  for (int k = p->kmax1 - 2; k >= 0; --k) {
+    if (chain_tc)
+      CK(launch_chain_tc(*p, k, reinterpret_cast<float*>(dP), kst, part, st), "chain (tensor core)");
+    else
+      CK(chain_step(dP + (k + 1) * mm, P + k * mm, dP + k * mm, m, kst, ns, st, part,
+                    L.off_dP - L.off_part),
+         "chain");
+  }
   if (dAbar) CK(to_f64<T>(dP, kst, dAbar, mm, mm, ns, st), "dAbar");
   if (dBbar) CK(to_f64<T>(dBb, mp, dBbar, mp, mp, ns, st), "dBbar");
   // trapezoidal discretisation (Eq. 4.2), Abar = c M^-1 (I + delta/2 A), Bbar = delta M^-1 B:

@@ -205,6 +205,7 @@ void free_batch(Plan* p) {
   p->d_seqs = nullptr;
   dfree(p->d_out_tiles);
   p->d_out_tiles = nullptr;
+  p->out_segs.clear();
   dfree(p->d_stage0_tiles);
   p->d_stage0_tiles = nullptr;
   dfree(p->d_all_tiles);
@@ -242,6 +243,9 @@ void free_system(Plan* p) {
                   p->ABbar32, p->C32, p->D32, p->A64, p->B64, p->delta64, p->scale64,
                   p->PThi, p->PTlo, p->PT64, p->Minv64, p->P32, p->Minv32};
   for (void* q : ptrs) dfree(q);
+  dfree(p->pc_hi);
+  dfree(p->pc_lo);
+  p->pc_hi = p->pc_lo = nullptr;
   dfree(p->zoh_f_adj);
   p->zoh_f_adj = nullptr;
   p->P64 = nullptr;
@@ -311,6 +315,7 @@ cascade_status_t finish_system(Plan* p, cudaStream_t st) {
     CK(launch_to_f32(p->ABbar64, p->ABbar32, (int64_t)ns * m * pp, st), "ABbar f32");
     CK(launch_to_f32(p->C64, p->C32, (int64_t)ns * q * m, st), "C f32");
     CK(launch_to_f32(p->D64, p->D32, (int64_t)ns * q * pp, st), "D f32");
+    if (p->pc_hi) CK(launch_proj_coef(*p, st), "projection operand planes");
   }
   CK(cudaStreamSynchronize(st), "set_system sync");
   p->have_system = true;
@@ -360,6 +365,15 @@ cascade_status_t alloc_system(Plan* p) {
     CK(dalloc(&p->ABbar32, (size_t)ns * m * pp), "alloc ABbar32");
     CK(dalloc(&p->C32, (size_t)ns * q * m), "alloc C32");
     CK(dalloc(&p->D32, (size_t)ns * q * pp), "alloc D32");
+    if (proj_tc_supported(*p)) {
+      const size_t n = proj_coef_elems(*p, p->pc_off);
+      uint8_t* ch = nullptr;
+      uint8_t* cl = nullptr;
+      CK(dalloc(&ch, n * 2), "alloc projection planes");
+      CK(dalloc(&cl, n * 2), "alloc projection planes");
+      p->pc_hi = ch;
+      p->pc_lo = cl;
+    }
   }
   return CASCADE_OK;
 }
@@ -374,6 +388,8 @@ struct Layout {
   size_t plane = 0, buf_stride = 0, lo_off = 0;
   int nV = 2;
   size_t off_W = 0, off_part = 0, off_dP = 0, off_R = 0, off_T = 0, off_Z = 0, total = 0;
+  // tensor-core projections: (hi, lo) BF16 planes of u [rows, p] and G [rows, q]
+  size_t off_U = 0, u_plane = 0, off_G = 0, g_plane = 0;
 };
 
 Layout layout(const Plan& p) {
@@ -412,6 +428,16 @@ Layout layout(const Plan& p) {
                            expm_scratch_doubles((int)n2, (int)ns) + ns) + 8);
     }
   }
+  if (proj_tc_supported(p)) {
+    L.u_plane = align256((size_t)p.rows * p.d.p * 2);
+    L.off_U = off;
+    off += 2 * L.u_plane;
+    if (save) {
+      L.g_plane = align256((size_t)p.rows * p.d.q * 2);
+      L.off_G = off;
+      off += 2 * L.g_plane;
+    }
+  }
   L.total = off + 256;
   return L;
 }
@@ -433,6 +459,12 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
   const Bufs V{static_cast<uint8_t*>(ws), L.buf_stride, L.lo_off};
   const bool save = keeps_states(*p);
   const bool timing = p->timing;
+  // tensor-core projections read u as (hi, lo) BF16 planes
+  const bool ptc = proj_tc_supported(*p);
+  const Bufs U{static_cast<uint8_t*>(ws) + L.off_U, 0, L.u_plane};
+  if (ptc)
+    CK(launch_split_rows(static_cast<const float*>(u), p->rows * p->d.p, U.hi(0), U.lo(0), st),
+       "input planes");
   if (timing) {
     CK(ensure_events(p, std::max(std::max(p->maxN, 1), (int)p->scan.size())), "timing events");
     p->ev_k.clear();
@@ -442,7 +474,10 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
     // work-efficient schedule, in place on buffer 0: the first up-sweep level
     // with the input projection, the other levels on the tensor cores, then
     // y = C x + D u for every row
-    CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, 0, true, st), "first level");
+    if (ptc)
+      CK(launch_proj_tc_stage0(*p, U, V, p->scan_rows_cap, 0, true, st), "first level");
+    else
+      CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, 0, true, st), "first level");
     for (const Plan::ScanLevel& lv : p->scan) {
       if (timing && lv.n > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
       CK(launch_stage_tc_strided(*p, lv.k, 2 << lv.k, lv.d_tiles, lv.n,
@@ -459,6 +494,9 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
       CK(launch_proj_rows_output(*p, p->d_scan_rows, p->n_scan_rows, p->d_scan_rows_sys,
                                  static_cast<const float*>(u), static_cast<float*>(y), V, 0, st),
          "output projection (rows 2^t - 1)");
+    else if (ptc)
+      CK(launch_proj_tc_output(*p, U, static_cast<float*>(y), V, p->scan_rows_cap, st),
+         "output projection");
     else
       CK(launch_proj_output(*p, static_cast<const float*>(u), static_cast<float*>(y), V, st),
          "output projection");
@@ -468,7 +506,9 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
   auto in_buf = [&](int k) { return fwd_buf(*p, k); };
   auto out_buf = [&](int k) { return fwd_buf(*p, k + 1); };
   // stage 0 fused with v^(0) = Bbar u
-  if (proj_supported(*p))
+  if (ptc)
+    CK(launch_proj_tc_stage0(*p, U, V, p->rows, out_buf(0), false, st), "first stage");
+  else if (proj_supported(*p))
     CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), false, st), "first stage");
   else
     CK(launch_stage0(*p, u, V.hi(out_buf(0)), V.lo(out_buf(0)), st), "first stage");
@@ -490,7 +530,9 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
       p->n_ev++;
     }
   }
-  if (proj_supported(*p))
+  if (ptc)
+    CK(launch_proj_tc_output(*p, U, static_cast<float*>(y), V, p->rows, st), "output projection");
+  else if (proj_supported(*p))
     CK(launch_proj_output(*p, static_cast<const float*>(u), static_cast<float*>(y), V, st),
        "output projection");
   else
@@ -506,15 +548,20 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
 // FP64 for the FP64 plan).
 cudaError_t gemm_t(const double* A, const double* B, double* C, int M, int N, int K, int lda,
                    int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch, double alpha,
-                   double beta, bool tA, bool tB, cudaStream_t st) {
+                   double beta, bool tA, bool tB, cudaStream_t st, void* = nullptr, size_t = 0) {
   return launch_dgemm(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, batch, alpha, beta, tA, tB, st);
 }
+// scratch (optional): room for a split-K of the long, narrow products
 cudaError_t gemm_t(const float* A, const float* B, float* C, int M, int N, int K, int lda,
                    int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch, double alpha,
-                   double beta, bool tA, bool tB, cudaStream_t st) {
-  if (M >= 128 && N >= 128)   // square-ish products: the 128 x 128 register-tiled kernel
+                   double beta, bool tA, bool tB, cudaStream_t st, void* scratch = nullptr,
+                   size_t scratch_bytes = 0) {
+  // square-ish products, or long ones with scratch for a split K: the
+  // register-tiled kernel (128 x 128 tiles, or 64 x 64 with K slices)
+  if ((M >= 128 && N >= 128) || (scratch && (int64_t)M * N * K >= (int64_t(1) << 24)))
     return launch_sgemm2(A, B, tA, tB, nullptr, nullptr, false, false, C, M, N, K, lda, ldb, ldc,
-                         sA, sB, sC, batch, (float)alpha, (float)beta, st);
+                         sA, sB, sC, batch, (float)alpha, (float)beta, st,
+                         static_cast<float*>(scratch), scratch_bytes / sizeof(float));
   return launch_sgemm(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, batch, (float)alpha,
                       (float)beta, tA, tB, st);
 }
@@ -580,12 +627,33 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   const int nall = p->chunk_lists[0].n;
 
   const bool proj = proj_supported(*p);
+  // tensor-core projections read G as (hi, lo) BF16 planes
+  const bool ptc = proj_tc_supported(*p);
+  const Bufs Gp{base + L.off_G, 0, L.g_plane};
+  const Bufs Up{base + L.off_U, 0, L.u_plane};
+  // p and q multiples of 16 with m of 128: the time reductions of dC, dD, R1 and
+  // R2 run on the tensor cores like the power gradients
+  const bool thin_tc = ptc && grad_tc_supported(*p);
+  if (ptc)
+    CK(launch_split_rows(static_cast<const float*>(dy), p->rows * q, Gp.hi(0), Gp.lo(0), st),
+       "adjoint planes");
+  if (thin_tc)
+    CK(launch_split_rows(static_cast<const float*>(u), p->rows * pp, Up.hi(0), Up.lo(0), st),
+       "input planes");
 
   // dC = sum G v^(N+1)^T: v^(N_i+1) sits in state buffer tile.fbuf.  This runs
   // first: with checkpoints, the recomputation below reuses those buffers.
   if (dC) {
     const TSrc VF{0, V, 1, 0, nullptr, 0};
-    if (wtreduce_supported(*p, m, q, 1))
+    if (thin_tc && p->all_fbuf >= 0) {   // dC^T = sum v^(N+1)_l G_l^T, stored transposed
+      CK(launch_grad_tc_xy(*p, p->d_all_tiles, chunks(0), nall, V.hi(p->all_fbuf),
+                           V.lo(p->all_fbuf), m, Gp.hi(0), Gp.lo(0), q, 0, true,
+                           static_cast<float*>(part), st),
+         "dC (tensor core)");
+      CK(launch_reduce_partials(*p, static_cast<const float*>(part), sysbeg(0), (int64_t)q * m,
+                                dC, true, (int64_t)q * m, st),
+         "dC reduction");
+    } else if (wtreduce_supported(*p, m, q, 1))
       CK(launch_wtreduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), VF, m, dy, q, 1, 0, 0,
                          true, part, dC, true, (int64_t)q * m, 0, st),
          "dC");
@@ -595,7 +663,14 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
          "dC");
   }
   if (dD) {   // dD = sum G u^T
-    if (wtreduce_supported(*p, q, pp, 1))
+    if (thin_tc) {
+      CK(launch_grad_tc_xy(*p, p->d_all_tiles, chunks(0), nall, Gp.hi(0), Gp.lo(0), q, Up.hi(0),
+                           Up.lo(0), pp, 0, false, static_cast<float*>(part), st),
+         "dD (tensor core)");
+      CK(launch_reduce_partials(*p, static_cast<const float*>(part), sysbeg(0), (int64_t)q * pp,
+                                dD, true, (int64_t)q * pp, st),
+         "dD reduction");
+    } else if (wtreduce_supported(*p, q, pp, 1))
       CK(launch_wtreduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), G, q, u, pp, 1, 0, 0,
                          false, part, dD, true, (int64_t)q * pp, 0, st),
          "dD");
@@ -605,7 +680,9 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
          "dD");
   }
   // W^(N_i+1) = C^T G, in the adjoint buffer the stage N_i reads
-  if (proj)
+  if (ptc)
+    CK(launch_proj_tc_adj_init(*p, Gp, W, st), "adjoint init");
+  else if (proj)
     CK(launch_proj_adj_init(*p, static_cast<const float*>(dy), W, st), "adjoint init");
   else
     CK(launch_adj_init(*p, dy, W, st), "adjoint init");
@@ -681,7 +758,9 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   }
   // first stage (fused with Bbar u): W^(1) is adjoint buffer 1
   if (du) {
-    if (proj)
+    if (ptc)
+      CK(launch_proj_tc_du(*p, Gp, W, 1, static_cast<float*>(du), st), "du");
+    else if (proj)
       CK(launch_proj_du(*p, static_cast<const float*>(dy), W, 1, static_cast<float*>(du), st),
          "du");
     else
@@ -689,7 +768,16 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   }
   // R1 = sum W^(1)_l u_l^T,  R2 = sum W^(1)_l u_(l-1)^T
   const TSrc W1{0, W, 0, 1, nullptr, 0};
-  if (wtreduce_supported(*p, m, pp, 2)) {
+  if (thin_tc) {
+    for (int sh = 0; sh < 2; ++sh) {
+      CK(launch_grad_tc_xy(*p, p->d_all_tiles, chunks(0), nall, W.hi(1), W.lo(1), m, Up.hi(0),
+                           Up.lo(0), pp, sh, false, static_cast<float*>(part), st),
+         sh ? "R2 (tensor core)" : "R1 (tensor core)");
+      CK(launch_reduce_partials(*p, static_cast<const float*>(part), sysbeg(0), mp,
+                                sh ? R2 : R1, tf64, mp, st),
+         "R1, R2 reduction");
+    }
+  } else if (wtreduce_supported(*p, m, pp, 2)) {
     CK(launch_wtreduce(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W1, m, u, pp, 2, 0, 1,
                        false, part, R1, tf64, mp, (int64_t)ns * mp, st),
        "R1, R2");
@@ -711,7 +799,9 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   // dP_0 += R2 Bbar^T;  dBbar = R1 + Abar^T R2
   CK(gemm_t(R2, Bbar, dP, m, m, pp, pp, pp, m, mp, mp, kst, ns, 1.0, 1.0, false, true, st), "dP0");
   CK(cudaMemcpyAsync(dBb, R1, sizeof(T) * ns * mp, cudaMemcpyDeviceToDevice, st), "copy");
-  CK(gemm_t(P, R2, dBb, m, pp, m, m, pp, pp, kst, mp, mp, ns, 1.0, 1.0, true, false, st), "dBbar");
+  CK(gemm_t(P, R2, dBb, m, pp, m, m, pp, pp, kst, mp, mp, ns, 1.0, 1.0, true, false, st, part,
+            L.off_dP - L.off_part),
+     "dBbar");
   // squaring chain P_(k+1) = P_k P_k:  dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1)
   // on the tensor cores for the BF16-split plans (the four split planes of
   // dP_(k+1) fit in the partial-sum region, free by now); FP32 / FP64 otherwise
@@ -1198,6 +1288,9 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     p->n_ck = 0;
   }
   for (Tile& t : all) t.fbuf = fwd_buf(*p, t.flags + 1);
+  p->all_fbuf = all.empty() ? -1 : all[0].fbuf;
+  for (const Tile& t : all)
+    if (t.fbuf != p->all_fbuf) p->all_fbuf = -1;
   p->h_tiles.assign(std::max(maxN + 1, 1), {});
   for (int i = 0; i < nseq; ++i) {
     const int64_t L = h_offsets[i + 1] - h_offsets[i];
@@ -1237,6 +1330,16 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
   }
   CK(upload(t0s, &p->d_stage0_tiles), "upload first-stage schedule");
   p->n_stage0_tiles = (int)t0s.size();
+  // output tiles grouped by the buffer holding their final states (the
+  // tensor-core output projection reads one buffer per launch)
+  std::stable_sort(outs.begin(), outs.end(),
+                   [](const Tile& a, const Tile& b) { return a.fbuf < b.fbuf; });
+  p->out_segs.clear();
+  for (int i = 0; i < (int)outs.size(); ++i) {
+    if (p->out_segs.empty() || p->out_segs.back()[0] != outs[i].fbuf)
+      p->out_segs.push_back({outs[i].fbuf, i, 0});
+    p->out_segs.back()[2]++;
+  }
   CK(upload(outs, &p->d_out_tiles), "upload output schedule");
   p->n_out_tiles = (int)outs.size();
   if (!seqs.empty()) {
@@ -1254,16 +1357,27 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     // Time-reduction chunks: runs of up to CH consecutive tiles of one system,
     // grouped by system (list 0: every tile; list k: the tiles of stage k).
     // Longer runs mean fewer partial sums to write and add; CH shrinks until
-    // the reductions have at least three blocks per SM.
+    // the reductions have at least three blocks per SM.  The tensor-core power
+    // gradients of lists k >= 1 split each chunk further into (m / 128) x
+    // (m / BN) output blocks: with large m their runs grow (up to 64 tiles)
+    // while there are still six blocks per SM, since each partial is m x m.
     int CH = 16;
     while (CH > 4 && (int64_t)all.size() < (int64_t)CH * 3 * p->num_sms) CH >>= 1;
+    const int64_t grad_blocks =
+        grad_tc_supported(*p) ? (int64_t)(p->d.m / 128) * (p->d.m / grad_tc_block_n(p->d.m)) : 0;
     std::vector<int32_t> data;
     p->chunk_lists.assign(std::max(maxN + 1, 1), ChunkList{});
     for (size_t li = 0; li < p->chunk_lists.size(); ++li) {
       const std::vector<Tile>& tl = li == 0 ? all : p->h_tiles[li];
+      int CHl = CH;
+      if (li > 0 && grad_blocks > 0) {
+        CHl = 64;
+        while (CHl > CH && (int64_t)tl.size() / CHl * grad_blocks < (int64_t)6 * p->num_sms)
+          CHl >>= 1;
+      }
       std::vector<std::array<int32_t, 3>> ch;
       for (int ti = 0; ti < (int)tl.size(); ++ti) {
-        if (ch.empty() || ch.back()[2] != tl[ti].sys || ch.back()[1] == CH ||
+        if (ch.empty() || ch.back()[2] != tl[ti].sys || ch.back()[1] == CHl ||
             ch.back()[0] + ch.back()[1] != ti)
           ch.push_back({ti, 0, tl[ti].sys});
         ch.back()[1]++;

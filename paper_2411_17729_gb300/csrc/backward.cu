@@ -122,6 +122,51 @@ __global__ void reduce_partials_kernel(const ACC* __restrict__ partial,
   }
 }
 
+// The same sum over FP32 partials, four consecutive elements per thread
+// (elems % 4 == 0) and four chunks' loads in flight per step; the additions
+// keep the chunk order, so the result is the scalar kernel's bit for bit.
+template <typename OUT>
+__global__ void reduce_partials4_kernel(const float* __restrict__ partial,
+                                        const int32_t* __restrict__ sys_begin, int64_t elems,
+                                        OUT* __restrict__ out, int64_t out_sys_stride,
+                                        int64_t seg, int64_t seg_stride, int accumulate) {
+  const int s = blockIdx.y;
+  const int c0 = sys_begin[s], c1 = sys_begin[s + 1];
+  const int64_t n4 = elems >> 2;
+  const float4* p4 = reinterpret_cast<const float4*>(partial);
+  for (int64_t e4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e4 < n4;
+       e4 += (int64_t)gridDim.x * blockDim.x) {
+    OUT v[4] = {0, 0, 0, 0};
+    int c = c0;
+    for (; c + 4 <= c1; c += 4) {
+      float4 a[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) a[h] = __ldg(p4 + (int64_t)(c + h) * n4 + e4);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        v[0] += (OUT)a[h].x;
+        v[1] += (OUT)a[h].y;
+        v[2] += (OUT)a[h].z;
+        v[3] += (OUT)a[h].w;
+      }
+    }
+    for (; c < c1; ++c) {
+      const float4 a = __ldg(p4 + (int64_t)c * n4 + e4);
+      v[0] += (OUT)a.x;
+      v[1] += (OUT)a.y;
+      v[2] += (OUT)a.z;
+      v[3] += (OUT)a.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t e = 4 * e4 + j;
+      const int64_t h = e / seg;
+      OUT* o = out + h * seg_stride + (int64_t)s * out_sys_stride + (e - h * seg);
+      *o = accumulate ? *o + v[j] : v[j];
+    }
+  }
+}
+
 // With few systems x elements the sum above has too little parallelism: the
 // chunks of each system are first split into G contiguous groups summed in
 // order into tmp[s][g][e], then the G group sums are added in order.
@@ -463,6 +508,16 @@ static void sum_chunks(const Plan& p, const ACC* partial, const int32_t* sys_beg
     while (G > 1 && (size_t)G * have * sizeof(ACC) > p.red_scratch_bytes) --G;
   }
   if (G <= 1) {
+    if (sizeof(ACC) == 4 && elems % 4 == 0 &&
+        reinterpret_cast<uintptr_t>(partial) % 16 == 0) {
+      const int64_t n4 = elems / 4;
+      const int b4 = (int)std::min<int64_t>((n4 + 255) / 256, 4 * (int64_t)p.num_sms);
+      reduce_partials4_kernel<OUT><<<dim3(b4, p.d.nsys), 256, 0, st>>>(
+          reinterpret_cast<const float*>(partial), sys_begin, elems, out, out_sys_stride, seg,
+          seg_stride, accumulate);
+      CASCADE_LAUNCHED();
+      return;
+    }
     reduce_partials_kernel<ACC, OUT><<<dim3(rblocks, p.d.nsys), 256, 0, st>>>(
         partial, sys_begin, elems, out, out_sys_stride, seg, seg_stride, accumulate);
     CASCADE_LAUNCHED();

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -118,6 +119,11 @@ struct Plan {
   float* ABbar32 = nullptr;
   float* C32 = nullptr;
   float* D32 = nullptr;
+  // (hi, lo) BF16 planes of the small matrices for the tensor-core projections
+  // (PC_* below, all systems of each matrix contiguous; null unless supported)
+  void* pc_hi = nullptr;
+  void* pc_lo = nullptr;
+  int64_t pc_off[8] = {};
   double* A64 = nullptr;         // continuous A (for the discretisation adjoint) [nsys,m,m]
   double* B64 = nullptr;         // continuous B [nsys,m,p]
   double* delta64 = nullptr;     // [nsys]
@@ -145,6 +151,7 @@ struct Plan {
   Tile* d_all_tiles = nullptr;               // every tile of every sequence (flags = N_i,
                                              // fbuf = buffer of its final states)
   int n_all_tiles = 0;
+  int all_fbuf = -1;                         // fbuf shared by every tile, or -1
   std::vector<ChunkList> chunk_lists;        // [0]: every tile; [k]: tiles of stage k
   int32_t* d_chunk_data = nullptr;           // chunks [n][3] (first tile, count, system) and
                                              // per-system chunk ranges [nsys + 1] of each list
@@ -155,7 +162,8 @@ struct Plan {
   int64_t saved_batch = -1;
   Seq* d_seqs = nullptr;                     // all sequences
   int n_out_tiles = 0;                       // tiles of sequences whose output is not fused
-  Tile* d_out_tiles = nullptr;               // (flags = workspace buffer of the final states)
+  Tile* d_out_tiles = nullptr;               // (fbuf = workspace buffer of the final states)
+  std::vector<std::array<int, 3>> out_segs;  // output tiles grouped by fbuf: (buf, first, count)
   Tile* d_stage0_tiles = nullptr;            // tiles for the first stage (all rows)
   int n_stage0_tiles = 0;
   bool fuse_output = false;
@@ -266,6 +274,21 @@ cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chu
                             cudaStream_t st);
 // Narrow projections as register-tiled GEMMs (proj.cu; tensor-core formats).
 bool proj_supported(const Plan& p);
+// Tensor-core projections (proj_tc.cu): BF16 split with p and q multiples of 16.
+// The B operands are the PC_* matrices, split at set_system time.
+enum { PC_B = 0, PC_AB, PC_C, PC_D, PC_CT, PC_BT, PC_ABT, PC_DT, PC_COUNT };
+bool proj_tc_supported(const Plan& p);
+size_t proj_coef_elems(const Plan& p, int64_t off[PC_COUNT]);
+cudaError_t launch_proj_coef(const Plan& p, cudaStream_t st);
+cudaError_t launch_split_rows(const float* x, int64_t n, void* hi, void* lo, cudaStream_t st);
+// U, G: (hi, lo) BF16 planes of u [rows, p] and G [rows, q] (buffer 0 of the Bufs)
+cudaError_t launch_proj_tc_stage0(const Plan& p, const Bufs& U, const Bufs& V, int64_t v_rows,
+                                  int buf, bool odd_only, cudaStream_t st);
+cudaError_t launch_proj_tc_output(const Plan& p, const Bufs& U, float* y, const Bufs& V,
+                                  int64_t v_rows, cudaStream_t st);
+cudaError_t launch_proj_tc_adj_init(const Plan& p, const Bufs& G, const Bufs& W, cudaStream_t st);
+cudaError_t launch_proj_tc_du(const Plan& p, const Bufs& G, const Bufs& W, int wbuf, float* du,
+                              cudaStream_t st);
 cudaError_t launch_proj_stage0(const Plan& p, const float* u, const Bufs& V, int buf,
                                bool odd_only, cudaStream_t st);
 cudaError_t launch_proj_adj_init(const Plan& p, const float* G, const Bufs& W, cudaStream_t st);
@@ -281,6 +304,11 @@ cudaError_t launch_reduce_partials(const Plan& p, const float* partial, const in
                                    int64_t elems, void* out, bool out_f64, int64_t out_sys_stride,
                                    cudaStream_t st);
 bool grad_tc_supported(const Plan& p);
+int grad_tc_block_n(int m);
+cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* chunks,
+                              int nchunks, const void* x_hi, const void* x_lo, int ma,
+                              const void* y_hi, const void* y_lo, int nb, int shift, bool trans,
+                              float* partial, cudaStream_t st);
 cudaError_t launch_grad_tc(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
                            const void* w_hi, const void* w_lo, const void* v_hi, const void* v_lo,
                            int shift, float* partial, cudaStream_t st);

@@ -9,7 +9,10 @@
 // Products: Whi Vhi + Whi Vlo + Wlo Vhi with FP32 accumulation in TMEM.
 // Rows past the sequence end (W side) and sources before its start (V side)
 // are zeroed in shared memory.  Partials [chunk][i][j] are summed per system
-// by the ordered reduction of backward.cu.
+// by the ordered reduction of backward.cu.  With p and q multiples of 32 the
+// same kernel forms the first-stage and output reductions over time,
+// R1 = sum W^(1)_l u_l^T, R2 = sum W^(1)_l u_(l-1)^T (m x p) and
+// dC^T = sum v_l G_l^T (m x q, stored transposed as dC).
 //
 // Block layout (192 threads, persistent over (chunk, row block, column block)):
 //   warp 0 TMA producer, warp 1 TMEM allocator + MMA issuer, warps 2..5 epilogue.
@@ -29,7 +32,8 @@ struct GradArgs {
   const Tile* tiles;
   const int32_t* chunks;   // [n][3]: first tile, count, system
   int32_t nchunks;
-  int32_t m;
+  int32_t ma, nb;          // columns of the W side (i) and of the V side (j)
+  int32_t trans;           // partials stored [chunk][j][i] instead of [chunk][i][j]
   int32_t BN;              // j per block (N)
   int32_t mblocks, nblocks;
   int32_t shift;
@@ -78,7 +82,6 @@ __global__ void __launch_bounds__(NTH, 1)
                    const __grid_constant__ CUtensorMap tm_vlo, const GradArgs args) {
   const int BN = args.BN;
   const int S = args.stages;
-  const int m = args.m;
   const int nwork = args.nchunks * args.mblocks * args.nblocks;
   const int shift = args.shift;
   const uint32_t a_bytes = (TM / 32) * BOX_BYTES;              // 16 KB per plane
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(NTH, 1)
         break;
       }
       ptx::tc_fence_after();
-      float* out = args.partial + (int64_t)c * m * m + (int64_t)(i0 + r) * m + j0;
+      float* pc = args.partial + (int64_t)c * args.ma * args.nb;
       const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(abuf * BN);
       for (int cc = 0; cc < BN / 32; ++cc) {
         float v[32];
@@ -290,9 +293,24 @@ __global__ void __launch_bounds__(NTH, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0.f;
         }
-        float4* o4 = reinterpret_cast<float4*>(out + cc * 32);
+        // rows i >= ma and columns j >= nb are the zero padding of the blocks
+        const int jn = min(32, args.nb - (j0 + cc * 32));
+        if (i0 + r < args.ma && jn > 0) {
+          if (args.trans) {
+            // column j of the block: the warp's 32 rows i are 128 contiguous bytes
+            float* o = pc + (int64_t)(j0 + cc * 32) * args.ma + i0 + r;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) o4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            for (int j = 0; j < 32; ++j)
+              if (j < jn) o[(int64_t)j * args.ma] = v[j];
+          } else {
+            float4* o4 = reinterpret_cast<float4*>(pc + (int64_t)(i0 + r) * args.nb + j0 + cc * 32);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (4 * j < jn)
+                o4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          }
+        }
+        __syncwarp();   // converged for the next tcgen05.ld
       }
       ptx::tc_fence_before();
       ptx::mbar_arrive(&acc_empty[abuf]);
@@ -308,24 +326,37 @@ __global__ void __launch_bounds__(NTH, 1)
 
 }  // namespace
 
+// j extent of one block: 256 where it divides m, else 128 (m is a multiple of 128)
+int grad_tc_block_n(int m) { return m % 256 == 0 ? 256 : 128; }
+
 bool grad_tc_supported(const Plan& p) {
   return p.d.precision == CASCADE_BF16_SPLIT && p.d.m % TM == 0;
 }
 
-// partial[c] = sum over the rows of chunk c of W[l] V[l - shift]^T (m x m, FP32).
-cudaError_t launch_grad_tc(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
-                           const void* w_hi, const void* w_lo, const void* v_hi, const void* v_lo,
-                           int shift, float* partial, cudaStream_t st) {
+// partial[c] = sum over the rows of chunk c of X[l] Y[l - shift]^T (ma x nb, FP32,
+// or its transpose with trans), X and Y (hi, lo) BF16 planes of [rows, ma] and
+// [rows, nb], ma and nb multiples of 8.  The blocks cover ma rounded up to 128
+// and nb rounded up to 32: TMA fills the columns past each matrix with zeros.
+cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* chunks,
+                              int nchunks, const void* x_hi, const void* x_lo, int ma,
+                              const void* y_hi, const void* y_lo, int nb, int shift, bool trans,
+                              float* partial, cudaStream_t st) {
   if (nchunks == 0) return cudaSuccess;
-  const int m = p.d.m;
-  const int BN = m >= 256 ? 256 : m;
+  if (ma <= 0 || nb <= 0 || ma % 8 != 0 || nb % 8 != 0) {
+    set_global_error("power-gradient shapes: ma and nb must be multiples of 8");
+    return cudaErrorInvalidValue;
+  }
+  const int mpad = (ma + TM - 1) / TM * TM, npad = (nb + 31) / 32 * 32;
+  int BN = 0;
+  for (int bn = 256; bn >= 32 && BN == 0; bn >>= 1)
+    if (npad % bn == 0) BN = bn;
   CUtensorMap maps[4];
   std::string err;
   const uint64_t rows = (uint64_t)p.rows;
-  if (!encode_tmap_2d(&maps[0], w_hi, 2, m, rows, 32, BMK, &err, 64) ||
-      !encode_tmap_2d(&maps[1], w_lo, 2, m, rows, 32, BMK, &err, 64) ||
-      !encode_tmap_2d(&maps[2], v_hi, 2, m, rows, 32, BMK, &err, 64) ||
-      !encode_tmap_2d(&maps[3], v_lo, 2, m, rows, 32, BMK, &err, 64)) {
+  if (!encode_tmap_2d(&maps[0], x_hi, 2, ma, rows, 32, BMK, &err, 64) ||
+      !encode_tmap_2d(&maps[1], x_lo, 2, ma, rows, 32, BMK, &err, 64) ||
+      !encode_tmap_2d(&maps[2], y_hi, 2, nb, rows, 32, BMK, &err, 64) ||
+      !encode_tmap_2d(&maps[3], y_lo, 2, nb, rows, 32, BMK, &err, 64)) {
     set_global_error("tensor map encode failed: " + err);
     return cudaErrorInvalidValue;
   }
@@ -333,10 +364,12 @@ cudaError_t launch_grad_tc(const Plan& p, const Tile* tiles, const int32_t* chun
   a.tiles = tiles;
   a.chunks = chunks;
   a.nchunks = nchunks;
-  a.m = m;
+  a.ma = ma;
+  a.nb = nb;
+  a.trans = trans ? 1 : 0;
   a.BN = BN;
-  a.mblocks = m / TM;
-  a.nblocks = m / BN;
+  a.mblocks = mpad / TM;
+  a.nblocks = npad / BN;
   a.shift = shift;
   a.stages = 2;
   a.partial = partial;
@@ -353,6 +386,14 @@ cudaError_t launch_grad_tc(const Plan& p, const Tile* tiles, const int32_t* chun
   grad_tc_kernel<<<grid, NTH, smem, st>>>(maps[0], maps[1], maps[2], maps[3], a);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
+}
+
+// partial[c] = sum over the rows of chunk c of W[l] V[l - shift]^T (m x m, FP32).
+cudaError_t launch_grad_tc(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
+                           const void* w_hi, const void* w_lo, const void* v_hi, const void* v_lo,
+                           int shift, float* partial, cudaStream_t st) {
+  return launch_grad_tc_xy(p, tiles, chunks, nchunks, w_hi, w_lo, p.d.m, v_hi, v_lo, p.d.m, shift,
+                           false, partial, st);
 }
 
 }  // namespace cascade

@@ -1,0 +1,128 @@
+"""GPU parity of the tensor-core projections (p and q multiples of 16, BF16
+split): the first stage fused with Bbar u, the output y = C v + D u, the
+adjoint seed W = C^T G and du = Bbar^T W_l + (Abar Bbar)^T W_(l+1) + D^T G,
+against the CPU FP64 oracle.  Two systems, ragged lengths around the 128-row
+tiles (so sequences end inside tiles and their N differ, which spreads the
+final states over both ping-pong buffers), one or several column blocks per
+projection; with p or q = 16 the 32-entry operand boxes are half filled by
+TMA with zeros.  The backward's time reductions (dC, dD, R1, R2) run on the
+same tensor-core kernel as the power gradients here.  Bars: 2e-3 on y, Cx and
+every gradient."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from _parity import OUT_EPS, TOL, cast_inputs, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+LENGTHS = (1, 2, 127, 128, 129, 300, 1000, 2100)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_17729_gb300 import build
+    build()
+    from paper_2411_17729_gb300 import cascade
+    return cascade
+
+
+def two_systems(m, p, q, N=11, seed=30):
+    w = wl.differentiation_form(m=m, p=p, q=q, L=8, batch=len(LENGTHS), N=N, delta=1e-2,
+                                seed=seed)
+    w.offsets = np.concatenate([[0], np.cumsum(LENGTHS)]).astype(np.int64)
+    w.u = np.random.default_rng(seed + 1).standard_normal((int(w.offsets[-1]), p))
+    w.sys_of_seq = (np.arange(len(LENGTHS)) % 2).astype(np.int32)
+    w.A = np.concatenate([w.A, w.A])
+    w.delta = np.array([1e-2, 3e-2])
+    for k in ("B", "C", "D"):
+        setattr(w, k, np.concatenate([getattr(w, k), 0.7 * getattr(w, k)]))
+    return cast_inputs(w, "bf16_split")
+
+
+def forward(lib, w, flags=0):
+    import torch
+    c = lib.from_workload(w, precision="bf16_split", flags=flags)
+    y = c.forward(torch.as_tensor(w.u, dtype=torch.float32).cuda().contiguous())
+    torch.cuda.synchronize()
+    assert c.device_error() == 0, c.lib.cascade_last_error(c.plan)
+    return c, y.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("m,p,q", [(128, 32, 32), (256, 64, 32), (384, 32, 96), (128, 16, 16),
+                                   (256, 16, 48)])
+def test_forward_wide_projections(lib, m, p, q):
+    """m = 384: three 128-column blocks for v^(1); q = 96: three 32-column
+    blocks for y."""
+    w = two_systems(m, p, q)
+    c, y = forward(lib, w)
+    Ns = c.seq_N()
+    assert len({int(n) % 2 for n in Ns if n >= 0}) == 2   # both final-state buffers
+    yo = oracle.cascade_forward(w, N_per_seq=Ns)
+    ey, ecx = rel_errors(w, y, yo, OUT_EPS["bf16_split"])
+    assert ey <= TOL["bf16_split"] and ecx <= TOL["bf16_split"], (ey, ecx)
+
+
+def test_forward_truncated(lib):
+    """N = 4 for every sequence (a truncated cascade, 2^(N+1) < L)."""
+    w = two_systems(128, 32, 64, N=4)
+    c, y = forward(lib, w)
+    yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
+    ey, ecx = rel_errors(w, y, yo, OUT_EPS["bf16_split"])
+    assert ey <= TOL["bf16_split"] and ecx <= TOL["bf16_split"], (ey, ecx)
+
+
+def test_scan_first_level_odd_rows(lib):
+    """Work-efficient schedule: the first level adds (Abar Bbar) u_(l-1) on odd
+    l only (even rows zeroed in shared memory before the tensor core reads
+    them)."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SCAN
+    w = two_systems(128, 32, 32)
+    c, y = forward(lib, w, CASCADE_FLAG_SCAN)
+    yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
+    ey, ecx = rel_errors(w, y, yo, OUT_EPS["bf16_split"])
+    assert ey <= TOL["bf16_split"] and ecx <= TOL["bf16_split"], (ey, ecx)
+
+
+def grads(lib, w, dy, flags):
+    import torch
+    c = lib.from_workload(w, precision="bf16_split", flags=flags)
+    u = torch.as_tensor(w.u, dtype=torch.float32).cuda().contiguous()
+    y = c.forward(u)
+    g = c.backward(u, torch.as_tensor(dy, dtype=torch.float32).cuda().contiguous())
+    torch.cuda.synchronize()
+    assert c.device_error() == 0, c.lib.cascade_last_error(c.plan)
+    return c, y.double().cpu().numpy(), {k: v.double().cpu().numpy() for k, v in g.items()}
+
+
+def check_grads(w, c, g, dy):
+    ref = oracle.cascade_backward(w, dy, N_per_seq=c.seq_N())
+    errs = {k: np.linalg.norm(g[k] - ref[k]) / np.linalg.norm(ref[k]) for k in g}
+    assert all(e <= TOL["bf16_split"] for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("m,p,q", [(256, 32, 64), (128, 64, 32), (384, 96, 32), (128, 16, 16),
+                                   (256, 48, 16)])
+def test_backward_wide_projections(lib, m, p, q):
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SAVE_STATES
+    w = two_systems(m, p, q)
+    dy = np.random.default_rng(32).standard_normal((w.rows, q)).astype(np.float32)
+    c, _, g = grads(lib, w, dy, CASCADE_FLAG_SAVE_STATES)
+    check_grads(w, c, g, dy.astype(np.float64))
+
+
+def test_backward_recompute_bitwise(lib):
+    """Checkpointed stage outputs give the same gradients, bit for bit."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_RECOMPUTE, CASCADE_FLAG_SAVE_STATES
+    w = two_systems(128, 32, 32)
+    dy = np.random.default_rng(33).standard_normal((w.rows, 32)).astype(np.float32)
+    c1, y1, g1 = grads(lib, w, dy, CASCADE_FLAG_SAVE_STATES)
+    c2, y2, g2 = grads(lib, w, dy, CASCADE_FLAG_RECOMPUTE)
+    assert np.array_equal(y1, y2)
+    for k in g1:
+        assert np.array_equal(g1[k], g2[k]), k
+    check_grads(w, c2, g2, dy.astype(np.float64))

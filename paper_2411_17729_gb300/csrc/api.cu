@@ -126,6 +126,36 @@ bool encode_tmap_3d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t
   return true;
 }
 
+// Row-major [rows, cols] viewed as (32 entries, rows, cols / 32 column blocks):
+// one box (32, box_rows, box_blocks) lands in shared memory as box_blocks
+// consecutive [box_rows][32] tiles, the layout of box_blocks 2-D boxes.
+bool encode_tmap_colblocks(CUtensorMap* map, const void* base, int elem_bytes, uint64_t cols,
+                           uint64_t rows, uint32_t box_rows, uint32_t box_blocks,
+                           std::string* err, int swizzle_bytes) {
+  EncodeTiledFn enc = get_encoder();
+  if (!enc) {
+    *err = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  const CUtensorMapDataType dt =
+      elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  cuuint64_t dims[3] = {32, rows, (cols + 31) / 32};
+  cuuint64_t strides[2] = {cols * (uint64_t)elem_bytes, 32 * (uint64_t)elem_bytes};
+  cuuint32_t box[3] = {32, box_rows, box_blocks};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled (column blocks) returned %d", (int)r);
+    *err = buf;
+    return false;
+  }
+  return true;
+}
+
 }  // namespace cascade
 
 using namespace cascade;
@@ -558,7 +588,7 @@ cudaError_t gemm_t(const float* A, const float* B, float* C, int M, int N, int K
                    size_t scratch_bytes = 0) {
   // square-ish products, or long ones with scratch for a split K: the
   // register-tiled kernel (128 x 128 tiles, or 64 x 64 with K slices)
-  if ((M >= 128 && N >= 128) || (scratch && (int64_t)M * N * K >= (int64_t(1) << 24)))
+  if ((M >= 128 && N >= 128) || (scratch && (int64_t)M * N * K >= (int64_t(1) << 20)))
     return launch_sgemm2(A, B, tA, tB, nullptr, nullptr, false, false, C, M, N, K, lda, ldb, ldc,
                          sA, sB, sC, batch, (float)alpha, (float)beta, st,
                          static_cast<float*>(scratch), scratch_bytes / sizeof(float));
@@ -855,7 +885,9 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
       CK(to_f64<T>(dAt, mm, dA, mm, mm, ns, st), "dA");
     }
     if (dB) {
-      CK(gemm_t(Minv, dBb, dBt, m, pp, m, m, pp, pp, mm, mp, mp, ns, 1.0, 0.0, true, false, st), "dB");
+      CK(gemm_t(Minv, dBb, dBt, m, pp, m, m, pp, pp, mm, mp, mp, ns, 1.0, 0.0, true, false, st,
+                part, L.off_dP - L.off_part),
+         "dB");
       CK(launch_axpy_sys<T>(dBt, mp, dBt, mp, mp, ns, p->delta64, 1.0, false, st), "dB");
       CK(to_f64<T>(dBt, mp, dB, mp, mp, ns, st), "dB");
     }
@@ -1398,9 +1430,9 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
       }
       p->max_chunks = std::max(p->max_chunks, cl.n);
     }
-    // group sums for the reductions with little parallelism: fewer than
-    // 2048 x SMs systems x elements, so G groups need under twice that
-    p->red_scratch_bytes = (size_t)2 * 2048 * p->num_sms * sizeof(double);
+    // group sums for the reductions with little parallelism (fewer than
+    // 2048 x SMs threads of one to four elements)
+    p->red_scratch_bytes = (size_t)4 * 2048 * p->num_sms * sizeof(double);
     CK(cudaMalloc(&p->d_red_scratch, p->red_scratch_bytes), "alloc reduction scratch");
     CK(cudaMalloc(&p->d_chunk_data, data.size() * sizeof(int32_t)), "alloc chunks");
     CK(cudaMemcpy(p->d_chunk_data, data.data(), data.size() * sizeof(int32_t),

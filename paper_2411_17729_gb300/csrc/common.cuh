@@ -371,6 +371,9 @@ TcConfig tc_default(int m, int precision);
 bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
                     uint64_t outer, uint32_t box_inner, uint32_t box_outer, std::string* err,
                     int swizzle_bytes = 128);
+bool encode_tmap_colblocks(CUtensorMap* map, const void* base, int elem_bytes, uint64_t cols,
+                           uint64_t rows, uint32_t box_rows, uint32_t box_blocks,
+                           std::string* err, int swizzle_bytes = 64);
 // Row-major [groups * S, inner] viewed as (inner, S, groups); box (box_inner, 1, box_groups).
 bool encode_tmap_3d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
                     uint64_t S, uint64_t groups, uint32_t box_inner, uint32_t box_groups,

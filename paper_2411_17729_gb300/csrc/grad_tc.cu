@@ -3,13 +3,15 @@
 //
 // The contraction runs over time: D[i][j] = sum_l W[l][i] V[l - s][j].  Both
 // operands are stored time-major with the state index contiguous, which is
-// the MN-major operand form of tcgen05: TMA loads boxes of 64 time rows x 32
-// state entries (64 bytes, 64-byte swizzle); a row-block of 8 time steps is
-// 512 bytes (SBO), and consecutive 32-entry column blocks sit 4 KB apart (LBO).
+// the MN-major operand form of tcgen05: one K step is 32 time rows, each
+// 32-entry column block of it a 2 KB tile (64-byte rows, 64-byte swizzle); a
+// row-block of 8 time steps is 512 bytes (SBO), and consecutive column blocks
+// sit 2 KB apart (LBO).  A map over column blocks brings all blocks of one
+// plane in one TMA copy.  Four K steps are in flight.
 // Products: Whi Vhi + Whi Vlo + Wlo Vhi with FP32 accumulation in TMEM.
 // Rows past the sequence end (W side) and sources before its start (V side)
 // are zeroed in shared memory.  Partials [chunk][i][j] are summed per system
-// by the ordered reduction of backward.cu.  With p and q multiples of 32 the
+// by the ordered reduction of backward.cu.  With p and q multiples of 16 the
 // same kernel forms the first-stage and output reductions over time,
 // R1 = sum W^(1)_l u_l^T, R2 = sum W^(1)_l u_(l-1)^T (m x p) and
 // dC^T = sum v_l G_l^T (m x q, stored transposed as dC).
@@ -22,11 +24,12 @@
 namespace cascade {
 namespace {
 
-constexpr int BMK = 64;                       // time rows per K step
+constexpr int BMK = 32;                       // time rows per K step
+constexpr int TK = 128 / BMK;                 // K steps per 128-row tile
 constexpr int TM = 128;                       // i per block (M)
 constexpr int NTH = 192;
 constexpr uint32_t ROWB = 64;                 // bytes per row of a box (32 BF16)
-constexpr uint32_t BOX_BYTES = BMK * ROWB;    // 4 KB: 64 rows x 32 entries
+constexpr uint32_t BOX_BYTES = BMK * ROWB;    // 2 KB: 32 rows x 32 entries
 
 struct GradArgs {
   const Tile* tiles;
@@ -38,6 +41,7 @@ struct GradArgs {
   int32_t mblocks, nblocks;
   int32_t shift;
   int32_t stages;
+  int32_t a3d, b3d;        // maps over column blocks: one TMA copy per plane and stage
   float* partial;          // [nchunks][m][m]
   int32_t* err;
   int32_t* diag;
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(NTH, 1)
         const int first = args.chunks[3 * c], count = args.chunks[3 * c + 1];
         for (int ti = first; ti < first + count && !*abort_flag; ++ti) {
           const Tile t = args.tiles[ti];
-          for (int kk = 0; kk < 2; ++kk) {
+          for (int kk = 0; kk < TK; ++kk) {
             if (!kstep_live(t, kk, shift)) continue;
             if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, limit, abort_flag)) {
               raise_grad_timeout(args, abort_flag, 1, w);
@@ -152,14 +156,26 @@ __global__ void __launch_bounds__(NTH, 1)
             uint8_t* sb = sa + 2 * a_bytes;
             const int wrow = (int)(t.seq_row0 + t.t0 + kk * BMK);
             ptx::mbar_arrive_expect_tx(&full[stage], stage_bytes);
-            for (int a = 0; a < TM / 32; ++a) {
-              ptx::tma_load_2d(sa + a * BOX_BYTES, &tm_whi, &full[stage], i0 + 32 * a, wrow);
-              ptx::tma_load_2d(sa + a_bytes + a * BOX_BYTES, &tm_wlo, &full[stage], i0 + 32 * a, wrow);
+            if (args.a3d) {
+              ptx::tma_load_3d(sa, &tm_whi, &full[stage], 0, wrow, i0 / 32);
+              ptx::tma_load_3d(sa + a_bytes, &tm_wlo, &full[stage], 0, wrow, i0 / 32);
+            } else {
+              for (int a = 0; a < TM / 32; ++a) {
+                ptx::tma_load_2d(sa + a * BOX_BYTES, &tm_whi, &full[stage], i0 + 32 * a, wrow);
+                ptx::tma_load_2d(sa + a_bytes + a * BOX_BYTES, &tm_wlo, &full[stage], i0 + 32 * a,
+                                 wrow);
+              }
             }
-            for (int b = 0; b < BN / 32; ++b) {
-              ptx::tma_load_2d(sb + b * BOX_BYTES, &tm_vhi, &full[stage], j0 + 32 * b, wrow - shift);
-              ptx::tma_load_2d(sb + b_bytes + b * BOX_BYTES, &tm_vlo, &full[stage], j0 + 32 * b,
-                               wrow - shift);
+            if (args.b3d) {
+              ptx::tma_load_3d(sb, &tm_vhi, &full[stage], 0, wrow - shift, j0 / 32);
+              ptx::tma_load_3d(sb + b_bytes, &tm_vlo, &full[stage], 0, wrow - shift, j0 / 32);
+            } else {
+              for (int b = 0; b < BN / 32; ++b) {
+                ptx::tma_load_2d(sb + b * BOX_BYTES, &tm_vhi, &full[stage], j0 + 32 * b,
+                                 wrow - shift);
+                ptx::tma_load_2d(sb + b_bytes + b * BOX_BYTES, &tm_vlo, &full[stage], j0 + 32 * b,
+                                 wrow - shift);
+              }
             }
             issued_parity[stage] = (int)phase;
             if (++stage == S) { stage = 0; phase ^= 1u; }
@@ -191,7 +207,7 @@ __global__ void __launch_bounds__(NTH, 1)
       bool any = false;
       for (int ti = first; ti < first + count && ok; ++ti) {
         const Tile t = args.tiles[ti];
-        for (int kk = 0; kk < 2; ++kk) {
+        for (int kk = 0; kk < TK; ++kk) {
           if (!kstep_live(t, kk, shift)) continue;
           if (!__all_sync(0xffffffffu, ptx::mbar_wait(&full[stage], phase, limit, abort_flag))) {
             raise_grad_timeout(args, abort_flag, 3, w);
@@ -275,7 +291,7 @@ __global__ void __launch_bounds__(NTH, 1)
       bool any = false;
       for (int ti = first; ti < first + count; ++ti) {
         const Tile t = args.tiles[ti];
-        any = any || kstep_live(t, 0, shift) || kstep_live(t, 1, shift);
+        for (int kk = 0; kk < TK; ++kk) any = any || kstep_live(t, kk, shift);
       }
       const int abuf = acc_i & 1;
       const uint32_t aph = (uint32_t)((acc_i >> 1) & 1);
@@ -353,14 +369,24 @@ cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* c
   CUtensorMap maps[4];
   std::string err;
   const uint64_t rows = (uint64_t)p.rows;
-  if (!encode_tmap_2d(&maps[0], x_hi, 2, ma, rows, 32, BMK, &err, 64) ||
-      !encode_tmap_2d(&maps[1], x_lo, 2, ma, rows, 32, BMK, &err, 64) ||
-      !encode_tmap_2d(&maps[2], y_hi, 2, nb, rows, 32, BMK, &err, 64) ||
-      !encode_tmap_2d(&maps[3], y_lo, 2, nb, rows, 32, BMK, &err, 64)) {
+  // Operands whose width is a multiple of 32 are read through column-block maps
+  // (one copy per plane and stage); the others (and any map the driver
+  // declines) through one 2-D box per 32-column block.
+  auto encode = [&](CUtensorMap* m2, const void* base, int cols, int blocks) -> int {
+    std::string e3;
+    if (cols % 32 == 0 && encode_tmap_colblocks(m2, base, 2, cols, rows, BMK, blocks, &e3, 64))
+      return 1;
+    return encode_tmap_2d(m2, base, 2, cols, rows, 32, BMK, &err, 64) ? 0 : -1;
+  };
+  const int ax = encode(&maps[0], x_hi, ma, TM / 32), al = encode(&maps[1], x_lo, ma, TM / 32);
+  const int bx = encode(&maps[2], y_hi, nb, BN / 32), bl = encode(&maps[3], y_lo, nb, BN / 32);
+  if (ax < 0 || al < 0 || bx < 0 || bl < 0 || ax != al || bx != bl) {
     set_global_error("tensor map encode failed: " + err);
     return cudaErrorInvalidValue;
   }
   GradArgs a{};
+  a.a3d = ax;
+  a.b3d = bx;
   a.tiles = tiles;
   a.chunks = chunks;
   a.nchunks = nchunks;
@@ -371,7 +397,7 @@ cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* c
   a.mblocks = mpad / TM;
   a.nblocks = npad / BN;
   a.shift = shift;
-  a.stages = 2;
+  a.stages = 4;
   a.partial = partial;
   a.err = p.err;
   a.diag = p.err + 1;

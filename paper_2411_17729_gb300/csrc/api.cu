@@ -245,6 +245,7 @@ void free_batch(Plan* p) {
   p->d_chunk_data = nullptr;
   p->chunk_lists.clear();
   p->max_chunks = 0;
+  p->chunks_all = 0;
   dfree(p->d_red_scratch);
   p->d_red_scratch = nullptr;
   p->red_scratch_bytes = 0;
@@ -438,11 +439,15 @@ Layout layout(const Plan& p) {
   if (save) {
     const size_t m = p.d.m, pp = p.d.p, q = p.d.q, ns = p.d.nsys;
     const size_t acc = p.d.precision == CASCADE_FP64 ? 8 : 4;
-    const size_t elems = std::max(std::max(m * m, q * m), std::max(q * pp, 2 * m * pp));
+    // partials: m x m per chunk of a stage list, q m, q p or 2 m p per chunk of
+    // the list of all tiles
+    const size_t elems0 = std::max(q * m, std::max(q * pp, 2 * m * pp));
     L.off_W = off;
     off += 2 * L.buf_stride;
     L.off_part = off;
-    off += align256((size_t)std::max(p.max_chunks, 1) * elems * acc);
+    off += align256(std::max((size_t)std::max(p.max_chunks, 1) * m * m,
+                             (size_t)std::max(p.chunks_all, 1) * elems0) *
+                    acc);
     L.off_dP = off;
     off += align256(ns * p.kmax1 * m * m * 8);
     L.off_R = off;                                  // R1, R2, dBbar, dB: [nsys, m, p] each
@@ -1395,13 +1400,19 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     // while there are still six blocks per SM, since each partial is m x m.
     int CH = 16;
     while (CH > 4 && (int64_t)all.size() < (int64_t)CH * 3 * p->num_sms) CH >>= 1;
+    // the list of all tiles feeds the wide-by-thin reductions (one block per
+    // chunk) unless they run on the tensor cores: then runs shrink to 4 tiles
+    // while there are fewer than 8 blocks per SM
+    int CH0 = CH;
+    if (!(proj_tc_supported(*p) && grad_tc_supported(*p)))
+      while (CH0 > 4 && (int64_t)all.size() < (int64_t)CH0 * 8 * p->num_sms) CH0 >>= 1;
     const int64_t grad_blocks =
         grad_tc_supported(*p) ? (int64_t)(p->d.m / 128) * (p->d.m / grad_tc_block_n(p->d.m)) : 0;
     std::vector<int32_t> data;
     p->chunk_lists.assign(std::max(maxN + 1, 1), ChunkList{});
     for (size_t li = 0; li < p->chunk_lists.size(); ++li) {
       const std::vector<Tile>& tl = li == 0 ? all : p->h_tiles[li];
-      int CHl = CH;
+      int CHl = li == 0 ? CH0 : CH;
       if (li > 0 && grad_blocks > 0) {
         CHl = 64;
         while (CHl > CH && (int64_t)tl.size() / CHl * grad_blocks < (int64_t)6 * p->num_sms)
@@ -1428,7 +1439,8 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
         while (ci < ch.size() && ch[ci][2] < sidx) ++ci;
         data.push_back((int32_t)ci);
       }
-      p->max_chunks = std::max(p->max_chunks, cl.n);
+      if (li == 0) p->chunks_all = cl.n;
+      else p->max_chunks = std::max(p->max_chunks, cl.n);
     }
     // group sums for the reductions with little parallelism (fewer than
     // 2048 x SMs threads of one to four elements)

@@ -547,6 +547,7 @@ static void sum_chunks(const Plan& p, const ACC* partial, const int32_t* sys_beg
   if (have < want && p.d_red_scratch) {
     G = (int)std::min<int64_t>(32, (want + have - 1) / have);
     while (G > 1 && (size_t)G * elems * p.d.nsys * sizeof(ACC) > p.red_scratch_bytes) --G;
+    if (G < 3) G = 1;   // two passes pay off only for a few groups or more
   }
   if (G <= 1) {
     if (sizeof(ACC) == 4 && elems % 4 == 0 &&

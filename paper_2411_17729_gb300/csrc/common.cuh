@@ -155,7 +155,8 @@ struct Plan {
   std::vector<ChunkList> chunk_lists;        // [0]: every tile; [k]: tiles of stage k
   int32_t* d_chunk_data = nullptr;           // chunks [n][3] (first tile, count, system) and
                                              // per-system chunk ranges [nsys + 1] of each list
-  int max_chunks = 0;
+  int max_chunks = 0;                        // chunks of the largest stage list
+  int chunks_all = 0;                        // chunks of the list of all tiles
   void* d_red_scratch = nullptr;             // group sums of the chunk reductions
   size_t red_scratch_bytes = 0;
   const void* saved_ws = nullptr;            // workspace of the last forward that kept states

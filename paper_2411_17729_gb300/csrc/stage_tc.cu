@@ -241,6 +241,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const unsigned long long limit = args.timeout_ns;
+  // The next launch of the stream (launched as a programmatic dependent) may
+  // start its prologue on SMs this grid leaves free; it waits for this grid's
+  // completion before it touches the states.
+  ptx::griddep_launch_dependents();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -249,6 +253,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t phase = 0;
       int issued_parity[8];
       for (int s = 0; s < 8; ++s) issued_parity[s] = -1;
+      bool waited = false;
       for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
         const Item it = load_item<QMAX>(args, w);
         if (it.copy) continue;                                   // no operands
@@ -259,7 +264,43 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int src_y = args.S ? src_row % args.S : src_row;
         const int src_z = args.S ? src_row / args.S : 0;
         const int prow = (it.t.sys * args.kmax1 + args.k) * m + it.n0;
-        for (int c = 0; c < nkc; ++c) {
+        int c0 = 0;
+        if (!waited) {
+          // The powers do not depend on the previous launch: the first stages'
+          // power chunks are requested before waiting for it, the state rows after.
+          const int pre = min(S, nkc);
+          int armed = 0;
+          for (int c = 0; c < pre; ++c) {      // fresh stages: the empty waits pass at once
+            if (!ptx::mbar_wait(&empty[c], 1u, limit, abort_flag)) {
+              raise_timeout(args, abort_flag, 1, w, c);
+              break;
+            }
+            uint8_t* sb_hi = bufs + (size_t)c * stage_bytes + 2 * a_bytes;
+            ptx::mbar_arrive_expect_tx(&full[c], stage_bytes);
+            ptx::tma_load_2d(sb_hi, &tm_phi, &full[c], c * KC, prow);
+            ptx::tma_load_2d(sb_hi + b_bytes, &tm_plo, &full[c], c * KC, prow);
+            issued_parity[c] = 0;
+            ++armed;
+          }
+          ptx::griddep_wait();
+          waited = true;
+          // every armed stage gets its state rows (its barrier expects them)
+          for (int c = 0; c < armed; ++c) {
+            uint8_t* sa_hi = bufs + (size_t)c * stage_bytes;
+            if (args.S) {
+              ptx::tma_load_3d(sa_hi, &tm_vhi, &full[c], c * KC, src_y, src_z);
+              ptx::tma_load_3d(sa_hi + a_bytes, &tm_vlo, &full[c], c * KC, src_y, src_z);
+            } else {
+              ptx::tma_load_2d(sa_hi, &tm_vhi, &full[c], c * KC, src_row);
+              ptx::tma_load_2d(sa_hi + a_bytes, &tm_vlo, &full[c], c * KC, src_row);
+            }
+          }
+          if (armed < pre) break;
+          stage = pre;
+          if (stage == S) { stage = 0; phase ^= 1u; }
+          c0 = pre;
+        }
+        for (int c = c0; c < nkc; ++c) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, limit, abort_flag)) {
             raise_timeout(args, abort_flag, 1, w, stage);
             break;
@@ -282,6 +323,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
       }
+      if (!waited) ptx::griddep_wait();
       // Never leave the block with copies in flight.
       for (int s = 0; s < S; ++s)
         if (issued_parity[s] >= 0)
@@ -368,6 +410,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 6) {
     // ------------------------------------------------------------ ring manager
     if (lane == 0) {
+      ptx::griddep_wait();             // the residual rows are the previous launch's output
       int lw = blockIdx.x, lcc = 0;    // load cursor, up to RING chunks ahead of the epilogue
       uint32_t issued = 0;
       auto issue_next = [&](int slot) {
@@ -438,6 +481,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    ptx::griddep_wait();                       // before any store to the states or y
     const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
     const int r = quad * 32 + lane;            // tile row == TMEM lane
     // Two epilogue groups share the tiles: chunk g (counted over the whole
@@ -646,8 +690,21 @@ cudaError_t launch_variant(const CUtensorMap* maps, const StageArgs& a, int grid
   auto kern = stage_tc_kernel<ELEM, QMAX, G>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, NTHREADS, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
+  // programmatic dependent launch: the prologue (barriers, TMEM, the first
+  // power chunks) overlaps the previous launch's tail on the SMs it leaves free
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
   CASCADE_LAUNCHED();
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -131,6 +131,10 @@ __global__ void __launch_bounds__(NTH, 1)
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const unsigned long long limit = args.timeout_ns;
+  // launched as a programmatic dependent: the set-up above overlaps the
+  // previous launch; nothing below runs before it has completed
+  ptx::griddep_launch_dependents();
+  ptx::griddep_wait();
   const int per_chunk = args.mblocks * args.nblocks;
 
   if (warp == 0) {
@@ -409,8 +413,19 @@ cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* c
   cudaError_t e = cudaFuncSetAttribute(grad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  grad_tc_kernel<<<grid, NTH, smem, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NTH);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, grad_tc_kernel, maps[0], maps[1], maps[2], maps[3], a);
   CASCADE_LAUNCHED();
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

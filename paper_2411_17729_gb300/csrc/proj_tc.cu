@@ -147,6 +147,10 @@ __global__ void __launch_bounds__(NTH, 1)
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const unsigned long long limit = args.timeout_ns;
+  // launched as a programmatic dependent: the set-up above overlaps the
+  // previous launch; nothing below runs before it has completed
+  ptx::griddep_launch_dependents();
+  ptx::griddep_wait();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -476,8 +480,19 @@ cudaError_t launch_proj_tc(const Plan& p, const Tile* tiles, int ntiles, int N, 
   if (e != cudaSuccess) return e;
   const int nwork = ntiles * a.nblocks;
   const int grid = std::min(nwork, p.num_sms);
-  proj_tc_kernel<<<grid, NTH, smem, st>>>(maps, a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NTH);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, proj_tc_kernel, maps, a);
   CASCADE_LAUNCHED();
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

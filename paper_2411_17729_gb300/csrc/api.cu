@@ -261,6 +261,12 @@ void free_batch(Plan* p) {
   p->d_scan_rows_sys = nullptr;
   p->n_scan_rows = 0;
   p->scan_rows_cap = 0;
+  dfree(p->d_top_seqs);
+  p->d_top_seqs = nullptr;
+  p->n_top_seqs = 0;
+  p->scan_top_k0 = -1;
+  p->scan_top_K = 0;
+  p->scan_top_pos = 0;
   p->matvecs = 0;
   p->have_batch = false;
   if (p->graph) {
@@ -501,7 +507,7 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
     CK(launch_split_rows(static_cast<const float*>(u), p->rows * p->d.p, U.hi(0), U.lo(0), st),
        "input planes");
   if (timing) {
-    CK(ensure_events(p, std::max(std::max(p->maxN, 1), (int)p->scan.size())), "timing events");
+    CK(ensure_events(p, std::max(std::max(p->maxN, 1), (int)p->scan.size() + 1)), "timing events");
     p->ev_k.clear();
     p->n_ev = 0;
   }
@@ -513,7 +519,21 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
       CK(launch_proj_tc_stage0(*p, U, V, p->scan_rows_cap, 0, true, st), "first level");
     else
       CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, 0, true, st), "first level");
-    for (const Plan::ScanLevel& lv : p->scan) {
+    for (size_t li = 0; li <= p->scan.size(); ++li) {
+      if ((int)li == p->scan_top_pos && p->scan_top_k0 >= 0 && p->n_top_seqs > 0) {
+        // levels k >= k0, up and down, one block per sequence
+        if (timing) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
+        CK(launch_scan_top(*p, V.hi(0), V.lo(0), (uint64_t)p->scan_rows_cap,
+                           static_cast<const float*>(u), static_cast<float*>(y), st),
+           "scan top levels");
+        if (timing) {
+          CK(cudaEventRecord(p->ev[2 * p->n_ev + 1], st), "event");
+          p->ev_k.push_back(300 + p->scan_top_k0);
+          p->n_ev++;
+        }
+      }
+      if (li == p->scan.size()) break;
+      const Plan::ScanLevel& lv = p->scan[li];
       if (timing && lv.n > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
       CK(launch_stage_tc_strided(*p, lv.k, 2 << lv.k, lv.d_tiles, lv.n,
                                  (uint64_t)p->scan_rows_cap, V.hi(0), V.lo(0),
@@ -1279,13 +1299,55 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
       p->scan.push_back(lv);
       return CASCADE_OK;
     };
+    // Levels k >= k0 touch only rows (t+1) 2^k0 - 1 of each sequence; with at most
+    // 128 such rows per sequence they run as one launch (a block per sequence,
+    // states in TMEM) instead of one launch each.  k0: the smallest level with
+    // L_i >> k0 <= 128 for every sequence; used when it replaces 3 or more launches.
+    int64_t maxL = 0;
+    for (int i = 0; i < nseq; ++i) maxL = std::max(maxL, h_offsets[i + 1] - h_offsets[i]);
+    int k0 = 1;
+    while ((maxL >> k0) > 128) ++k0;
+    const bool top = scan_top_supported(*p) && K - k0 >= 2 &&
+                     (K - k0) + (K - 1 - k0) >= 3;
     for (int k = 1; k <= K - 1; ++k) {
+      if (top && k >= k0) {   // counted here, run by the top launch
+        for (int i = 0; i < nseq; ++i) {
+          const int64_t L = h_offsets[i + 1] - h_offsets[i];
+          p->matvecs += L / (int64_t(2) << k);
+        }
+        continue;
+      }
       const cascade_status_t r = level(k, false);
       if (r != CASCADE_OK) return r;
     }
+    p->scan_top_pos = (int)p->scan.size();
     for (int k = K - 2; k >= 0; --k) {
+      if (top && k >= k0) {
+        const int64_t S = int64_t(2) << k, d = int64_t(1) << k;
+        for (int i = 0; i < nseq; ++i) {
+          const int64_t L = h_offsets[i + 1] - h_offsets[i];
+          p->matvecs += L > d ? (L - d) / S : 0;
+        }
+        continue;
+      }
       const cascade_status_t r = level(k, true);
       if (r != CASCADE_OK) return r;
+    }
+    if (top) {
+      std::vector<Seq> ts;
+      for (int i = 0; i < nseq; ++i) {
+        const int64_t L = h_offsets[i + 1] - h_offsets[i];
+        if ((L >> k0) >= 2)
+          ts.push_back(Seq{h_offsets[i], (int32_t)L, p->sys_of_seq[i], p->seq_N[i], 0});
+      }
+      p->scan_top_k0 = k0;
+      p->scan_top_K = K;
+      p->n_top_seqs = (int)ts.size();
+      if (!ts.empty()) {
+        CK(cudaMalloc(&p->d_top_seqs, ts.size() * sizeof(Seq)), "alloc top schedule");
+        CK(cudaMemcpy(p->d_top_seqs, ts.data(), ts.size() * sizeof(Seq), cudaMemcpyHostToDevice),
+           "upload top schedule");
+      }
     }
     if (p->fuse_output) {
       // rows l = 2^t - 1 are never written by the down-sweep: their y is formed

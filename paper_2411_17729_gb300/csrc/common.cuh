@@ -182,6 +182,12 @@ struct Plan {
   int32_t* d_scan_rows_sys = nullptr;  // down-sweep) and their systems: their y when the
   int n_scan_rows = 0;                 // levels form y themselves
   int64_t matvecs = 0;           // products by powers in one forward of the batch
+  // levels k >= scan_top_k0 (up and down) run in one launch, a block per sequence with
+  // its compact rows in TMEM (-1: every level is its own launch); scan_top_pos: index in
+  // `scan` of the first down-sweep level below k0 (the top launch runs before it)
+  int scan_top_k0 = -1, scan_top_K = 0, scan_top_pos = 0;
+  Seq* d_top_seqs = nullptr;
+  int n_top_seqs = 0;
   // stage-output checkpoints (CASCADE_FLAG_RECOMPUTE): v^(j) is kept for
   // j = 1, 1 + ck_seg, 1 + 2 ck_seg, ... <= maxN; the backward recomputes the
   // others one segment at a time
@@ -275,6 +281,9 @@ cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chu
                             cudaStream_t st);
 // Narrow projections as register-tiled GEMMs (proj.cu; tensor-core formats).
 bool proj_supported(const Plan& p);
+bool scan_top_supported(const Plan& p);
+cudaError_t launch_scan_top(const Plan& p, void* v_hi, void* v_lo, uint64_t rows_cap,
+                            const float* u, float* y, cudaStream_t st);
 // Tensor-core projections (proj_tc.cu): BF16 split with p and q multiples of 16.
 // The B operands are the PC_* matrices, split at set_system time.
 enum { PC_B = 0, PC_AB, PC_C, PC_D, PC_CT, PC_BT, PC_ABT, PC_DT, PC_COUNT };

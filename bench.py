@@ -296,7 +296,7 @@ def main():
     def step():
         c.forward(u, y)
 
-    shape = c.autotune(u, y, reps=2) if not f64 else (0, 0, 0)   # kernel shape (untimed)
+    shape = c.autotune(u, y, reps=3) if not f64 else (0, 0, 0)   # kernel shape (untimed)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -429,7 +429,7 @@ def main():
         # whole schedule (captured once per buffer set), without per-level events
         cg = cascade.from_workload(w, precision=precision,
                                    flags=CASCADE_FLAG_SCAN | CASCADE_FLAG_GRAPH, device=dev)
-        cg.autotune(u, y, reps=2)
+        scan_shape = cg.autotune(u, y, reps=6)
         for _ in range(max(args.warmup, 3)):
             cg.forward(u, y)
         sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -449,7 +449,7 @@ def main():
         torch.cuda.empty_cache()
         # per-level durations: the same schedule launched directly, with events
         cs = cascade.from_workload(w, precision=precision, flags=CASCADE_FLAG_SCAN, device=dev)
-        cs.autotune(u, y, reps=2)
+        cs.set_kernel_shape(*scan_shape)      # the shape the timed steps ran
         for _ in range(max(args.warmup, 3)):
             cs.forward(u, y)
         cs.enable_stage_timing(True)
@@ -487,7 +487,9 @@ def main():
                 "schedule": "up-sweep k=1..K-1, down-sweep k=K-2..0 (first level fused "
                             "with Bbar u), in place",
                 "timing": "CUDA graph replay of the level launches; per-level durations "
-                          "from separate direct launches with events"}
+                          "from separate direct launches with events",
+                "kernel_shape": {"stages": scan_shape[0], "ring": scan_shape[1],
+                                 "chunks_per_step": scan_shape[2]}}
         cs.close()
         torch.cuda.empty_cache()
         torch.cuda.nvtx.range_pop()

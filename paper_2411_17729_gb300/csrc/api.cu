@@ -611,9 +611,9 @@ cudaError_t gemm_t(const float* A, const float* B, float* C, int M, int N, int K
                    int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC, int batch, double alpha,
                    double beta, bool tA, bool tB, cudaStream_t st, void* scratch = nullptr,
                    size_t scratch_bytes = 0) {
-  // square-ish products, or long ones with scratch for a split K: the
+  // square-ish products, or any product with scratch for a split K: the
   // register-tiled kernel (128 x 128 tiles, or 64 x 64 with K slices)
-  if ((M >= 128 && N >= 128) || (scratch && (int64_t)M * N * K >= (int64_t(1) << 20)))
+  if ((M >= 128 && N >= 128) || scratch)
     return launch_sgemm2(A, B, tA, tB, nullptr, nullptr, false, false, C, M, N, K, lda, ldb, ldc,
                          sA, sB, sC, batch, (float)alpha, (float)beta, st,
                          static_cast<float*>(scratch), scratch_bytes / sizeof(float));

@@ -469,15 +469,18 @@ Layout layout(const Plan& p) {
                            expm_scratch_doubles((int)n2, (int)ns) + ns) + 8);
     }
   }
-  if (proj_tc_supported(p)) {
-    L.u_plane = align256((size_t)p.rows * p.d.p * 2);
+  // (hi, lo) BF16 planes of u and G for the tensor-core projections and, in the
+  // backward, the tensor-core time reductions (rows of pad8(p) and pad8(q) entries)
+  const bool ptc = proj_tc_supported(p), thin = save && ptc && thin_tc_supported(p);
+  if (ptc || thin) {
+    L.u_plane = align256((size_t)p.rows * pad8(p.d.p) * 2);
     L.off_U = off;
     off += 2 * L.u_plane;
-    if (save) {
-      L.g_plane = align256((size_t)p.rows * p.d.q * 2);
-      L.off_G = off;
-      off += 2 * L.g_plane;
-    }
+  }
+  if (save && (ptc || thin)) {
+    L.g_plane = align256((size_t)p.rows * pad8(p.d.q) * 2);
+    L.off_G = off;
+    off += 2 * L.g_plane;
   }
   L.total = off + 256;
   return L;
@@ -504,7 +507,8 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
   const bool ptc = proj_tc_supported(*p);
   const Bufs U{static_cast<uint8_t*>(ws) + L.off_U, 0, L.u_plane};
   if (ptc)
-    CK(launch_split_rows(static_cast<const float*>(u), p->rows * p->d.p, U.hi(0), U.lo(0), st),
+    CK(launch_split_rows(static_cast<const float*>(u), p->rows, p->d.p, p->d.p, U.hi(0), U.lo(0),
+                         st),
        "input planes");
   if (timing) {
     CK(ensure_events(p, std::max(std::max(p->maxN, 1), (int)p->scan.size() + 1)), "timing events");
@@ -686,14 +690,17 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   const bool ptc = proj_tc_supported(*p);
   const Bufs Gp{base + L.off_G, 0, L.g_plane};
   const Bufs Up{base + L.off_U, 0, L.u_plane};
-  // p and q multiples of 16 with m of 128: the time reductions of dC, dD, R1 and
-  // R2 run on the tensor cores like the power gradients
-  const bool thin_tc = ptc && grad_tc_supported(*p);
-  if (ptc)
-    CK(launch_split_rows(static_cast<const float*>(dy), p->rows * q, Gp.hi(0), Gp.lo(0), st),
+  // p and q multiples of 16 with m of 128: the time reductions of dC, dD, R1 and R2
+  // run on the tensor cores like the power gradients.  (Narrower p and q were
+  // measured on the same kernel with zero-padded planes: no faster than the
+  // wide-by-thin CUDA-core kernels, whose one pass forms R1 and R2 together.)
+  const bool thin_tc = ptc && thin_tc_supported(*p);
+  const int ppad = pad8(pp), qpad = pad8(q);
+  if (ptc || thin_tc)
+    CK(launch_split_rows(static_cast<const float*>(dy), p->rows, q, qpad, Gp.hi(0), Gp.lo(0), st),
        "adjoint planes");
   if (thin_tc)
-    CK(launch_split_rows(static_cast<const float*>(u), p->rows * pp, Up.hi(0), Up.lo(0), st),
+    CK(launch_split_rows(static_cast<const float*>(u), p->rows, pp, ppad, Up.hi(0), Up.lo(0), st),
        "input planes");
 
   // dC = sum G v^(N+1)^T: v^(N_i+1) sits in state buffer tile.fbuf.  This runs
@@ -702,7 +709,7 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
     const TSrc VF{0, V, 1, 0, nullptr, 0};
     if (thin_tc && p->all_fbuf >= 0) {   // dC^T = sum v^(N+1)_l G_l^T, stored transposed
       CK(launch_grad_tc_xy(*p, p->d_all_tiles, chunks(0), nall, V.hi(p->all_fbuf),
-                           V.lo(p->all_fbuf), m, Gp.hi(0), Gp.lo(0), q, 0, true,
+                           V.lo(p->all_fbuf), m, m, Gp.hi(0), Gp.lo(0), q, qpad, 0, true,
                            static_cast<float*>(part), st),
          "dC (tensor core)");
       CK(launch_reduce_partials(*p, static_cast<const float*>(part), sysbeg(0), (int64_t)q * m,
@@ -719,8 +726,8 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   }
   if (dD) {   // dD = sum G u^T
     if (thin_tc) {
-      CK(launch_grad_tc_xy(*p, p->d_all_tiles, chunks(0), nall, Gp.hi(0), Gp.lo(0), q, Up.hi(0),
-                           Up.lo(0), pp, 0, false, static_cast<float*>(part), st),
+      CK(launch_grad_tc_xy(*p, p->d_all_tiles, chunks(0), nall, Gp.hi(0), Gp.lo(0), q, qpad,
+                           Up.hi(0), Up.lo(0), pp, ppad, 0, false, static_cast<float*>(part), st),
          "dD (tensor core)");
       CK(launch_reduce_partials(*p, static_cast<const float*>(part), sysbeg(0), (int64_t)q * pp,
                                 dD, true, (int64_t)q * pp, st),
@@ -825,8 +832,8 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   const TSrc W1{0, W, 0, 1, nullptr, 0};
   if (thin_tc) {
     for (int sh = 0; sh < 2; ++sh) {
-      CK(launch_grad_tc_xy(*p, p->d_all_tiles, chunks(0), nall, W.hi(1), W.lo(1), m, Up.hi(0),
-                           Up.lo(0), pp, sh, false, static_cast<float*>(part), st),
+      CK(launch_grad_tc_xy(*p, p->d_all_tiles, chunks(0), nall, W.hi(1), W.lo(1), m, m, Up.hi(0),
+                           Up.lo(0), pp, ppad, sh, false, static_cast<float*>(part), st),
          sh ? "R2 (tensor core)" : "R1 (tensor core)");
       CK(launch_reduce_partials(*p, static_cast<const float*>(part), sysbeg(0), mp,
                                 sh ? R2 : R1, tf64, mp, st),
@@ -1466,7 +1473,7 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     // chunk) unless they run on the tensor cores: then runs shrink to 4 tiles
     // while there are fewer than 8 blocks per SM
     int CH0 = CH;
-    if (!(proj_tc_supported(*p) && grad_tc_supported(*p)))
+    if (!(proj_tc_supported(*p) && thin_tc_supported(*p)))
       while (CH0 > 4 && (int64_t)all.size() < (int64_t)CH0 * 8 * p->num_sms) CH0 >>= 1;
     const int64_t grad_blocks =
         grad_tc_supported(*p) ? (int64_t)(p->d.m / 128) * (p->d.m / grad_tc_block_n(p->d.m)) : 0;

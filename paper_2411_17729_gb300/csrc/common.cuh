@@ -290,7 +290,9 @@ enum { PC_B = 0, PC_AB, PC_C, PC_D, PC_CT, PC_BT, PC_ABT, PC_DT, PC_COUNT };
 bool proj_tc_supported(const Plan& p);
 size_t proj_coef_elems(const Plan& p, int64_t off[PC_COUNT]);
 cudaError_t launch_proj_coef(const Plan& p, cudaStream_t st);
-cudaError_t launch_split_rows(const float* x, int64_t n, void* hi, void* lo, cudaStream_t st);
+// FP32 rows of w entries -> (hi, lo) BF16 planes of rows of wp >= w entries (zero past w)
+cudaError_t launch_split_rows(const float* x, int64_t rows, int w, int wp, void* hi, void* lo,
+                              cudaStream_t st);
 // U, G: (hi, lo) BF16 planes of u [rows, p] and G [rows, q] (buffer 0 of the Bufs)
 cudaError_t launch_proj_tc_stage0(const Plan& p, const Bufs& U, const Bufs& V, int64_t v_rows,
                                   int buf, bool odd_only, cudaStream_t st);
@@ -315,10 +317,14 @@ cudaError_t launch_reduce_partials(const Plan& p, const float* partial, const in
                                    cudaStream_t st);
 bool grad_tc_supported(const Plan& p);
 int grad_tc_block_n(int m);
+// The time reductions can run on the power-gradient kernel: BF16-split plans with m a
+// multiple of 128 (u and G as planes of rows padded to multiples of 8 entries).
+bool thin_tc_supported(const Plan& p);
 cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* chunks,
-                              int nchunks, const void* x_hi, const void* x_lo, int ma,
-                              const void* y_hi, const void* y_lo, int nb, int shift, bool trans,
-                              float* partial, cudaStream_t st);
+                              int nchunks, const void* x_hi, const void* x_lo, int ma, int ldx,
+                              const void* y_hi, const void* y_lo, int nb, int ldy, int shift,
+                              bool trans, float* partial, cudaStream_t st);
+inline int pad8(int w) { return (w + 7) & ~7; }
 cudaError_t launch_grad_tc(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
                            const void* w_hi, const void* w_lo, const void* v_hi, const void* v_lo,
                            int shift, float* partial, cudaStream_t st);

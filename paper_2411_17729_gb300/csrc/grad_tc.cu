@@ -11,8 +11,8 @@
 // Products: Whi Vhi + Whi Vlo + Wlo Vhi with FP32 accumulation in TMEM.
 // Rows past the sequence end (W side) and sources before its start (V side)
 // are zeroed in shared memory.  Partials [chunk][i][j] are summed per system
-// by the ordered reduction of backward.cu.  With p and q multiples of 16 the
-// same kernel forms the first-stage and output reductions over time,
+// by the ordered reduction of backward.cu.  The same kernel forms the first-stage
+// and output reductions over time (u and G padded to planes of 8-entry rows),
 // R1 = sum W^(1)_l u_l^T, R2 = sum W^(1)_l u_(l-1)^T (m x p) and
 // dC^T = sum v_l G_l^T (m x q, stored transposed as dC).
 //
@@ -322,12 +322,17 @@ __global__ void __launch_bounds__(NTH, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j)
               if (j < jn) o[(int64_t)j * args.ma] = v[j];
-          } else {
+          } else if (args.nb % 4 == 0) {   // rows of whole 16-byte groups
             float4* o4 = reinterpret_cast<float4*>(pc + (int64_t)(i0 + r) * args.nb + j0 + cc * 32);
 #pragma unroll
             for (int j = 0; j < 8; ++j)
               if (4 * j < jn)
                 o4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          } else {
+            float* o = pc + (int64_t)(i0 + r) * args.nb + j0 + cc * 32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < jn) o[j] = v[j];
           }
         }
         __syncwarp();   // converged for the next tcgen05.ld
@@ -353,17 +358,20 @@ bool grad_tc_supported(const Plan& p) {
   return p.d.precision == CASCADE_BF16_SPLIT && p.d.m % TM == 0;
 }
 
+bool thin_tc_supported(const Plan& p) { return grad_tc_supported(p) && tile_rows(p) == 128; }
+
 // partial[c] = sum over the rows of chunk c of X[l] Y[l - shift]^T (ma x nb, FP32,
-// or its transpose with trans), X and Y (hi, lo) BF16 planes of [rows, ma] and
-// [rows, nb], ma and nb multiples of 8.  The blocks cover ma rounded up to 128
-// and nb rounded up to 32: TMA fills the columns past each matrix with zeros.
+// or its transpose with trans), X and Y (hi, lo) BF16 planes of [rows, ldx] and
+// [rows, ldy] whose first ma and nb entries are used (ldx, ldy multiples of 8, any
+// entries past ma and nb zero).  The blocks cover ma rounded up to 128 and nb
+// rounded up to 32: TMA fills the columns past each plane with zeros.
 cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* chunks,
-                              int nchunks, const void* x_hi, const void* x_lo, int ma,
-                              const void* y_hi, const void* y_lo, int nb, int shift, bool trans,
-                              float* partial, cudaStream_t st) {
+                              int nchunks, const void* x_hi, const void* x_lo, int ma, int ldx,
+                              const void* y_hi, const void* y_lo, int nb, int ldy, int shift,
+                              bool trans, float* partial, cudaStream_t st) {
   if (nchunks == 0) return cudaSuccess;
-  if (ma <= 0 || nb <= 0 || ma % 8 != 0 || nb % 8 != 0) {
-    set_global_error("power-gradient shapes: ma and nb must be multiples of 8");
+  if (ma <= 0 || nb <= 0 || ldx < ma || ldy < nb || ldx % 8 != 0 || ldy % 8 != 0) {
+    set_global_error("power-gradient shapes: row strides must be multiples of 8 entries");
     return cudaErrorInvalidValue;
   }
   const int mpad = (ma + TM - 1) / TM * TM, npad = (nb + 31) / 32 * 32;
@@ -376,14 +384,14 @@ cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* c
   // Operands whose width is a multiple of 32 are read through column-block maps
   // (one copy per plane and stage); the others (and any map the driver
   // declines) through one 2-D box per 32-column block.
-  auto encode = [&](CUtensorMap* m2, const void* base, int cols, int blocks) -> int {
+  auto encode = [&](CUtensorMap* m2, const void* base, int ld, int blocks) -> int {
     std::string e3;
-    if (cols % 32 == 0 && encode_tmap_colblocks(m2, base, 2, cols, rows, BMK, blocks, &e3, 64))
+    if (ld % 32 == 0 && encode_tmap_colblocks(m2, base, 2, ld, rows, BMK, blocks, &e3, 64))
       return 1;
-    return encode_tmap_2d(m2, base, 2, cols, rows, 32, BMK, &err, 64) ? 0 : -1;
+    return encode_tmap_2d(m2, base, 2, ld, rows, 32, BMK, &err, 64) ? 0 : -1;
   };
-  const int ax = encode(&maps[0], x_hi, ma, TM / 32), al = encode(&maps[1], x_lo, ma, TM / 32);
-  const int bx = encode(&maps[2], y_hi, nb, BN / 32), bl = encode(&maps[3], y_lo, nb, BN / 32);
+  const int ax = encode(&maps[0], x_hi, ldx, TM / 32), al = encode(&maps[1], x_lo, ldx, TM / 32);
+  const int bx = encode(&maps[2], y_hi, ldy, BN / 32), bl = encode(&maps[3], y_lo, ldy, BN / 32);
   if (ax < 0 || al < 0 || bx < 0 || bl < 0 || ax != al || bx != bl) {
     set_global_error("tensor map encode failed: " + err);
     return cudaErrorInvalidValue;
@@ -433,8 +441,8 @@ cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* c
 cudaError_t launch_grad_tc(const Plan& p, const Tile* tiles, const int32_t* chunks, int nchunks,
                            const void* w_hi, const void* w_lo, const void* v_hi, const void* v_lo,
                            int shift, float* partial, cudaStream_t st) {
-  return launch_grad_tc_xy(p, tiles, chunks, nchunks, w_hi, w_lo, p.d.m, v_hi, v_lo, p.d.m, shift,
-                           false, partial, st);
+  return launch_grad_tc_xy(p, tiles, chunks, nchunks, w_hi, w_lo, p.d.m, p.d.m, v_hi, v_lo, p.d.m,
+                           p.d.m, shift, false, partial, st);
 }
 
 }  // namespace cascade

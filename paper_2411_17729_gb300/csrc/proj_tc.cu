@@ -381,6 +381,22 @@ __global__ void split_rows_kernel(const float4* __restrict__ x, int64_t n4,
   }
 }
 
+// Rows of w FP32 values -> rows of wp >= w BF16 (hi, lo) entries, zero past w.
+__global__ void split_rows_pad_kernel(const float* __restrict__ x, int64_t rows, int w, int wp,
+                                      __nv_bfloat16* __restrict__ hi,
+                                      __nv_bfloat16* __restrict__ lo) {
+  const int64_t n = rows * wp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / wp;
+    const int j = (int)(e - r * wp);
+    const float v = j < w ? x[r * w + j] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
 // out[s][i][j] = split(M[s * ss + i * si + j * sj]), i < R, j < C.
 __global__ void split_coef_kernel(const float* __restrict__ M, int64_t ss, int64_t si, int64_t sj,
                                   int R, int C, int ns, __nv_bfloat16* __restrict__ hi,
@@ -544,12 +560,21 @@ cudaError_t launch_proj_coef(const Plan& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_rows(const float* x, int64_t n, void* hi, void* lo, cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
-  const int64_t n4 = n / 4;
-  const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, 8192);
-  split_rows_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(x), n4,
-                                            static_cast<uint2*>(hi), static_cast<uint2*>(lo));
+cudaError_t launch_split_rows(const float* x, int64_t rows, int w, int wp, void* hi, void* lo,
+                              cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  if (w == wp && w % 4 == 0) {
+    const int64_t n4 = rows * w / 4;
+    const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, 8192);
+    split_rows_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(x), n4,
+                                              static_cast<uint2*>(hi), static_cast<uint2*>(lo));
+  } else {
+    const int64_t n = rows * wp;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8192);
+    split_rows_pad_kernel<<<blocks, 256, 0, st>>>(x, rows, w, wp,
+                                                  static_cast<__nv_bfloat16*>(hi),
+                                                  static_cast<__nv_bfloat16*>(lo));
+  }
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }

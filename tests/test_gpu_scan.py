@@ -145,3 +145,21 @@ def test_scan_refuses_truncation_and_backward(lib):
     with pytest.raises(CascadeError):
         lib.from_workload(w2, precision="bf16_split",
                           flags=CASCADE_FLAG_SCAN | CASCADE_FLAG_SAVE_STATES)
+
+
+def test_scan_graph_replay_bitwise(lib):
+    """The work-efficient schedule replayed as a CUDA graph (the timed path of the
+    benchmark) gives the direct launches' output bit for bit, over three replays."""
+    import torch
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_GRAPH, CASCADE_FLAG_SCAN
+    w = cast_inputs(wl.precision_form(m=256, L=4096, batch=5, N=11), "bf16_split")
+    _, y1 = run(lib, w, "bf16_split", CASCADE_FLAG_SCAN)
+    c = lib.from_workload(w, precision="bf16_split", flags=CASCADE_FLAG_SCAN | CASCADE_FLAG_GRAPH)
+    u = torch.as_tensor(w.u, dtype=torch.float32).cuda()
+    y = torch.empty((w.rows, w.q), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        y.zero_()
+        c.forward(u, y)
+        torch.cuda.synchronize()
+        assert c.device_error() == 0
+        assert np.array_equal(y.double().cpu().numpy(), y1)

@@ -134,8 +134,16 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             cmd = ["nvidia-smi", f"--query-gpu=uuid,{self.FIELDS}", "--format=csv,noheader,nounits",
-                   "-lms", "200"]
+                   "-lms", "50"]
             self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # sampling has begun once the first line is out (at most 3 s): the timed
+            # region then starts with the sampler running
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.01)
+            self.n_before = sum(1 for _ in open(self.path))
         except Exception:
             self.proc = None
 
@@ -147,14 +155,18 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
+        rows, before = [], []
+        for i, line in enumerate(open(self.path)):
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
             if self.uuid and parts[0] != self.uuid:
                 continue
-            rows.append(parts)
+            # samples taken before the timed region are kept aside: a region shorter
+            # than the sampling period falls back to the one just before it
+            (before if i < getattr(self, "n_before", 0) else rows).append(parts)
+        if not rows:
+            rows = before[-1:]
         os.unlink(self.path)
         if not rows:
             return None

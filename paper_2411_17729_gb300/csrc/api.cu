@@ -818,8 +818,16 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
       }
     }
   }
-  // first stage (fused with Bbar u): W^(1) is adjoint buffer 1
-  if (du) {
+  // first stage (fused with Bbar u): W^(1) is adjoint buffer 1.  Narrow p and q: du,
+  // R1 and R2 in one pass over W^(1)
+  const bool fused_first = !f64 && !thin_tc && du && first_adj_thin_supported(*p);
+  if (fused_first) {
+    CK(launch_first_adj_thin(*p, p->d_all_tiles, chunks(0), nall, sysbeg(0), W, 1,
+                             static_cast<const float*>(u), static_cast<const float*>(dy),
+                             static_cast<float*>(du), static_cast<float*>(part), R1, tf64, mp,
+                             (int64_t)ns * mp, st),
+       "du, R1, R2");
+  } else if (du) {
     if (ptc)
       CK(launch_proj_tc_du(*p, Gp, W, 1, static_cast<float*>(du), st), "du");
     else if (proj)
@@ -830,7 +838,9 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
   }
   // R1 = sum W^(1)_l u_l^T,  R2 = sum W^(1)_l u_(l-1)^T
   const TSrc W1{0, W, 0, 1, nullptr, 0};
-  if (thin_tc) {
+  if (fused_first) {
+    // formed above
+  } else if (thin_tc) {
     for (int sh = 0; sh < 2; ++sh) {
       CK(launch_grad_tc_xy(*p, p->d_all_tiles, chunks(0), nall, W.hi(1), W.lo(1), m, m, Up.hi(0),
                            Up.lo(0), pp, ppad, sh, false, static_cast<float*>(part), st),

@@ -531,6 +531,181 @@ __global__ void convert_sys_kernel(const TI* __restrict__ in, int64_t in_stride,
 
 }  // namespace
 
+// First-stage adjoint for narrow p and q, one pass over W = W^(1):
+//   du_l = Bbar^T W_l + (Abar Bbar)^T W_(l+1) + D^T G_l        (W past the sequence end is 0)
+//   R1  += W_l u_l^T,   R2 += W_l u_(l-1)^T                     (u before the start is 0)
+// One block per chunk of tiles (one system), eight warps.  A warp walks 16 rows of
+// each tile plus the next row (whose (Abar Bbar)^T W completes the warp's last du);
+// lane l owns the 8-column groups 8 (l + 32 g), g < NG, of every row, so a row is one
+// coalesced read and the two p-wide dot products of du are warp reductions.  The
+// warps' R1, R2 partials are added in a fixed order into partial[chunk][h][i][j]
+// (h = 0: R1, 1: R2), summed per system afterwards.
+constexpr int FA_PMAX = 4;   // p, q <= 4
+constexpr int FA_CMAX = 2;   // NG * p <= 2 (accumulators per lane: 2 x 8 x NG x p)
+// CM >= NG * p: accumulator groups per lane; PM >= p, q
+template <int FMT, int CM, int PM>
+__global__ void __launch_bounds__(256, 2) first_adj_thin_kernel(
+    const Tile* __restrict__ tiles, const int32_t* __restrict__ chunks, int m, int p, int q,
+    Bufs W, int wbuf, const float* __restrict__ u, const float* __restrict__ G,
+    const float* __restrict__ Bbar, const float* __restrict__ ABbar,
+    const float* __restrict__ D, float* __restrict__ du, float* __restrict__ partial) {
+  extern __shared__ __align__(16) float fa_red[];   // [8 warps][2][m][p]
+  const int c = blockIdx.x;
+  const int first = chunks[3 * c], count = chunks[3 * c + 1], sys = chunks[3 * c + 2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NG = (m + 255) / 256;
+  const void* wh = W.hi(wbuf);
+  const void* wl = W.lo(wbuf);
+  // this lane's coefficients: Bbar[col][j], ABbar[col][j]
+  float cb[CM][8], cab[CM][8];
+  float acc1[CM][8], acc2[CM][8];
+#pragma unroll
+  for (int gj = 0; gj < CM; ++gj) {
+    const int g = gj / p, j = gj - g * p;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int col = 8 * (lane + 32 * g) + e;
+      const bool ok = gj < NG * p && col < m;
+      cb[gj][e] = ok ? Bbar[((int64_t)sys * m + col) * p + j] : 0.f;
+      cab[gj][e] = ok ? ABbar[((int64_t)sys * m + col) * p + j] : 0.f;
+      acc1[gj][e] = 0.f;
+      acc2[gj][e] = 0.f;
+    }
+  }
+  float Ds[PM][PM];
+#pragma unroll
+  for (int i = 0; i < PM; ++i)
+#pragma unroll
+    for (int j = 0; j < PM; ++j)
+      Ds[i][j] = (i < q && j < p) ? D[((int64_t)sys * q + i) * p + j] : 0.f;
+
+  constexpr int RB = CM == 1 ? 4 : 2;   // rows loaded ahead of their arithmetic
+  for (int ti = first; ti < first + count; ++ti) {
+    const Tile t = tiles[ti];
+    const int r0 = 16 * warp;
+    float aprev[PM];
+#pragma unroll
+    for (int j = 0; j < PM; ++j) aprev[j] = 0.f;
+    for (int rb = r0; rb <= r0 + 16; rb += RB) {
+      float xs[RB][CM][8];
+      float ul[RB][PM], um[RB][PM], gp[RB][PM];   // u_l, u_(l-1), G_(l-1)
+#pragma unroll
+      for (int v = 0; v < RB; ++v) {
+        const int l = t.t0 + rb + v;
+        const bool live = rb + v <= r0 + 16 && l < t.len;
+        const int64_t row = t.seq_row0 + l;
+#pragma unroll
+        for (int j = 0; j < PM; ++j) {
+          ul[v][j] = (live && j < p) ? __ldg(u + row * p + j) : 0.f;
+          um[v][j] = (live && j < p && l >= 1) ? __ldg(u + (row - 1) * p + j) : 0.f;
+          gp[v][j] = (rb + v <= r0 + 16 && l >= 1 && l - 1 < t.len && j < q)
+                         ? __ldg(G + (row - 1) * q + j) : 0.f;
+        }
+#pragma unroll
+        for (int g = 0; g < CM; ++g) {
+          const int col0 = 8 * (lane + 32 * g);
+          if (g < NG && live && col0 < m) {
+            load_row_vec<FMT, 8>(wh, wl, row * m + col0, xs[v][g]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) xs[v][g][e] = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < RB; ++v) {
+        const int r = rb + v;
+        if (r > r0 + 16) break;
+        const int l = t.t0 + r;                 // time step in the sequence
+        const bool live = l < t.len;
+        const int64_t row = t.seq_row0 + l;
+        // lane partials of Bbar^T W_l and (Abar Bbar)^T W_l, then warp sums
+        float a[PM], b[PM];
+#pragma unroll
+        for (int j = 0; j < PM; ++j) { a[j] = 0.f; b[j] = 0.f; }
+#pragma unroll
+        for (int gj = 0; gj < CM; ++gj) {
+          if (gj >= NG * p) break;
+          const int g = gj / p, j = gj - g * p;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            a[j] = fmaf(cb[gj][e], xs[v][g][e], a[j]);
+            b[j] = fmaf(cab[gj][e], xs[v][g][e], b[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < PM; ++j) {
+          if (j >= p) break;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            a[j] += __shfl_xor_sync(0xffffffffu, a[j], o);
+            b[j] += __shfl_xor_sync(0xffffffffu, b[j], o);
+          }
+        }
+        // du of the previous row: Bbar^T W_(l-1) + (Abar Bbar)^T W_l + D^T G_(l-1)
+        if (r > r0 && lane == 0 && l - 1 < t.len) {
+          const int64_t prow = row - 1;
+#pragma unroll
+          for (int j = 0; j < PM; ++j) {
+            if (j >= p) break;
+            float val = aprev[j] + b[j];
+#pragma unroll
+            for (int i = 0; i < PM; ++i) val = fmaf(Ds[i][j], gp[v][i], val);
+            du[prow * p + j] = val;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < PM; ++j) aprev[j] = a[j];
+        // R1 += W_l u_l^T, R2 += W_l u_(l-1)^T over the warp's own rows
+        if (r < r0 + 16 && live) {
+#pragma unroll
+          for (int gj = 0; gj < CM; ++gj) {
+            if (gj >= NG * p) break;
+            const int g = gj / p, j = gj - g * p;
+            float u1 = 0.f, u0 = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < PM; ++jj)
+              if (jj == j) { u1 = ul[v][jj]; u0 = um[v][jj]; }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              acc1[gj][e] = fmaf(xs[v][g][e], u1, acc1[gj][e]);
+              acc2[gj][e] = fmaf(xs[v][g][e], u0, acc2[gj][e]);
+            }
+          }
+        }
+      }
+    }
+  }
+  // the warps' partials, added in warp order
+  const int mp = m * p;
+#pragma unroll
+  for (int gj = 0; gj < CM; ++gj) {
+    if (gj >= NG * p) break;
+    const int g = gj / p, j = gj - g * p;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int col = 8 * (lane + 32 * g) + e;
+      if (col < m) {
+        fa_red[(warp * 2 + 0) * mp + col * p + j] = acc1[gj][e];
+        fa_red[(warp * 2 + 1) * mp + col * p + j] = acc2[gj][e];
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * mp; e += blockDim.x) {
+    const int h = e / mp, idx = e - h * mp;
+    float v = 0.f;
+    for (int w8 = 0; w8 < 8; ++w8) v += fa_red[(w8 * 2 + h) * mp + idx];
+    partial[(int64_t)c * 2 * mp + e] = v;
+  }
+}
+
+bool first_adj_thin_supported(const Plan& p) {
+  const int NG = (p.d.m + 255) / 256;
+  return p.d.precision != CASCADE_FP64 && tile_rows(p) == 128 && p.d.m % 8 == 0 &&
+         p.d.p <= FA_PMAX && p.d.q <= FA_PMAX && NG * p.d.p <= FA_CMAX;
+}
+
 // ------------------------------------------------------------------ launchers
 // Sum the chunk partials of every system into out (see reduce_partials_kernel),
 // in two grouped passes when systems x elements alone cannot fill the GPU.
@@ -719,6 +894,41 @@ cudaError_t launch_reduce_partials(const Plan& p, const float* partial, const in
   else
     sum_chunks<float, float>(p, partial, sys_begin, elems, (float*)out, out_sys_stride, elems, 0,
                              0, st);
+  return cudaGetLastError();
+}
+
+// du (FP32 [rows, p]) and R1, R2 (out, out + seg_stride; [nsys, m, p] each) from W^(1)
+// (buffer wbuf of W) in one pass; see first_adj_thin_kernel.
+cudaError_t launch_first_adj_thin(const Plan& p, const Tile* tiles, const int32_t* chunks,
+                                  int nchunks, const int32_t* sys_begin, const Bufs& W, int wbuf,
+                                  const float* u, const float* G, float* du, float* partial,
+                                  void* out, bool out_f64, int64_t out_sys_stride,
+                                  int64_t seg_stride, cudaStream_t st) {
+  if (nchunks == 0) return cudaSuccess;
+  if (!first_adj_thin_supported(p)) return cudaErrorInvalidValue;
+  const int m = p.d.m, pp = p.d.p, q = p.d.q;
+  const size_t smem = (size_t)8 * 2 * m * pp * sizeof(float);
+  const int cm = ((m + 255) / 256) * pp;
+  const bool bf = p.d.precision == CASCADE_BF16_SPLIT;
+  const bool one = pp == 1 && q == 1;
+  auto kern = cm <= 1 ? (one ? (bf ? first_adj_thin_kernel<FMT_BF16, 1, 1>
+                                   : first_adj_thin_kernel<FMT_F32, 1, 1>)
+                             : (bf ? first_adj_thin_kernel<FMT_BF16, 1, FA_PMAX>
+                                   : first_adj_thin_kernel<FMT_F32, 1, FA_PMAX>))
+                      : (bf ? first_adj_thin_kernel<FMT_BF16, 2, FA_PMAX>
+                            : first_adj_thin_kernel<FMT_F32, 2, FA_PMAX>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<nchunks, 256, smem, st>>>(tiles, chunks, m, pp, q, W, wbuf, u, G, p.Bbar32, p.ABbar32,
+                                   p.D32, du, partial);
+  CASCADE_LAUNCHED();
+  const int64_t elems = (int64_t)2 * m * pp, seg = (int64_t)m * pp;
+  if (out_f64)
+    sum_chunks<float, double>(p, partial, sys_begin, elems, (double*)out, out_sys_stride, seg,
+                              seg_stride, 0, st);
+  else
+    sum_chunks<float, float>(p, partial, sys_begin, elems, (float*)out, out_sys_stride, seg,
+                             seg_stride, 0, st);
   return cudaGetLastError();
 }
 

@@ -271,6 +271,13 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
                            int shift, void* partial, void* out, bool out_f64,
                            int64_t out_sys_stride, int accumulate, cudaStream_t st);
 cudaError_t launch_adj_init(const Plan& p, const void* G, const Bufs& W, cudaStream_t st);
+// du and R1, R2 in one pass over W^(1) (p, q <= 4, ceil(m / 256) p <= 2)
+bool first_adj_thin_supported(const Plan& p);
+cudaError_t launch_first_adj_thin(const Plan& p, const Tile* tiles, const int32_t* chunks,
+                                  int nchunks, const int32_t* sys_begin, const Bufs& W, int wbuf,
+                                  const float* u, const float* G, float* du, float* partial,
+                                  void* out, bool out_f64, int64_t out_sys_stride,
+                                  int64_t seg_stride, cudaStream_t st);
 // Wide-by-thin time reduction (one narrow side, see backward.cu); false if the
 // shape is outside what the kernel handles (the caller then uses launch_treduce).
 bool wtreduce_supported(const Plan& p, int a, int tc, int nsh);

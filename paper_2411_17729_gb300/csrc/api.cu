@@ -881,7 +881,8 @@ cascade_status_t run_backward_t(Plan* p, const T* P, const T* Bbar, const T* Min
                         chain_tc_scratch_bytes(*p) <= L.off_dP - L.off_part;
   for (int k = p->kmax1 - 2; k >= 0; --k) {
     if (chain_tc)
-      CK(launch_chain_tc(*p, k, reinterpret_cast<float*>(dP), kst, part, st), "chain (tensor core)");
+      CK(launch_chain_tc(*p, k, k == p->kmax1 - 2, reinterpret_cast<float*>(dP), kst, part, st),
+         "chain (tensor core)");
     else
       CK(chain_step(dP + (k + 1) * mm, P + k * mm, dP + k * mm, m, kst, ns, st, part,
                     L.off_dP - L.off_part),

@@ -26,6 +26,8 @@ struct ChainArgs {
   int m, kmax1, k, BN;
   float* dP;            // [nsys][kmax1][m][m]
   int64_t kst;          // elements between systems in dP
+  // split planes of the finished dP_k for the next level (X and X^T, hi and lo), or null
+  __nv_bfloat16 *oxh, *oxl, *oth, *otl;
   int32_t* err;
   unsigned long long timeout_ns;
 };
@@ -169,8 +171,9 @@ __global__ void __launch_bounds__(128, 1)
   // warp-uniform decision: the TMEM loads below are warp-collective
   if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
     const int r = warp * 32 + lane;                  // tile row == TMEM lane
-    float* out = args.dP + (int64_t)s * args.kst + (int64_t)args.k * m * m +
-                 (int64_t)(i0 + r) * m + j0;
+    const int i = i0 + r;
+    float* out = args.dP + (int64_t)s * args.kst + (int64_t)args.k * m * m + (int64_t)i * m + j0;
+    const int64_t xb = (int64_t)s * m * m;
     for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       ptx::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
@@ -180,6 +183,30 @@ __global__ void __launch_bounds__(128, 1)
         float4 t = o[e];
         t.x += v[4 * e]; t.y += v[4 * e + 1]; t.z += v[4 * e + 2]; t.w += v[4 * e + 3];
         o[e] = t;
+        v[4 * e] = t.x; v[4 * e + 1] = t.y; v[4 * e + 2] = t.z; v[4 * e + 3] = t.w;
+      }
+      if (args.oxh) {
+        // dP_k is final here: its split planes feed the next level, as X (row i)
+        // and as X^T (column i: the warp's 32 rows are 64 contiguous bytes per j)
+        __nv_bfloat16 hv[32], lv[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          hv[e] = __float2bfloat16_rn(v[e]);
+          lv[e] = __float2bfloat16_rn(v[e] - __bfloat162float(hv[e]));
+        }
+        uint4* xh4 = reinterpret_cast<uint4*>(args.oxh + xb + (int64_t)i * m + j0 + c0);
+        uint4* xl4 = reinterpret_cast<uint4*>(args.oxl + xb + (int64_t)i * m + j0 + c0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          xh4[e] = *reinterpret_cast<const uint4*>(&hv[8 * e]);
+          xl4[e] = *reinterpret_cast<const uint4*>(&lv[8 * e]);
+        }
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const int64_t tix = xb + (int64_t)(j0 + c0 + e) * m + i;
+          args.oth[tix] = hv[e];
+          args.otl[tix] = lv[e];
+        }
       }
     }
   } else if (!ok) {
@@ -198,22 +225,28 @@ bool chain_tc_supported(const Plan& p) {
 }
 
 size_t chain_tc_scratch_bytes(const Plan& p) {
-  return (size_t)4 * p.d.nsys * p.d.m * p.d.m * sizeof(__nv_bfloat16);
+  return (size_t)8 * p.d.nsys * p.d.m * p.d.m * sizeof(__nv_bfloat16);
 }
 
-// dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1) for every system; scratch holds the
-// four split planes (chain_tc_scratch_bytes).
-cudaError_t launch_chain_tc(const Plan& p, int k, float* dP, int64_t kst, void* scratch,
-                            cudaStream_t st) {
+// dP_k += dP_(k+1) P_k^T + P_k^T dP_(k+1) for every system.  scratch holds two sets
+// of the four split planes (chain_tc_scratch_bytes): level k reads set k & 1 (split
+// here from dP_(k+1) on the first level, first = true) and its epilogue writes the
+// planes of the finished dP_k into the other set for level k - 1.
+cudaError_t launch_chain_tc(const Plan& p, int k, bool first, float* dP, int64_t kst,
+                            void* scratch, cudaStream_t st) {
   const int m = p.d.m, ns = p.d.nsys;
   const int64_t mm = (int64_t)m * m;
-  __nv_bfloat16* xh = static_cast<__nv_bfloat16*>(scratch);
+  __nv_bfloat16* set0 = static_cast<__nv_bfloat16*>(scratch);
+  __nv_bfloat16* xh = set0 + (int64_t)(k & 1) * 4 * ns * mm;
   __nv_bfloat16* xl = xh + ns * mm;
   __nv_bfloat16* th = xl + ns * mm;
   __nv_bfloat16* tl = th + ns * mm;
-  chain_split_kernel<<<dim3(m / 32, m / 32, ns), dim3(32, 8), 0, st>>>(
-      dP + (int64_t)(k + 1) * mm, kst, m, xh, xl, th, tl);
-  CASCADE_LAUNCHED();
+  __nv_bfloat16* oh = set0 + (int64_t)((k + 1) & 1) * 4 * ns * mm;
+  if (first) {
+    chain_split_kernel<<<dim3(m / 32, m / 32, ns), dim3(32, 8), 0, st>>>(
+        dP + (int64_t)(k + 1) * mm, kst, m, xh, xl, th, tl);
+    CASCADE_LAUNCHED();
+  }
   const int BN = m % 256 == 0 ? 256 : 128;
   CUtensorMap maps[8];
   std::string err;
@@ -236,6 +269,12 @@ cudaError_t launch_chain_tc(const Plan& p, int k, float* dP, int64_t kst, void* 
   a.BN = BN;
   a.dP = dP;
   a.kst = kst;
+  if (k > 0) {   // dP_0 feeds no further level
+    a.oxh = oh;
+    a.oxl = oh + ns * mm;
+    a.oth = oh + 2 * ns * mm;
+    a.otl = oh + 3 * ns * mm;
+  }
   a.err = p.err;
   a.timeout_ns = 2000000000ull;
   const size_t smem = 1024 + (size_t)CSTAGES * (2 * CA_BYTES + 2 * (size_t)BN * 64) +

@@ -363,8 +363,8 @@ cudaError_t launch_recursion_f64(const Plan& p, const double* u, double* y, cuda
 // Squaring-chain adjoint on the tensor cores (chain_tc.cu, BF16-split plans).
 bool chain_tc_supported(const Plan& p);
 size_t chain_tc_scratch_bytes(const Plan& p);
-cudaError_t launch_chain_tc(const Plan& p, int k, float* dP, int64_t kst, void* scratch,
-                            cudaStream_t st);
+cudaError_t launch_chain_tc(const Plan& p, int k, bool first, float* dP, int64_t kst,
+                            void* scratch, cudaStream_t st);
 // Zero-order hold (zoh.cu): matrix exponentials by scaling and squaring, FP64.
 size_t expm_scratch_doubles(int n, int ns);
 int expm_squarings(double norm1);

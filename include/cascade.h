@@ -28,6 +28,12 @@
  *     otherwise.  System matrices and their gradients are always double.
  *   - `stream` is a cudaStream_t (0 = legacy default stream).  Calls that
  *     launch work are asynchronous on that stream unless stated otherwise.
+ *     The tensor-core kernels are programmatic dependent launches: each may
+ *     start its set-up while the previous kernel of the stream finishes, and
+ *     waits for that kernel before touching memory.  Each also allows the next
+ *     kernel to do the same; a caller's kernel launched without the
+ *     programmatic-serialization attribute still starts after the library's
+ *     last kernel has completed, as with any stream.
  *   - Every call returns a cascade_status_t; no call aborts or throws.  On
  *     failure the plan keeps its previous state and cascade_last_error()
  *     returns a one-line description.

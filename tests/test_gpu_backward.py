@@ -231,3 +231,23 @@ def test_recompute_matches_saved_states(lib, precision, m):
     for k in g1:
         assert np.array_equal(g1[k], g2[k]), k
     compare(w, c2, g2, dy, GTOL[precision])
+
+
+@pytest.mark.parametrize("m,p,q", [(512, 1, 1), (256, 2, 4), (128, 4, 1)])
+def test_first_stage_adjoint_one_pass(lib, m, p, q):
+    """du, R1 and R2 from one pass over W^(1) (p, q <= 4): one or two 8-column groups
+    per lane, ragged lengths (rows past a sequence end inside a tile, a one-row
+    sequence), two systems."""
+    w = wl.differentiation_form(m=m, p=p, q=q, L=8, batch=4, N=10, delta=1e-2, seed=17)
+    lengths = (1, 129, 700, 300)
+    w.offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    w.u = np.random.default_rng(18).standard_normal((int(w.offsets[-1]), p))
+    w.sys_of_seq = np.array([0, 1, 0, 1], np.int32)
+    w.A = np.concatenate([w.A, w.A])
+    w.delta = np.array([1e-2, 2e-2])
+    for k in ("B", "C", "D"):
+        setattr(w, k, np.concatenate([getattr(w, k), 0.8 * getattr(w, k)]))
+    w = cast_inputs(w, "bf16_split")
+    dy = np.random.default_rng(19).standard_normal((w.rows, q)).astype(np.float32).astype(np.float64)
+    c, _, g = gpu_grads(lib, w, "bf16_split", dy)
+    compare(w, c, g, dy, GTOL["bf16_split"])

@@ -57,7 +57,8 @@ LENGTHS = (1, 2, 3, 4, 5, 64, 127, 128, 129, 255, 256, 257, 1000, 2048, 3001)
 
 @pytest.mark.parametrize("precision,m,q", [("bf16_split", 128, 2), ("bf16_split", 256, 2),
                                            ("fp32", 128, 2), ("fp32", 64, 2),
-                                           ("bf16_split", 128, 6)])
+                                           ("bf16_split", 128, 6), ("bf16_split", 64, 1),
+                                           ("bf16_split", 192, 4)])
 def test_scan_matches_oracle(lib, precision, m, q):
     """Ragged lengths around every power of two the tiles and levels meet
     (1 .. 3001), two systems, MIMO.  With q <= 4 the down-sweep levels form y

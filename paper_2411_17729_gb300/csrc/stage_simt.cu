@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(256) stage0_vec_kernel(const Tile* __restrict_
 }
 
 // ---------------------------------------------------------------- FP64 stage
-// Block: 64 rows x 64 state columns of one tile, 256 threads, 4x4 outputs each.
+// Block: 64 rows x NB state columns of one tile, 256 threads, 4 x (NB / 16) outputs
+// each.  NB = 64, or 32 / 16 when a stage has too few tiles to fill the GPU.
+template <int NB>
 __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__ tiles, int m,
                                                         int shift, int reverse,
                                                         const double* __restrict__ P,
@@ -113,19 +115,20 @@ __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__
                                                         const double* __restrict__ vin,
                                                         double* __restrict__ vout) {
   constexpr int BMF = 64;
+  constexpr int NJ = NB / 16;
   __shared__ double As[16][65];   // [k][row]
-  __shared__ double Bs[16][65];   // [k][col]
+  __shared__ double Bs[16][NB + 1];   // [k][col]
   const Tile t = tiles[blockIdx.x];
-  const int n0 = blockIdx.y * 64;
+  const int n0 = blockIdx.y * NB;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const double* Ps = P + (int64_t)t.sys * p_sys_stride;
   // adjoint stages (reverse): source l + s and the transposed power
   const bool copy = reverse ? (t.t0 + shift >= t.len) : (t.t0 + BMF <= shift);
-  double acc[4][4];
+  double acc[4][NJ];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0;
   if (!copy) {
     for (int k0 = 0; k0 < m; k0 += 16) {
       for (int e = threadIdx.x; e < 1024; e += 256) {
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__
           v = vin[(t.seq_row0 + l) * (int64_t)m + gk];
         As[kk][rr] = v;
       }
-      for (int e = threadIdx.x; e < 1024; e += 256) {
+      for (int e = threadIdx.x; e < 16 * NB; e += 256) {
         const int kk = e & 15, nn = e >> 4;
         const int gn = n0 + nn, gk = k0 + kk;
         Bs[kk][nn] = (gn < m && gk < m) ? Ps[(int64_t)gn * m + gk] : 0.0;
@@ -145,15 +148,15 @@ __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) {
-        double a[4], b[4];
+        double a[4], b[NJ];
 #pragma unroll
         for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+        for (int j = 0; j < NJ; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < NJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
       __syncthreads();
     }
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(256) stage_f64_kernel(const Tile* __restrict__
     if (t.t0 + rr >= t.len) continue;
     const int64_t row = t.seq_row0 + t.t0 + rr;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < NJ; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= m) continue;
       vout[row * m + gn] = vin[row * m + gn] + acc[i][j];
@@ -314,11 +317,19 @@ cudaError_t launch_stage_f64(const Plan& p, int k, const double* vin, double* vo
     set_global_error("stage launch without its powers or state buffers");
     return cudaErrorInvalidValue;
   }
-  dim3 grid(n, (p.d.m + 63) / 64);
-  stage_f64_kernel<<<grid, 256, 0, st>>>(reverse ? p.d_adj_tiles[k] : p.d_tiles[k], p.d.m, 1 << k,
-                                         reverse ? 1 : 0,
-                                         (reverse ? p.PT64 : p.P64) + (int64_t)k * p.d.m * p.d.m,
-                                         (int64_t)p.kmax1 * p.d.m * p.d.m, vin, vout);
+  // column blocks of 64, or narrower while a launch would leave SMs idle
+  int nb = 64;
+  while (nb > 16 && (int64_t)n * ((p.d.m + nb - 1) / nb) < p.num_sms) nb >>= 1;
+  const Tile* tl = reverse ? p.d_adj_tiles[k] : p.d_tiles[k];
+  const double* Pk = (reverse ? p.PT64 : p.P64) + (int64_t)k * p.d.m * p.d.m;
+  const int64_t pss = (int64_t)p.kmax1 * p.d.m * p.d.m;
+  const dim3 grid(n, (p.d.m + nb - 1) / nb);
+  if (nb == 64)
+    stage_f64_kernel<64><<<grid, 256, 0, st>>>(tl, p.d.m, 1 << k, reverse ? 1 : 0, Pk, pss, vin, vout);
+  else if (nb == 32)
+    stage_f64_kernel<32><<<grid, 256, 0, st>>>(tl, p.d.m, 1 << k, reverse ? 1 : 0, Pk, pss, vin, vout);
+  else
+    stage_f64_kernel<16><<<grid, 256, 0, st>>>(tl, p.d.m, 1 << k, reverse ? 1 : 0, Pk, pss, vin, vout);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }

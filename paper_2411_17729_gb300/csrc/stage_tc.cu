@@ -734,7 +734,7 @@ std::vector<TcConfig> tc_candidates(int m, int precision) {
   const int BN = block_n(m, precision);
   std::vector<TcConfig> out;
   for (int g : {1, 2})
-    for (int ring : {4, 6, 8})
+    for (int ring : {2, 4, 6, 8})
       for (int st = 6; st >= 2; --st) {
         TcConfig c{st, ring, g};
         if (tc_config_fits(BN, c)) { out.push_back(c); break; }

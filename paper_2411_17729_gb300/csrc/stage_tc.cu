@@ -711,19 +711,21 @@ cudaError_t launch_variant(const CUtensorMap* maps, const StageArgs& a, int grid
 size_t stage_bytes_for(int BN) { return 2 * (size_t)PLANE_TILE + 2 * (size_t)BN * ROWB; }
 
 // Shared memory besides the operand stages: alignment slack, the staging ring,
-// the mbarriers (room for RING_MAX ring barriers of each kind) and the TMEM slot.
-size_t fixed_smem_bytes(int S, int ring) {
-  // alignment, ring, mbarriers, TMEM slot and abort flag, the partial y sums
+// the mbarriers (room for RING_MAX ring barriers of each kind), the TMEM slot and,
+// when one tile spans all m columns (the output may be formed in the epilogue),
+// the partial y sums.
+size_t fixed_smem_bytes(int S, int ring, bool ysum) {
   return 1024 + (size_t)ring * SLOT_BYTES + 8 * (2 * S + 7 + 2 * RING_MAX) + 16 +
-         sizeof(float) * 4 * 128;
+         (ysum ? sizeof(float) * 4 * 128 : 0);
 }
 
-bool tc_config_fits(int BN, const TcConfig& c) {
+bool tc_config_fits(int m, int BN, const TcConfig& c) {
   if (c.group != 1 && c.group != 2) return false;
   // each ring slot always serves the same epilogue group: ring % (2 group) == 0
   if (c.ring < 2 * c.group || c.ring > RING_MAX || c.ring % (2 * c.group) != 0) return false;
   if (c.stages < 2 || c.stages > 8) return false;
-  return fixed_smem_bytes(c.stages, c.ring) + (size_t)c.stages * stage_bytes_for(BN) <= 227 * 1024;
+  return fixed_smem_bytes(c.stages, c.ring, BN >= m) + (size_t)c.stages * stage_bytes_for(BN) <=
+         227 * 1024;
 }
 
 }  // namespace
@@ -737,7 +739,7 @@ std::vector<TcConfig> tc_candidates(int m, int precision) {
     for (int ring : {2, 4, 6, 8})
       for (int st = 6; st >= 2; --st) {
         TcConfig c{st, ring, g};
-        if (tc_config_fits(BN, c)) { out.push_back(c); break; }
+        if (tc_config_fits(m, BN, c)) { out.push_back(c); break; }
       }
   return out;
 }
@@ -747,7 +749,7 @@ std::vector<TcConfig> tc_candidates(int m, int precision) {
 TcConfig tc_default(int m, int precision) {
   const int BN = block_n(m, precision);
   TcConfig c{4, 4, 1};
-  while (c.stages > 2 && !tc_config_fits(BN, c)) --c.stages;
+  while (c.stages > 2 && !tc_config_fits(m, BN, c)) --c.stages;
   return c;
 }
 
@@ -769,7 +771,7 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   const int elem = (int)plane_elem_bytes(p.d.precision);
   const int BN = block_n(m, p.d.precision);
   TcConfig cfg{p.tc_stages, p.tc_ring, p.tc_group};
-  if (!tc_config_fits(BN, cfg)) cfg = tc_default(m, p.d.precision);
+  if (!tc_config_fits(m, BN, cfg)) cfg = tc_default(m, p.d.precision);
   const uint32_t row_elems = ROWB / (uint32_t)elem;
   CUtensorMap maps[6];
   std::string err;
@@ -815,7 +817,8 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   a.err = p.err;
   a.diag = p.err + 1;
   a.timeout_ns = 2000000000ull;
-  const size_t smem = fixed_smem_bytes(a.stages, a.ring) + (size_t)a.stages * stage_bytes_for(BN);
+  const size_t smem =
+      fixed_smem_bytes(a.stages, a.ring, BN >= m) + (size_t)a.stages * stage_bytes_for(BN);
   const int nwork = ntiles * a.nblocks;
   const int grid = nwork < p.num_sms ? nwork : p.num_sms;
   const int q = p.d.q;

@@ -286,66 +286,125 @@ __device__ __forceinline__ int thin_idx(int j, int c, int stride) {
 }
 __host__ __device__ __forceinline__ int thin_stride(int m) { return (m + 255) & ~255; }
 
-// expand: thread item = (row, 8 columns); 2 items in flight per thread.
-template <int FMT, bool TWO>
-__global__ void __launch_bounds__(256) expand_thin_kernel(const Tile* __restrict__ tiles, int m,
-                                                          int px, const float* __restrict__ X,
-                                                          int ldx, Coef M1, Coef M2, Bufs out,
-                                                          int buf_mode, int buf_fixed,
-                                                          int odd_only) {
-  __shared__ __align__(16) float M1s[THIN_ELEMS];
-  __shared__ __align__(16) float M2s[TWO ? THIN_ELEMS : 4];
-  __shared__ float Xs[(PBM + 1) * 8];      // rows t0 - 1 .. t0 + 127 of X (px <= 8)
-  const Tile t = tiles[blockIdx.x];
+// expand: v[l, c] = sum_j M1[c, j] X[l, j] + [second term] sum_j M2[c, j] X[l - 1, j]
+// over the rows of each tile.  Persistent: block b takes the contiguous tiles
+// [b * per, (b + 1) * per), so the coefficients are reloaded only when the
+// system changes.  Thread layout: column group g = tid % G (8 columns,
+// G = m / 8), row phase tid / G, RPI = 256 / G rows per pass; with PXR = px = 1
+// a thread's coefficients stay in registers, otherwise they are read from
+// shared memory in the [j][c] layout above.  The next tile's X rows are fetched
+// into registers while the current tile is stored (its record one tile earlier).
+constexpr int XPF = ((PBM + 1) * 8 + 255) / 256;   // X values per thread (px <= 8)
+constexpr int EXPAND_BLOCKS_PER_SM = 4;
+
+template <int FMT, bool TWO, int PXR>
+__global__ void __launch_bounds__(256, EXPAND_BLOCKS_PER_SM)
+    expand_thin_kernel(const Tile* __restrict__ tiles, int ntiles, int per, int m, int px,
+                       const float* __restrict__ X, int ldx, Coef M1, Coef M2, Bufs out,
+                       int buf_mode, int buf_fixed, int odd_only) {
+  extern __shared__ __align__(16) float esm[];
+  const int PX = PXR > 0 ? PXR : px;
   const int stride = thin_stride(m);
-  for (int e = threadIdx.x; e < px * m; e += 256) {
-    const int j = e / m, c = e - j * m;
-    M1s[thin_idx(j, c, stride)] = M1.at(t.sys, c, j);
-    if (TWO) M2s[thin_idx(j, c, stride)] = M2.at(t.sys, c, j);
-  }
-  for (int e = threadIdx.x; e < (PBM + 1) * px; e += 256) {
-    const int r = e / px, j = e - r * px;
-    const int l = t.t0 - 1 + r;
-    Xs[e] = (l >= 0 && l < t.len) ? X[(t.seq_row0 + l) * ldx + j] : 0.f;
-  }
-  __syncthreads();
-  const int b = buf_mode ? ((t.flags + 1) & 1) : buf_fixed;
-  void* hi = out.hi(b);
-  void* lo = out.lo(b);
-  const int groups = m >> 3;
-  const int rows = min(PBM, t.len - t.t0);
-  const int items = rows * groups;
-  for (int it0 = threadIdx.x; it0 < items; it0 += 512) {
+  float* Xs = esm;                           // [(PBM + 1) * PX], row 0: time t0 - 1
+  float* M1s = esm + (PBM + 1) * 8;          // [PX][stride] (PXR == 0)
+  float* M2s = M1s + PX * stride;
+  const int tid = threadIdx.x;
+  const int G = m >> 3, RPI = 256 / G;
+  const int g = tid % G, rph = tid / G;
+  const int c0 = g * 8;
+  const bool active = rph < RPI;
+  const int nx = (PBM + 1) * PX;
+  const int tb = blockIdx.x * per, te = min(ntiles, tb + per);
+  float m1[PXR > 0 ? PXR : 1][8], m2[PXR > 0 && TWO ? PXR : 1][8];
+  float xr[XPF];
+  auto fetch = [&](const Tile& t) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int it = it0 + h * 256;
-      if (it >= items) continue;
-      const int r = it / groups, c0 = (it - r * groups) * 8;
+    for (int i = 0; i < XPF; ++i) {
+      const int e = tid + i * 256;
+      float v = 0.f;
+      if (e < nx) {
+        const int r = e / PX, j = e - r * PX;
+        const int l = t.t0 - 1 + r;
+        if (l >= 0 && l < t.len) v = __ldg(X + (t.seq_row0 + l) * ldx + j);
+      }
+      xr[i] = v;
+    }
+  };
+  // Tile records run two ahead of the stores, X rows one ahead.
+  Tile tnext{};
+  if (tb < te) {
+    fetch(tiles[tb]);
+    tnext = tiles[tb + 1 < te ? tb + 1 : tb];
+  }
+  int cur_sys = -1;
+  for (int ti = tb; ti < te; ++ti) {
+    const Tile t = tiles[ti];
+    __syncthreads();   // every read of Xs (and M1s, M2s) for the previous tile is done
+#pragma unroll
+    for (int i = 0; i < XPF; ++i)
+      if (tid + i * 256 < nx) Xs[tid + i * 256] = xr[i];
+    if (t.sys != cur_sys) {   // block-uniform
+      cur_sys = t.sys;
+      if constexpr (PXR == 0) {
+        for (int e = tid; e < PX * m; e += 256) {
+          const int j = e / m, c = e - j * m;
+          M1s[thin_idx(j, c, stride)] = M1.at(t.sys, c, j);
+          if (TWO) M2s[thin_idx(j, c, stride)] = M2.at(t.sys, c, j);
+        }
+      } else if (active) {
+#pragma unroll
+        for (int j = 0; j < PXR; ++j)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            m1[j][e] = M1.at(t.sys, c0 + e, j);
+            if (TWO) m2[j][e] = M2.at(t.sys, c0 + e, j);
+          }
+      }
+    }
+    __syncthreads();
+    if (ti + 1 < te) {
+      fetch(tnext);
+      tnext = tiles[ti + 2 < te ? ti + 2 : ti + 1];
+    }
+    if (!active) continue;
+    const int b = buf_mode ? ((t.flags + 1) & 1) : buf_fixed;
+    void* hi = out.hi(b);
+    void* lo = out.lo(b);
+    const int rows = min(PBM, t.len - t.t0);
+#pragma unroll 2
+    for (int r = rph; r < rows; r += RPI) {
       const int l = t.t0 + r;
-      const int64_t row = t.seq_row0 + l;
       const bool second = TWO && l >= 1 && (!odd_only || (l & 1));
       float acc[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) acc[e] = 0.f;
-      for (int j = 0; j < px; ++j) {
-        const float x1 = Xs[(r + 1) * px + j];
-        const float x0 = second ? Xs[r * px + j] : 0.f;
-        const float4 a0 = *reinterpret_cast<const float4*>(&M1s[thin_idx(j, c0, stride)]);
-        const float4 a1 = *reinterpret_cast<const float4*>(&M1s[thin_idx(j, c0 + 4, stride)]);
-        acc[0] = fmaf(a0.x, x1, acc[0]); acc[1] = fmaf(a0.y, x1, acc[1]);
-        acc[2] = fmaf(a0.z, x1, acc[2]); acc[3] = fmaf(a0.w, x1, acc[3]);
-        acc[4] = fmaf(a1.x, x1, acc[4]); acc[5] = fmaf(a1.y, x1, acc[5]);
-        acc[6] = fmaf(a1.z, x1, acc[6]); acc[7] = fmaf(a1.w, x1, acc[7]);
-        if (TWO) {
-          const float4 b0 = *reinterpret_cast<const float4*>(&M2s[thin_idx(j, c0, stride)]);
-          const float4 b1 = *reinterpret_cast<const float4*>(&M2s[thin_idx(j, c0 + 4, stride)]);
-          acc[0] = fmaf(b0.x, x0, acc[0]); acc[1] = fmaf(b0.y, x0, acc[1]);
-          acc[2] = fmaf(b0.z, x0, acc[2]); acc[3] = fmaf(b0.w, x0, acc[3]);
-          acc[4] = fmaf(b1.x, x0, acc[4]); acc[5] = fmaf(b1.y, x0, acc[5]);
-          acc[6] = fmaf(b1.z, x0, acc[6]); acc[7] = fmaf(b1.w, x0, acc[7]);
+      for (int j = 0; j < PX; ++j) {
+        const float x1 = Xs[(r + 1) * PX + j];
+        const float x0 = second ? Xs[r * PX + j] : 0.f;
+        if constexpr (PXR > 0) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            acc[e] = fmaf(m1[j][e], x1, acc[e]);
+            if (TWO) acc[e] = fmaf(m2[j][e], x0, acc[e]);
+          }
+        } else {
+          const float4 a0 = *reinterpret_cast<const float4*>(&M1s[thin_idx(j, c0, stride)]);
+          const float4 a1 = *reinterpret_cast<const float4*>(&M1s[thin_idx(j, c0 + 4, stride)]);
+          acc[0] = fmaf(a0.x, x1, acc[0]); acc[1] = fmaf(a0.y, x1, acc[1]);
+          acc[2] = fmaf(a0.z, x1, acc[2]); acc[3] = fmaf(a0.w, x1, acc[3]);
+          acc[4] = fmaf(a1.x, x1, acc[4]); acc[5] = fmaf(a1.y, x1, acc[5]);
+          acc[6] = fmaf(a1.z, x1, acc[6]); acc[7] = fmaf(a1.w, x1, acc[7]);
+          if (TWO) {
+            const float4 b0 = *reinterpret_cast<const float4*>(&M2s[thin_idx(j, c0, stride)]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&M2s[thin_idx(j, c0 + 4, stride)]);
+            acc[0] = fmaf(b0.x, x0, acc[0]); acc[1] = fmaf(b0.y, x0, acc[1]);
+            acc[2] = fmaf(b0.z, x0, acc[2]); acc[3] = fmaf(b0.w, x0, acc[3]);
+            acc[4] = fmaf(b1.x, x0, acc[4]); acc[5] = fmaf(b1.y, x0, acc[5]);
+            acc[6] = fmaf(b1.z, x0, acc[6]); acc[7] = fmaf(b1.w, x0, acc[7]);
+          }
         }
       }
-      store8<FMT>(hi, lo, row * (int64_t)m + c0, acc);
+      store8<FMT>(hi, lo, (t.seq_row0 + l) * (int64_t)m + c0, acc);
     }
   }
 }
@@ -491,17 +550,27 @@ cudaError_t contract_dispatch(const Tile* tiles, int ntiles, int m, int nout, co
 }
 
 template <bool TWO>
-cudaError_t expand_dispatch(int precision, const Tile* tiles, int ntiles, int m, int px,
+cudaError_t expand_dispatch(int precision, int nsms, const Tile* tiles, int ntiles, int m, int px,
                             const float* X, int ldx, const Coef& M1, const Coef& M2,
                             const Bufs& out, int buf_mode, int buf_fixed, int odd_only,
                             cudaStream_t st) {
-  if (px <= 8 && thin_stride(m) * px <= THIN_ELEMS) {
-    if (precision == CASCADE_BF16_SPLIT)
-      expand_thin_kernel<FMT_BF16, TWO><<<ntiles, 256, 0, st>>>(tiles, m, px, X, ldx, M1, M2, out,
-                                                               buf_mode, buf_fixed, odd_only);
-    else
-      expand_thin_kernel<FMT_F32, TWO><<<ntiles, 256, 0, st>>>(tiles, m, px, X, ldx, M1, M2, out,
-                                                              buf_mode, buf_fixed, odd_only);
+  if (px <= 8 && thin_stride(m) * px <= THIN_ELEMS && m / 8 <= 256) {
+    const int want = (nsms > 0 ? nsms : 1) * EXPAND_BLOCKS_PER_SM;
+    const int per = (ntiles + want - 1) / want;
+    const int grid = (ntiles + per - 1) / per;
+    const size_t coef = px == 1 ? 0 : (TWO ? 2 : 1) * (size_t)px * thin_stride(m);
+    const size_t smem = sizeof(float) * ((size_t)(PBM + 1) * 8 + coef);
+#define CASCADE_ETHIN(F, R)                                                                    \
+  expand_thin_kernel<F, TWO, R><<<grid, 256, smem, st>>>(tiles, ntiles, per, m, px, X, ldx, M1, \
+                                                         M2, out, buf_mode, buf_fixed, odd_only)
+    if (precision == CASCADE_BF16_SPLIT) {
+      if (px == 1) CASCADE_ETHIN(FMT_BF16, 1);
+      else CASCADE_ETHIN(FMT_BF16, 0);
+    } else {
+      if (px == 1) CASCADE_ETHIN(FMT_F32, 1);
+      else CASCADE_ETHIN(FMT_F32, 0);
+    }
+#undef CASCADE_ETHIN
     CASCADE_LAUNCHED();
     return cudaGetLastError();
   }
@@ -560,8 +629,8 @@ cudaError_t launch_proj_stage0(const Plan& p, const float* u, const Bufs& V, int
   const int m = p.d.m, pp = p.d.p;
   const Coef B{p.Bbar32, (int64_t)m * pp, pp, 1};     // Bbar [m, p]: (c, j)
   const Coef AB{p.ABbar32, (int64_t)m * pp, pp, 1};
-  return expand_dispatch<true>(p.d.precision, p.d_stage0_tiles, p.n_stage0_tiles, m, pp, u, pp, B,
-                               AB, V, 0, buf, odd_only ? 1 : 0, st);
+  return expand_dispatch<true>(p.d.precision, p.num_sms, p.d_stage0_tiles, p.n_stage0_tiles, m,
+                               pp, u, pp, B, AB, V, 0, buf, odd_only ? 1 : 0, st);
 }
 
 // W^(N_i+1) = C^T G into adjoint buffer (N_i + 1) & 1 of every tile.
@@ -569,8 +638,8 @@ cudaError_t launch_proj_adj_init(const Plan& p, const float* G, const Bufs& W, c
   if (p.n_all_tiles == 0) return cudaSuccess;
   const int m = p.d.m, q = p.d.q;
   const Coef Ct{p.C32, (int64_t)q * m, 1, m};          // C [q, m]: (c, j) = C[j][c]
-  return expand_dispatch<false>(p.d.precision, p.d_all_tiles, p.n_all_tiles, m, q, G, q, Ct, Ct,
-                                W, 1, 0, 0, st);
+  return expand_dispatch<false>(p.d.precision, p.num_sms, p.d_all_tiles, p.n_all_tiles, m, q, G,
+                                q, Ct, Ct, W, 1, 0, 0, st);
 }
 
 // y = C v + D u for the tiles whose output was not fused (state buffer tile.fbuf).

@@ -538,10 +538,44 @@ __global__ void convert_sys_kernel(const TI* __restrict__ in, int64_t in_stride,
 // each tile plus the next row (whose (Abar Bbar)^T W completes the warp's last du);
 // lane l owns the 8-column groups 8 (l + 32 g), g < NG, of every row, so a row is one
 // coalesced read and the two p-wide dot products of du are warp reductions.  The
-// warps' R1, R2 partials are added in a fixed order into partial[chunk][h][i][j]
-// (h = 0: R1, 1: R2), summed per system afterwards.
+// rows are read in batches of RB; each thread copies its own 16-byte pieces of the
+// batch FA_ST - 1 ahead into shared memory (cp.async), and the first lanes of a warp
+// copy the batch's u and G values, so the loads stay in flight while earlier rows
+// are reduced.  The warps' R1, R2 partials are added in a fixed order into
+// partial[chunk][h][i][j] (h = 0: R1, 1: R2), summed per system afterwards.
 constexpr int FA_PMAX = 4;   // p, q <= 4
 constexpr int FA_CMAX = 2;   // NG * p <= 2 (accumulators per lane: 2 x 8 x NG x p)
+constexpr int FA_ST = 3;     // batches in shared memory (FA_ST - 1 in flight)
+constexpr int FA_SW = 8;     // 16-byte words a thread copies per batch
+template <int FMT>
+__host__ __device__ constexpr int fa_vw() { return FMT == FMT_BF16 ? 1 : 2; }   // words / 8 cols
+template <int FMT, int CM>
+__host__ __device__ constexpr int fa_rb() { return FA_SW / (CM * 2 * fa_vw<FMT>()); }
+__host__ __device__ constexpr int fa_scalars(int rb, int pm) { return rb * 3 * pm; }
+// Shared memory: the batch ring, then the scalar ring; the R1, R2 reduction
+// at the end reuses the space.
+__host__ __device__ constexpr size_t fa_smem_bytes(int rb, int pm) {
+  return (size_t)FA_ST * FA_SW * 256 * 16 + (size_t)FA_ST * 8 * fa_scalars(rb, pm) * 4;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(ptx::smem_addr(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(ptx::smem_addr(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // CM >= NG * p: accumulator groups per lane; PM >= p, q
 template <int FMT, int CM, int PM>
 __global__ void __launch_bounds__(256, 2) first_adj_thin_kernel(
@@ -549,13 +583,21 @@ __global__ void __launch_bounds__(256, 2) first_adj_thin_kernel(
     Bufs W, int wbuf, const float* __restrict__ u, const float* __restrict__ G,
     const float* __restrict__ Bbar, const float* __restrict__ ABbar,
     const float* __restrict__ D, float* __restrict__ du, float* __restrict__ partial) {
-  extern __shared__ __align__(16) float fa_red[];   // [8 warps][2][m][p]
+  extern __shared__ __align__(16) float fa_smem[];
+  constexpr int VW = fa_vw<FMT>();
+  constexpr int RB = fa_rb<FMT, CM>();      // rows per batch
+  constexpr int NBT = 16 / RB + 1;          // batches per tile: rows r0 .. r0 + 16
+  constexpr int SC = fa_scalars(RB, PM);    // u_l, u_(l-1), G_(l-1) of a batch
+  constexpr int ELEM = FMT == FMT_BF16 ? 2 : 4;
+  static_assert(RB >= 1 && RB * CM * 2 * VW == FA_SW, "batch words");
+  uint4* ring = reinterpret_cast<uint4*>(fa_smem);                   // [FA_ST][FA_SW][256]
+  float* scal = reinterpret_cast<float*>(ring + FA_ST * FA_SW * 256);   // [FA_ST][8][SC]
   const int c = blockIdx.x;
   const int first = chunks[3 * c], count = chunks[3 * c + 1], sys = chunks[3 * c + 2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NG = (m + 255) / 256;
-  const void* wh = W.hi(wbuf);
-  const void* wl = W.lo(wbuf);
+  const char* wh = static_cast<const char*>(W.hi(wbuf));
+  const char* wl = static_cast<const char*>(W.lo(wbuf));
   // this lane's coefficients: Bbar[col][j], ABbar[col][j]
   float cb[CM][8], cab[CM][8];
   float acc1[CM][8], acc2[CM][8];
@@ -579,104 +621,163 @@ __global__ void __launch_bounds__(256, 2) first_adj_thin_kernel(
     for (int j = 0; j < PM; ++j)
       Ds[i][j] = (i < q && j < p) ? D[((int64_t)sys * q + i) * p + j] : 0.f;
 
-  constexpr int RB = CM == 1 ? 4 : 2;   // rows loaded ahead of their arithmetic
-  for (int ti = first; ti < first + count; ++ti) {
-    const Tile t = tiles[ti];
-    const int r0 = 16 * warp;
-    float aprev[PM];
-#pragma unroll
-    for (int j = 0; j < PM; ++j) aprev[j] = 0.f;
-    for (int rb = r0; rb <= r0 + 16; rb += RB) {
-      float xs[RB][CM][8];
-      float ul[RB][PM], um[RB][PM], gp[RB][PM];   // u_l, u_(l-1), G_(l-1)
+  const int r0 = 16 * warp;
+  const int nb = count * NBT;
+  // Batch b: rows r0 + (b % NBT) RB .. + RB - 1 of tile first + b / NBT.  Every
+  // call commits one group (empty past the end), so wait_group counts batches.
+  auto issue = [&](int b) {
+    if (b < nb) {
+      const Tile t = tiles[first + b / NBT];
+      const int rb = r0 + (b % NBT) * RB;
+      const int st = b % FA_ST;
 #pragma unroll
       for (int v = 0; v < RB; ++v) {
         const int l = t.t0 + rb + v;
         const bool live = rb + v <= r0 + 16 && l < t.len;
         const int64_t row = t.seq_row0 + l;
 #pragma unroll
-        for (int j = 0; j < PM; ++j) {
-          ul[v][j] = (live && j < p) ? __ldg(u + row * p + j) : 0.f;
-          um[v][j] = (live && j < p && l >= 1) ? __ldg(u + (row - 1) * p + j) : 0.f;
-          gp[v][j] = (rb + v <= r0 + 16 && l >= 1 && l - 1 < t.len && j < q)
-                         ? __ldg(G + (row - 1) * q + j) : 0.f;
-        }
-#pragma unroll
         for (int g = 0; g < CM; ++g) {
           const int col0 = 8 * (lane + 32 * g);
-          if (g < NG && live && col0 < m) {
-            load_row_vec<FMT, 8>(wh, wl, row * m + col0, xs[v][g]);
-          } else {
+          const bool ok = live && g < NG && col0 < m;
+          const int64_t off = ok ? (row * m + col0) * ELEM : 0;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) xs[v][g][e] = 0.f;
+          for (int w = 0; w < VW; ++w) {
+            uint4* dh = ring + ((st * FA_SW) + ((v * CM + g) * 2 + 0) * VW + w) * 256 + threadIdx.x;
+            uint4* dl = ring + ((st * FA_SW) + ((v * CM + g) * 2 + 1) * VW + w) * 256 + threadIdx.x;
+            cp_async16(dh, wh + off + 16 * w, ok ? 16 : 0);
+            cp_async16(dl, wl + off + 16 * w, ok ? 16 : 0);
           }
         }
       }
-#pragma unroll
-      for (int v = 0; v < RB; ++v) {
-        const int r = rb + v;
-        if (r > r0 + 16) break;
-        const int l = t.t0 + r;                 // time step in the sequence
-        const bool live = l < t.len;
+      for (int e = lane; e < SC; e += 32) {
+        const int v = e / (3 * PM), kind = (e / PM) % 3, j = e % PM;
+        const int l = t.t0 + rb + v;
         const int64_t row = t.seq_row0 + l;
-        // lane partials of Bbar^T W_l and (Abar Bbar)^T W_l, then warp sums
-        float a[PM], b[PM];
+        const bool in16 = rb + v <= r0 + 16;
+        bool ok;
+        const float* src;
+        if (kind == 0) {
+          ok = in16 && l < t.len && j < p;
+          src = u + row * p + j;
+        } else if (kind == 1) {
+          ok = in16 && l < t.len && j < p && l >= 1;
+          src = u + (row - 1) * p + j;
+        } else {
+          ok = in16 && l >= 1 && l - 1 < t.len && j < q;
+          src = G + (row - 1) * q + j;
+        }
+        cp_async4(scal + (st * 8 + warp) * SC + e, ok ? src : u, ok ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
 #pragma unroll
-        for (int j = 0; j < PM; ++j) { a[j] = 0.f; b[j] = 0.f; }
+  for (int b = 0; b < FA_ST - 1; ++b) issue(b);
+
+  float aprev[PM];
+  for (int b = 0; b < nb; ++b) {
+    issue(b + FA_ST - 1);
+    cp_async_wait<FA_ST - 1>();   // this thread's copies of batch b have landed
+    __syncwarp();                 // and the other lanes' scalar copies
+    const Tile t = tiles[first + b / NBT];
+    const int rb = r0 + (b % NBT) * RB;
+    const int st = b % FA_ST;
+    if (rb == r0) {
+#pragma unroll
+      for (int j = 0; j < PM; ++j) aprev[j] = 0.f;
+    }
+    const float* sb = scal + (st * 8 + warp) * SC;
+#pragma unroll
+    for (int v = 0; v < RB; ++v) {
+      const int r = rb + v;
+      if (r > r0 + 16) break;
+      float xs[CM][8];
+#pragma unroll
+      for (int g = 0; g < CM; ++g) {
+        const uint4* sh = ring + ((st * FA_SW) + ((v * CM + g) * 2 + 0) * VW) * 256 + threadIdx.x;
+        const uint4* sl = ring + ((st * FA_SW) + ((v * CM + g) * 2 + 1) * VW) * 256 + threadIdx.x;
+        if constexpr (FMT == FMT_BF16) {
+          const uint4 h4 = sh[0], l4 = sl[0];
+          const uint32_t h[4] = {h4.x, h4.y, h4.z, h4.w}, lw[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            // a BF16 value is the top half of the FP32 with the same bits
+            xs[g][2 * i] = __uint_as_float(h[i] << 16) + __uint_as_float(lw[i] << 16);
+            xs[g][2 * i + 1] =
+                __uint_as_float(h[i] & 0xffff0000u) + __uint_as_float(lw[i] & 0xffff0000u);
+          }
+        } else {
+#pragma unroll
+          for (int w = 0; w < 2; ++w) {
+            const uint4 h4 = sh[w * 256], l4 = sl[w * 256];
+            xs[g][4 * w + 0] = __uint_as_float(h4.x) + __uint_as_float(l4.x);
+            xs[g][4 * w + 1] = __uint_as_float(h4.y) + __uint_as_float(l4.y);
+            xs[g][4 * w + 2] = __uint_as_float(h4.z) + __uint_as_float(l4.z);
+            xs[g][4 * w + 3] = __uint_as_float(h4.w) + __uint_as_float(l4.w);
+          }
+        }
+      }
+      const int l = t.t0 + r;                 // time step in the sequence
+      const bool live = l < t.len;
+      const int64_t row = t.seq_row0 + l;
+      // lane partials of Bbar^T W_l and (Abar Bbar)^T W_l, then warp sums
+      float a[PM], bsum[PM];
+#pragma unroll
+      for (int j = 0; j < PM; ++j) { a[j] = 0.f; bsum[j] = 0.f; }
+#pragma unroll
+      for (int gj = 0; gj < CM; ++gj) {
+        if (gj >= NG * p) break;
+        const int g = gj / p, j = gj - g * p;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          a[j] = fmaf(cb[gj][e], xs[g][e], a[j]);
+          bsum[j] = fmaf(cab[gj][e], xs[g][e], bsum[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < PM; ++j) {
+        if (j >= p) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a[j] += __shfl_xor_sync(0xffffffffu, a[j], o);
+          bsum[j] += __shfl_xor_sync(0xffffffffu, bsum[j], o);
+        }
+      }
+      // du of the previous row: Bbar^T W_(l-1) + (Abar Bbar)^T W_l + D^T G_(l-1)
+      if (r > r0 && lane == 0 && l - 1 < t.len) {
+        const int64_t prow = row - 1;
+#pragma unroll
+        for (int j = 0; j < PM; ++j) {
+          if (j >= p) break;
+          float val = aprev[j] + bsum[j];
+#pragma unroll
+          for (int i = 0; i < PM; ++i) val = fmaf(Ds[i][j], sb[v * 3 * PM + 2 * PM + i], val);
+          du[prow * p + j] = val;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < PM; ++j) aprev[j] = a[j];
+      // R1 += W_l u_l^T, R2 += W_l u_(l-1)^T over the warp's own rows
+      if (r < r0 + 16 && live) {
 #pragma unroll
         for (int gj = 0; gj < CM; ++gj) {
           if (gj >= NG * p) break;
           const int g = gj / p, j = gj - g * p;
+          const float u1 = sb[v * 3 * PM + j], u0 = sb[v * 3 * PM + PM + j];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            a[j] = fmaf(cb[gj][e], xs[v][g][e], a[j]);
-            b[j] = fmaf(cab[gj][e], xs[v][g][e], b[j]);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < PM; ++j) {
-          if (j >= p) break;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            a[j] += __shfl_xor_sync(0xffffffffu, a[j], o);
-            b[j] += __shfl_xor_sync(0xffffffffu, b[j], o);
-          }
-        }
-        // du of the previous row: Bbar^T W_(l-1) + (Abar Bbar)^T W_l + D^T G_(l-1)
-        if (r > r0 && lane == 0 && l - 1 < t.len) {
-          const int64_t prow = row - 1;
-#pragma unroll
-          for (int j = 0; j < PM; ++j) {
-            if (j >= p) break;
-            float val = aprev[j] + b[j];
-#pragma unroll
-            for (int i = 0; i < PM; ++i) val = fmaf(Ds[i][j], gp[v][i], val);
-            du[prow * p + j] = val;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < PM; ++j) aprev[j] = a[j];
-        // R1 += W_l u_l^T, R2 += W_l u_(l-1)^T over the warp's own rows
-        if (r < r0 + 16 && live) {
-#pragma unroll
-          for (int gj = 0; gj < CM; ++gj) {
-            if (gj >= NG * p) break;
-            const int g = gj / p, j = gj - g * p;
-            float u1 = 0.f, u0 = 0.f;
-#pragma unroll
-            for (int jj = 0; jj < PM; ++jj)
-              if (jj == j) { u1 = ul[v][jj]; u0 = um[v][jj]; }
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              acc1[gj][e] = fmaf(xs[v][g][e], u1, acc1[gj][e]);
-              acc2[gj][e] = fmaf(xs[v][g][e], u0, acc2[gj][e]);
-            }
+            acc1[gj][e] = fmaf(xs[g][e], u1, acc1[gj][e]);
+            acc2[gj][e] = fmaf(xs[g][e], u0, acc2[gj][e]);
           }
         }
       }
     }
+    __syncwarp();   // every lane has read the scalars of slot st before it is refilled
   }
+  cp_async_wait<0>();
+  __syncthreads();   // the ring is reused for the reduction below
   // the warps' partials, added in warp order
+  float* fa_red = fa_smem;   // [8 warps][2][m][p]
   const int mp = m * p;
 #pragma unroll
   for (int gj = 0; gj < CM; ++gj) {
@@ -766,7 +867,6 @@ cudaError_t launch_treduce(const Plan& p, const Tile* tiles, const int32_t* chun
   const TSrc xs = X, ys = Y;
   dim3 grid((b + 63) / 64, (a + 63) / 64, nchunks);
   const int64_t elems = (int64_t)a * b;
-  const int rblocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
   if (p.d.precision == CASCADE_FP64) {
     treduce_kernel<FMT_F64, double><<<grid, 256, 0, st>>>(tiles, chunks, BM, p.d.m, xs, a, ys, b,
                                                          shift, (double*)partial);
@@ -856,7 +956,6 @@ cudaError_t launch_wtreduce(const Plan& p, const Tile* tiles, const int32_t* chu
   // vector loads: a state buffer whose rows the column groups cover exactly
   const int vec = (X.kind == 0 && a == p.d.m && a % CPT == 0) ? 1 : 0;
   const int64_t elems = (int64_t)nsh * a * tc;
-  const int rblocks = (int)((elems + 255) / 256 < 1024 ? (elems + 255) / 256 : 1024);
   const int64_t seg = (int64_t)a * tc;
   if (p.d.precision == CASCADE_FP64) {
     wt_dispatch<FMT_F64, double>(TT, nchunks, tiles, chunks, BM, p.d.m, X, a,
@@ -907,10 +1006,14 @@ cudaError_t launch_first_adj_thin(const Plan& p, const Tile* tiles, const int32_
   if (nchunks == 0) return cudaSuccess;
   if (!first_adj_thin_supported(p)) return cudaErrorInvalidValue;
   const int m = p.d.m, pp = p.d.p, q = p.d.q;
-  const size_t smem = (size_t)8 * 2 * m * pp * sizeof(float);
   const int cm = ((m + 255) / 256) * pp;
   const bool bf = p.d.precision == CASCADE_BF16_SPLIT;
   const bool one = pp == 1 && q == 1;
+  const int rb = cm <= 1 ? (bf ? fa_rb<FMT_BF16, 1>() : fa_rb<FMT_F32, 1>())
+                         : (bf ? fa_rb<FMT_BF16, 2>() : fa_rb<FMT_F32, 2>());
+  const size_t red = (size_t)8 * 2 * m * pp * sizeof(float);
+  const size_t ring = fa_smem_bytes(rb, cm <= 1 && one ? 1 : FA_PMAX);
+  const size_t smem = ring > red ? ring : red;
   auto kern = cm <= 1 ? (one ? (bf ? first_adj_thin_kernel<FMT_BF16, 1, 1>
                                    : first_adj_thin_kernel<FMT_F32, 1, 1>)
                              : (bf ? first_adj_thin_kernel<FMT_BF16, 1, FA_PMAX>

@@ -363,14 +363,22 @@ def main():
     avg_ms = sum(tot_ms.values()) / max(1, sum(len(v) for v in stage_ms.values()))
     launches_per_step = len(stage_ms)
     bytes_per_launch, flops_per_launch = [], []
+    fused = c.output_fused()
     for k in stage_ms:
         s = 1 << k
         live = Ns >= k
+        last = live & (Ns == k) if fused else np.zeros_like(live)
+        mid = live & ~last
         upd = int(np.maximum(Ls[live] - s, 0).sum())
-        rows_read = int(Ls[live].sum())
-        # read every row of v^(k) once and write the updated rows of v^(k+1) (esize bytes
-        # per element), plus the power's operand planes per system
-        bytes_per_launch.append(esize * m * (rows_read + upd) + w.nsys * m * m * esize)
+        upd_mid = int(np.maximum(Ls[mid] - s, 0).sum())
+        rows_mid, rows_last = int(Ls[mid].sum()), int(Ls[last].sum())
+        # before a sequence's last stage: read every row of v^(k) once and write the
+        # updated rows of v^(k+1) (esize bytes per element); its last stage with the
+        # output fused reads every row of v^(k) and u and writes y, not v; plus the
+        # power's operand planes per system
+        bytes_per_launch.append(esize * m * (rows_mid + upd_mid)
+                                + (esize * m + 4 * (w.p + w.q)) * rows_last
+                                + w.nsys * m * m * esize)
         flops_per_launch.append((1 if f64 else 3) * 2 * m * m * upd)
     alg_bytes = float(np.mean(bytes_per_launch)) if bytes_per_launch else 0.0
     alg_flops = float(np.mean(flops_per_launch)) if flops_per_launch else 0.0

@@ -192,6 +192,14 @@ cascade_status_t cascade_get_seq_N(cascade_plan_t plan, int32_t* h_N);
    is applied to.  Host-side count of the schedule; *h_count. */
 cascade_status_t cascade_get_matvec_count(cascade_plan_t plan, int64_t* h_count);
 
+/* Whether the output y = C v + D u (§3) is formed in the epilogue of each
+   sequence's last stage (the stage then reads v^(N_i) and u and writes y;
+   it writes v^(N_i+1) only when the plan keeps its stage outputs), or by a
+   separate projection after the last stage.  Fixed at plan creation: FP32
+   or BF16-split plans with q <= 4 whose stage tiles span all m columns,
+   unless created with CASCADE_FLAG_NO_FUSED_OUTPUT.  *h_fused = 1 or 0. */
+cascade_status_t cascade_get_output_fused(cascade_plan_t plan, int32_t* h_fused);
+
 /* Size of the fixed device scratch array behind cascade_forward_fixed_scratch. */
 #define CASCADE_FIXED_SCRATCH_BYTES ((size_t)32 << 20)
 

@@ -101,6 +101,12 @@ class Cascade:
         self._check(self.lib.cascade_get_powers(self.plan, sys, kmax, _ptr(out), _stream(stream)))
         return out
 
+    def output_fused(self):
+        """True when y = C v + D u is formed in the last stage's epilogue."""
+        f = C.c_int32()
+        self._check(self.lib.cascade_get_output_fused(self.plan, C.byref(f)))
+        return bool(f.value)
+
     def workspace_size(self):
         n = C.c_size_t()
         self._check(self.lib.cascade_workspace_size(self.plan, C.byref(n)))

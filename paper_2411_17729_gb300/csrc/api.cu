@@ -1552,6 +1552,13 @@ cascade_status_t cascade_get_matvec_count(cascade_plan_t plan, int64_t* h_count)
   return CASCADE_OK;
 }
 
+cascade_status_t cascade_get_output_fused(cascade_plan_t plan, int32_t* h_fused) {
+  Plan* p = plan;
+  if (!p || !h_fused) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  *h_fused = p->fuse_output ? 1 : 0;
+  return CASCADE_OK;
+}
+
 cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes) {
   Plan* p = plan;
   if (!p || !bytes) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");

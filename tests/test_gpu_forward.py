@@ -178,6 +178,20 @@ def test_tc_unfused_matches_fused(lib, precision):
     assert ey < 1e-5
 
 
+def test_output_fused_query(lib):
+    """cascade_get_output_fused: y formed in the last stage's epilogue for
+    q <= 4 when a stage tile spans all columns (not FP64, not opted out)."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_NO_FUSED_OUTPUT
+    cases = [(128, 1, 1, "bf16_split", 0, True), (128, 4, 4, "fp32", 0, True),
+             (128, 3, 16, "bf16_split", 0, False), (512, 2, 3, "bf16_split", 0, False),
+             (64, 1, 1, "fp64", 0, False),
+             (128, 1, 1, "bf16_split", CASCADE_FLAG_NO_FUSED_OUTPUT, False)]
+    for m, p, q, precision, flags, want in cases:
+        c = lib.Cascade(m, p, q, N=8, precision=precision, flags=flags, max_len=1024)
+        assert c.output_fused() == want, (m, p, q, precision, flags)
+        c.close()
+
+
 @pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
 def test_tc_truncation_and_growth(lib, precision):
     """Spectral radius above one with N below log2 L (truncated polynomial)."""

@@ -309,6 +309,9 @@ def main():
         c.forward(u, y)
 
     shape = c.autotune(u, y, reps=3) if not f64 else (0, 0, 0)   # kernel shape (untimed)
+    # stages whose fastest shape differs from the plan-wide one
+    stage_shapes = {} if f64 else {str(k): list(v) for k, v in c.stage_shapes().items()
+                                   if tuple(v) != tuple(shape)}
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -596,7 +599,8 @@ def main():
                        "l2": "flushed before each timed step (256 MiB write)",
                        "timing": "CUDA events on the launching stream, sum over steps",
                        "kernel_shape": {"stages": shape[0], "ring": shape[1],
-                                        "chunks_per_step": shape[2]}},
+                                        "chunks_per_step": shape[2],
+                                        "per_stage": stage_shapes}},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "states/s",

@@ -281,8 +281,12 @@ int64_t cascade_launch_count(void);
    epilogue staging ring, column chunks per epilogue step; every candidate
    fits shared and tensor memory), `reps` timed passes each after one
    warm-up, with CUDA events on `stream`, and keeps the fastest in the plan
-   for later forwards.  d_u, d_y and d_workspace are as for cascade_forward
-   (d_y is overwritten).  h_choice (NULL or int32[3]) receives the chosen
+   for later forwards.  On the §3 stage schedule each candidate also runs
+   `reps` passes with every stage timed on its own, and each stage k keeps
+   the candidate that ran it fastest (cascade_get_stage_shapes); the
+   fastest whole forward's shape serves the adjoint stages and the scan
+   levels.  d_u, d_y and d_workspace are as for cascade_forward (d_y is
+   overwritten).  h_choice (NULL or int32[3]) receives the plan-wide
    stages, ring slots and chunks per step.  Synchronous; a no-op for FP64
    plans. */
 cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_y,
@@ -294,9 +298,18 @@ cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_
    step}.  The kernel's two epilogue groups take alternate steps and each ring
    slot must always serve the same group, so ring slots must be a multiple of
    2 x chunks per step.  CASCADE_ERR_INVALID_ARG if that fails or the shape
-   does not fit shared/tensor memory for this plan's m and precision.  A no-op
-   for FP64 plans. */
+   does not fit shared/tensor memory for this plan's m and precision.  The
+   shape then applies to every stage (per-stage choices are cleared).  A
+   no-op for FP64 plans. */
 cascade_status_t cascade_set_kernel_shape(cascade_plan_t plan, const int32_t* h_shape);
+
+/* Per-stage kernel shapes chosen by cascade_autotune for the §3 schedule:
+   h_shape[3 k + j], j = stages, ring slots, chunks per step, for stage
+   k < min(cap, *n); {0, 0, 0} where the plan-wide shape applies.  *n = the
+   number of entries the plan holds (0 before tuning or after
+   cascade_set_kernel_shape). */
+cascade_status_t cascade_get_stage_shapes(cascade_plan_t plan, int32_t cap, int32_t* h_shape,
+                                          int32_t* n);
 
 /* Per-launch timing of the stage kernels.  When enabled, every later
    forward records a CUDA event pair on its stream around each tensor-core

@@ -172,6 +172,14 @@ class Cascade:
         shape = (C.c_int32 * 3)(stages, ring, group)
         self._check(self.lib.cascade_set_kernel_shape(self.plan, shape))
 
+    def stage_shapes(self, cap=64):
+        """{stage k: (stages, ring slots, chunks per step)} chosen per stage by autotune."""
+        buf = (C.c_int32 * (3 * cap))()
+        n = C.c_int32()
+        self._check(self.lib.cascade_get_stage_shapes(self.plan, cap, buf, C.byref(n)))
+        return {k: tuple(buf[3 * k:3 * k + 3]) for k in range(min(cap, n.value))
+                if buf[3 * k] > 0}
+
     def enable_stage_timing(self, on=True):
         self._check(self.lib.cascade_enable_stage_timing(self.plan, 1 if on else 0))
 

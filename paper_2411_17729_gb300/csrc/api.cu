@@ -1016,6 +1016,24 @@ size_t forward_workspace_bytes(const Plan& p) { return forward_workspace(p, p.ro
 }  // namespace cascade
 
 // =================================================================== C ABI
+// One forward with an event pair around every stage launch; adds each stage
+// k's duration to acc[k].
+static cascade_status_t timed_stages(Plan* p, const void* u, void* y, void* ws, cudaStream_t st,
+                                     std::vector<float>& acc) {
+  p->timing = true;
+  const cascade_status_t r = run_forward(p, u, y, ws, st);
+  p->timing = false;
+  if (r != CASCADE_OK) return r;
+  CK(cudaStreamSynchronize(st), "sync");
+  for (int i = 0; i < p->n_ev; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]), "elapsed");
+    const int k = p->ev_k[i];
+    if (k >= 0 && k < (int)acc.size()) acc[k] += ms;
+  }
+  return CASCADE_OK;
+}
+
 extern "C" {
 
 const char* cascade_status_string(cascade_status_t s) {
@@ -1692,7 +1710,14 @@ cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_
   float best = 1e30f;
   TcConfig best_c = tc_default(p->d.m, p->d.precision);
   cascade_status_t r = CASCADE_OK;
-  for (const TcConfig& c : tc_candidates(p->d.m, p->d.precision)) {
+  // §3 schedule: each candidate's stages are also timed one by one, and every
+  // stage k keeps the candidate that ran it fastest (the plan-wide shape, the
+  // fastest whole forward, serves the adjoint stages and the scan levels)
+  const bool per_stage = !scans(*p) && p->maxN >= 1;
+  const std::vector<TcConfig> cands = tc_candidates(p->d.m, p->d.precision);
+  std::vector<std::vector<float>> stage_ms;
+  p->tc_stage_shape.clear();
+  for (const TcConfig& c : cands) {
     p->tc_stages = c.stages;
     p->tc_ring = c.ring;
     p->tc_group = c.group;
@@ -1708,6 +1733,13 @@ cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_
       break;
     }
     if (ms < best) { best = ms; best_c = c; }
+    if (per_stage) {
+      std::vector<float> acc(p->maxN + 1, 0.f);
+      for (int i = 0; i < reps && r == CASCADE_OK; ++i)
+        r = timed_stages(p, d_u, d_y, d_workspace, st, acc);
+      if (r != CASCADE_OK) break;
+      stage_ms.push_back(std::move(acc));
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1715,6 +1747,16 @@ cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_
   p->tc_stages = best_c.stages;
   p->tc_ring = best_c.ring;
   p->tc_group = best_c.group;
+  if (r == CASCADE_OK && per_stage && stage_ms.size() == cands.size() && !cands.empty()) {
+    p->tc_stage_shape.assign(p->maxN + 1, {0, 0, 0});
+    for (int k = 1; k <= p->maxN; ++k) {
+      size_t bi = 0;
+      for (size_t ci = 1; ci < cands.size(); ++ci)
+        if (stage_ms[ci][k] < stage_ms[bi][k]) bi = ci;
+      if (stage_ms[bi][k] > 0.f)
+        p->tc_stage_shape[k] = {cands[bi].stages, cands[bi].ring, cands[bi].group};
+    }
+  }
   p->tuned = (r == CASCADE_OK);
   if (p->graph) {   // the recorded graph holds the old kernel shape
     cudaGraphExecDestroy(p->graph);
@@ -1740,10 +1782,22 @@ cascade_status_t cascade_set_kernel_shape(cascade_plan_t plan, const int32_t* h_
   p->tc_stages = h_shape[0];
   p->tc_ring = h_shape[1];
   p->tc_group = h_shape[2];
+  p->tc_stage_shape.clear();   // one shape for every stage
   if (p->graph) {
     cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
   }
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_get_stage_shapes(cascade_plan_t plan, int32_t cap, int32_t* h_shape,
+                                          int32_t* n) {
+  Plan* p = plan;
+  if (!p || !n || (cap > 0 && !h_shape)) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  const int size = (int)p->tc_stage_shape.size();
+  for (int k = 0; k < std::min<int>(cap, size); ++k)
+    for (int j = 0; j < 3; ++j) h_shape[3 * k + j] = p->tc_stage_shape[k][j];
+  *n = size;
   return CASCADE_OK;
 }
 

@@ -195,6 +195,9 @@ struct Plan {
   // tensor-core stage kernel shape: operand stages, epilogue ring slots,
   // chunks per epilogue step (0 = heuristic); set by cascade_autotune
   int tc_stages = 0, tc_ring = 0, tc_group = 0;
+  // per stage k of the §3 schedule (forward, dense tiles): the autotuner's
+  // fastest shape for that stage, {0, 0, 0} where the plan-wide shape applies
+  std::vector<std::array<int32_t, 3>> tc_stage_shape;
   bool tuned = false;
   void* last_stream = nullptr;
   // per-launch stage timing

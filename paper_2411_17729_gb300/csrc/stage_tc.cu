@@ -772,6 +772,11 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   const int BN = block_n(m, p.d.precision);
   TcConfig cfg{p.tc_stages, p.tc_ring, p.tc_group};
   if (!tc_config_fits(m, BN, cfg)) cfg = tc_default(m, p.d.precision);
+  if (!reverse && S == 0 && k >= 0 && k < (int)p.tc_stage_shape.size() &&
+      p.tc_stage_shape[k][0] > 0) {
+    const TcConfig ck{p.tc_stage_shape[k][0], p.tc_stage_shape[k][1], p.tc_stage_shape[k][2]};
+    if (tc_config_fits(m, BN, ck)) cfg = ck;
+  }
   const uint32_t row_elems = ROWB / (uint32_t)elem;
   CUtensorMap maps[6];
   std::string err;

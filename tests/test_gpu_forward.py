@@ -313,11 +313,19 @@ def test_autotuned_shape_keeps_parity(lib, precision, m):
     u = torch.as_tensor(w.u, dtype=torch.float32).cuda()
     stages, ring, group = c.autotune(u)
     assert 2 <= stages <= 8 and ring in (2, 4, 6, 8) and group in (1, 2) and ring % group == 0
+    # the per-stage choices: one for each stage 1..N with tiles, all valid shapes
+    per = c.stage_shapes()
+    assert set(per) <= set(range(1, 11)) and len(per) >= 1
+    for s_, r_, g_ in per.values():
+        assert 2 <= s_ <= 8 and r_ in (2, 4, 6, 8) and g_ in (1, 2) and r_ % (2 * g_) == 0
     y = c.forward(u).double().cpu().numpy()
     assert c.device_error() == 0
     yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
     ey, ecx = rel_errors(w, y, yo, OUT_EPS[precision])
     assert ey <= TOL[precision] and ecx <= TOL[precision], (ey, ecx)
+    # an explicit shape applies to every stage
+    c.set_kernel_shape(stages, ring, group)
+    assert c.stage_shapes() == {}
 
 
 @pytest.mark.parametrize("precision,m", [("bf16_split", 256), ("bf16_split", 128), ("fp32", 128),

@@ -103,7 +103,14 @@ enum {
      be invertible.  FP64 scaling and squaring with a [13/13] Pade approximant.
      The backward's dA, dB go through the Frechet derivative of the
      exponential.                                                           */
-  CASCADE_FLAG_ZOH = 32
+  CASCADE_FLAG_ZOH = 32,
+  /* Write v^(1) = Bbar u_l + Abar Bbar u_(l-1) (the first stage, §3) to
+     device memory and read it back in stage 1, instead of forming it on
+     chip inside stage 1 (diagnostics).  Forming it on chip applies to the
+     §3 schedule of tensor-core plans with p = 1 that keep no stage outputs;
+     sequences too short for a stage 1 (N_i = 0) still get v^(1) written,
+     since their output reads it.  Results are the same bit for bit.        */
+  CASCADE_FLAG_NO_FUSED_FIRST = 64
 };
 
 typedef struct cascade_plan_s* cascade_plan_t;

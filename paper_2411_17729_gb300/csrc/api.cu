@@ -221,6 +221,11 @@ int ceil_log2(int64_t L) {
 }
 
 // Stages with shift 2^k >= L do nothing; a sequence of length L runs k = 0..min(N, ceil(log2 L)-1).
+// Largest p for which stage 1 forms v^(1) on chip: its row warps and epilogue
+// form p-term dot products per element, which stays cheaper than the round
+// trip of v^(1) through memory for p = 1 only (measured: p = 4 was slower).
+constexpr int FUSE_FIRST_PMAX = 1;
+
 int effective_N(int N, int64_t L) {
   if (L <= 1) return 0;
   return std::min(N, ceil_log2(L) - 1);
@@ -564,8 +569,12 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
   // buffer holding v^(k) read by stage k, and the one stage k writes
   auto in_buf = [&](int k) { return fwd_buf(*p, k); };
   auto out_buf = [&](int k) { return fwd_buf(*p, k + 1); };
-  // stage 0 fused with v^(0) = Bbar u
-  if (ptc)
+  // stage 0 fused with v^(0) = Bbar u (formed inside stage 1 with fuse_first,
+  // here only for the sequences without a stage 1)
+  if (p->fuse_first)
+    CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), false, st),
+       "first stage");
+  else if (ptc)
     CK(launch_proj_tc_stage0(*p, U, V, p->rows, out_buf(0), false, st), "first stage");
   else if (proj_supported(*p))
     CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), false, st), "first stage");
@@ -1277,6 +1286,18 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     }
   }
   p->maxN = maxN;
+  // Stage 1 forms v^(1) on chip when nothing else needs it in memory; then
+  // the first-stage kernel runs only for the sequences without a stage 1
+  // (N_i = 0), whose output reads v^(1).
+  p->fuse_first = p->d.precision != CASCADE_FP64 && !keeps_states(*p) && !scans(*p) &&
+                  !(p->d.flags & CASCADE_FLAG_NO_FUSED_FIRST) && p->d.p <= FUSE_FIRST_PMAX &&
+                  proj_supported(*p) && maxN >= 1;
+  if (p->fuse_first) {
+    std::vector<Tile> keep;
+    for (const Tile& t : t0s)
+      if (effective_N(p->N_sys[t.sys], t.len) == 0) keep.push_back(t);
+    t0s.swap(keep);
+  }
   // products by powers: the Abar Bbar u term of the first stage on every row
   // l >= 1 (odd rows only in the work-efficient schedule), then the stages
   p->matvecs = 0;

@@ -71,6 +71,9 @@ struct StageArgs {
   const float* D32;       // [nsys, q, p]
   const float* u;         // [rows, p]
   float* y;               // [rows, q]
+  int32_t gen;            // stage 1 with v^(1) formed on chip from u (vin not read)
+  const float* Bb;        // [nsys, m, p] Bbar            (gen)
+  const float* ABb;       // [nsys, m, p] Abar Bbar       (gen)
   int32_t* err;           // device error word
   int32_t* diag;          // where the first bounded wait gave up (5 words) or null
   unsigned long long timeout_ns;
@@ -168,6 +171,9 @@ struct Plan {
   Tile* d_stage0_tiles = nullptr;            // tiles for the first stage (all rows)
   int n_stage0_tiles = 0;
   bool fuse_output = false;
+  // stage 1 forms v^(1) = Bbar u_l + Abar Bbar u_(l-1) on chip; the first-stage
+  // kernel does not run (set per batch)
+  bool fuse_first = false;
   // work-efficient schedule (CASCADE_FLAG_SCAN): its launches in order, each
   // one level k of the up-sweep or the down-sweep over rows 2^(k+1) apart
   struct ScanLevel {

@@ -119,6 +119,10 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
 }
 // Generic-proxy writes to shared memory made visible to the async proxy
 // (tensor core reads of operands).
+// Barrier `id` (1..15) among `nthreads` threads of the block (a multiple of 32).
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

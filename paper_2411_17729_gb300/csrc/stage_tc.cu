@@ -53,6 +53,7 @@ constexpr int BM = 128;
 // warps: 0 TMA producer, 1 MMA issuer, 6 ring manager, 2-5 and 7-10 epilogue
 // (two groups of four, one warp per TMEM lane quadrant in each)
 constexpr int NTHREADS = 352;
+constexpr int GEN_THREADS = 128;              // first-stage row warps (stage 1 on chip)
 constexpr int RING_MAX = 8;                   // staging slots (runtime ring <= 8)
 constexpr uint32_t ROWB = 64;                 // bytes per row of every shared tile
 constexpr uint32_t PLANE_TILE = BM * ROWB;    // one plane of a 128-row chunk: 8 KB
@@ -117,6 +118,39 @@ struct Fmt<4> {
   }
 };
 
+// v[e] += Bbar[col0 + e] . x1 + (Abar Bbar)[col0 + e] . x0 for e < NV, with
+// Bs, ABs the [m, p] coefficient matrices of one system and x1, x0 the p
+// inputs u_l, u_(l-1): the first stage fused with the input projection, with
+// the first-stage kernel's operation order (from v = 0 the same value).
+template <int NV>
+__device__ __forceinline__ void add_first_stage(const float* __restrict__ Bs,
+                                                const float* __restrict__ ABs, int p, int col0,
+                                                const float* x1, const float* x0, float* v) {
+  if (p == 1) {
+#pragma unroll
+    for (int e = 0; e < NV; e += 4) {
+      const float4 b = __ldg(reinterpret_cast<const float4*>(Bs + col0 + e));
+      const float4 a = __ldg(reinterpret_cast<const float4*>(ABs + col0 + e));
+      v[e + 0] += fmaf(a.x, x0[0], b.x * x1[0]);
+      v[e + 1] += fmaf(a.y, x0[0], b.y * x1[0]);
+      v[e + 2] += fmaf(a.z, x0[0], b.z * x1[0]);
+      v[e + 3] += fmaf(a.w, x0[0], b.w * x1[0]);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < NV; ++e) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < p) {
+          acc = fmaf(__ldg(Bs + (int64_t)(col0 + e) * p + j), x1[j], acc);
+          acc = fmaf(__ldg(ABs + (int64_t)(col0 + e) * p + j), x0[j], acc);
+        }
+      v[e] += acc;
+    }
+  }
+}
+
 // Record the first bounded wait that gave up: the error word, and where
 // (site, block, two counters of that wait) in the diagnostic words.
 __device__ __forceinline__ void raise_timeout(const StageArgs& a, volatile int* abort_flag, int site,
@@ -157,8 +191,13 @@ __device__ __forceinline__ Item load_item(const StageArgs& a, int w) {
 // QMAX: 0 = never fuse the output; otherwise the largest q the fused
 // epilogue handles (register accumulators for y).  G: column chunks the
 // epilogue processes per step (their instructions interleave).
-template <int ELEM, int QMAX, int G>
-__global__ void __launch_bounds__(NTHREADS, 1)
+// GEN (stage 1 only): no copy of v^(1) is read.  Four more warps form the
+// operand rows v^(1)_(l-2) from u in shared memory, and the epilogue forms the
+// residual v^(1)_l from u, so the first stage never goes through device memory.
+// Both round v^(1) to the state format as the first-stage kernel does: the
+// results equal those of the path through memory bit for bit.
+template <int ELEM, int QMAX, int G, bool GEN>
+__global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
     stage_tc_kernel(const __grid_constant__ CUtensorMap tm_vhi,
                     const __grid_constant__ CUtensorMap tm_vlo,
                     const __grid_constant__ CUtensorMap tm_phi,
@@ -209,7 +248,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&full[s], GEN ? 2 : 1);   // GEN: the power copies and the row warps
       ptx::mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -276,7 +315,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               break;
             }
             uint8_t* sb_hi = bufs + (size_t)c * stage_bytes + 2 * a_bytes;
-            ptx::mbar_arrive_expect_tx(&full[c], stage_bytes);
+            ptx::mbar_arrive_expect_tx(&full[c], GEN ? 2 * b_bytes : stage_bytes);
             ptx::tma_load_2d(sb_hi, &tm_phi, &full[c], c * KC, prow);
             ptx::tma_load_2d(sb_hi + b_bytes, &tm_plo, &full[c], c * KC, prow);
             issued_parity[c] = 0;
@@ -285,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ptx::griddep_wait();
           waited = true;
           // every armed stage gets its state rows (its barrier expects them)
-          for (int c = 0; c < armed; ++c) {
+          for (int c = 0; c < armed && !GEN; ++c) {
             uint8_t* sa_hi = bufs + (size_t)c * stage_bytes;
             if (args.S) {
               ptx::tma_load_3d(sa_hi, &tm_vhi, &full[c], c * KC, src_y, src_z);
@@ -309,8 +348,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint8_t* sa_lo = sa_hi + a_bytes;
           uint8_t* sb_hi = sa_lo + a_bytes;
           uint8_t* sb_lo = sb_hi + b_bytes;
-          ptx::mbar_arrive_expect_tx(&full[stage], stage_bytes);
-          if (args.S) {
+          ptx::mbar_arrive_expect_tx(&full[stage], GEN ? 2 * b_bytes : stage_bytes);
+          if (GEN) {
+            // the row warps write this stage's operand rows
+          } else if (args.S) {
             ptx::tma_load_3d(sa_hi, &tm_vhi, &full[stage], c * KC, src_y, src_z);
             ptx::tma_load_3d(sa_lo, &tm_vlo, &full[stage], c * KC, src_y, src_z);
           } else {
@@ -419,14 +460,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int x = (lw % args.nblocks) * BN + lcc * CW;
         const int yrow = (int)(lt.seq_row0 + lt.t0);
         uint8_t* sh = ring + (size_t)slot * SLOT_BYTES;
-        ptx::mbar_arrive_expect_tx(&res_full[slot], SLOT_BYTES);
-        if (args.S) {
-          ptx::tma_load_3d(sh, &tm_vhi, &res_full[slot], x, yrow % args.S, yrow / args.S);
-          ptx::tma_load_3d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow % args.S,
-                           yrow / args.S);
+        if (GEN) {
+          ptx::mbar_arrive(&res_full[slot]);   // the epilogue forms the residual from u
         } else {
-          ptx::tma_load_2d(sh, &tm_vhi, &res_full[slot], x, yrow);
-          ptx::tma_load_2d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow);
+          ptx::mbar_arrive_expect_tx(&res_full[slot], SLOT_BYTES);
+          if (args.S) {
+            ptx::tma_load_3d(sh, &tm_vhi, &res_full[slot], x, yrow % args.S, yrow / args.S);
+            ptx::tma_load_3d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow % args.S,
+                             yrow / args.S);
+          } else {
+            ptx::tma_load_2d(sh, &tm_vhi, &res_full[slot], x, yrow);
+            ptx::tma_load_2d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow);
+          }
         }
         ++issued;
         if (++lcc == nch) { lcc = 0; lw += gridDim.x; }
@@ -479,6 +524,61 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (uint32_t h = g; h < issued; ++h)
         ptx::mbar_wait(&res_full[h % RING], (h / RING) & 1u, limit, nullptr);
     }
+  } else if (GEN && warp >= NTHREADS / 32) {
+    // ------------------------------------------------------------ first-stage rows
+    // Operand rows v^(1)_(l-s) = Bbar u_(l-s) + Abar Bbar u_(l-s-1) of each K
+    // chunk, written in the swizzled layout the TMA copy would give (zero where
+    // the source precedes the sequence).  One thread per tile row; thread 0
+    // waits for the stage and the others follow it through named barrier 1.
+    const int r = threadIdx.x - NTHREADS;
+    volatile int* gen_ok = reinterpret_cast<volatile int*>(tmem_slot + 2);
+    ptx::griddep_wait();
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+      const Item it = load_item<QMAX>(args, w);
+      if (it.copy) continue;
+      const int src = it.t.t0 + r - shift;
+      const bool live = it.t.t0 + r < it.t.len && src >= 0;
+      float x1[4] = {0.f, 0.f, 0.f, 0.f}, x0[4] = {0.f, 0.f, 0.f, 0.f};
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j < args.p) {
+            x1[j] = __ldg(args.u + (it.t.seq_row0 + src) * args.p + j);
+            if (src >= 1) x0[j] = __ldg(args.u + (it.t.seq_row0 + src - 1) * args.p + j);
+          }
+      }
+      const float* Bs = args.Bb + (int64_t)it.t.sys * m * args.p;
+      const float* ABs = args.ABb + (int64_t)it.t.sys * m * args.p;
+      bool ok = true;
+      for (int c = 0; c < nkc; ++c) {
+        if (r == 0) *gen_ok = ptx::mbar_wait(&empty[stage], phase ^ 1u, limit, abort_flag) ? 1 : 0;
+        ptx::named_bar_sync(1, GEN_THREADS);
+        if (!*gen_ok) {
+          if (r == 0) raise_timeout(args, abort_flag, 12, w, stage);
+          ok = false;
+          break;
+        }
+        float x[KC];
+#pragma unroll
+        for (int e = 0; e < KC; ++e) x[e] = 0.f;
+        if (live) add_first_stage<KC>(Bs, ABs, args.p, c * KC, x1, x0, x);
+        uint8_t* sa_hi = bufs + (size_t)stage * stage_bytes;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          uint4 hv, lv;
+          Fmt<ELEM>::split16(x + q4 * (KC / 4), hv, lv);
+          *reinterpret_cast<uint4*>(sa_hi + ptx::sw64_offset(r, q4)) = hv;
+          *reinterpret_cast<uint4*>(sa_hi + a_bytes + ptx::sw64_offset(r, q4)) = lv;
+        }
+        ptx::fence_proxy_async_smem();          // visible to the tensor core's reads
+        ptx::named_bar_sync(1, GEN_THREADS);
+        if (r == 0) ptx::mbar_arrive(&full[stage]);
+        if (++stage == S) { stage = 0; phase ^= 1u; }
+      }
+      if (!ok) break;
+    }
   } else {
     // ------------------------------------------------------------ epilogue
     ptx::griddep_wait();                       // before any store to the states or y
@@ -501,6 +601,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool valid = tr < it.t.len;
       const int64_t grow = args.S ? it.t.seq_row0 + (int64_t)r * args.S : it.t.seq_row0 + tr;
       const int abuf = acc_i & 1;
+      float ur[4] = {0.f, 0.f, 0.f, 0.f}, ur1[4] = {0.f, 0.f, 0.f, 0.f};   // GEN: u_l, u_(l-1)
+      const float* Bs = nullptr;
+      const float* ABs = nullptr;
+      if constexpr (GEN) {
+        Bs = args.Bb + (int64_t)it.t.sys * m * args.p;
+        ABs = args.ABb + (int64_t)it.t.sys * m * args.p;
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j < args.p) {
+              ur[j] = __ldg(args.u + (it.t.seq_row0 + tr) * args.p + j);
+              if (tr >= 1) ur1[j] = __ldg(args.u + (it.t.seq_row0 + tr - 1) * args.p + j);
+            }
+        }
+      }
       if (it.copy && tma_out && !it.fused) {
         // the manager forwards the residual as is; acknowledge each chunk once
         // it has arrived, keeping both slot barriers phase-locked
@@ -579,17 +694,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int j = 0; j < CW; ++j) v[h][j] = 0.f;
         }
         uint4 hq[G][4], lq[G][4];
+        if constexpr (GEN) {
+          // residual v^(1)_l of this row from u, rounded to the (hi, lo) pair the
+          // first-stage kernel would have stored, so that results are the same
+          // bit for bit (rows past the sequence end are not stored: zero)
 #pragma unroll
-        for (int h = 0; h < G; ++h)
+          for (int h = 0; h < G; ++h)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            hq[h][c] = *reinterpret_cast<const uint4*>(sh[h] + ptx::sw64_offset(r, c));
-            lq[h][c] = *reinterpret_cast<const uint4*>(sh[h] + PLANE_TILE + ptx::sw64_offset(r, c));
-          }
+            for (int c = 0; c < 4; ++c) {
+              float x[CW / 4];
 #pragma unroll
-        for (int h = 0; h < G; ++h)
+              for (int e = 0; e < CW / 4; ++e) x[e] = 0.f;
+              if (valid)
+                add_first_stage<CW / 4>(Bs, ABs, args.p, it.n0 + (cc + h) * CW + c * (CW / 4), ur,
+                                        ur1, x);
+              Fmt<ELEM>::split16(x, hq[h][c], lq[h][c]);
+              Fmt<ELEM>::add16(hq[h][c], lq[h][c], v[h] + c * (CW / 4));
+            }
+        } else {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) Fmt<ELEM>::add16(hq[h][c], lq[h][c], v[h] + c * (CW / 4));
+          for (int h = 0; h < G; ++h)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              hq[h][c] = *reinterpret_cast<const uint4*>(sh[h] + ptx::sw64_offset(r, c));
+              lq[h][c] =
+                  *reinterpret_cast<const uint4*>(sh[h] + PLANE_TILE + ptx::sw64_offset(r, c));
+            }
+#pragma unroll
+          for (int h = 0; h < G; ++h)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) Fmt<ELEM>::add16(hq[h][c], lq[h][c], v[h] + c * (CW / 4));
+        }
         if (it.fused) {
           if (valid) {
 #pragma unroll
@@ -684,17 +819,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 1) ptx::tmem_dealloc(tmem_base, tmem_cols);
 }
 
-template <int ELEM, int QMAX, int G>
+template <int ELEM, int QMAX, int G, bool GEN>
 cudaError_t launch_variant(const CUtensorMap* maps, const StageArgs& a, int grid, size_t smem,
                            cudaStream_t st) {
-  auto kern = stage_tc_kernel<ELEM, QMAX, G>;
+  auto kern = stage_tc_kernel<ELEM, QMAX, G, GEN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // programmatic dependent launch: the prologue (barriers, TMEM, the first
   // power chunks) overlaps the previous launch's tail on the SMs it leaves free
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(NTHREADS);
+  cfg.blockDim = dim3(GEN ? NTHREADS + GEN_THREADS : NTHREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -819,6 +954,18 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   a.D32 = p.D32;
   a.u = u;
   a.y = y;
+  // stage 1 of a plan that forms v^(1) on chip (one column chunk per step:
+  // the row warps' registers fit only that variant)
+  const bool gen = p.fuse_first && k == 1 && !reverse && S == 0 && u != nullptr;
+  a.gen = gen ? 1 : 0;
+  a.Bb = p.Bbar32;
+  a.ABb = p.ABbar32;
+  if (gen && cfg.group != 1) {
+    const TcConfig c1{cfg.stages, cfg.ring, 1};
+    cfg = tc_config_fits(m, BN, c1) ? c1 : tc_default(m, p.d.precision);
+    a.stages = cfg.stages;
+    a.ring = cfg.ring;
+  }
   a.err = p.err;
   a.diag = p.err + 1;
   a.timeout_ns = 2000000000ull;
@@ -831,9 +978,10 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   // the backward recomputes are not)
   const bool fuse = p.fuse_output && !reverse && y != nullptr;
   const int G = cfg.group;
-#define CASCADE_TC_DISPATCH(E, Q)                                               \
-  return G == 2 ? launch_variant<E, Q, 2>(maps, a, grid, smem, st)               \
-                : launch_variant<E, Q, 1>(maps, a, grid, smem, st)
+#define CASCADE_TC_DISPATCH(E, Q)                                                     \
+  return gen      ? launch_variant<E, Q, 1, true>(maps, a, grid, smem, st)             \
+         : G == 2 ? launch_variant<E, Q, 2, false>(maps, a, grid, smem, st)            \
+                  : launch_variant<E, Q, 1, false>(maps, a, grid, smem, st)
   if (elem == 2) {
     if (!fuse) CASCADE_TC_DISPATCH(2, 0);
     if (q == 1) CASCADE_TC_DISPATCH(2, 1);

@@ -178,6 +178,47 @@ def test_tc_unfused_matches_fused(lib, precision):
     assert ey < 1e-5
 
 
+@pytest.mark.parametrize("precision,m,p,q", [("bf16_split", 256, 1, 1), ("bf16_split", 128, 1, 4),
+                                             ("fp32", 128, 1, 4), ("bf16_split", 512, 1, 3),
+                                             ("fp32", 64, 1, 1), ("bf16_split", 192, 1, 2)])
+def test_first_stage_on_chip(lib, precision, m, p, q):
+    """Stage 1 forming v^(1) = Bbar u_l + Abar Bbar u_(l-1) on chip gives the
+    results of the path that writes v^(1) to memory bit for bit, and matches
+    the oracle.  Ragged lengths with sequences too short for a stage 1 (their
+    v^(1) is still written), one system per sequence."""
+    import torch
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_NO_FUSED_FIRST
+    lengths = (3, 1, 127, 128, 129, 2, 700, 1000)
+    if q == 1:
+        w = wl.precision_form(m=m, L=8, batch=len(lengths), N=10)
+    else:
+        w = wl.differentiation_form(m=m, p=p, q=q, L=8, batch=len(lengths), N=10, delta=1e-2)
+    rng = np.random.default_rng(11)
+    w.offsets = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    w.u = rng.standard_normal((int(w.offsets[-1]), p))
+    w.precision = precision
+    c, y1, yo = check(lib, w, precision)
+    w2 = cast_inputs(w, precision)
+    _, y2 = run_gpu(lib, w2, precision, flags=CASCADE_FLAG_NO_FUSED_FIRST)
+    assert np.array_equal(y1, y2)
+    # without sequences shorter than 3 steps no first-stage launch remains
+    w3 = cast_inputs(w, precision)
+    keep = [i for i, L in enumerate(lengths) if L >= 3]
+    w3 = w3.subset(keep)
+    launches = []
+    for flags in (0, CASCADE_FLAG_NO_FUSED_FIRST):
+        c3 = lib.from_workload(w3, precision=precision, flags=flags)
+        u3 = torch.as_tensor(w3.u, dtype=torch.float32).cuda().contiguous()
+        c3.forward(u3)
+        torch.cuda.synchronize()
+        n0 = c3.lib.cascade_launch_count()
+        c3.forward(u3)
+        torch.cuda.synchronize()
+        launches.append(c3.lib.cascade_launch_count() - n0)
+        assert c3.device_error() == 0
+    assert launches[0] == launches[1] - 1, launches
+
+
 def test_output_fused_query(lib):
     """cascade_get_output_fused: y formed in the last stage's epilogue for
     q <= 4 when a stage tile spans all columns (not FP64, not opted out)."""

@@ -207,6 +207,13 @@ cascade_status_t cascade_get_matvec_count(cascade_plan_t plan, int64_t* h_count)
    unless created with CASCADE_FLAG_NO_FUSED_OUTPUT.  *h_fused = 1 or 0. */
 cascade_status_t cascade_get_output_fused(cascade_plan_t plan, int32_t* h_fused);
 
+/* Whether stage 1 of the current batch forms v^(1) = Bbar u_l + Abar Bbar
+   u_(l-1) on chip (§3 schedule, p = 1, no stage outputs kept, not disabled
+   by CASCADE_FLAG_NO_FUSED_FIRST): stage 1 then reads u instead of v^(1)
+   and the first-stage kernel runs only for sequences with N_i = 0.
+   *h_fused = 1 or 0; CASCADE_ERR_STATE before cascade_set_batch. */
+cascade_status_t cascade_get_first_fused(cascade_plan_t plan, int32_t* h_fused);
+
 /* Size of the fixed device scratch array behind cascade_forward_fixed_scratch. */
 #define CASCADE_FIXED_SCRATCH_BYTES ((size_t)32 << 20)
 

@@ -60,6 +60,7 @@ SIGNATURES = [
     ("cascade_get_seq_N", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
     ("cascade_get_matvec_count", C.c_int, [cascade_plan_t, C.POINTER(C.c_int64)]),
     ("cascade_get_output_fused", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
+    ("cascade_get_first_fused", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
     ("cascade_get_stage_shapes", C.c_int,
      [cascade_plan_t, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("cascade_workspace_size", C.c_int, [cascade_plan_t, C.POINTER(C.c_size_t)]),

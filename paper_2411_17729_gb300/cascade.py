@@ -172,6 +172,12 @@ class Cascade:
         shape = (C.c_int32 * 3)(stages, ring, group)
         self._check(self.lib.cascade_set_kernel_shape(self.plan, shape))
 
+    def first_fused(self):
+        """True when stage 1 of the current batch forms v^(1) on chip."""
+        f = C.c_int32()
+        self._check(self.lib.cascade_get_first_fused(self.plan, C.byref(f)))
+        return bool(f.value)
+
     def stage_shapes(self, cap=64):
         """{stage k: (stages, ring slots, chunks per step)} chosen per stage by autotune."""
         buf = (C.c_int32 * (3 * cap))()

@@ -1598,6 +1598,14 @@ cascade_status_t cascade_get_output_fused(cascade_plan_t plan, int32_t* h_fused)
   return CASCADE_OK;
 }
 
+cascade_status_t cascade_get_first_fused(cascade_plan_t plan, int32_t* h_fused) {
+  Plan* p = plan;
+  if (!p || !h_fused) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  if (!p->have_batch) return fail(p, CASCADE_ERR_STATE, "no batch set");
+  *h_fused = p->fuse_first ? 1 : 0;
+  return CASCADE_OK;
+}
+
 cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes) {
   Plan* p = plan;
   if (!p || !bytes) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");

@@ -198,8 +198,10 @@ def test_first_stage_on_chip(lib, precision, m, p, q):
     w.u = rng.standard_normal((int(w.offsets[-1]), p))
     w.precision = precision
     c, y1, yo = check(lib, w, precision)
+    assert c.first_fused()
     w2 = cast_inputs(w, precision)
-    _, y2 = run_gpu(lib, w2, precision, flags=CASCADE_FLAG_NO_FUSED_FIRST)
+    c2, y2 = run_gpu(lib, w2, precision, flags=CASCADE_FLAG_NO_FUSED_FIRST)
+    assert not c2.first_fused()
     assert np.array_equal(y1, y2)
     # without sequences shorter than 3 steps no first-stage launch remains
     w3 = cast_inputs(w, precision)

@@ -66,25 +66,32 @@ struct Fmt;
 template <>
 struct Fmt<2> {
   static constexpr int CW = 32;
+  // a BF16 pair word as two FP32 lanes (a BF16 value is the top half of the
+  // FP32 with the same bits)
+  static __device__ __forceinline__ uint64_t widen(uint32_t w) {
+    return ptx::f2_pack(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
+  // v += hi + lo, two lanes per operation
   static __device__ __forceinline__ void add16(uint4 h, uint4 l, float* v) {
     const uint32_t aw[4] = {h.x, h.y, h.z, h.w};
     const uint32_t bw[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&aw[j]));
-      const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bw[j]));
-      v[2 * j] += fa.x + fb.x;
-      v[2 * j + 1] += fa.y + fb.y;
+      const uint64_t t = ptx::f2_add(widen(aw[j]), widen(bw[j]));
+      const float2 r = ptx::f2_unpack(ptx::f2_add(ptx::f2_pack(v[2 * j], v[2 * j + 1]), t));
+      v[2 * j] = r.x;
+      v[2 * j + 1] = r.y;
     }
   }
+  // hi = RN_bf16(x), lo = RN_bf16(x - hi)
   static __device__ __forceinline__ void split16(const float* v, uint4& h, uint4& l) {
     uint32_t hw[4], lw[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-      const float2 hf = __bfloat1622float2(hh);
-      const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
       hw[j] = *reinterpret_cast<const uint32_t*>(&hh);
+      const float2 d = ptx::f2_unpack(ptx::f2_sub(ptx::f2_pack(v[2 * j], v[2 * j + 1]), widen(hw[j])));
+      const __nv_bfloat162 ll = __floats2bfloat162_rn(d.x, d.y);
       lw[j] = *reinterpret_cast<const uint32_t*>(&ll);
     }
     h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -127,14 +134,22 @@ __device__ __forceinline__ void add_first_stage(const float* __restrict__ Bs,
                                                 const float* __restrict__ ABs, int p, int col0,
                                                 const float* x1, const float* x0, float* v) {
   if (p == 1) {
+    // v += fma(ABbar, u_(l-1), Bbar * u_l), two lanes per operation
+    const uint64_t u1 = ptx::f2_pack(x1[0], x1[0]), u0 = ptx::f2_pack(x0[0], x0[0]);
 #pragma unroll
     for (int e = 0; e < NV; e += 4) {
       const float4 b = __ldg(reinterpret_cast<const float4*>(Bs + col0 + e));
       const float4 a = __ldg(reinterpret_cast<const float4*>(ABs + col0 + e));
-      v[e + 0] += fmaf(a.x, x0[0], b.x * x1[0]);
-      v[e + 1] += fmaf(a.y, x0[0], b.y * x1[0]);
-      v[e + 2] += fmaf(a.z, x0[0], b.z * x1[0]);
-      v[e + 3] += fmaf(a.w, x0[0], b.w * x1[0]);
+      const uint64_t s01 =
+          ptx::f2_fma(ptx::f2_pack(a.x, a.y), u0, ptx::f2_mul(ptx::f2_pack(b.x, b.y), u1));
+      const uint64_t s23 =
+          ptx::f2_fma(ptx::f2_pack(a.z, a.w), u0, ptx::f2_mul(ptx::f2_pack(b.z, b.w), u1));
+      const float2 r01 = ptx::f2_unpack(ptx::f2_add(ptx::f2_pack(v[e], v[e + 1]), s01));
+      const float2 r23 = ptx::f2_unpack(ptx::f2_add(ptx::f2_pack(v[e + 2], v[e + 3]), s23));
+      v[e] = r01.x;
+      v[e + 1] = r01.y;
+      v[e + 2] = r23.x;
+      v[e + 3] = r23.y;
     }
   } else {
 #pragma unroll

@@ -28,9 +28,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cascade states/s (fwd)"
 # DRAM bytes (read + write) per launch of the stage kernel on the precision workload: an ncu
-# capture of stage k = 8 on 8 of the 64 sequences measured 226.29 MB (138.97 MB read, 87.32 MB
+# capture of stage k = 8 on 8 of the 64 sequences measured 225.75 MB (138.22 MB read, 87.53 MB
 # written); the traffic grows with the rows processed, so a full launch moves 8x that.
-TRAFFIC_NOTE = {"bytes_per_launch": 8 * 226.29e6,
+TRAFFIC_NOTE = {"bytes_per_launch": 8 * 225.75e6,
                 "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of stage_tc_kernel, "
                         "stage 8, 8 of 64 sequences, scaled x8 to the full launch"}
 WORKLOAD = ("precision_form: HiPPO-LegS m=256 p=q=1, 64 seqs x L=16384, N=13, "

@@ -105,23 +105,31 @@ struct Fmt<2> {
 template <>
 struct Fmt<4> {
   static constexpr int CW = 16;
+  // v += hi + lo, two lanes per operation
   static __device__ __forceinline__ void add16(uint4 h, uint4 l, float* v) {
-    v[0] += __uint_as_float(h.x) + __uint_as_float(l.x);
-    v[1] += __uint_as_float(h.y) + __uint_as_float(l.y);
-    v[2] += __uint_as_float(h.z) + __uint_as_float(l.z);
-    v[3] += __uint_as_float(h.w) + __uint_as_float(l.w);
+    const uint64_t t01 = ptx::f2_add(ptx::f2_pack(__uint_as_float(h.x), __uint_as_float(h.y)),
+                                     ptx::f2_pack(__uint_as_float(l.x), __uint_as_float(l.y)));
+    const uint64_t t23 = ptx::f2_add(ptx::f2_pack(__uint_as_float(h.z), __uint_as_float(h.w)),
+                                     ptx::f2_pack(__uint_as_float(l.z), __uint_as_float(l.w)));
+    const float2 r01 = ptx::f2_unpack(ptx::f2_add(ptx::f2_pack(v[0], v[1]), t01));
+    const float2 r23 = ptx::f2_unpack(ptx::f2_add(ptx::f2_pack(v[2], v[3]), t23));
+    v[0] = r01.x;
+    v[1] = r01.y;
+    v[2] = r23.x;
+    v[3] = r23.y;
   }
   static __device__ __forceinline__ void split16(const float* v, uint4& h, uint4& l) {
-    float hv[4], lv[4];
+    float hv[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      hv[j] = ptx::tf32_rna(v[j]);
-      lv[j] = ptx::tf32_rna(v[j] - hv[j]);
-    }
+    for (int j = 0; j < 4; ++j) hv[j] = ptx::tf32_rna(v[j]);
+    const float2 d01 =
+        ptx::f2_unpack(ptx::f2_sub(ptx::f2_pack(v[0], v[1]), ptx::f2_pack(hv[0], hv[1])));
+    const float2 d23 =
+        ptx::f2_unpack(ptx::f2_sub(ptx::f2_pack(v[2], v[3]), ptx::f2_pack(hv[2], hv[3])));
     h = make_uint4(__float_as_uint(hv[0]), __float_as_uint(hv[1]), __float_as_uint(hv[2]),
                    __float_as_uint(hv[3]));
-    l = make_uint4(__float_as_uint(lv[0]), __float_as_uint(lv[1]), __float_as_uint(lv[2]),
-                   __float_as_uint(lv[3]));
+    l = make_uint4(__float_as_uint(ptx::tf32_rna(d01.x)), __float_as_uint(ptx::tf32_rna(d01.y)),
+                   __float_as_uint(ptx::tf32_rna(d23.x)), __float_as_uint(ptx::tf32_rna(d23.y)));
   }
 };
 

@@ -254,6 +254,7 @@ void free_batch(Plan* p) {
   dfree(p->d_red_scratch);
   p->d_red_scratch = nullptr;
   p->red_scratch_bytes = 0;
+  for (Tile* t : p->d_adj_tiles) dfree(t);
   p->d_adj_tiles.clear();
   p->n_adj_tiles.clear();
   p->saved_ws = nullptr;
@@ -1504,10 +1505,17 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
        "upload sequences");
   }
   if (save) {
-    // adjoint stage k walks the same tiles as forward stage k (all tiles of the
-    // sequences with N_i >= k)
-    p->d_adj_tiles = p->d_tiles;
+    // adjoint stage k walks the tiles of forward stage k (all tiles of the
+    // sequences with N_i >= k) in reverse time order: its source rows l + s
+    // then lie in tiles walked just before, and come from L2 as the forward's
+    // sources l - s do (each tile's result does not depend on the order)
+    p->d_adj_tiles.assign(p->d_tiles.size(), nullptr);
     p->n_adj_tiles = p->n_tiles;
+    for (size_t k = 0; k < p->h_tiles.size(); ++k) {
+      if (p->h_tiles[k].empty()) continue;
+      const std::vector<Tile> rev(p->h_tiles[k].rbegin(), p->h_tiles[k].rend());
+      CK(upload(rev, &p->d_adj_tiles[k]), "upload adjoint schedule");
+    }
     CK(upload(all, &p->d_all_tiles), "upload tiles");
     p->n_all_tiles = (int)all.size();
     // Time-reduction chunks: runs of up to CH consecutive tiles of one system,

@@ -511,7 +511,11 @@ def main():
         upd = nmv.value - sum(int(L) // 2 for L in Ls)      # products made on the tensor cores
         nlev = len(lev_ms)
         lev_tot = sum(sum(v) for v in lev_ms.values()) / args.steps
-        lev_bytes = 3 * esize * m * upd + nlev * w.nsys * m * m * esize
+        # destination row read and written, source row read; with the even rows of
+        # v^(1) formed on chip the last level reads only its source rows and u
+        upd0 = sum(max(int(L) - 1, 0) // 2 for L in Ls) if cs.first_fused() else 0
+        lev_bytes = (3 * esize * m * (upd - upd0) + (esize * m + 4 * w.p) * upd0
+                     + nlev * w.nsys * m * m * esize)
         lev_gbs = lev_bytes / (lev_tot / 1000.0) / 1e9 if lev_tot > 0 else 0.0
         scan = {"value": whole_job_rate(states_per_step, world, scan_ms), "unit": "states/s",
                 "ms_per_step": scan_ms, "matvecs_per_step": int(nmv.value),

@@ -105,11 +105,13 @@ enum {
      exponential.                                                           */
   CASCADE_FLAG_ZOH = 32,
   /* Write v^(1) = Bbar u_l + Abar Bbar u_(l-1) (the first stage, §3) to
-     device memory and read it back in stage 1, instead of forming it on
-     chip inside stage 1 (diagnostics).  Forming it on chip applies to the
-     §3 schedule of tensor-core plans with p = 1 that keep no stage outputs;
-     sequences too short for a stage 1 (N_i = 0) still get v^(1) written,
-     since their output reads it.  Results are the same bit for bit.        */
+     device memory and read it back, instead of forming it on chip where it
+     is used (diagnostics).  Forming it on chip applies to tensor-core plans
+     with p = 1: on the §3 schedule (no stage outputs kept) inside stage 1,
+     with sequences too short for a stage 1 (N_i = 0) still written since
+     their output reads it; on the work-efficient schedule with the output
+     fused, for the even rows in the last down-sweep level.  Results are the
+     same bit for bit (cascade_get_first_fused).                           */
   CASCADE_FLAG_NO_FUSED_FIRST = 64
 };
 
@@ -207,11 +209,14 @@ cascade_status_t cascade_get_matvec_count(cascade_plan_t plan, int64_t* h_count)
    unless created with CASCADE_FLAG_NO_FUSED_OUTPUT.  *h_fused = 1 or 0. */
 cascade_status_t cascade_get_output_fused(cascade_plan_t plan, int32_t* h_fused);
 
-/* Whether stage 1 of the current batch forms v^(1) = Bbar u_l + Abar Bbar
-   u_(l-1) on chip (§3 schedule, p = 1, no stage outputs kept, not disabled
-   by CASCADE_FLAG_NO_FUSED_FIRST): stage 1 then reads u instead of v^(1)
-   and the first-stage kernel runs only for sequences with N_i = 0.
-   *h_fused = 1 or 0; CASCADE_ERR_STATE before cascade_set_batch. */
+/* Whether first-stage values v^(1) = Bbar u_l + Abar Bbar u_(l-1) are formed
+   on chip for the current batch instead of read from memory (p = 1, not
+   disabled by CASCADE_FLAG_NO_FUSED_FIRST).  §3 schedule (no stage outputs
+   kept): stage 1 reads u instead of v^(1), and the first-stage kernel runs
+   only for sequences with N_i = 0.  Work-efficient schedule (fused output):
+   the first level stores only the odd rows and row 0, and the last
+   down-sweep level forms the even rows' v^(1) = Bbar u_l from u and writes
+   only y.  *h_fused = 1 or 0; CASCADE_ERR_STATE before cascade_set_batch. */
 cascade_status_t cascade_get_first_fused(cascade_plan_t plan, int32_t* h_fused);
 
 /* Size of the fixed device scratch array behind cascade_forward_fixed_scratch. */

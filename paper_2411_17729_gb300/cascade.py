@@ -173,7 +173,7 @@ class Cascade:
         self._check(self.lib.cascade_set_kernel_shape(self.plan, shape))
 
     def first_fused(self):
-        """True when stage 1 of the current batch forms v^(1) on chip."""
+        """True when the current batch forms first-stage values v^(1) on chip."""
         f = C.c_int32()
         self._check(self.lib.cascade_get_first_fused(self.plan, C.byref(f)))
         return bool(f.value)

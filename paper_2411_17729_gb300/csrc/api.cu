@@ -528,7 +528,9 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
     if (ptc)
       CK(launch_proj_tc_stage0(*p, U, V, p->scan_rows_cap, 0, true, st), "first level");
     else
-      CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, 0, true, st), "first level");
+      CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, 0,
+                            p->scan_even_on_chip ? 2 : 1, st),
+         "first level");
     for (size_t li = 0; li <= p->scan.size(); ++li) {
       if ((int)li == p->scan_top_pos && p->scan_top_k0 >= 0 && p->n_top_seqs > 0) {
         // levels k >= k0, up and down, one block per sequence
@@ -547,7 +549,8 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
       if (timing && lv.n > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
       CK(launch_stage_tc_strided(*p, lv.k, 2 << lv.k, lv.d_tiles, lv.n,
                                  (uint64_t)p->scan_rows_cap, V.hi(0), V.lo(0),
-                                 static_cast<const float*>(u), static_cast<float*>(y), st),
+                                 static_cast<const float*>(u), static_cast<float*>(y), st,
+                                 p->scan_even_on_chip && lv.down && lv.k == 0),
          "scan level");
       if (timing && lv.n > 0) {
         CK(cudaEventRecord(p->ev[2 * p->n_ev + 1], st), "event");
@@ -573,12 +576,12 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
   // stage 0 fused with v^(0) = Bbar u (formed inside stage 1 with fuse_first,
   // here only for the sequences without a stage 1)
   if (p->fuse_first)
-    CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), false, st),
+    CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), 0, st),
        "first stage");
   else if (ptc)
     CK(launch_proj_tc_stage0(*p, U, V, p->rows, out_buf(0), false, st), "first stage");
   else if (proj_supported(*p))
-    CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), false, st), "first stage");
+    CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), 0, st), "first stage");
   else
     CK(launch_stage0(*p, u, V.hi(out_buf(0)), V.lo(out_buf(0)), st), "first stage");
   for (int k = 1; k <= p->maxN; ++k) {
@@ -1293,6 +1296,14 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
   p->fuse_first = p->d.precision != CASCADE_FP64 && !keeps_states(*p) && !scans(*p) &&
                   !(p->d.flags & CASCADE_FLAG_NO_FUSED_FIRST) && p->d.p <= FUSE_FIRST_PMAX &&
                   proj_supported(*p) && maxN >= 1;
+  // The work-efficient schedule reads the even rows of v^(1) only in its last
+  // down-sweep level, which with the output fused writes nothing but y: that
+  // level forms them from u, and the first level stores only the odd rows and
+  // row 0 (whose y the row-output kernel forms).
+  p->scan_even_on_chip = scans(*p) && p->fuse_output &&
+                         !(p->d.flags & CASCADE_FLAG_NO_FUSED_FIRST) &&
+                         p->d.p <= FUSE_FIRST_PMAX && proj_supported(*p) &&
+                         !proj_tc_supported(*p);
   if (p->fuse_first) {
     std::vector<Tile> keep;
     for (const Tile& t : t0s)
@@ -1610,7 +1621,7 @@ cascade_status_t cascade_get_first_fused(cascade_plan_t plan, int32_t* h_fused) 
   Plan* p = plan;
   if (!p || !h_fused) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
   if (!p->have_batch) return fail(p, CASCADE_ERR_STATE, "no batch set");
-  *h_fused = p->fuse_first ? 1 : 0;
+  *h_fused = (p->fuse_first || p->scan_even_on_chip) ? 1 : 0;
   return CASCADE_OK;
 }
 

@@ -174,6 +174,9 @@ struct Plan {
   // stage 1 forms v^(1) = Bbar u_l + Abar Bbar u_(l-1) on chip; the first-stage
   // kernel does not run (set per batch)
   bool fuse_first = false;
+  // work-efficient schedule: the first level stores only odd rows (and row 0),
+  // the last down-sweep level forms its even rows' v^(1) from u (set per batch)
+  bool scan_even_on_chip = false;
   // work-efficient schedule (CASCADE_FLAG_SCAN): its launches in order, each
   // one level k of the up-sweep or the down-sweep over rows 2^(k+1) apart
   struct ScanLevel {
@@ -251,9 +254,12 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
 // In-place stage k over rows S apart (the work-efficient schedule); the state
 // planes hold rows_cap rows, a multiple of S.  Tiles flagged TILE_FINAL_FUSED
 // also form y = C v + D u for their rows (u, y may be null otherwise).
+// even_resid: the destination rows are even rows of the work-efficient
+// schedule's last level; their v^(1) = Bbar u is formed from u, not read, and
+// only y is written.
 cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,
                                     uint64_t rows_cap, void* v_hi, void* v_lo, const float* u,
-                                    float* y, cudaStream_t st);
+                                    float* y, cudaStream_t st, bool even_resid = false);
 // Workspace buffer j of a family of equally sized state buffers.
 struct Bufs {
   uint8_t* base;
@@ -318,7 +324,7 @@ cudaError_t launch_proj_tc_adj_init(const Plan& p, const Bufs& G, const Bufs& W,
 cudaError_t launch_proj_tc_du(const Plan& p, const Bufs& G, const Bufs& W, int wbuf, float* du,
                               cudaStream_t st);
 cudaError_t launch_proj_stage0(const Plan& p, const float* u, const Bufs& V, int buf,
-                               bool odd_only, cudaStream_t st);
+                               int odd_mode, cudaStream_t st);
 cudaError_t launch_proj_adj_init(const Plan& p, const float* G, const Bufs& W, cudaStream_t st);
 cudaError_t launch_proj_output(const Plan& p, const float* u, float* y, const Bufs& V,
                                cudaStream_t st);

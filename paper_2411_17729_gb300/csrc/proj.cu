@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(256) expand_kernel(const Tile* __restrict__ ti
   for (int i = 0; i < 4; ++i) {
     const int r = rg + 32 * i;
     if (t.t0 + r >= t.len) continue;
+    if (odd_only == 2 && ((t.t0 + r) & 1) == 0 && t.t0 + r != 0) continue;   // formed later
     store8<FMT>(hi, lo, (t.seq_row0 + t.t0 + r) * (int64_t)m + c, acc[i]);
   }
 }
@@ -404,6 +405,7 @@ __global__ void __launch_bounds__(256, EXPAND_BLOCKS_PER_SM)
           }
         }
       }
+      if (odd_only == 2 && !(l & 1) && l != 0) continue;   // formed later from u
       store8<FMT>(hi, lo, (t.seq_row0 + l) * (int64_t)m + c0, acc);
     }
   }
@@ -622,15 +624,17 @@ bool proj_supported(const Plan& p) {
 }
 
 // v^(1) = Bbar u_l + (Abar Bbar) u_(l-1) into state buffer `buf` (first stage);
-// odd_only: the second term on odd l only (first up-sweep level).
+// odd_mode 1: the second term on odd l only (first up-sweep level); 2: as 1,
+// and of the even rows only row 0 is stored (the last down-sweep level forms
+// the others from u).
 cudaError_t launch_proj_stage0(const Plan& p, const float* u, const Bufs& V, int buf,
-                               bool odd_only, cudaStream_t st) {
+                               int odd_mode, cudaStream_t st) {
   if (p.n_stage0_tiles == 0) return cudaSuccess;
   const int m = p.d.m, pp = p.d.p;
   const Coef B{p.Bbar32, (int64_t)m * pp, pp, 1};     // Bbar [m, p]: (c, j)
   const Coef AB{p.ABbar32, (int64_t)m * pp, pp, 1};
   return expand_dispatch<true>(p.d.precision, p.num_sms, p.d_stage0_tiles, p.n_stage0_tiles, m,
-                               pp, u, pp, B, AB, V, 0, buf, odd_only ? 1 : 0, st);
+                               pp, u, pp, B, AB, V, 0, buf, odd_mode, st);
 }
 
 // W^(N_i+1) = C^T G into adjoint buffer (N_i + 1) & 1 of every tile.

@@ -214,13 +214,17 @@ __device__ __forceinline__ Item load_item(const StageArgs& a, int w) {
 // QMAX: 0 = never fuse the output; otherwise the largest q the fused
 // epilogue handles (register accumulators for y).  G: column chunks the
 // epilogue processes per step (their instructions interleave).
-// GEN (stage 1 only): no copy of v^(1) is read.  Four more warps form the
-// operand rows v^(1)_(l-2) from u in shared memory, and the epilogue forms the
-// residual v^(1)_l from u, so the first stage never goes through device memory.
-// Both round v^(1) to the state format as the first-stage kernel does: the
-// results equal those of the path through memory bit for bit.
-template <int ELEM, int QMAX, int G, bool GEN>
-__global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
+// GEN = 1 (stage 1 of the §3 schedule): no copy of v^(1) is read.  Four more
+// warps form the operand rows v^(1)_(l-2) from u in shared memory, and the
+// epilogue forms the residual v^(1)_l from u, so the first stage never goes
+// through device memory.  GEN = 2 (the last down-sweep level of the
+// work-efficient schedule, rows 2 apart): the destination rows are even, and
+// an even row still holds v^(1)_l = Bbar u_l there; the epilogue forms that
+// residual from u, the operand rows come by TMA as usual.  Both round v^(1) to
+// the state format as the first-stage kernel does: the results equal those of
+// the path through memory bit for bit.
+template <int ELEM, int QMAX, int G, int GEN>
+__global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 1)
     stage_tc_kernel(const __grid_constant__ CUtensorMap tm_vhi,
                     const __grid_constant__ CUtensorMap tm_vlo,
                     const __grid_constant__ CUtensorMap tm_phi,
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      ptx::mbar_init(&full[s], GEN ? 2 : 1);   // GEN: the power copies and the row warps
+      ptx::mbar_init(&full[s], GEN == 1 ? 2 : 1);   // the power copies and the row warps
       ptx::mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
               break;
             }
             uint8_t* sb_hi = bufs + (size_t)c * stage_bytes + 2 * a_bytes;
-            ptx::mbar_arrive_expect_tx(&full[c], GEN ? 2 * b_bytes : stage_bytes);
+            ptx::mbar_arrive_expect_tx(&full[c], GEN == 1 ? 2 * b_bytes : stage_bytes);
             ptx::tma_load_2d(sb_hi, &tm_phi, &full[c], c * KC, prow);
             ptx::tma_load_2d(sb_hi + b_bytes, &tm_plo, &full[c], c * KC, prow);
             issued_parity[c] = 0;
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
           ptx::griddep_wait();
           waited = true;
           // every armed stage gets its state rows (its barrier expects them)
-          for (int c = 0; c < armed && !GEN; ++c) {
+          for (int c = 0; c < armed && GEN != 1; ++c) {
             uint8_t* sa_hi = bufs + (size_t)c * stage_bytes;
             if (args.S) {
               ptx::tma_load_3d(sa_hi, &tm_vhi, &full[c], c * KC, src_y, src_z);
@@ -371,8 +375,8 @@ __global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
           uint8_t* sa_lo = sa_hi + a_bytes;
           uint8_t* sb_hi = sa_lo + a_bytes;
           uint8_t* sb_lo = sb_hi + b_bytes;
-          ptx::mbar_arrive_expect_tx(&full[stage], GEN ? 2 * b_bytes : stage_bytes);
-          if (GEN) {
+          ptx::mbar_arrive_expect_tx(&full[stage], GEN == 1 ? 2 * b_bytes : stage_bytes);
+          if (GEN == 1) {
             // the row warps write this stage's operand rows
           } else if (args.S) {
             ptx::tma_load_3d(sa_hi, &tm_vhi, &full[stage], c * KC, src_y, src_z);
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
         const int x = (lw % args.nblocks) * BN + lcc * CW;
         const int yrow = (int)(lt.seq_row0 + lt.t0);
         uint8_t* sh = ring + (size_t)slot * SLOT_BYTES;
-        if (GEN) {
+        if (GEN != 0) {
           ptx::mbar_arrive(&res_full[slot]);   // the epilogue forms the residual from u
         } else {
           ptx::mbar_arrive_expect_tx(&res_full[slot], SLOT_BYTES);
@@ -547,7 +551,7 @@ __global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
       for (uint32_t h = g; h < issued; ++h)
         ptx::mbar_wait(&res_full[h % RING], (h / RING) & 1u, limit, nullptr);
     }
-  } else if (GEN && warp >= NTHREADS / 32) {
+  } else if (GEN == 1 && warp >= NTHREADS / 32) {
     // ------------------------------------------------------------ first-stage rows
     // Operand rows v^(1)_(l-s) = Bbar u_(l-s) + Abar Bbar u_(l-s-1) of each K
     // chunk, written in the swizzled layout the TMA copy would give (zero where
@@ -624,18 +628,19 @@ __global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
       const bool valid = tr < it.t.len;
       const int64_t grow = args.S ? it.t.seq_row0 + (int64_t)r * args.S : it.t.seq_row0 + tr;
       const int abuf = acc_i & 1;
-      float ur[4] = {0.f, 0.f, 0.f, 0.f}, ur1[4] = {0.f, 0.f, 0.f, 0.f};   // GEN: u_l, u_(l-1)
+      float ur[4] = {0.f, 0.f, 0.f, 0.f}, ur1[4] = {0.f, 0.f, 0.f, 0.f};   // u_l, u_(l-1)
       const float* Bs = nullptr;
       const float* ABs = nullptr;
-      if constexpr (GEN) {
+      if constexpr (GEN != 0) {
         Bs = args.Bb + (int64_t)it.t.sys * m * args.p;
         ABs = args.ABb + (int64_t)it.t.sys * m * args.p;
         if (valid) {
+          // GEN = 2: an even row of the work-efficient schedule, v^(1) = Bbar u_l
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             if (j < args.p) {
-              ur[j] = __ldg(args.u + (it.t.seq_row0 + tr) * args.p + j);
-              if (tr >= 1) ur1[j] = __ldg(args.u + (it.t.seq_row0 + tr - 1) * args.p + j);
+              ur[j] = __ldg(args.u + grow * args.p + j);
+              if (GEN == 1 && tr >= 1) ur1[j] = __ldg(args.u + (grow - 1) * args.p + j);
             }
         }
       }
@@ -717,7 +722,7 @@ __global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
             for (int j = 0; j < CW; ++j) v[h][j] = 0.f;
         }
         uint4 hq[G][4], lq[G][4];
-        if constexpr (GEN) {
+        if constexpr (GEN != 0) {
           // residual v^(1)_l of this row from u, rounded to the (hi, lo) pair the
           // first-stage kernel would have stored, so that results are the same
           // bit for bit (rows past the sequence end are not stored: zero)
@@ -842,7 +847,7 @@ __global__ void __launch_bounds__(GEN ? NTHREADS + GEN_THREADS : NTHREADS, 1)
   if (warp == 1) ptx::tmem_dealloc(tmem_base, tmem_cols);
 }
 
-template <int ELEM, int QMAX, int G, bool GEN>
+template <int ELEM, int QMAX, int G, int GEN>
 cudaError_t launch_variant(const CUtensorMap* maps, const StageArgs& a, int grid, size_t smem,
                            cudaStream_t st) {
   auto kern = stage_tc_kernel<ELEM, QMAX, G, GEN>;
@@ -852,7 +857,7 @@ cudaError_t launch_variant(const CUtensorMap* maps, const StageArgs& a, int grid
   // power chunks) overlaps the previous launch's tail on the SMs it leaves free
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(GEN ? NTHREADS + GEN_THREADS : NTHREADS);
+  cfg.blockDim = dim3(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -915,11 +920,13 @@ namespace {
 
 // One launch of the stage kernel over `tiles` (stage k).  S = 0: dense tiles,
 // 2-D state maps; S > 0: strided in-place tiles (vin == vout), 3-D state maps
-// over `rows_cap` rows (a multiple of S).
+// over `rows_cap` rows (a multiple of S).  even_resid: the destination rows'
+// residual is v^(1) = Bbar u of an even row, formed from u (the last
+// down-sweep level), and only y is written.
 cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, int S,
                           uint64_t rows_cap, const void* vin_hi, const void* vin_lo,
                           void* vout_hi, void* vout_lo, const float* u, float* y,
-                          cudaStream_t st, bool reverse) {
+                          cudaStream_t st, bool reverse, bool even_resid = false) {
   if (ntiles == 0) return cudaSuccess;
   if (!(reverse ? p.PThi : p.Phi) || !vin_hi || !vin_lo || !vout_hi || !vout_lo) {
     set_global_error("stage launch without its power or state planes");
@@ -978,12 +985,18 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   a.u = u;
   a.y = y;
   // stage 1 of a plan that forms v^(1) on chip (one column chunk per step:
-  // the row warps' registers fit only that variant)
-  const bool gen = p.fuse_first && k == 1 && !reverse && S == 0 && u != nullptr;
-  a.gen = gen ? 1 : 0;
+  // the row warps' registers fit only that variant), or the last down-sweep
+  // level forming its even rows' v^(1) (also one chunk per step: fewer
+  // kernel variants)
+  const bool fuse = p.fuse_output && !reverse && y != nullptr;
+  const int gen = (p.fuse_first && k == 1 && !reverse && S == 0 && u != nullptr) ? 1
+                  : (even_resid && fuse && S > 0 && u != nullptr)               ? 2
+                                                                               : 0;
+  a.gen = gen;
   a.Bb = p.Bbar32;
   a.ABb = p.ABbar32;
-  if (gen && cfg.group != 1) {
+  if (gen == 2) a.keep_v = 0;   // nothing reads these rows after the last level
+  if (gen != 0 && cfg.group != 1) {
     const TcConfig c1{cfg.stages, cfg.ring, 1};
     cfg = tc_config_fits(m, BN, c1) ? c1 : tc_default(m, p.d.precision);
     a.stages = cfg.stages;
@@ -999,20 +1012,21 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   const int q = p.d.q;
   // the fused output applies to forward stages that are given y (the stages
   // the backward recomputes are not)
-  const bool fuse = p.fuse_output && !reverse && y != nullptr;
   const int G = cfg.group;
-#define CASCADE_TC_DISPATCH(E, Q)                                                     \
-  return gen      ? launch_variant<E, Q, 1, true>(maps, a, grid, smem, st)             \
-         : G == 2 ? launch_variant<E, Q, 2, false>(maps, a, grid, smem, st)            \
-                  : launch_variant<E, Q, 1, false>(maps, a, grid, smem, st)
+#define CASCADE_TC_DISPATCH(E, Q, GEN2)                                               \
+  return gen == 1 ? launch_variant<E, Q, 1, 1>(maps, a, grid, smem, st)                \
+         : gen == 2 ? launch_variant<E, Q, 1, GEN2>(maps, a, grid, smem, st)           \
+         : G == 2 ? launch_variant<E, Q, 2, 0>(maps, a, grid, smem, st)                \
+                  : launch_variant<E, Q, 1, 0>(maps, a, grid, smem, st)
+  // (mode 2 needs the fused output: the Q = 0 variants never take it)
   if (elem == 2) {
-    if (!fuse) CASCADE_TC_DISPATCH(2, 0);
-    if (q == 1) CASCADE_TC_DISPATCH(2, 1);
-    CASCADE_TC_DISPATCH(2, 4);
+    if (!fuse) CASCADE_TC_DISPATCH(2, 0, 0);
+    if (q == 1) CASCADE_TC_DISPATCH(2, 1, 2);
+    CASCADE_TC_DISPATCH(2, 4, 2);
   } else {
-    if (!fuse) CASCADE_TC_DISPATCH(4, 0);
-    if (q == 1) CASCADE_TC_DISPATCH(4, 1);
-    CASCADE_TC_DISPATCH(4, 4);
+    if (!fuse) CASCADE_TC_DISPATCH(4, 0, 0);
+    if (q == 1) CASCADE_TC_DISPATCH(4, 1, 2);
+    CASCADE_TC_DISPATCH(4, 4, 2);
   }
 #undef CASCADE_TC_DISPATCH
 }
@@ -1029,9 +1043,10 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
 
 cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,
                                     uint64_t rows_cap, void* v_hi, void* v_lo, const float* u,
-                                    float* y, cudaStream_t st) {
+                                    float* y, cudaStream_t st, bool even_resid) {
   if (S <= 0 || rows_cap % (uint64_t)S != 0) return cudaErrorInvalidValue;
-  return stage_tc_core(p, k, tiles, ntiles, S, rows_cap, v_hi, v_lo, v_hi, v_lo, u, y, st, false);
+  return stage_tc_core(p, k, tiles, ntiles, S, rows_cap, v_hi, v_lo, v_hi, v_lo, u, y, st, false,
+                       even_resid);
 }
 
 }  // namespace cascade

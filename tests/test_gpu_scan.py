@@ -84,6 +84,30 @@ def test_scan_matches_oracle(lib, precision, m, q):
     assert want <= sum(oracle.matvec_counts(11, L)["paper_bound"] for L in LENGTHS)
 
 
+@pytest.mark.parametrize("precision,m,q", [("bf16_split", 256, 1), ("bf16_split", 128, 3),
+                                           ("fp32", 128, 1), ("fp32", 64, 4)])
+def test_scan_even_rows_on_chip(lib, precision, m, q):
+    """p = 1 with the output fused: the first level stores only the odd rows
+    and row 0, and the last down-sweep level forms the even rows' v^(1) =
+    Bbar u from u.  Same results, bit for bit, as the path that stores every
+    row (CASCADE_FLAG_NO_FUSED_FIRST), and oracle parity."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_NO_FUSED_FIRST, CASCADE_FLAG_SCAN
+    if q == 1:
+        w = wl.precision_form(m=m, L=8, batch=len(LENGTHS), N=11)
+    else:
+        w = wl.differentiation_form(m=m, p=1, q=q, L=8, batch=len(LENGTHS), N=11, delta=1e-2)
+    w.offsets = np.concatenate([[0], np.cumsum(LENGTHS)]).astype(np.int64)
+    w.u = np.random.default_rng(23).standard_normal((int(w.offsets[-1]), 1))
+    w = cast_inputs(w, precision)
+    c1, y1 = run(lib, w, precision, CASCADE_FLAG_SCAN)
+    c2, y2 = run(lib, w, precision, CASCADE_FLAG_SCAN | CASCADE_FLAG_NO_FUSED_FIRST)
+    assert c1.first_fused() and not c2.first_fused()
+    assert np.array_equal(y1, y2)
+    yo = oracle.cascade_forward(w, N_per_seq=c1.seq_N())
+    ey, ecx = rel_errors(w, y1, yo, OUT_EPS[precision])
+    assert ey <= TOL[precision] and ecx <= TOL[precision], (ey, ecx)
+
+
 def test_stage_schedule_count(lib):
     """The stage schedule's count is the oracle's sum_k (L - 2^k)^+ per sequence."""
     w = wl.precision_form(m=64, L=8, batch=len(LENGTHS), N=12)

@@ -692,6 +692,23 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
           alive = false;
           break;
         }
+        // GEN = 2 (p = 1): the even rows' residual Bbar u_l, formed before the
+        // TMEM load it does not depend on, so its coefficient loads overlap it
+        float xr[GEN == 2 ? G : 1][GEN == 2 ? CW : 1];
+        if constexpr (GEN == 2) {
+#pragma unroll
+          for (int h = 0; h < G; ++h) {
+            const float4* b4 = reinterpret_cast<const float4*>(Bs + it.n0 + (cc + h) * CW);
+#pragma unroll
+            for (int e4 = 0; e4 < CW / 4; ++e4) {
+              const float4 b = valid ? __ldg(b4 + e4) : make_float4(0.f, 0.f, 0.f, 0.f);
+              xr[h][4 * e4] = b.x * ur[0];
+              xr[h][4 * e4 + 1] = b.y * ur[0];
+              xr[h][4 * e4 + 2] = b.z * ur[0];
+              xr[h][4 * e4 + 3] = b.w * ur[0];
+            }
+          }
+        }
         float v[G][CW];
         if (!it.copy) {
           uint32_t ra[G][CW];
@@ -722,7 +739,16 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
             for (int j = 0; j < CW; ++j) v[h][j] = 0.f;
         }
         uint4 hq[G][4], lq[G][4];
-        if constexpr (GEN != 0) {
+        if constexpr (GEN == 2) {
+          // rounded to the (hi, lo) pair the first level would have stored
+#pragma unroll
+          for (int h = 0; h < G; ++h)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              Fmt<ELEM>::split16(xr[h] + c * (CW / 4), hq[h][c], lq[h][c]);
+              Fmt<ELEM>::add16(hq[h][c], lq[h][c], v[h] + c * (CW / 4));
+            }
+        } else if constexpr (GEN == 1) {
           // residual v^(1)_l of this row from u, rounded to the (hi, lo) pair the
           // first-stage kernel would have stored, so that results are the same
           // bit for bit (rows past the sequence end are not stored: zero)
@@ -758,12 +784,20 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
 #pragma unroll
             for (int qq = 0; qq < QN; ++qq) {
               if (qq < args.q) {
-                const float* crow = Cs + (int64_t)qq * m + it.n0 + cc * CW;
+                // C row segment as 16-byte loads (m, n0 and CW are multiples of 4)
+                const float4* crow =
+                    reinterpret_cast<const float4*>(Cs + (int64_t)qq * m + it.n0 + cc * CW);
                 float s = 0.f;
 #pragma unroll
                 for (int h = 0; h < G; ++h)
 #pragma unroll
-                  for (int j = 0; j < CW; ++j) s = fmaf(__ldg(crow + h * CW + j), v[h][j], s);
+                  for (int j4 = 0; j4 < CW / 4; ++j4) {
+                    const float4 c4 = __ldg(crow + h * (CW / 4) + j4);
+                    s = fmaf(c4.x, v[h][4 * j4], s);
+                    s = fmaf(c4.y, v[h][4 * j4 + 1], s);
+                    s = fmaf(c4.z, v[h][4 * j4 + 2], s);
+                    s = fmaf(c4.w, v[h][4 * j4 + 3], s);
+                  }
                 yacc[qq] += s;
               }
             }

@@ -484,11 +484,13 @@ def main():
             raise RuntimeError("device wait timed out in the scan region")
         scan_ms = sum(a.elapsed_time(b) for a, b in sev) / args.steps
         scan_ms = max_over_ranks(scan_ms, world, dev)
+        scan_levels = cg.stage_shapes()
         cg.close()
         torch.cuda.empty_cache()
         # per-level durations: the same schedule launched directly, with events
         cs = cascade.from_workload(w, precision=precision, flags=CASCADE_FLAG_SCAN, device=dev)
-        cs.set_kernel_shape(*scan_shape)      # the shape the timed steps ran
+        cs.set_kernel_shape(*scan_shape)      # the shapes the timed steps ran
+        cs.set_stage_shapes(scan_levels)
         for _ in range(max(args.warmup, 3)):
             cs.forward(u, y)
         cs.enable_stage_timing(True)
@@ -532,7 +534,9 @@ def main():
                 "timing": "CUDA graph replay of the level launches; per-level durations "
                           "from separate direct launches with events",
                 "kernel_shape": {"stages": scan_shape[0], "ring": scan_shape[1],
-                                 "chunks_per_step": scan_shape[2]}}
+                                 "chunks_per_step": scan_shape[2],
+                                 "per_level": {str(k): list(v) for k, v in scan_levels.items()
+                                               if tuple(v) != tuple(scan_shape)}}}
         cs.close()
         torch.cuda.empty_cache()
         torch.cuda.nvtx.range_pop()

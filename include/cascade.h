@@ -322,13 +322,20 @@ cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_
    no-op for FP64 plans. */
 cascade_status_t cascade_set_kernel_shape(cascade_plan_t plan, const int32_t* h_shape);
 
-/* Per-stage kernel shapes chosen by cascade_autotune for the §3 schedule:
-   h_shape[3 k + j], j = stages, ring slots, chunks per step, for stage
-   k < min(cap, *n); {0, 0, 0} where the plan-wide shape applies.  *n = the
-   number of entries the plan holds (0 before tuning or after
-   cascade_set_kernel_shape). */
+/* Per-stage kernel shapes chosen by cascade_autotune: h_shape[3 k + j],
+   j = stages, ring slots, chunks per step, for entry k < min(cap, *n);
+   {0, 0, 0} where the plan-wide shape applies.  Entry k is stage k of the §3
+   schedule; with CASCADE_FLAG_SCAN it is up-sweep level k, and entry 100 + k
+   down-sweep level k.  *n = the number of entries the plan holds (0 before
+   tuning or after cascade_set_kernel_shape). */
 cascade_status_t cascade_get_stage_shapes(cascade_plan_t plan, int32_t cap, int32_t* h_shape,
                                           int32_t* n);
+
+/* Set per-stage kernel shapes (e.g. saved from cascade_get_stage_shapes):
+   n entries laid out as there.  Every non-zero entry must be a shape
+   cascade_set_kernel_shape accepts for this plan (CASCADE_ERR_INVALID_ARG
+   otherwise, nothing changed).  n = 0 clears them.  A no-op for FP64 plans. */
+cascade_status_t cascade_set_stage_shapes(cascade_plan_t plan, int32_t n, const int32_t* h_shape);
 
 /* Per-launch timing of the stage kernels.  When enabled, every later
    forward records a CUDA event pair on its stream around each tensor-core

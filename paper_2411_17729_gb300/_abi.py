@@ -63,6 +63,7 @@ SIGNATURES = [
     ("cascade_get_first_fused", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
     ("cascade_get_stage_shapes", C.c_int,
      [cascade_plan_t, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    ("cascade_set_stage_shapes", C.c_int, [cascade_plan_t, C.c_int32, C.POINTER(C.c_int32)]),
     ("cascade_workspace_size", C.c_int, [cascade_plan_t, C.POINTER(C.c_size_t)]),
     ("cascade_forward", C.c_int, [cascade_plan_t, _P, _P, _P, C.c_size_t, _P]),
     ("cascade_forward_fixed_scratch", C.c_int, [cascade_plan_t, _P, _P, _P]),

@@ -178,13 +178,26 @@ class Cascade:
         self._check(self.lib.cascade_get_first_fused(self.plan, C.byref(f)))
         return bool(f.value)
 
-    def stage_shapes(self, cap=64):
-        """{stage k: (stages, ring slots, chunks per step)} chosen per stage by autotune."""
-        buf = (C.c_int32 * (3 * cap))()
+    def stage_shapes(self):
+        """{entry: (stages, ring slots, chunks per step)} chosen per stage by autotune
+        (entry k: stage k; work-efficient schedule: up-sweep level k, 100 + k: down-sweep
+        level k)."""
         n = C.c_int32()
+        self._check(self.lib.cascade_get_stage_shapes(self.plan, 0, None, C.byref(n)))
+        cap = n.value
+        buf = (C.c_int32 * max(3 * cap, 1))()
         self._check(self.lib.cascade_get_stage_shapes(self.plan, cap, buf, C.byref(n)))
         return {k: tuple(buf[3 * k:3 * k + 3]) for k in range(min(cap, n.value))
                 if buf[3 * k] > 0}
+
+    def set_stage_shapes(self, shapes):
+        """Per-stage shapes {entry: (stages, ring slots, chunks per step)}, as
+        stage_shapes() returns them; {} clears them."""
+        n = (max(shapes) + 1) if shapes else 0
+        buf = (C.c_int32 * max(3 * n, 1))()
+        for k, v in shapes.items():
+            buf[3 * k:3 * k + 3] = list(v)
+        self._check(self.lib.cascade_set_stage_shapes(self.plan, n, buf))
 
     def enable_stage_timing(self, on=True):
         self._check(self.lib.cascade_enable_stage_timing(self.plan, 1 if on else 0))

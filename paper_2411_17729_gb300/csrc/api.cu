@@ -550,7 +550,8 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
       CK(launch_stage_tc_strided(*p, lv.k, 2 << lv.k, lv.d_tiles, lv.n,
                                  (uint64_t)p->scan_rows_cap, V.hi(0), V.lo(0),
                                  static_cast<const float*>(u), static_cast<float*>(y), st,
-                                 p->scan_even_on_chip && lv.down && lv.k == 0),
+                                 p->scan_even_on_chip && lv.down && lv.k == 0,
+                                 lv.down ? 100 + lv.k : lv.k),
          "scan level");
       if (timing && lv.n > 0) {
         CK(cudaEventRecord(p->ev[2 * p->n_ev + 1], st), "event");
@@ -1758,10 +1759,12 @@ cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_
   float best = 1e30f;
   TcConfig best_c = tc_default(p->d.m, p->d.precision);
   cascade_status_t r = CASCADE_OK;
-  // §3 schedule: each candidate's stages are also timed one by one, and every
-  // stage k keeps the candidate that ran it fastest (the plan-wide shape, the
-  // fastest whole forward, serves the adjoint stages and the scan levels)
-  const bool per_stage = !scans(*p) && p->maxN >= 1;
+  // Each candidate's stages (or scan levels) are also timed one by one, and
+  // every stage keeps the candidate that ran it fastest (the plan-wide shape,
+  // the fastest whole forward, serves the adjoint stages and the top of the
+  // scan tree).  Keys as the stage timings: k, or 100 + k for down-sweep levels.
+  const bool per_stage = p->maxN >= 1;
+  const int nkeys = scans(*p) ? 100 + p->maxN + 2 : p->maxN + 1;
   const std::vector<TcConfig> cands = tc_candidates(p->d.m, p->d.precision);
   std::vector<std::vector<float>> stage_ms;
   p->tc_stage_shape.clear();
@@ -1782,7 +1785,7 @@ cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_
     }
     if (ms < best) { best = ms; best_c = c; }
     if (per_stage) {
-      std::vector<float> acc(p->maxN + 1, 0.f);
+      std::vector<float> acc(nkeys, 0.f);
       for (int i = 0; i < reps && r == CASCADE_OK; ++i)
         r = timed_stages(p, d_u, d_y, d_workspace, st, acc);
       if (r != CASCADE_OK) break;
@@ -1796,8 +1799,8 @@ cascade_status_t cascade_autotune(cascade_plan_t plan, const void* d_u, void* d_
   p->tc_ring = best_c.ring;
   p->tc_group = best_c.group;
   if (r == CASCADE_OK && per_stage && stage_ms.size() == cands.size() && !cands.empty()) {
-    p->tc_stage_shape.assign(p->maxN + 1, {0, 0, 0});
-    for (int k = 1; k <= p->maxN; ++k) {
+    p->tc_stage_shape.assign(nkeys, {0, 0, 0});
+    for (int k = 0; k < nkeys; ++k) {
       size_t bi = 0;
       for (size_t ci = 1; ci < cands.size(); ++ci)
         if (stage_ms[ci][k] < stage_ms[bi][k]) bi = ci;
@@ -1832,6 +1835,31 @@ cascade_status_t cascade_set_kernel_shape(cascade_plan_t plan, const int32_t* h_
   p->tc_group = h_shape[2];
   p->tc_stage_shape.clear();   // one shape for every stage
   if (p->graph) {
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_set_stage_shapes(cascade_plan_t plan, int32_t n,
+                                          const int32_t* h_shape) {
+  Plan* p = plan;
+  if (!p || n < 0 || n > 4096 || (n > 0 && !h_shape))
+    return fail(p, CASCADE_ERR_INVALID_ARG, "bad stage-shape array");
+  if (p->d.precision == CASCADE_FP64) return CASCADE_OK;
+  const std::vector<TcConfig> cands = tc_candidates(p->d.m, p->d.precision);
+  std::vector<std::array<int32_t, 3>> sh(n, {0, 0, 0});
+  for (int k = 0; k < n; ++k) {
+    const int32_t* e = h_shape + 3 * k;
+    if (e[0] == 0 && e[1] == 0 && e[2] == 0) continue;
+    bool ok = false;
+    for (const TcConfig& c : cands)
+      ok = ok || (c.ring == e[1] && c.group == e[2] && e[0] >= 2 && e[0] <= c.stages);
+    if (!ok) return fail(p, CASCADE_ERR_INVALID_ARG, "a stage shape does not fit this plan");
+    sh[k] = {e[0], e[1], e[2]};
+  }
+  p->tc_stage_shape.swap(sh);
+  if (p->graph) {   // the recorded graph holds the old kernel shapes
     cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
   }

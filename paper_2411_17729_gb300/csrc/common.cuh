@@ -204,8 +204,10 @@ struct Plan {
   // tensor-core stage kernel shape: operand stages, epilogue ring slots,
   // chunks per epilogue step (0 = heuristic); set by cascade_autotune
   int tc_stages = 0, tc_ring = 0, tc_group = 0;
-  // per stage k of the §3 schedule (forward, dense tiles): the autotuner's
-  // fastest shape for that stage, {0, 0, 0} where the plan-wide shape applies
+  // per stage k of the §3 schedule (forward, dense tiles), or per level of the
+  // work-efficient schedule (entry k: up-sweep level k, 100 + k: down-sweep
+  // level k): the autotuner's fastest shape, {0, 0, 0} where the plan-wide
+  // shape applies
   std::vector<std::array<int32_t, 3>> tc_stage_shape;
   bool tuned = false;
   void* last_stream = nullptr;
@@ -259,7 +261,8 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
 // only y is written.
 cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,
                                     uint64_t rows_cap, void* v_hi, void* v_lo, const float* u,
-                                    float* y, cudaStream_t st, bool even_resid = false);
+                                    float* y, cudaStream_t st, bool even_resid = false,
+                                    int shape_key = -1);
 // Workspace buffer j of a family of equally sized state buffers.
 struct Bufs {
   uint8_t* base;

@@ -960,7 +960,8 @@ namespace {
 cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, int S,
                           uint64_t rows_cap, const void* vin_hi, const void* vin_lo,
                           void* vout_hi, void* vout_lo, const float* u, float* y,
-                          cudaStream_t st, bool reverse, bool even_resid = false) {
+                          cudaStream_t st, bool reverse, bool even_resid = false,
+                          int shape_key = -1) {
   if (ntiles == 0) return cudaSuccess;
   if (!(reverse ? p.PThi : p.Phi) || !vin_hi || !vin_lo || !vout_hi || !vout_lo) {
     set_global_error("stage launch without its power or state planes");
@@ -971,9 +972,12 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   const int BN = block_n(m, p.d.precision);
   TcConfig cfg{p.tc_stages, p.tc_ring, p.tc_group};
   if (!tc_config_fits(m, BN, cfg)) cfg = tc_default(m, p.d.precision);
-  if (!reverse && S == 0 && k >= 0 && k < (int)p.tc_stage_shape.size() &&
-      p.tc_stage_shape[k][0] > 0) {
-    const TcConfig ck{p.tc_stage_shape[k][0], p.tc_stage_shape[k][1], p.tc_stage_shape[k][2]};
+  // the autotuner's shape for this stage (§3: key k) or scan level (shape_key)
+  const int key = S == 0 ? k : shape_key;
+  if (!reverse && key >= 0 && key < (int)p.tc_stage_shape.size() &&
+      p.tc_stage_shape[key][0] > 0) {
+    const TcConfig ck{p.tc_stage_shape[key][0], p.tc_stage_shape[key][1],
+                      p.tc_stage_shape[key][2]};
     if (tc_config_fits(m, BN, ck)) cfg = ck;
   }
   const uint32_t row_elems = ROWB / (uint32_t)elem;
@@ -1077,10 +1081,10 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
 
 cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,
                                     uint64_t rows_cap, void* v_hi, void* v_lo, const float* u,
-                                    float* y, cudaStream_t st, bool even_resid) {
+                                    float* y, cudaStream_t st, bool even_resid, int shape_key) {
   if (S <= 0 || rows_cap % (uint64_t)S != 0) return cudaErrorInvalidValue;
   return stage_tc_core(p, k, tiles, ntiles, S, rows_cap, v_hi, v_lo, v_hi, v_lo, u, y, st, false,
-                       even_resid);
+                       even_resid, shape_key);
 }
 
 }  // namespace cascade

@@ -366,9 +366,13 @@ def test_autotuned_shape_keeps_parity(lib, precision, m):
     yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
     ey, ecx = rel_errors(w, y, yo, OUT_EPS[precision])
     assert ey <= TOL[precision] and ecx <= TOL[precision], (ey, ecx)
-    # an explicit shape applies to every stage
+    # an explicit shape applies to every stage; saved per-stage shapes come back
     c.set_kernel_shape(stages, ring, group)
     assert c.stage_shapes() == {}
+    c.set_stage_shapes(per)
+    assert c.stage_shapes() == per
+    y2 = c.forward(u).double().cpu().numpy()
+    assert np.array_equal(y, y2)
 
 
 @pytest.mark.parametrize("precision,m", [("bf16_split", 256), ("bf16_split", 128), ("fp32", 128),

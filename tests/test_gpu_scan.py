@@ -108,6 +108,32 @@ def test_scan_even_rows_on_chip(lib, precision, m, q):
     assert ey <= TOL[precision] and ecx <= TOL[precision], (ey, ecx)
 
 
+def test_scan_autotuned_levels(lib):
+    """The autotuner's per-level shapes on the work-efficient schedule (keys k
+    for up-sweep levels, 100 + k for down-sweep levels) keep oracle parity,
+    and setting the saved shapes again gives the same output bit for bit."""
+    import torch
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SCAN
+    w = cast_inputs(wl.precision_form(m=128, L=8, batch=len(LENGTHS), N=11), "bf16_split")
+    w.offsets = np.concatenate([[0], np.cumsum(LENGTHS)]).astype(np.int64)
+    w.u = np.random.default_rng(24).standard_normal((int(w.offsets[-1]), 1))
+    c = lib.from_workload(w, precision="bf16_split", flags=CASCADE_FLAG_SCAN)
+    u = torch.as_tensor(w.u, dtype=torch.float32).cuda().contiguous()
+    shape = c.autotune(u, reps=1)
+    per = c.stage_shapes()
+    K = int(np.ceil(np.log2(max(LENGTHS))))
+    assert per and set(per) <= set(range(1, K)) | set(range(100, 100 + K))
+    y1 = c.forward(u).double().cpu().numpy()
+    assert c.device_error() == 0
+    yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
+    ey, ecx = rel_errors(w, y1, yo, OUT_EPS["bf16_split"])
+    assert ey <= TOL["bf16_split"] and ecx <= TOL["bf16_split"], (ey, ecx)
+    c.set_kernel_shape(*shape)
+    c.set_stage_shapes(per)
+    assert c.stage_shapes() == per
+    assert np.array_equal(y1, c.forward(u).double().cpu().numpy())
+
+
 def test_stage_schedule_count(lib):
     """The stage schedule's count is the oracle's sum_k (L - 2^k)^+ per sequence."""
     w = wl.precision_form(m=64, L=8, batch=len(LENGTHS), N=12)

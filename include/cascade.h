@@ -245,13 +245,22 @@ cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y
    it until the process exits.  Batches whose workspace
    (cascade_workspace_size) exceeds it are rejected with
    CASCADE_ERR_UNSUPPORTED and a message giving both sizes; stage timing must
-   be off (CASCADE_ERR_UNSUPPORTED otherwise).  The call itself allocates
-   nothing.  The first call on each device resolves the array's device
-   address (cudaGetSymbolAddress) with that device current; make that first
-   call before any stream capture.  All calls share the one array, which
+   be off (CASCADE_ERR_UNSUPPORTED otherwise).  The call makes no allocation
+   of its own, but the array is a module variable: with lazy module loading
+   (CUDA_MODULE_LOADING=LAZY, the default) the first call on each device
+   loads it and commits its 32 MiB there, and a device that has no room
+   left then fails with CASCADE_ERR_OOM; with eager loading the memory is
+   committed when the library is loaded.  That first call resolves the
+   array's device address (cudaGetSymbolAddress) with the device current;
+   make it before any stream capture.  All calls share the one array, which
    keeps the last call's contents (the forward writes every byte it reads, so
    nothing needs clearing); calls whose executions overlap on the GPU, on any
    streams or plans, race on it and must be serialised by the caller.
+   The call always launches the forward's kernels directly: a plan's
+   CASCADE_FLAG_GRAPH applies to cascade_forward only.  Stage outputs that a
+   CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE plan keeps are written
+   into the shared array and are not available to cascade_backward, which
+   still refers to the last cascade_forward with a caller workspace.
    Otherwise as cascade_forward: d_u [rows,p], d_y [rows,q], asynchronous. */
 cascade_status_t cascade_forward_fixed_scratch(cascade_plan_t plan, const void* d_u, void* d_y,
                                                void* stream);
@@ -333,8 +342,12 @@ cascade_status_t cascade_get_stage_shapes(cascade_plan_t plan, int32_t cap, int3
 
 /* Set per-stage kernel shapes (e.g. saved from cascade_get_stage_shapes):
    n entries laid out as there.  Every non-zero entry must be a shape
-   cascade_set_kernel_shape accepts for this plan (CASCADE_ERR_INVALID_ARG
-   otherwise, nothing changed).  n = 0 clears them.  A no-op for FP64 plans. */
+   cascade_set_kernel_shape accepts for this plan, at an entry the current
+   batch's schedule launches (§3: stages 1..maxN; work-efficient: its up- and
+   down-sweep levels), and n may not exceed the entries that schedule has
+   (maxN + 1, or 100 + maxN + 2): CASCADE_ERR_INVALID_ARG otherwise, nothing
+   changed.  Needs a batch (CASCADE_ERR_STATE) unless n = 0, which clears
+   them.  A no-op for FP64 plans. */
 cascade_status_t cascade_set_stage_shapes(cascade_plan_t plan, int32_t n, const int32_t* h_shape);
 
 /* Per-launch timing of the stage kernels.  When enabled, every later

@@ -1847,11 +1847,29 @@ cascade_status_t cascade_set_stage_shapes(cascade_plan_t plan, int32_t n,
   if (!p || n < 0 || n > 4096 || (n > 0 && !h_shape))
     return fail(p, CASCADE_ERR_INVALID_ARG, "bad stage-shape array");
   if (p->d.precision == CASCADE_FP64) return CASCADE_OK;
+  if (n > 0 && !p->have_batch)
+    return fail(p, CASCADE_ERR_STATE, "per-stage shapes need a batch (their keys follow its schedule)");
+  // keys: stage k = 1..maxN of the §3 schedule; up-sweep level k or 100 + k
+  // for down-sweep level k of the work-efficient one (the levels it launches)
+  const int nkeys = scans(*p) ? 100 + p->maxN + 2 : p->maxN + 1;
+  if (n > nkeys)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "more stage-shape entries than this plan's schedule has");
+  std::vector<char> launched(std::max(nkeys, 0), 0);
+  if (scans(*p)) {
+    for (const Plan::ScanLevel& lv : p->scan) {
+      const int key = lv.down ? 100 + lv.k : lv.k;
+      if (key >= 0 && key < nkeys) launched[key] = 1;
+    }
+  } else {
+    for (int k = 1; k <= p->maxN; ++k) launched[k] = 1;
+  }
   const std::vector<TcConfig> cands = tc_candidates(p->d.m, p->d.precision);
   std::vector<std::array<int32_t, 3>> sh(n, {0, 0, 0});
   for (int k = 0; k < n; ++k) {
     const int32_t* e = h_shape + 3 * k;
     if (e[0] == 0 && e[1] == 0 && e[2] == 0) continue;
+    if (!launched[k])
+      return fail(p, CASCADE_ERR_INVALID_ARG, "a stage shape names a stage or level this plan does not launch");
     bool ok = false;
     for (const TcConfig& c : cands)
       ok = ok || (c.ring == e[1] && c.group == e[2] && e[0] >= 2 && e[0] <= c.stages);

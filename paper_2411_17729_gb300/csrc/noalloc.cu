@@ -46,10 +46,17 @@ cascade_status_t scratch_on_current_device(Plan* p, void** out) {
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (!g_scratch_ptr[dev]) {
     void* ptr = nullptr;
+    // With lazy module loading this first lookup loads the module that holds
+    // the array, which commits its device memory now: an out-of-memory
+    // failure there is reported as such.
     e = cudaGetSymbolAddress(&ptr, g_fixed_scratch);
-    if (e != cudaSuccess || !ptr)
-      return nofail(p, CASCADE_ERR_CUDA,
+    if (e != cudaSuccess || !ptr) {
+      const cascade_status_t code =
+          e == cudaErrorMemoryAllocation ? CASCADE_ERR_OOM : CASCADE_ERR_CUDA;
+      if (e != cudaSuccess) cudaGetLastError();   // reset the runtime's last-error state
+      return nofail(p, code,
                     std::string("cudaGetSymbolAddress(fixed scratch): ") + cudaGetErrorString(e));
+    }
     g_scratch_ptr[dev] = ptr;
   }
   *out = g_scratch_ptr[dev];
@@ -87,6 +94,15 @@ extern "C" cascade_status_t cascade_forward_fixed_scratch(cascade_plan_t plan, c
   cascade_status_t r = scratch_on_current_device(p, &ws);
   if (r != CASCADE_OK) return r;
   // Every workspace byte the forward reads is written earlier in the same
-  // call, so the previous call's contents need no clearing.
-  return forward_with_workspace(p, d_u, d_y, ws, static_cast<cudaStream_t>(stream));
+  // call, so the previous call's contents need no clearing.  The stage
+  // outputs a SAVE_STATES or RECOMPUTE plan keeps land in the shared array,
+  // which the next call may overwrite: they are not offered to
+  // cascade_backward, whose record of the last forward stays as it was.
+  const void* const saved_ws = p->saved_ws;
+  const int64_t saved_batch = p->saved_batch;
+  const cascade_status_t r2 =
+      forward_with_workspace(p, d_u, d_y, ws, static_cast<cudaStream_t>(stream));
+  p->saved_ws = saved_ws;
+  p->saved_batch = saved_batch;
+  return r2;
 }

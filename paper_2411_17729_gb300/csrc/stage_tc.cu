@@ -25,16 +25,20 @@
 // the two in the epilogue: the large partial sum is then rounded once per
 // MMA instead of three times.
 //
-// Block layout (224 threads, one block per SM, persistent over work items):
+// Block layout (352 threads, or 480 when stage 1 forms v^(1) on chip; one
+// block per SM, persistent over work items):
 //   warp 0      TMA producer of the MMA operands (one elected lane)
 //   warp 1      TMEM allocator and MMA issuer (one elected lane)
-//   warps 2..5  epilogue, thread = tile row = TMEM lane: accumulator row +
-//               residual row -> new (hi, lo) row, written back into the
-//               staging slot the residual arrived in
+//   warps 2..5  epilogue group 0 and warps 7..10 epilogue group 1 (the two
+//               take alternate column-chunk steps), thread = tile row = TMEM
+//               lane: accumulator row + residual row -> new (hi, lo) row,
+//               written back into the staging slot the residual arrived in
 //   warp 6      staging-ring manager (one elected lane): TMA loads of the
 //               residual column chunks RING chunks ahead (across tiles), TMA
 //               stores of finished chunks, refill of each slot once its store
 //               has read it
+//   warps 11..14 (stage 1 on chip only) write the operand rows v^(1)_(l-s)
+//               formed from u into the operand stages
 // HBM traffic is whole lines in both directions, and the 64-byte swizzle of
 // every shared tile keeps the thread-per-row accesses free of bank conflicts.
 // No named barrier joins the epilogue warps: they signal a finished chunk

@@ -1,17 +1,17 @@
 """GPU parity of the reverse-mode derivative (through the C ABI) against the
 CPU FP64 oracle's adjoint, plus central finite differences through the GPU's
-own FP64 forward.  Bars: relative Frobenius error per gradient tensor, 1e-10
-for the FP64 path, 1e-5 for FP32, 2e-3 for the BF16 split."""
+own FP64 forward.  Bars, per sequence for du and per system for the
+system-matrix gradients, as the relative Frobenius error and element-wise
+(max |g - g_o| / max |g_o|): 1e-10 for the FP64 path, 1e-5 for FP32, 2e-3
+for the BF16 split."""
 import numpy as np
 import pytest
 
 import oracle
 import workloads as wl
-from _parity import cast_inputs
+from _parity import cast_inputs, gate_grads
 
 pytestmark = pytest.mark.gpu
-
-GTOL = {"fp64": 1e-10, "fp32": 1e-5, "bf16_split": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -39,17 +39,9 @@ def gpu_grads(lib, w, precision, dy, flags=None):
     return c, y.double().cpu().numpy(), {k: v.double().cpu().numpy() for k, v in g.items()}
 
 
-def compare(w, c, g, dy, tol):
+def compare(w, c, g, dy, precision):
     ref = oracle.cascade_backward(w, dy, N_per_seq=c.seq_N())
-    worst = {}
-    for k, v in g.items():
-        r = ref[k]
-        nr = np.linalg.norm(r)
-        err = np.linalg.norm(v - r) / nr if nr > 0 else np.linalg.norm(v)
-        worst[k] = err
-    bad = {k: e for k, e in worst.items() if not e <= tol}
-    assert not bad, (bad, worst)
-    return worst
+    return gate_grads(w, g, ref, precision)
 
 
 @pytest.mark.parametrize("discrete", [True, False])
@@ -58,7 +50,7 @@ def test_fp64_backward_matches_oracle(lib, discrete):
                         radius=0.97, discrete=discrete, delta=0.2, precision="fp64")
     dy = np.random.default_rng(1).standard_normal((w.rows, w.q))
     c, _, g = gpu_grads(lib, w, "fp64", dy)
-    compare(w, c, g, dy, GTOL["fp64"])
+    compare(w, c, g, dy, "fp64")
 
 
 def test_fp64_backward_truncated_and_growing(lib):
@@ -66,7 +58,7 @@ def test_fp64_backward_truncated_and_growing(lib):
     w = wl.small_system(m=7, p=3, q=2, lengths=(100, 41), N=3, seed=5, radius=1.03)
     dy = np.random.default_rng(2).standard_normal((w.rows, w.q))
     c, _, g = gpu_grads(lib, w, "fp64", dy)
-    compare(w, c, g, dy, GTOL["fp64"])
+    compare(w, c, g, dy, "fp64")
 
 
 def test_fp64_backward_finite_differences_on_gpu(lib):
@@ -108,7 +100,7 @@ def test_tc_backward_matches_oracle(lib, precision, m):
     w = cast_inputs(w, precision)
     dy = np.random.default_rng(6).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
     c, _, g = gpu_grads(lib, w, precision, dy)
-    compare(w, c, g, dy, GTOL[precision])
+    compare(w, c, g, dy, precision)
 
 
 @pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
@@ -122,7 +114,7 @@ def test_tc_backward_discrete_multisystem(lib, precision):
     w = cast_inputs(w, precision)
     dy = np.random.default_rng(8).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
     c, _, g = gpu_grads(lib, w, precision, dy)
-    compare(w, c, g, dy, GTOL[precision])
+    compare(w, c, g, dy, precision)
 
 
 def test_autograd_function(lib):
@@ -145,9 +137,9 @@ def test_autograd_function(lib):
     (y * dy).sum().backward()
     dy_np = dy.double().cpu().numpy()
     ref = oracle.cascade_backward(w, dy_np, N_per_seq=c.seq_N())
-    for t, k in ((A, "dA"), (B, "dB"), (C, "dC"), (D, "dD"), (u, "du")):
-        gt = t.grad.double().cpu().numpy()
-        assert np.linalg.norm(gt - ref[k]) <= 2e-3 * np.linalg.norm(ref[k]), k
+    g = {k: t.grad.double().cpu().numpy()
+         for t, k in ((A, "dA"), (B, "dB"), (C, "dC"), (D, "dD"), (u, "du"))}
+    gate_grads(w, g, ref, "bf16_split")
 
 
 def test_backward_requires_saved_states(lib):
@@ -170,7 +162,23 @@ def test_differentiation_form_full_size(lib):
     w = cast_inputs(wl.differentiation_form(), "bf16_split")
     dy = np.random.default_rng(10).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
     c, _, g = gpu_grads(lib, w, "bf16_split", dy, flags=CASCADE_FLAG_RECOMPUTE)
-    compare(w, c, g, dy, GTOL["bf16_split"])
+    compare(w, c, g, dy, "bf16_split")
+
+
+def test_large_form_backward_full_length(lib):
+    """The large form at full length: one sequence of 65536 steps, m = 1024,
+    p = q = 64, Abar = 0.9999 Q + rank-4 E, N = 15 (every stage, shifts up to
+    2^15, dAbar through 15 levels of the squaring chain), BF16 split with
+    stage outputs recomputed from checkpoints, as the benchmark's
+    forward + backward runs them.  Every gradient against the oracle's FP64
+    adjoint, element-wise and in norm."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_RECOMPUTE
+    w = wl.large_form(batch=1)
+    w = cast_inputs(w, "bf16_split")
+    dy = np.random.default_rng(26).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
+    c, _, g = gpu_grads(lib, w, "bf16_split", dy, flags=CASCADE_FLAG_RECOMPUTE)
+    assert np.all(c.seq_N() == 15)
+    compare(w, c, g, dy, "bf16_split")
 
 
 def test_large_form_backward_reduced_length(lib):
@@ -182,7 +190,7 @@ def test_large_form_backward_reduced_length(lib):
     w = cast_inputs(w, "bf16_split")
     dy = np.random.default_rng(16).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
     c, _, g = gpu_grads(lib, w, "bf16_split", dy)
-    compare(w, c, g, dy, GTOL["bf16_split"])
+    compare(w, c, g, dy, "bf16_split")
 
 
 @pytest.mark.parametrize("p,q", [(1, 1), (8, 2), (16, 16), (3, 20), (64, 64)])
@@ -197,7 +205,7 @@ def test_tc_backward_mimo_shapes(lib, p, q):
     w = cast_inputs(w, "bf16_split")
     dy = np.random.default_rng(12).standard_normal((w.rows, w.q)).astype(np.float32).astype(np.float64)
     c, _, g = gpu_grads(lib, w, "bf16_split", dy)
-    compare(w, c, g, dy, GTOL["bf16_split"])
+    compare(w, c, g, dy, "bf16_split")
 
 
 @pytest.mark.parametrize("precision,m", [("bf16_split", 128), ("fp32", 64), ("fp64", 24)])
@@ -230,7 +238,7 @@ def test_recompute_matches_saved_states(lib, precision, m):
     assert c2.workspace_size() < c1.workspace_size()
     for k in g1:
         assert np.array_equal(g1[k], g2[k]), k
-    compare(w, c2, g2, dy, GTOL[precision])
+    compare(w, c2, g2, dy, precision)
 
 
 @pytest.mark.parametrize("m,p,q", [(512, 1, 1), (256, 2, 4), (128, 4, 1)])
@@ -250,4 +258,4 @@ def test_first_stage_adjoint_one_pass(lib, m, p, q):
     w = cast_inputs(w, "bf16_split")
     dy = np.random.default_rng(19).standard_normal((w.rows, q)).astype(np.float32).astype(np.float64)
     c, _, g = gpu_grads(lib, w, "bf16_split", dy)
-    compare(w, c, g, dy, GTOL["bf16_split"])
+    compare(w, c, g, dy, "bf16_split")

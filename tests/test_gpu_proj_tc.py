@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from _parity import OUT_EPS, TOL, cast_inputs, rel_errors
+from _parity import cast_inputs, gate, gate_grads
 
 pytestmark = pytest.mark.gpu
 
@@ -63,8 +63,7 @@ def test_forward_wide_projections(lib, m, p, q):
     Ns = c.seq_N()
     assert len({int(n) % 2 for n in Ns if n >= 0}) == 2   # both final-state buffers
     yo = oracle.cascade_forward(w, N_per_seq=Ns)
-    ey, ecx = rel_errors(w, y, yo, OUT_EPS["bf16_split"])
-    assert ey <= TOL["bf16_split"] and ecx <= TOL["bf16_split"], (ey, ecx)
+    gate(w, y, yo, "bf16_split")
 
 
 def test_forward_truncated(lib):
@@ -72,8 +71,7 @@ def test_forward_truncated(lib):
     w = two_systems(128, 32, 64, N=4)
     c, y = forward(lib, w)
     yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
-    ey, ecx = rel_errors(w, y, yo, OUT_EPS["bf16_split"])
-    assert ey <= TOL["bf16_split"] and ecx <= TOL["bf16_split"], (ey, ecx)
+    gate(w, y, yo, "bf16_split")
 
 
 def test_scan_first_level_odd_rows(lib):
@@ -84,8 +82,7 @@ def test_scan_first_level_odd_rows(lib):
     w = two_systems(128, 32, 32)
     c, y = forward(lib, w, CASCADE_FLAG_SCAN)
     yo = oracle.cascade_forward(w, N_per_seq=c.seq_N())
-    ey, ecx = rel_errors(w, y, yo, OUT_EPS["bf16_split"])
-    assert ey <= TOL["bf16_split"] and ecx <= TOL["bf16_split"], (ey, ecx)
+    gate(w, y, yo, "bf16_split")
 
 
 def grads(lib, w, dy, flags):
@@ -101,8 +98,7 @@ def grads(lib, w, dy, flags):
 
 def check_grads(w, c, g, dy):
     ref = oracle.cascade_backward(w, dy, N_per_seq=c.seq_N())
-    errs = {k: np.linalg.norm(g[k] - ref[k]) / np.linalg.norm(ref[k]) for k in g}
-    assert all(e <= TOL["bf16_split"] for e in errs.values()), errs
+    gate_grads(w, g, ref, "bf16_split")
 
 
 @pytest.mark.parametrize("m,p,q", [(256, 32, 64), (128, 64, 32), (384, 96, 32), (128, 16, 16),

@@ -378,3 +378,35 @@ def test_packed_batch_matches_per_sequence():
         N = oracle.effective_N(w.N, sl.stop - sl.start)
         yi = oracle.brute_force_seq(Abar, Bbar, C, D, w.u[sl], 2 ** (N + 1))
         assert np.max(np.abs(y[sl] - yi)) <= 1e-12 * max(1.0, np.max(np.abs(yi)))
+
+
+# --------------------------------------------------------------- counts by running the stages
+def _rows_updated_by_stages(N, L, m=3, seed=0):
+    """Rows each §3 stage k = 0..N changes, counted by running oracle.stage on
+    random states with a power that has no zero row (every updated row then
+    differs from its input), independently of the counting formulas."""
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal((L, m)) + 2.0
+    P = np.eye(m) + 0.25                           # positive entries, no zero row
+    counts = []
+    for k in range(N + 1):
+        Vn = oracle.stage(V, P, 2 ** k)
+        counts.append(int(np.sum(np.any(Vn != V, axis=1))))
+        V = Vn
+    return counts
+
+
+@pytest.mark.parametrize("L", [0, 1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 32, 33, 64, 100])
+@pytest.mark.parametrize("N", [0, 1, 2, 3, 4, 6, 8])
+def test_matvec_count_and_effective_N_by_running_stages(N, L):
+    """oracle.matvec_counts (executed) equals the rows the stages update, and
+    oracle.effective_N is the last stage that updates a row (0 when none):
+    lengths on both sides of every power of two catch a < / <= slip at
+    2^k = L."""
+    counts = _rows_updated_by_stages(N, L)
+    assert oracle.matvec_counts(N, L)["executed"] == sum(counts)
+    working = [k for k, c in enumerate(counts) if c > 0]
+    assert oracle.effective_N(N, L) == (max(working) if working else 0)
+    assert oracle.stage_count(N, L) == len(working)
+    # every stage up to the last working one updates rows: no gaps
+    assert working == list(range(len(working)))

@@ -1,13 +1,24 @@
 #!/usr/bin/env python
-"""Throughput of the cascade (states/s) on the BF16-split precision workload.
+"""Throughput of the cascade (states/s) against the plain FP64 cascade, at the
+stated error, on one GB300.
 
-Workload (seeded, synthetic): HiPPO-LegS state matrix, m = 256, p = q = 1,
-64 sequences of L = 16384 steps, one trapezoidal step size per sequence drawn
-log-uniform in [1e-4, 1e-1] (64 systems), N = 13 (14 stages, 2^14 >= L),
-u ~ N(0, 1).  A step is one forward pass of the whole cascade over the batch:
-first stage fused with Bbar u, stages 1..13 on the tensor cores, y = C v + D u
-fused into the last stage.  The powers Abar^(2^k) are prepared once (FP64
-squaring chain) outside the timed region; their cost is reported separately.
+Headline workload (seeded, synthetic): the large fused form, m = 1024,
+p = q = 64, 8 sequences of L = 65536 steps, Abar = 0.9999 Q + rank-4 E (Q
+Haar-orthogonal), N = 15 (16 stages), BF16 hi/lo split with FP32
+accumulation, powers by FP64 squaring.  A step is one forward pass of the
+whole cascade over the batch (first stage fused with Bbar u, stages 1..15 on
+the tensor cores, y = C v + D u); the forward + backward, the work-efficient
+(about 2L products) schedule, the FP64 plain cascade and the FP64 sequential
+recursion on the same GPU are measured beside it.  The precision form (m =
+256, p = q = 1, 64 sequences x 16384 steps, one trapezoidal step per
+sequence, N = 13) is measured the same way and reported under
+"precision_form".  The powers are prepared once outside the timed region;
+set-up plus forward is reported separately (e2e_with_setup).
+
+The error of the timed output against the CPU FP64 oracle comes from the
+cpu_baseline leg: the oracle's outputs on its timed sample (whole sequences,
+the last one of the batch first) are compared with the GPU's y, in norm and
+element-wise, per sequence; the run fails above the bar.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 launch with torch.distributed.run: every rank runs an independent
@@ -26,15 +37,40 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "cascade states/s (fwd)"
-# DRAM bytes (read + write) per launch of the stage kernel on the precision workload: an ncu
-# capture of stage k = 8 on 8 of the 64 sequences measured 225.75 MB (138.22 MB read, 87.53 MB
-# written); the traffic grows with the rows processed, so a full launch moves 8x that.
-TRAFFIC_NOTE = {"bytes_per_launch": 8 * 225.75e6,
-                "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of stage_tc_kernel, "
-                        "stage 8, 8 of 64 sequences, scaled x8 to the full launch"}
-WORKLOAD = ("precision_form: HiPPO-LegS m=256 p=q=1, 64 seqs x L=16384, N=13, "
-            "delta log-uniform [1e-4,1e-1] per sequence, BF16 hi/lo split, FP32 accumulate")
+METRIC = "cascade states/s (fwd, fwd+bwd) vs plain FP64 cascade on GB300 at stated error"
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16_split": 2e-3}
+
+# name -> (precision, one-line description, run backward?)
+SPECS = {
+    "large_form": ("bf16_split", "large_form: Abar=0.9999 Q + rank-4 E, m=1024 p=q=64, 8 seqs x "
+                   "L=65536, N=15, BF16 hi/lo split, FP32 accumulate, FP64 squaring, fwd+bwd",
+                   True),
+    "precision_form": ("bf16_split", "precision_form: HiPPO-LegS m=256 p=q=1, 64 seqs x L=16384, "
+                       "N=13, delta log-uniform [1e-4,1e-1] per sequence, BF16 hi/lo split, "
+                       "FP32 accumulate", True),
+    "plain_fp64": ("fp64", "plain_fp64: HiPPO-LegS m=64 p=q=1, 1 seq x L=4096, delta=1/4096, "
+                   "N=11, FP64 (equals the recursion)", False),
+    "batching_form": ("fp32", "batching_form: HiPPO-LegS m=128 p=q=4, 512 seqs, L_i log-uniform "
+                      "[1024,65536] (8.85e6 rows), Abar*(1+1e-6), N_i from eps=1e-6, FP32 "
+                      "(3xTF32)", False),
+    "differentiation_form": ("bf16_split", "differentiation_form: HiPPO-LegS m=256 p=q=16, "
+                             "32 seqs x L=8192, delta=1e-3, N=12, BF16 split, fwd+bwd", True),
+}
+
+# DRAM bytes (read + write) of one stage_tc_kernel launch, from ncu captures of
+# the current kernel on a smaller case, scaled by the rows processed to the
+# full launch (the traffic of these launches grows in proportion to the rows).
+# workload -> (bytes per full launch, the stage captured, note); absent: null.
+TRAFFIC = {
+    "large_form": (8 * 515.6e6, 8,
+                   "ncu dram__bytes_read.sum + dram__bytes_write.sum of stage_tc_kernel, stage 8, "
+                   "1 of 8 sequences (288.4 + 227.2 MB), x8 to the full launch; about 40 MB of "
+                   "writes still dirty in L2 at kernel end are not counted"),
+    "precision_form": (4 * 506.6e6, 8,
+                       "ncu dram__bytes_read.sum + dram__bytes_write.sum of stage_tc_kernel, "
+                       "stage 8, 16 of 64 sequences (285.2 + 221.5 MB), x4 to the full launch; "
+                       "about 43 MB of writes still dirty in L2 at kernel end are not counted"),
+}
 
 
 def parse():
@@ -43,15 +79,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 cascade comparator")
+    ap.add_argument("--workload", default="large_form", choices=sorted(SPECS),
+                    help="headline workload (large_form is the benchmark)")
+    ap.add_argument("--also", default="precision_form",
+                    help="second workload measured the same way ('none' to skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle leg (and with it the error check)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparators")
     ap.add_argument("--no-bwd", action="store_true", help="skip the forward+backward measurement")
     ap.add_argument("--no-scan", action="store_true",
                     help="skip the work-efficient (about 2L products) schedule measurement")
     ap.add_argument("--seqs", type=int, default=0,
                     help="keep only the first SEQS sequences (profiler captures only)")
-    ap.add_argument("--workload", default="precision_form", choices=sorted(SPECS),
-                    help="precision_form is the benchmark; the others are the other configurations")
     return ap.parse_args()
 
 
@@ -78,7 +117,27 @@ def whole_job_rate(units_per_rank, world, ms):
     return units_per_rank * world / (ms / 1000.0)
 
 
-# --------------------------------------------------------------------- helpers
+def load_workload(name, seqs=0):
+    """The seeded workload, with u cast to float32 for the tensor-core
+    precisions (the oracle then sees the same float32 values)."""
+    import numpy as np
+    import workloads as wl
+    w = wl.WORKLOADS[name]()
+    if seqs and seqs < w.nseq:
+        w = w.subset(range(seqs))
+    if SPECS[name][0] != "fp64":
+        w.u = w.u.astype(np.float32).astype(np.float64)
+    return w
+
+
+def config_of(name, w, world):
+    """The config object: the same keys on both arms."""
+    return {"workload": SPECS[name][1], "global_batch": int(w.nseq) * world,
+            "seq_len": int(w.lengths.max()),
+            "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
+# --------------------------------------------------------------------- oracle leg
 def blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -90,30 +149,73 @@ def blas_threads():
     return os.cpu_count() or 1
 
 
-def oracle_states_per_s(w, budget_s=12.0):
-    """The oracle as it stands, on whole sequences of the workload until the
-    time budget is used (at least one sequence)."""
+def oracle_sample(w, budget_s=12.0, keep=False):
+    """The oracle as it stands on whole sequences of the workload, the last one
+    of the batch first (its rows sit at the highest offsets), then from the
+    first on, until the time budget is used (at least one sequence).  Returns
+    (states/s, sample description, seconds, {sequence: oracle y} if keep)."""
     import oracle
     t0 = time.perf_counter()
     states = 0
-    seqs = 0
+    outs = {}
     cache = {}
-    for i in range(w.nseq):
+    order = [w.nseq - 1] + list(range(w.nseq - 1))
+    done = []
+    for i in order:
         sl = w.seq(i)
+        L = sl.stop - sl.start
+        if L == 0:
+            continue
         s = int(w.sys_of_seq[i])
         if s not in cache:
             cache[s] = oracle.system_matrices(w, s)
         Abar, Bbar, C, D = cache[s]
-        L = sl.stop - sl.start
         N = w.N if w.N >= 0 else oracle.choose_N(Abar, int(w.lengths.max()), w.eps)
-        oracle.cascade_forward_seq(Abar, Bbar, C, D, w.u[sl], oracle.effective_N(N, L))
+        y = oracle.cascade_forward_seq(Abar, Bbar, C, D, w.u[sl], oracle.effective_N(N, L))
+        if keep:
+            outs[i] = y
         states += L
-        seqs += 1
+        done.append(i)
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return (states / dt, f"first {seqs} of {w.nseq} sequences ({states} states), powers included",
-            dt)
+    desc = (f"{len(done)} of {w.nseq} whole sequences ({states} states; the last sequence, "
+            f"then from the first), powers included")
+    return states / dt, desc, dt, outs
+
+
+def seq_errors(yg, yo, Du, out_eps):
+    """Relative Frobenius and element-wise errors of one sequence on y and on
+    Cx = y - Du (beyond the rounding of y to float)."""
+    import numpy as np
+    d = yg - yo
+    ny, my = np.linalg.norm(yo), np.max(np.abs(yo))
+    nd, md = np.linalg.norm(d), np.max(np.abs(d))
+    cx = yo - Du
+    ncx, mcx = np.linalg.norm(cx), np.max(np.abs(cx))
+    return (nd / ny if ny > 0 else nd,
+            max(nd - 2 * out_eps * ny, 0.0) / ncx if ncx > 0 else 0.0,
+            md / my if my > 0 else md,
+            max(md - 2 * out_eps * my, 0.0) / mcx if mcx > 0 else 0.0)
+
+
+def error_of(w, y_gpu, outs, precision, sample):
+    """The error object: worst per-sequence errors of the timed y against the
+    oracle's outputs on the cpu_baseline sample."""
+    import numpy as np
+    out_eps = 2.0 ** -53 if precision == "fp64" else 2.0 ** -24
+    worst = np.zeros(4)
+    for i, yo in outs.items():
+        sl = w.seq(i)
+        D = w.D[min(int(w.sys_of_seq[i]), w.D.shape[0] - 1)]
+        worst = np.maximum(worst, seq_errors(y_gpu[sl], yo, w.u[sl] @ D.T, out_eps))
+    bar = TOL[precision]
+    return {"frob_y": float(worst[0]), "frob_cx": float(worst[1]), "elem_y": float(worst[2]),
+            "elem_cx": float(worst[3]), "bar": bar, "pass": bool(np.all(worst <= bar)),
+            "sequences": sorted(int(i) for i in outs),
+            "what": "per sequence, worst over the sample: ||y - y_o|| / ||y_o|| and on Cx = "
+                    "y - Du; max|y - y_o| / max|y_o| and on Cx; oracle = CPU FP64 cascade",
+            "sample": sample}
 
 
 class ClockSampler:
@@ -202,18 +304,13 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-    import workloads as wl
-    w = wl.WORKLOADS[args.workload]()
-    if args.seqs and args.seqs < w.nseq:
-        w = w.subset(range(args.seqs))
-    description = SPECS[args.workload][1]
+    w = load_workload(args.workload, args.seqs)
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_states_per_s(w, budget_s=min(per_step, 2.0))
+        oracle_sample(w, budget_s=min(per_step, 2.0))
     vals, samples, secs = [], [], 0.0
     for _ in range(args.steps):
-        v, sample, dt = oracle_states_per_s(w, budget_s=per_step)
+        v, sample, dt, _ = oracle_sample(w, budget_s=per_step)
         vals.append(v)
         samples.append(sample)
         secs += dt
@@ -223,9 +320,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * secs / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": description, "global_batch": int(w.nseq),
-                       "seq_len": int(w.lengths.max()), "parallelism": "single",
-                       "oracle": "numpy float64 cascade (CPU)"},
+            "config": config_of(args.workload, w, 1),
             "cpu_baseline": {"value": value, "unit": "states/s", "cores": cores,
                              "kind": "oracle", "sample": samples[-1]},
             "e2e": {"value": value, "unit": "states/s", "h2d_bytes_per_step": 0,
@@ -233,26 +328,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# --------------------------------------------------------------------- workloads
-# name -> (generator kwargs builder, precision, one-line description, run backward?)
-SPECS = {
-    "precision_form": ("bf16_split", WORKLOAD, True),
-    "plain_fp64": ("fp64", "plain_fp64: HiPPO-LegS m=64 p=q=1, 1 seq x L=4096, delta=1/4096, "
-                   "N=11, FP64 (equals the recursion)", False),
-    "batching_form": ("fp32", "batching_form: HiPPO-LegS m=128 p=q=4, 512 seqs, L_i log-uniform "
-                      "[1024,65536] (8.85e6 rows), Abar*(1+1e-6), N_i from eps=1e-6, FP32 "
-                      "(3xTF32)", False),
-    "differentiation_form": ("bf16_split", "differentiation_form: HiPPO-LegS m=256 p=q=16, "
-                             "32 seqs x L=8192, delta=1e-3, N=12, BF16 split, fwd+bwd", True),
-    "large_form": ("bf16_split", "large_form: Abar=0.9999 Q + rank-4 E, m=1024 p=q=64, 8 seqs x "
-                   "L=65536, N=15, BF16 split, fwd+bwd", True),
-}
+# --------------------------------------------------------------------- our arm
+def events(n):
+    import torch
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(n)]
 
 
 def timed_steps(fn, steps, flush, stream):
+    """Per-step device milliseconds of fn, L2 flushed before each step."""
     import torch
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
+    ev = events(steps)
     torch.cuda.synchronize()
     for i in range(steps):
         flush.fill_(i & 0xFF)
@@ -263,38 +349,115 @@ def timed_steps(fn, steps, flush, stream):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-# --------------------------------------------------------------------- our arm
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
+def stage_roofline(w, c, stage_ms, precision, args):
+    """Roofline of the stage kernel from its per-launch durations (a separate
+    pass with an event pair around every stage launch)."""
+    import numpy as np
+    hbm_peak, bf16_peak, bf16_sustained, peak_kind = peaks()
+    m = w.m
+    f64 = precision == "fp64"
+    esize = 4 if precision == "bf16_split" else 8
+    Ls = w.lengths.astype(np.int64)
+    Ns = c.seq_N()
+    # stage 1 forming v^(1) on chip is another kernel variant (more warps, bound by
+    # instruction issue): reported on its own, with the bytes it moves
+    first = (not f64) and c.first_fused()
+    first_ms = float(np.mean(stage_ms[1])) if first and 1 in stage_ms else 0.0
+    plain = {k: v for k, v in stage_ms.items() if not (first and k == 1)}
+    tot = {k: sum(v) for k, v in plain.items()}
+    nl = sum(len(v) for v in plain.values())
+    avg_ms = sum(tot.values()) / max(1, nl)
+    fused = c.output_fused()
+    bytes_l, flops_l = [], []
+    for k in plain:
+        s = 1 << k
+        live = Ns >= k
+        last = live & (Ns == k) if fused else np.zeros_like(live)
+        mid = live & ~last
+        upd = int(np.maximum(Ls[live] - s, 0).sum())
+        upd_mid = int(np.maximum(Ls[mid] - s, 0).sum())
+        rows_mid, rows_last = int(Ls[mid].sum()), int(Ls[last].sum())
+        # before a sequence's last stage: read every row of v^(k) once and write the
+        # updated rows of v^(k+1) (esize bytes per element); its last stage with the
+        # output fused reads every row of v^(k) and u and writes y, not v (v as well
+        # when the plan keeps its stage outputs); plus the power's operand planes
+        bytes_l.append(esize * m * (rows_mid + upd_mid) + (esize * m + 4 * (w.p + w.q)) * rows_last
+                       + w.nsys * m * m * esize)
+        flops_l.append((1 if f64 else 3) * 2 * m * m * upd)
+    alg_bytes = float(np.mean(bytes_l)) if bytes_l else 0.0
+    alg_flops = float(np.mean(flops_l)) if flops_l else 0.0
+    gbs = alg_bytes / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else 0.0
+    tfs = alg_flops / (avg_ms / 1000.0) / 1e12 if avg_ms > 0 else 0.0
+    stage_total = sum(tot.values()) / max(1, args.steps)
+    if f64:
+        return {"bound": "alu", "achieved": tfs, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": tfs / 1.25, "traffic": None, "kernel": "stage_f64_kernel",
+                "peak_kind": "nominal FP64 (1.25 TFLOP/s)", "alg_flops_per_launch": alg_flops,
+                "avg_launch_ms": avg_ms, "launches_per_step": len(plain)}
+    # Tensor peak: the BF16 pair's measured rate (the TF32 pair's is half of it, the
+    # nominal 1.1 vs 2.25 PFLOP/s); the sustained figure when the stage launches of one
+    # step keep the tensor cores busy for 10 ms or more (the power cap then holds the
+    # clock down), the burst figure otherwise.
+    long_step = stage_total >= 10.0
+    tpk = (bf16_sustained if long_step else bf16_peak) * (1.0 if esize == 4 else 0.5)
+    tpk_kind = (f"{peak_kind} BF16 {'sustained' if long_step else 'burst'}"
+                + ("" if esize == 4 else " x 0.5 (TF32)"))
+    hbm_part = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
+    tensor_part = {"achieved": tfs, "peak": tpk, "unit": "TFLOP/s", "frac": tfs / tpk,
+                   "alg_flops_per_launch": alg_flops, "peak_kind": tpk_kind}
+    intensity = alg_flops / alg_bytes if alg_bytes > 0 else 0.0
+    ridge = tpk * 1e12 / (hbm_peak * 1e9)
+    tensor_bound = intensity > ridge
+    main, other = (tensor_part, hbm_part) if tensor_bound else (hbm_part, tensor_part)
+    kname = f"stage_tc_kernel<{'bf16' if esize == 4 else 'tf32'}>"
+    traffic, traffic_note = None, None
+    tr = TRAFFIC.get(args.cur_workload)
+    traffic_alg = None
+    if tr and not args.seqs and tr[1] in plain:
+        traffic, traffic_note = tr[0], tr[2]
+        traffic_alg = float(bytes_l[list(plain).index(tr[1])])
+    roof = {"bound": "tensor" if tensor_bound else "hbm", "achieved": main["achieved"],
+            "peak": main["peak"], "unit": main["unit"], "frac": main["frac"],
+            "traffic": traffic, "traffic_note": traffic_note,
+            "traffic_stage": tr[1] if traffic else None,
+            "alg_bytes_traffic_stage": traffic_alg,
+            "kernel": kname + (" (stages 2..N; stage 1 with v^(1) formed on chip under "
+                               "stage1_on_chip)" if first else " (stages 1..N)"),
+            "peak_kind": main["peak_kind"], "intensity_flop_per_byte": intensity,
+            "ridge_flop_per_byte": ridge, "alg_bytes_per_launch": alg_bytes,
+            "alg_flops_per_launch": alg_flops, "avg_launch_ms": avg_ms,
+            "launches_per_step": len(plain), "stage_ms_per_step": stage_total,
+            "hbm" if tensor_bound else "tensor": other}
+    if first and first_ms > 0:
+        rows1 = int(Ls[Ns >= 1].sum())
+        b1 = (esize * m + 4 * w.p) * rows1 + w.nsys * m * m * esize
+        roof["stage1_on_chip"] = {
+            "kernel": kname + " with v^(1) = Bbar u + Abar Bbar u_(l-1) formed on chip",
+            "ms": first_ms, "alg_bytes": b1, "achieved": b1 / (first_ms / 1000.0) / 1e9,
+            "unit": "GB/s", "frac_of_hbm": b1 / (first_ms / 1000.0) / 1e9 / hbm_peak}
+    return roof
+
+
+def measure(name, args, dev, world, rank):
+    """Every figure of one workload: forward (timed without per-stage events),
+    per-stage times (separate pass), end to end with host buffers and with
+    set-up, the work-efficient schedule, forward + backward, the FP64
+    comparators, and the oracle leg with the error of the timed y."""
+    import ctypes
     import numpy as np
     import torch
     import torch.distributed as dist
 
-    import workloads as wl
-    from paper_2411_17729_gb300 import build
-    build()
     from paper_2411_17729_gb300 import cascade
     from paper_2411_17729_gb300._abi import (CASCADE_FLAG_GRAPH, CASCADE_FLAG_RECOMPUTE,
                                              CASCADE_FLAG_SAVE_STATES, CASCADE_FLAG_SCAN)
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local)
-
-    precision, description, has_bwd = SPECS[args.workload]
-    w = wl.WORKLOADS[args.workload]()
-    if args.seqs and args.seqs < w.nseq:
-        w = w.subset(range(args.seqs))
+    args.cur_workload = name
+    precision, description, has_bwd = SPECS[name]
+    w = load_workload(name, args.seqs)
     m = w.m
     f64 = precision == "fp64"
     dt = torch.float64 if f64 else torch.float32
-    esize = 8  # bytes of one state element (both planes, or the FP64 plane)
-    if precision == "bf16_split":
-        esize = 4
     t_prep0 = time.perf_counter()
     c = cascade.from_workload(w, precision=precision, device=dev)
     torch.cuda.synchronize()
@@ -308,8 +471,8 @@ def main():
     def step():
         c.forward(u, y)
 
+    Ns = c.seq_N()
     shape = c.autotune(u, y, reps=3) if not f64 else (0, 0, 0)   # kernel shape (untimed)
-    # stages whose fastest shape differs from the plan-wide one
     stage_shapes = {} if f64 else {str(k): list(v) for k, v in c.stage_shapes().items()
                                    if tuple(v) != tuple(shape)}
     for _ in range(max(args.warmup, 3)):
@@ -318,11 +481,8 @@ def main():
     if c.device_error() != 0:
         raise RuntimeError("device wait timed out during warm-up")
 
-    # ---- timed region: K forward passes, L2 flushed before each
-    c.enable_stage_timing(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    stage_ms = {}
+    # ---- timed region: K forward passes, L2 flushed before each, no per-stage events
+    ev = events(args.steps)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -335,134 +495,82 @@ def main():
     torch.cuda.synchronize()
     sampler.start()
     launches0 = lib.cascade_launch_count()
+    torch.cuda.nvtx.range_push("timed")         # profiler filter (ncu --nvtx-include timed/)
     t0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
-        for k, ms in c.stage_times():
-            stage_ms.setdefault(k, []).append(ms)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
     launches = lib.cascade_launch_count() - launches0
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    c.enable_stage_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms_per_step = sum(step_ms) / len(step_ms)
-    ms_per_step = max_over_ranks(ms_per_step, world, dev)
+    ms_per_step = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
     states_per_step = int(w.rows)
     value = whole_job_rate(states_per_step, world, ms_per_step)
     if c.device_error() != 0:
         raise RuntimeError("device wait timed out in the timed region")
+    y_host = y.double().cpu().numpy()        # the timed output, for the error check
 
-    # ---- roofline of the dominant kernel (the stage kernel), per launch
-    hbm_peak, bf16_peak, bf16_sustained, peak_kind = peaks()
-    Ls = w.lengths.astype(np.int64)
-    Ns = c.seq_N()
-    # stage 1 forming v^(1) on chip is another kernel variant (more warps, bound by
-    # instruction issue): reported on its own, with the bytes it moves
-    first = (not f64) and c.first_fused()
-    first_ms = float(np.mean(stage_ms[1])) if first and 1 in stage_ms else 0.0
-    stage_ms_all = dict(stage_ms)
-    stage_ms = {k: v for k, v in stage_ms.items() if not (first and k == 1)}
-    tot_ms = {k: sum(v) for k, v in stage_ms.items()}
-    avg_ms = sum(tot_ms.values()) / max(1, sum(len(v) for v in stage_ms.values()))
-    launches_per_step = len(stage_ms)
-    bytes_per_launch, flops_per_launch = [], []
-    fused = c.output_fused()
-    for k in stage_ms:
-        s = 1 << k
-        live = Ns >= k
-        last = live & (Ns == k) if fused else np.zeros_like(live)
-        mid = live & ~last
-        upd = int(np.maximum(Ls[live] - s, 0).sum())
-        upd_mid = int(np.maximum(Ls[mid] - s, 0).sum())
-        rows_mid, rows_last = int(Ls[mid].sum()), int(Ls[last].sum())
-        # before a sequence's last stage: read every row of v^(k) once and write the
-        # updated rows of v^(k+1) (esize bytes per element); its last stage with the
-        # output fused reads every row of v^(k) and u and writes y, not v; plus the
-        # power's operand planes per system
-        bytes_per_launch.append(esize * m * (rows_mid + upd_mid)
-                                + (esize * m + 4 * (w.p + w.q)) * rows_last
-                                + w.nsys * m * m * esize)
-        flops_per_launch.append((1 if f64 else 3) * 2 * m * m * upd)
-    alg_bytes = float(np.mean(bytes_per_launch)) if bytes_per_launch else 0.0
-    alg_flops = float(np.mean(flops_per_launch)) if flops_per_launch else 0.0
-    achieved_gbs = alg_bytes / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else 0.0
-    achieved_tfs = alg_flops / (avg_ms / 1000.0) / 1e12 if avg_ms > 0 else 0.0
-    stage_share = sum(tot_ms.values()) / max(1e-9, sum(step_ms))
-    if f64:
-        roofline = {"bound": "alu", "achieved": achieved_tfs, "peak": 1.25, "unit": "TFLOP/s",
-                    "frac": achieved_tfs / 1.25, "traffic": None,
-                    "kernel": "stage_f64_kernel", "peak_kind": "nominal FP64 (1.25 TFLOP/s)",
-                    "alg_flops_per_launch": alg_flops, "avg_launch_ms": avg_ms,
-                    "launches_per_step": launches_per_step, "share_of_step": stage_share}
-    else:
-        # Tensor peak: the BF16 pair's measured rate (the TF32 pair's is half of it, the
-        # nominal 1.1 vs 2.25 PFLOP/s); the sustained figure when the stage launches of one
-        # step keep the tensor cores busy for 10 ms or more (the power cap then holds the
-        # clock down), the burst figure otherwise.
-        long_step = sum(tot_ms.values()) / max(1, args.steps) >= 10.0
-        tpk = (bf16_sustained if long_step else bf16_peak) * (1.0 if esize == 4 else 0.5)
-        tpk_kind = f"{peak_kind} BF16 {'sustained' if long_step else 'burst'}" + \
-            ("" if esize == 4 else " x 0.5 (TF32)")
-        hbm_part = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm_peak, "alg_bytes_per_launch": alg_bytes,
-                    "peak_kind": peak_kind}
-        tensor_part = {"achieved": achieved_tfs, "peak": tpk, "unit": "TFLOP/s",
-                       "frac": achieved_tfs / tpk, "alg_flops_per_launch": alg_flops,
-                       "peak_kind": tpk_kind}
-        # the binding roof: algorithmic intensity against the ridge of the two peaks
-        intensity = alg_flops / alg_bytes if alg_bytes > 0 else 0.0
-        ridge = tpk * 1e12 / (hbm_peak * 1e9)
-        tensor_bound = intensity > ridge
-        main, other = (tensor_part, hbm_part) if tensor_bound else (hbm_part, tensor_part)
-        kname = f"stage_tc_kernel<{'bf16' if esize == 4 else 'tf32'}>"
-        roofline = {"bound": "tensor" if tensor_bound else "hbm", "achieved": main["achieved"],
-                    "peak": main["peak"], "unit": main["unit"], "frac": main["frac"],
-                    "traffic": None,
-                    "kernel": kname + (" (stages 2..N; stage 1 with v^(1) formed on chip under "
-                                       "stage1_on_chip)" if first else " (stages 1..N)"),
-                    "peak_kind": main["peak_kind"],
-                    "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
-                    "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": alg_flops,
-                    "avg_launch_ms": avg_ms, "launches_per_step": launches_per_step,
-                    "share_of_step": stage_share,
-                    "hbm" if tensor_bound else "tensor": other}
-        if first and first_ms > 0:
-            # reads u (4 p bytes per row) and the power, writes every row of v^(2)
-            rows1 = int(Ls[Ns >= 1].sum())
-            b1 = (esize * m + 4 * w.p) * rows1 + w.nsys * m * m * esize
-            roofline["stage1_on_chip"] = {
-                "kernel": kname + " with v^(1) = Bbar u + Abar Bbar u_(l-1) formed on chip",
-                "ms": first_ms, "alg_bytes": b1, "achieved": b1 / (first_ms / 1000.0) / 1e9,
-                "unit": "GB/s", "frac_of_hbm": b1 / (first_ms / 1000.0) / 1e9 / hbm_peak}
-        if args.workload == "precision_form" and args.seqs in (0, 64) and TRAFFIC_NOTE:
-            roofline["traffic"] = TRAFFIC_NOTE["bytes_per_launch"]
-            roofline["traffic_note"] = TRAFFIC_NOTE["note"]
+    # ---- per-stage durations: a separate pass with an event pair per stage launch
+    c.enable_stage_timing(True)
+    stage_ms = {}
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        step()
+        for k, ms in c.stage_times():
+            stage_ms.setdefault(k, []).append(ms)
+    torch.cuda.synchronize()
+    c.enable_stage_timing(False)
+    roofline = stage_roofline(w, c, stage_ms, precision, args)
+    roofline["share_of_step"] = roofline.get("stage_ms_per_step", 0.0) / ms_per_step
 
     # ---- end to end through the public API with host buffers
-    u_host = torch.as_tensor(w.u, dtype=dt).pin_memory()
-    y_host = torch.empty((w.rows, w.q), dtype=dt).pin_memory()
+    u_pin = torch.as_tensor(w.u, dtype=dt).pin_memory()
+    y_pin = torch.empty((w.rows, w.q), dtype=dt).pin_memory()
 
     def e2e_step():
-        u.copy_(u_host, non_blocking=True)
+        u.copy_(u_pin, non_blocking=True)
         c.forward(u, y)
-        y_host.copy_(y, non_blocking=True)
+        y_pin.copy_(y, non_blocking=True)
 
-    e2e_ms = sum(timed_steps(e2e_step, args.steps, flush, stream)) / args.steps
-    e2e_ms = max_over_ranks(e2e_ms, world, dev)
-    e2e_value = whole_job_rate(states_per_step, world, e2e_ms)
+    e2e_ms = max_over_ranks(sum(timed_steps(e2e_step, args.steps, flush, stream)) / args.steps,
+                            world, dev)
+    shape_now = (shape, {int(k): tuple(v) for k, v in stage_shapes.items()})
     c.close()
     torch.cuda.empty_cache()
+
+    # ---- set-up (discretisation, squaring chain, operand split) plus one forward,
+    # host buffers in and out, the kernel shape saved from the tuning above
+    def setup_and_forward():
+        cc = cascade.from_workload(w, precision=precision, device=dev)
+        if not f64:
+            cc.set_kernel_shape(*shape_now[0])
+            cc.set_stage_shapes(shape_now[1])
+        u.copy_(u_pin, non_blocking=True)
+        cc.forward(u, y)
+        y_pin.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        return cc
+
+    setup_and_forward().close()                     # warm (first-touch of the host arrays)
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        cc = setup_and_forward()
+        ts.append(time.perf_counter() - ta)
+        cc.close()
+    setup_fwd_ms = 1000.0 * statistics.median(ts)
 
     # ---- the work-efficient schedule (about 2L products per sequence), same workload
     scan = None
     if not f64 and not args.no_scan:
-        import ctypes
         torch.cuda.nvtx.range_push("scan")         # profiler filter (ncu --nvtx-include scan/)
         # the level launches are short: the timed steps replay a CUDA graph of the
         # whole schedule (captured once per buffer set), without per-level events
@@ -471,19 +579,11 @@ def main():
         scan_shape = cg.autotune(u, y, reps=6)
         for _ in range(max(args.warmup, 3)):
             cg.forward(u, y)
-        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            sev[i][0].record(stream)
-            cg.forward(u, y)
-            sev[i][1].record(stream)
-        torch.cuda.synchronize()
+        scan_ms = max_over_ranks(
+            sum(timed_steps(lambda: cg.forward(u, y), args.steps, flush, stream)) / args.steps,
+            world, dev)
         if cg.device_error() != 0:
             raise RuntimeError("device wait timed out in the scan region")
-        scan_ms = sum(a.elapsed_time(b) for a, b in sev) / args.steps
-        scan_ms = max_over_ranks(scan_ms, world, dev)
         scan_levels = cg.stage_shapes()
         cg.close()
         torch.cuda.empty_cache()
@@ -507,28 +607,39 @@ def main():
             raise RuntimeError("device wait timed out in the scan region")
         nmv = ctypes.c_int64()
         cs._check(cs.lib.cascade_get_matvec_count(cs.plan, ctypes.byref(nmv)))
+        Ls = w.lengths.astype(np.int64)
         # algorithmic bytes of the level launches: per updated row, read the
         # destination and the source row and write the destination (esize bytes
         # per element), plus the power planes per system and launch
+        esize = 4 if precision == "bf16_split" else 8
         upd = nmv.value - sum(int(L) // 2 for L in Ls)      # products made on the tensor cores
-        nlev = len(lev_ms)
-        lev_tot = sum(sum(v) for v in lev_ms.values()) / args.steps
-        # destination row read and written, source row read; with the even rows of
-        # v^(1) formed on chip the last level reads only its source rows and u
+        stage_lev = {k: v for k, v in lev_ms.items() if k < 300}
+        nlev = len(stage_lev)
+        lev_tot = sum(sum(v) for v in stage_lev.values()) / args.steps
+        top_ms = sum(sum(v) for k, v in lev_ms.items() if k >= 300) / args.steps
         upd0 = sum(max(int(L) - 1, 0) // 2 for L in Ls) if cs.first_fused() else 0
         lev_bytes = (3 * esize * m * (upd - upd0) + (esize * m + 4 * w.p) * upd0
                      + nlev * w.nsys * m * m * esize)
         lev_gbs = lev_bytes / (lev_tot / 1000.0) / 1e9 if lev_tot > 0 else 0.0
+        hbm_peak, bf16_peak = peaks()[:2]
+        # 3 BF16 products of 2 m^2 per level product (the first level's products are
+        # the input projection's, not a level launch's)
+        lev_flops = 6.0 * m * m * upd
+        tpk = bf16_peak * (1.0 if esize == 4 else 0.5)
+        lev_tfs = lev_flops / (lev_tot / 1000.0) / 1e12 if lev_tot > 0 else 0.0
+        scan_tensor = lev_bytes > 0 and lev_flops / lev_bytes > tpk * 1e12 / (hbm_peak * 1e9)
         scan = {"value": whole_job_rate(states_per_step, world, scan_ms), "unit": "states/s",
                 "ms_per_step": scan_ms, "matvecs_per_step": int(nmv.value),
-                "matvecs_stage_schedule": int(sum(
-                    sum(max(int(L) - (1 << k), 0) for k in range(int(Nk) + 1))
-                    for L, Nk in zip(Ls, Ns))),
-                "levels": nlev, "level_ms_per_step": lev_tot,
-                "roofline": {"bound": "hbm", "achieved": lev_gbs, "peak": hbm_peak,
-                             "unit": "GB/s", "frac": lev_gbs / hbm_peak,
-                             "kernel": "stage_tc_kernel, strided in-place levels",
-                             "alg_bytes_per_step": lev_bytes, "peak_kind": peak_kind},
+                "levels": nlev, "level_ms_per_step": lev_tot, "top_of_tree_ms_per_step": top_ms,
+                "roofline": ({"bound": "tensor", "achieved": lev_tfs, "peak": tpk,
+                              "unit": "TFLOP/s", "frac": lev_tfs / tpk,
+                              "hbm_frac": lev_gbs / hbm_peak}
+                             if scan_tensor else
+                             {"bound": "hbm", "achieved": lev_gbs, "peak": hbm_peak,
+                              "unit": "GB/s", "frac": lev_gbs / hbm_peak,
+                              "tensor_frac": lev_tfs / tpk})
+                | {"kernel": "stage_tc_kernel, strided in-place levels",
+                   "alg_bytes_per_step": lev_bytes, "alg_flops_per_step": lev_flops},
                 "schedule": "up-sweep k=1..K-1, down-sweep k=K-2..0 (first level fused "
                             "with Bbar u), in place",
                 "timing": "CUDA graph replay of the level launches; per-level durations "
@@ -541,12 +652,12 @@ def main():
         torch.cuda.empty_cache()
         torch.cuda.nvtx.range_pop()
 
-    # ---- forward + backward (plan that keeps its stage outputs), same workload
+    # ---- forward + backward, same workload
     fb = None
     if has_bwd and not args.no_bwd:
         torch.cuda.nvtx.range_push("fwd_bwd")
         # the differentiation workload recomputes stage outputs from checkpoints
-        recompute = args.workload == "differentiation_form"
+        recompute = name == "differentiation_form"
         cb = cascade.from_workload(w, precision=precision,
                                    flags=CASCADE_FLAG_RECOMPUTE if recompute
                                    else CASCADE_FLAG_SAVE_STATES, device=dev)
@@ -592,64 +703,110 @@ def main():
         c64.forward(u64)
         ms = timed_steps(lambda: c64.forward(u64), 1, flush, stream)[0]
         fp64 = {"value": sub.rows / (ms / 1000.0), "unit": "states/s",
-                "sample": f"{sub.nseq} of {w.nseq} sequences, one pass"}
+                "sample": f"{sub.nseq} of {w.nseq} sequences, one pass", "error_bar": TOL["fp64"]}
         c64.close()
-    if args.workload in ("large_form", "plain_fp64") and not args.no_fp64:
-        sub = w.subset(range(nsub))
-        cr = cascade.from_workload(sub, precision="fp64", device=dev)
+    if not args.no_fp64:
+        # one block per sequence, one step after the other: its rate does not depend
+        # on the length, so a prefix of the first sequence bounds the time
+        nrec = min(int(w.lengths[0]), 4096 if m >= 512 else 65536)
+        sub = w.subset([0])
+        sub.offsets = np.array([0, nrec], np.int64)
+        sub.u = sub.u[:nrec]
+        cr = cascade.from_workload(sub, precision="fp64", device=dev, max_len=nrec)
         u64 = torch.as_tensor(sub.u, dtype=torch.float64).to(dev)
         ms = timed_steps(lambda: cr.recursion(u64), 1, flush, stream)[0]
-        rec = {"value": sub.rows / (ms / 1000.0), "unit": "states/s",
-               "sample": f"{sub.nseq} of {w.nseq} sequences, one pass, one block per sequence"}
+        rec = {"value": nrec / (ms / 1000.0), "unit": "states/s",
+               "sample": f"the first {nrec} steps of one sequence, one block"}
         cr.close()
 
-    # ---- oracle on the host cores (rank 0, N = 1 only)
-    cpu = None
+    # ---- oracle on the host cores (rank 0, N = 1 only), and the error of the timed y
+    cpu, error = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sample, _ = oracle_states_per_s(w, budget_s=12.0)
+        v, sample, _, outs = oracle_sample(w, budget_s=12.0, keep=True)
         cpu = {"value": v, "unit": "states/s", "cores": blas_threads(), "kind": "oracle",
                "sample": sample}
+        error = error_of(w, y_host, outs, precision, sample)
 
+    Ls = w.lengths.astype(np.int64)
+    res = {
+        "value": value, "ms_per_step": ms_per_step,
+        "dtype": {"bf16_split": "bf16", "fp32": "tf32", "fp64": "f64"}[precision],
+        "config": config_of(name, w, world),
+        "roofline": roofline,
+        "error": error,
+        "cpu_baseline": cpu,
+        "e2e": {"value": whole_job_rate(states_per_step, world, e2e_ms), "unit": "states/s",
+                "h2d_bytes_per_step": int(u.numel() * u.element_size()),
+                "d2h_bytes_per_step": int(y.numel() * y.element_size())},
+        "e2e_with_setup": {"value": states_per_step / (setup_fwd_ms / 1000.0), "unit": "states/s",
+                           "ms": setup_fwd_ms,
+                           "what": "plan creation, discretisation, FP64 squaring chain and "
+                                   "operand split, host-to-device u, forward, device-to-host y "
+                                   "(host clock, median of 3)"},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "fwd_bwd": fb,
+        "scan_fwd": scan,
+        "fp64_cascade": fp64,
+        "fp64_recursion": rec,
+        # products by powers per step: executed by the stage schedule of §3, the 2L
+        # bound of the abstract and §6, and the L of the recursion (Eq. 1.2)
+        "op_count": {
+            "stage_schedule": int(sum(sum(max(int(L) - (1 << k), 0) for k in range(int(Nk) + 1))
+                                      for L, Nk in zip(Ls, Ns))),
+            "work_efficient_schedule": scan["matvecs_per_step"] if scan else None,
+            "paper_bound_2L": int(2 * Ls.sum()), "recursion_L": int(Ls.sum())},
+        "precompute_s": prep_s,
+        "kernel_shape": {"stages": shape[0], "ring": shape[1], "chunks_per_step": shape[2],
+                         "per_stage": stage_shapes},
+        "stage_ms": {str(k): statistics.median(v) for k, v in sorted(stage_ms.items())},
+        "wall_s": wall,
+    }
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_17729_gb300 import build
+    build()
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    head = measure(args.workload, args, dev, world, rank)
+    also = None
+    if args.also and args.also != "none" and args.also != args.workload:
+        also = measure(args.also, args, dev, world, rank)
+
+    failed = [r for r in (head, also) if r and r["error"] and not r["error"]["pass"]]
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": world,
-            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16_split": "bf16", "fp32": "tf32", "fp64": "f64"}[precision],
-            "data": "synthetic",
-            "config": {"workload": description, "global_batch": int(w.nseq) * world,
-                       "seq_len": int(Ls.max()),
-                       "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "l2": "flushed before each timed step (256 MiB write)",
-                       "timing": "CUDA events on the launching stream, sum over steps",
-                       "kernel_shape": {"stages": shape[0], "ring": shape[1],
-                                        "chunks_per_step": shape[2],
-                                        "per_stage": stage_shapes}},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "states/s",
-                    "h2d_bytes_per_step": int(u.numel() * u.element_size()),
-                    "d2h_bytes_per_step": int(y.numel() * y.element_size())},
-            "gpu_launches": int(launches),
-            "clocks": clocks,
-            "fwd_bwd": fb,
-            "scan_fwd": scan,
-            # products by powers per step: executed by the stage schedule of §3, the
-            # 2L bound of the abstract and §6, and the L of the recursion (Eq. 1.2)
-            "op_count": {"stage_schedule": int(sum(
-                sum(max(int(L) - (1 << k), 0) for k in range(int(Nk) + 1))
-                for L, Nk in zip(Ls, Ns))),
-                "work_efficient_schedule": scan["matvecs_per_step"] if scan else None,
-                "paper_bound_2L": int(2 * Ls.sum()), "recursion_L": int(Ls.sum())},
-            "fp64_cascade": fp64,
-            "fp64_recursion": rec,
-            "precompute_s": prep_s,
-            "stage_ms": {str(k): statistics.median(v) for k, v in sorted(stage_ms_all.items())},
-            "wall_s": wall,
-        }
+        line = {"metric": METRIC, "value": head["value"], "unit": "states/s", "n_gpus": world,
+                "steps": args.steps, "warmup": max(args.warmup, 3),
+                "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic",
+                "config": head["config"],
+                "timing": "CUDA events on the launching stream around each step, L2 flushed "
+                          "(256 MiB write) before each timed step, no per-stage events in the "
+                          "timed steps",
+                **{k: v for k, v in head.items()
+                   if k not in ("value", "ms_per_step", "dtype", "config")}}
+        if also:
+            line[args.also] = also
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    if failed:
+        print("error above the bar: " + "; ".join(json.dumps(r["error"]) for r in failed),
+              file=sys.stderr, flush=True)
+        sys.exit(3)
 
 
 if __name__ == "__main__":

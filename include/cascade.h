@@ -112,7 +112,14 @@ enum {
      their output reads it; on the work-efficient schedule with the output
      fused, for the even rows in the last down-sweep level.  Results are the
      same bit for bit (cascade_get_first_fused).                           */
-  CASCADE_FLAG_NO_FUSED_FIRST = 64
+  CASCADE_FLAG_NO_FUSED_FIRST = 64,
+  /* Discretise and square with the dense kernels even when every A (or Abar)
+     is lower-triangular (diagnostics).  For lower-triangular systems, such as
+     HiPPO-LegS, the set-up otherwise skips the zero triangle in the
+     elimination of Eq. (4.2) and in the squaring chain; the pivots are chosen
+     the same way and only exact zeros are left out, so the powers are the
+     same bit for bit.                                                      */
+  CASCADE_FLAG_DENSE_SETUP = 128
 };
 
 typedef struct cascade_plan_s* cascade_plan_t;

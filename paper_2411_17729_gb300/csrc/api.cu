@@ -301,17 +301,48 @@ void free_system(Plan* p) {
   p->P32 = p->Minv32 = nullptr;
 }
 
+// Whether every one of the plan's nsys matrices X[s] (sys_stride apart) is
+// lower-triangular (exact zeros above the diagonal).  Synchronises st; false on
+// any CUDA error (the dense paths then run).
+void check_lower(Plan* p, const double* X, int64_t sys_stride, bool* lower, cudaStream_t st) {
+  *lower = false;
+  if (p->d.flags & CASCADE_FLAG_DENSE_SETUP) return;
+  int32_t* flag = nullptr;
+  int32_t h = 1;
+  cudaError_t e = cudaMalloc(&flag, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = launch_upper_nonzero(X, sys_stride, p->d.nsys, p->d.m, flag, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (flag) cudaFree(flag);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  *lower = (h == 0);
+}
+
 // Squaring chain, accuracy rule, Abar*Bbar, operand planes; P64[:,0] and
 // Bbar64, C64, D64 are set.  Synchronises st.
 cascade_status_t finish_system(Plan* p, cudaStream_t st) {
   const int m = p->d.m, pp = p->d.p, q = p->d.q, ns = p->d.nsys;
   const int64_t mm = (int64_t)m * m;
   const int64_t sys_stride = (int64_t)p->kmax1 * mm;
+  // Lower-triangular Abar (the HiPPO-LegS systems): its powers are lower-triangular
+  // too, and the squaring skips the zero triangle (same results bit for bit)
+  bool lower = false;
+  check_lower(p, p->P64, sys_stride, &lower, st);
+  p->lower_powers = lower;
   // P_{k+1} = P_k P_k  (end of §2), batched over systems
   for (int k = 0; k + 1 < p->kmax1; ++k) {
-    CK(launch_dgemm(p->P64 + k * mm, p->P64 + k * mm, p->P64 + (k + 1) * mm, m, m, m, m, m, m,
-                    sys_stride, sys_stride, sys_stride, ns, 1.0, 0.0, false, false, st),
-       "squaring chain");
+    if (lower)
+      CK(launch_dgemm_lower(p->P64 + k * mm, p->P64 + k * mm, p->P64 + (k + 1) * mm, m,
+                            sys_stride, sys_stride, sys_stride, ns, st),
+         "squaring chain");
+    else
+      CK(launch_dgemm(p->P64 + k * mm, p->P64 + k * mm, p->P64 + (k + 1) * mm, m, m, m, m, m, m,
+                      sys_stride, sys_stride, sys_stride, ns, 1.0, 0.0, false, false, st),
+         "squaring chain");
   }
   // Abar Bbar for the first stage fused with the input projection
   CK(launch_dgemm(p->P64, p->Bbar64, p->ABbar64, m, pp, m, m, pp, pp, sys_stride, (int64_t)m * pp,
@@ -1186,10 +1217,13 @@ cascade_status_t cascade_set_system_continuous(cascade_plan_t plan, const double
   if (!p->Minv64) CK(dalloc(&p->Minv64, (size_t)ns * m * m), "alloc M^-1");
   cudaError_t e = cudaMalloc(&sing, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(sing, 0, sizeof(int32_t), st);
+  // lower-triangular A (HiPPO-LegS): the elimination skips the zero triangle
+  bool lower = false;
+  if (e == cudaSuccess) check_lower(p, p->A64, (int64_t)m * m, &lower, st);
   if (e == cudaSuccess)
     e = launch_discretise(p->A64, p->B64, p->delta64, p->scale64, p->P64,
                           (int64_t)p->kmax1 * m * m, p->Bbar64, p->Minv64, work, ns, m, pp, sing,
-                          st);
+                          lower, st);
   int32_t h_sing = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_sing, sing, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -136,6 +136,7 @@ struct Plan {
   std::vector<int> zoh_sq, zoh_sq_adj;
   double* zoh_f_adj = nullptr;   // [nsys] 2^-zoh_sq_adj
   std::vector<int32_t> N_sys;
+  bool lower_powers = false;     // every Abar lower-triangular: triangular squaring chain
   int32_t* err = nullptr;        // device error word, then 7 diagnostic words
   // batch
   bool have_batch = false;
@@ -235,7 +236,13 @@ size_t state_bytes_per_row(const Plan& p);    // bytes of one state row (all pla
 cudaError_t launch_discretise(const double* A, const double* B, const double* delta,
                               const double* scale, double* Abar_out, int64_t abar_sys_stride,
                               double* Bbar_out, double* Minv_out, double* work, int nsys, int m,
-                              int p, int32_t* singular, cudaStream_t st);
+                              int p, int32_t* singular, bool lower, cudaStream_t st);
+// flag = 1 if a matrix of the batch has a non-zero above its diagonal
+cudaError_t launch_upper_nonzero(const double* X, int64_t sys_stride, int ns, int m, int32_t* flag,
+                                 cudaStream_t st);
+// C = A B for lower-triangular n x n A, B (batched), skipping the exact zeros
+cudaError_t launch_dgemm_lower(const double* A, const double* B, double* C, int n, int64_t sA,
+                               int64_t sB, int64_t sC, int batch, cudaStream_t st);
 cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
                          int lda, int ldb, int ldc, int64_t sA, int64_t sB, int64_t sC,
                          int batch, double alpha, double beta, bool transA, bool transB,

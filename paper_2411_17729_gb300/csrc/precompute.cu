@@ -21,11 +21,13 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
     const double* __restrict__ A, const double* __restrict__ B, const double* __restrict__ delta,
     const double* __restrict__ scale, double* __restrict__ Abar, int64_t abar_stride,
     double* __restrict__ Bbar, double* __restrict__ Minv, double* __restrict__ work, int m, int p,
-    int32_t* singular) {
-  extern __shared__ double fac[];          // m elimination factors
+    int32_t* singular, int lower) {
+  extern __shared__ double fac[];          // m elimination factors, then m row labels
+  int* orig = reinterpret_cast<int*>(fac + m);
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_piv;
+  __shared__ int s_U;
   __shared__ double s_inv;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -45,8 +47,17 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
     else v = (i == j - 2 * m - p) ? 1.0 : 0.0;
     T[idx] = v;
   }
+  for (int i = tid; i < m; i += nt) orig[i] = i;
+  if (tid == 0) s_U = -1;
   __syncthreads();
 
+  // lower (A lower-triangular): in the three triangular blocks (M, I + delta/2 A,
+  // I) a row that started as row r holds non-zeros only at block offsets <= r, and
+  // the elimination mixes in pivot rows that started at rows <= U (the largest
+  // starting row of any pivot so far).  The pivot row at step c is then zero past
+  // offset U in those blocks, so the normalisation and the elimination skip those
+  // columns: the skipped updates would subtract exact zeros, and the pivots are
+  // chosen as before, so the result is the dense elimination's bit for bit.
   for (int c = 0; c < m; ++c) {
     // pivot: largest |T[i][c]| for i >= c (smallest index on ties)
     double best = -1.0;
@@ -69,6 +80,10 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
         if (red_v[w] > b || (red_v[w] == b && red_i[w] < i0)) { b = red_v[w]; i0 = red_i[w]; }
       s_piv = i0;
       if (!(b > 0.0)) atomicExch(singular, 1);
+      if (orig[i0] > s_U) s_U = orig[i0];
+      const int t = orig[c];
+      orig[c] = orig[i0];
+      orig[i0] = t;
     }
     __syncthreads();
     const int piv = s_piv;
@@ -86,12 +101,26 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
     }
     __syncthreads();
     const double inv = s_inv;
-    for (int j = c + tid; j < W; j += nt) T[(int64_t)c * W + j] *= inv;
+    // columns of the pivot row that may be non-zero: all W - c of them, or with
+    // lower the offsets <= U of the three triangular blocks and every column of B
+    const int U = s_U;
+    const int n1 = lower ? U - c + 1 : m - c;      // M block, from column c
+    const int n2 = lower ? U + 1 : m;              // I + delta/2 A block
+    const int nc = lower ? n1 + n2 + p + (U + 1) : W - c;
+    auto col = [&](int t) -> int {
+      if (!lower) return c + t;
+      if (t < n1) return c + t;
+      t -= n1;
+      if (t < n2) return m + t;
+      t -= n2;
+      if (t < p) return 2 * m + t;
+      return 2 * m + p + (t - p);
+    };
+    for (int t = tid; t < nc; t += nt) T[(int64_t)c * W + col(t)] *= inv;
     for (int i = tid; i < m; i += nt) fac[i] = (i == c) ? 0.0 : T[(int64_t)i * W + c];
     __syncthreads();
-    const int wc = W - c;
-    for (int64_t idx = tid; idx < (int64_t)m * wc; idx += nt) {
-      const int i = (int)(idx / wc), j = c + (int)(idx % wc);
+    for (int64_t idx = tid; idx < (int64_t)m * nc; idx += nt) {
+      const int i = (int)(idx / nc), j = col((int)(idx % nc));
       const double f = fac[i];
       if (f != 0.0) T[(int64_t)i * W + j] -= f * T[(int64_t)c * W + j];
     }
@@ -121,15 +150,16 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
 cudaError_t launch_discretise(const double* A, const double* B, const double* delta,
                               const double* scale, double* Abar_out, int64_t abar_sys_stride,
                               double* Bbar_out, double* Minv_out, double* work, int nsys, int m,
-                              int p, int32_t* singular, cudaStream_t st) {
-  const size_t smem = sizeof(double) * (size_t)m;
+                              int p, int32_t* singular, bool lower, cudaStream_t st) {
+  const size_t smem = (sizeof(double) + sizeof(int)) * (size_t)m;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(discretise_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   discretise_kernel<<<nsys, 1024, smem, st>>>(A, B, delta, scale, Abar_out, abar_sys_stride,
-                                               Bbar_out, Minv_out, work, m, p, singular);
+                                               Bbar_out, Minv_out, work, m, p, singular,
+                                               lower ? 1 : 0);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }
@@ -143,7 +173,7 @@ template <typename T, bool TA, bool TB>
 __global__ void __launch_bounds__(256) gemm_kernel(const T* __restrict__ A, const T* __restrict__ B,
                                                    T* __restrict__ C, int M, int N, int K, int lda,
                                                    int ldb, int ldc, int64_t sA, int64_t sB,
-                                                   int64_t sC, T alpha, T beta) {
+                                                   int64_t sC, T alpha, T beta, int lower = 0) {
   __shared__ T As[16][65];
   __shared__ T Bs[16][65];
   A += (int64_t)blockIdx.z * sA;
@@ -157,7 +187,15 @@ __global__ void __launch_bounds__(256) gemm_kernel(const T* __restrict__ A, cons
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0;
 
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  // lower: A and B lower-triangular (C = A B is too).  A tile above the diagonal
+  // is zero, and the K loop runs over k in [n0, m0 + 64) only: every product left
+  // out has an exactly zero factor, so the sums are the full loop's bit for bit.
+  int kbeg = 0, kend = K;
+  if (lower) {
+    kbeg = n0 < m0 + 64 ? n0 : 0;
+    kend = n0 < m0 + 64 ? min(K, m0 + 64) : 0;
+  }
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
     for (int e = threadIdx.x; e < 1024; e += 256) {
       int mm, kk;
       if (!TA) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
@@ -217,6 +255,38 @@ cudaError_t launch_gemm(const T* A, const T* B, T* C, int M, int N, int K, int l
     gemm_kernel<T, false, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
   else
     gemm_kernel<T, true, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+// flag = 1 if any of the ns matrices X[s] (m x m, row-major, sys_stride apart)
+// has a non-zero entry above the diagonal (flag is not cleared here).
+__global__ void upper_nonzero_kernel(const double* __restrict__ X, int64_t sys_stride, int ns,
+                                     int m, int32_t* flag) {
+  const int64_t mm = (int64_t)m * m, n = mm * ns;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx / mm, r = idx % mm;
+    if (r % m > r / m && X[s * sys_stride + r] != 0.0) *flag = 1;
+  }
+}
+
+cudaError_t launch_upper_nonzero(const double* X, int64_t sys_stride, int ns, int m, int32_t* flag,
+                                 cudaStream_t st) {
+  if (ns <= 0 || m <= 0) return cudaSuccess;
+  const int64_t n = (int64_t)ns * m * m;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  upper_nonzero_kernel<<<grid, 256, 0, st>>>(X, sys_stride, ns, m, flag);
+  CASCADE_LAUNCHED();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dgemm_lower(const double* A, const double* B, double* C, int n, int64_t sA,
+                               int64_t sB, int64_t sC, int batch, cudaStream_t st) {
+  if (n <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((n + 63) / 64, (n + 63) / 64, batch);
+  gemm_kernel<double, false, false><<<grid, 256, 0, st>>>(A, B, C, n, n, n, n, n, n, sA, sB, sC,
+                                                          1.0, 0.0, 1);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }

@@ -407,3 +407,41 @@ def test_many_items_per_block(lib, precision):
     sequence start) interleaved with computed ones."""
     w = wl.precision_form(m=128, L=2048, batch=40, N=10)
     c, y, yo = check(lib, w, precision)
+
+
+@pytest.mark.parametrize("discrete", [False, True])
+def test_lower_triangular_setup_bitwise(lib, discrete):
+    """HiPPO-LegS is lower-triangular: the set-up then skips the zero triangle in
+    the elimination of Eq. (4.2) and in the squaring chain.  Powers and outputs
+    equal the dense set-up's (CASCADE_FLAG_DENSE_SETUP) bit for bit, with step
+    sizes up to 0.3, where the pivot search swaps rows (an off-diagonal entry of
+    I - delta/2 A exceeds the diagonal), and they match the oracle."""
+    import torch
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_DENSE_SETUP
+    w = wl.precision_form(m=256, L=1500, batch=4, N=10)
+    w.delta = np.array([1e-4, 1e-2, 0.1, 0.3])
+    if discrete:
+        mats = [oracle.system_matrices(w, s) for s in range(4)]
+        w.Abar = np.stack([mt[0] for mt in mats])
+        w.B = np.stack([mt[1] for mt in mats])
+        w.A, w.delta = None, None
+    w = cast_inputs(w, "bf16_split")
+    u = torch.as_tensor(w.u, dtype=torch.float32).cuda()
+    out = []
+    for flags in (0, CASCADE_FLAG_DENSE_SETUP):
+        c = lib.from_workload(w, precision="bf16_split", flags=flags)
+        P = [c.powers(s, 10).cpu().numpy() for s in range(4)]
+        y = c.forward(u).double().cpu().numpy()
+        torch.cuda.synchronize()
+        assert c.device_error() == 0
+        out.append((P, y, c))
+    for s in range(4):
+        assert np.array_equal(out[0][0][s], out[1][0][s]), s
+        assert np.all(np.triu(out[0][0][s][0], 1) == 0.0)
+    assert np.array_equal(out[0][1], out[1][1])
+    yo = oracle.cascade_forward(w, N_per_seq=out[0][2].seq_N())
+    gate(w, out[0][1], yo, "bf16_split")
+    for s in range(4):
+        Abar, _, _, _ = oracle.system_matrices(w, s)
+        P = oracle.squaring_chain(Abar, 10)
+        assert np.max(np.abs(out[0][0][s][0] - P[0])) <= 1e-12 * np.max(np.abs(P[0]))

@@ -115,10 +115,12 @@ enum {
   CASCADE_FLAG_NO_FUSED_FIRST = 64,
   /* Discretise and square with the dense kernels even when every A (or Abar)
      is lower-triangular (diagnostics).  For lower-triangular systems, such as
-     HiPPO-LegS, the set-up otherwise skips the zero triangle in the
-     elimination of Eq. (4.2) and in the squaring chain; the pivots are chosen
-     the same way and only exact zeros are left out, so the powers are the
-     same bit for bit.                                                      */
+     HiPPO-LegS, the set-up otherwise solves Eq. (4.2) by forward elimination
+     without row exchanges (a triangular system needs none), over the non-zero
+     triangle only, so Abar comes out exactly lower-triangular, and squares it
+     with a triangular product that leaves out only exact zeros.  Where the
+     dense elimination exchanges no rows either (small delta), the powers are
+     the same bit for bit.                                                  */
   CASCADE_FLAG_DENSE_SETUP = 128
 };
 

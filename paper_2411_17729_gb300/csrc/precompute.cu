@@ -22,12 +22,10 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
     const double* __restrict__ scale, double* __restrict__ Abar, int64_t abar_stride,
     double* __restrict__ Bbar, double* __restrict__ Minv, double* __restrict__ work, int m, int p,
     int32_t* singular, int lower) {
-  extern __shared__ double fac[];          // m elimination factors, then m row labels
-  int* orig = reinterpret_cast<int*>(fac + m);
+  extern __shared__ double fac[];          // m elimination factors
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_piv;
-  __shared__ int s_U;
   __shared__ double s_inv;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -47,43 +45,44 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
     else v = (i == j - 2 * m - p) ? 1.0 : 0.0;
     T[idx] = v;
   }
-  for (int i = tid; i < m; i += nt) orig[i] = i;
-  if (tid == 0) s_U = -1;
   __syncthreads();
 
-  // lower (A lower-triangular): in the three triangular blocks (M, I + delta/2 A,
-  // I) a row that started as row r holds non-zeros only at block offsets <= r, and
-  // the elimination mixes in pivot rows that started at rows <= U (the largest
-  // starting row of any pivot so far).  The pivot row at step c is then zero past
-  // offset U in those blocks, so the normalisation and the elimination skip those
-  // columns: the skipped updates would subtract exact zeros, and the pivots are
-  // chosen as before, so the result is the dense elimination's bit for bit.
+  // lower (A lower-triangular, so M = I - delta/2 A is): a triangular system
+  // needs no row exchanges (forward elimination without them is backward
+  // stable), so the pivot is the diagonal.  In the three triangular blocks (M,
+  // I + delta/2 A, I) row c is then zero past offset c and the rows above c have
+  // a zero in column c, so the elimination touches rows below c and, in those
+  // blocks, offsets up to c only; the result is exactly lower-triangular.  When
+  // the dense elimination exchanges no rows either, the two agree bit for bit.
   for (int c = 0; c < m; ++c) {
-    // pivot: largest |T[i][c]| for i >= c (smallest index on ties)
-    double best = -1.0;
-    int bi = c;
-    for (int i = c + tid; i < m; i += nt) {
-      const double a = fabs(T[(int64_t)i * W + c]);
-      if (a > best) { best = a; bi = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double b = red_v[0];
-      int i0 = red_i[0];
-      for (int w = 1; w < (nt + 31) / 32; ++w)
-        if (red_v[w] > b || (red_v[w] == b && red_i[w] < i0)) { b = red_v[w]; i0 = red_i[w]; }
-      s_piv = i0;
-      if (!(b > 0.0)) atomicExch(singular, 1);
-      if (orig[i0] > s_U) s_U = orig[i0];
-      const int t = orig[c];
-      orig[c] = orig[i0];
-      orig[i0] = t;
+    if (lower) {
+      if (tid == 0) {
+        s_piv = c;
+        if (!(T[(int64_t)c * W + c] != 0.0)) atomicExch(singular, 1);
+      }
+    } else {
+      // pivot: largest |T[i][c]| for i >= c (smallest index on ties)
+      double best = -1.0;
+      int bi = c;
+      for (int i = c + tid; i < m; i += nt) {
+        const double a = fabs(T[(int64_t)i * W + c]);
+        if (a > best) { best = a; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        double b = red_v[0];
+        int i0 = red_i[0];
+        for (int w = 1; w < (nt + 31) / 32; ++w)
+          if (red_v[w] > b || (red_v[w] == b && red_i[w] < i0)) { b = red_v[w]; i0 = red_i[w]; }
+        s_piv = i0;
+        if (!(b > 0.0)) atomicExch(singular, 1);
+      }
     }
     __syncthreads();
     const int piv = s_piv;
@@ -101,26 +100,25 @@ __global__ void __launch_bounds__(1024) discretise_kernel(
     }
     __syncthreads();
     const double inv = s_inv;
-    // columns of the pivot row that may be non-zero: all W - c of them, or with
-    // lower the offsets <= U of the three triangular blocks and every column of B
-    const int U = s_U;
-    const int n1 = lower ? U - c + 1 : m - c;      // M block, from column c
-    const int n2 = lower ? U + 1 : m;              // I + delta/2 A block
-    const int nc = lower ? n1 + n2 + p + (U + 1) : W - c;
+    // columns of row c that may be non-zero: all W - c of them, or with lower
+    // column c of M, offsets 0..c of the other two triangular blocks and all of B
+    const int nc = lower ? 1 + (c + 1) + p + (c + 1) : W - c;
     auto col = [&](int t) -> int {
       if (!lower) return c + t;
-      if (t < n1) return c + t;
-      t -= n1;
-      if (t < n2) return m + t;
-      t -= n2;
+      if (t == 0) return c;
+      t -= 1;
+      if (t <= c) return m + t;
+      t -= c + 1;
       if (t < p) return 2 * m + t;
       return 2 * m + p + (t - p);
     };
     for (int t = tid; t < nc; t += nt) T[(int64_t)c * W + col(t)] *= inv;
     for (int i = tid; i < m; i += nt) fac[i] = (i == c) ? 0.0 : T[(int64_t)i * W + c];
     __syncthreads();
-    for (int64_t idx = tid; idx < (int64_t)m * nc; idx += nt) {
-      const int i = (int)(idx / nc), j = col((int)(idx % nc));
+    const int r0 = lower ? c + 1 : 0;                 // rows that may hold a non-zero factor
+    const int64_t nupd = (int64_t)(m - r0) * nc;
+    for (int64_t idx = tid; idx < nupd; idx += nt) {
+      const int i = r0 + (int)(idx / nc), j = col((int)(idx % nc));
       const double f = fac[i];
       if (f != 0.0) T[(int64_t)i * W + j] -= f * T[(int64_t)c * W + j];
     }
@@ -151,7 +149,7 @@ cudaError_t launch_discretise(const double* A, const double* B, const double* de
                               const double* scale, double* Abar_out, int64_t abar_sys_stride,
                               double* Bbar_out, double* Minv_out, double* work, int nsys, int m,
                               int p, int32_t* singular, bool lower, cudaStream_t st) {
-  const size_t smem = (sizeof(double) + sizeof(int)) * (size_t)m;
+  const size_t smem = sizeof(double) * (size_t)m;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(discretise_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

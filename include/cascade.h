@@ -82,7 +82,10 @@ enum {
      precedence when both flags are given.                                  */
   CASCADE_FLAG_RECOMPUTE = 2,
   /* Do not fuse y = C v + D u into the last stage (diagnostics).  The fused
-     epilogue is used for q <= 4 when one tile spans all m columns.          */
+     output is formed on the CUDA cores in the epilogue for q <= 4 when one
+     tile spans all m columns, and on the tensor cores (a second tcgen05
+     product of the finished state tile with C, plus D u) for BF16-split
+     plans with p and q multiples of 16 and q <= 64.                         */
   CASCADE_FLAG_NO_FUSED_OUTPUT = 4,
   /* Record the forward launch sequence once per (u, y, workspace) triple in
      a CUDA graph and replay it on later calls.                             */
@@ -214,8 +217,13 @@ cascade_status_t cascade_get_matvec_count(cascade_plan_t plan, int64_t* h_count)
    sequence's last stage (the stage then reads v^(N_i) and u and writes y;
    it writes v^(N_i+1) only when the plan keeps its stage outputs), or by a
    separate projection after the last stage.  Fixed at plan creation: FP32
-   or BF16-split plans with q <= 4 whose stage tiles span all m columns,
-   unless created with CASCADE_FLAG_NO_FUSED_OUTPUT.  *h_fused = 1 or 0. */
+   or BF16-split plans with q <= 4 whose stage tiles span all m columns (y on
+   the CUDA cores), and BF16-split plans on the §3 schedule with p and q
+   multiples of 16 and q <= 64 (y on the tensor cores: the finished (hi, lo)
+   state chunks times C, plus u times D, accumulated in TMEM; with m above
+   one column block the partial sums over the blocks are added in a fixed
+   order), unless created with CASCADE_FLAG_NO_FUSED_OUTPUT.  *h_fused = 1
+   or 0. */
 cascade_status_t cascade_get_output_fused(cascade_plan_t plan, int32_t* h_fused);
 
 /* Whether first-stage values v^(1) = Bbar u_l + Abar Bbar u_(l-1) are formed

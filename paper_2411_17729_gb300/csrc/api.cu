@@ -625,7 +625,8 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
          "stage (fp64)");
     } else {
       CK(launch_stage_tc(*p, k, V.hi(in), V.lo(in), V.hi(out), V.lo(out),
-                         static_cast<const float*>(u), static_cast<float*>(y), st),
+                         static_cast<const float*>(u), static_cast<float*>(y), st, false,
+                         ptc ? U.hi(0) : nullptr, ptc ? U.lo(0) : nullptr),
          "stage (tensor core)");
     }
     if (timing && p->n_tiles[k] > 0) {
@@ -1151,6 +1152,13 @@ cascade_status_t cascade_plan_create(cascade_plan_t* out, const cascade_desc_t* 
   // separate output GEMM
   p->fuse_output = d.precision != CASCADE_FP64 && !(d.flags & CASCADE_FLAG_NO_FUSED_OUTPUT) &&
                    block_n(d.m, d.precision) == d.m && d.q <= 4;
+  // wider outputs of BF16-split plans whose projections run on the tensor cores
+  // (p, q multiples of 16): y = C v + D u as a second tensor-core product in the
+  // last stage, C v from the staged final state chunks (q <= 64: the y columns
+  // fit inside one tile's accumulator)
+  p->fuse_output_mma = !p->fuse_output && d.precision == CASCADE_BF16_SPLIT &&
+                       !(d.flags & (CASCADE_FLAG_NO_FUSED_OUTPUT | CASCADE_FLAG_SCAN)) &&
+                       d.m % 64 == 0 && d.p % 16 == 0 && d.q % 16 == 0 && d.q <= 64;
   e = cudaMalloc(&p->err, 8 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(p->err, 0, 8 * sizeof(int32_t));
   if (e != cudaSuccess) {
@@ -1499,7 +1507,7 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     const int64_t L = h_offsets[i + 1] - h_offsets[i];
     if (L == 0) continue;
     const int N = p->seq_N[i], sys = p->sys_of_seq[i];
-    const bool fused_last = p->fuse_output && N >= 1 && !scans(*p);
+    const bool fused_last = (p->fuse_output || p->fuse_output_mma) && N >= 1 && !scans(*p);
     // (the work-efficient schedule forms y in its down-sweep levels instead)
     for (int k = 1; k <= N && !scans(*p); ++k) {   // stage schedule (§3)
       const bool fused = fused_last && k == N;
@@ -1648,7 +1656,7 @@ cascade_status_t cascade_get_matvec_count(cascade_plan_t plan, int64_t* h_count)
 cascade_status_t cascade_get_output_fused(cascade_plan_t plan, int32_t* h_fused) {
   Plan* p = plan;
   if (!p || !h_fused) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
-  *h_fused = p->fuse_output ? 1 : 0;
+  *h_fused = (p->fuse_output || p->fuse_output_mma) ? 1 : 0;
   return CASCADE_OK;
 }
 

@@ -172,6 +172,9 @@ struct Plan {
   Tile* d_stage0_tiles = nullptr;            // tiles for the first stage (all rows)
   int n_stage0_tiles = 0;
   bool fuse_output = false;
+  // y = C v + D u formed on the tensor cores in the last stage (BF16 pairs, p and
+  // q multiples of 16, q <= 64, §3 schedule), where fuse_output does not apply
+  bool fuse_output_mma = false;
   // stage 1 forms v^(1) = Bbar u_l + Abar Bbar u_(l-1) on chip; the first-stage
   // kernel does not run (set per batch)
   bool fuse_first = false;
@@ -257,9 +260,12 @@ cudaError_t launch_stage0(const Plan& p, const void* u, void* out_hi, void* out_
                           cudaStream_t st);
 cudaError_t launch_stage_f64(const Plan& p, int k, const double* vin, double* vout,
                              cudaStream_t st, bool reverse = false);
+// u_hi, u_lo: u as (hi, lo) BF16 planes [rows, p], read by the last stage when
+// it forms y = C v + D u on the tensor cores (Plan::fuse_output_mma).
 cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
                             void* vout_hi, void* vout_lo, const float* u, float* y,
-                            cudaStream_t st, bool reverse = false);
+                            cudaStream_t st, bool reverse = false, const void* u_hi = nullptr,
+                            const void* u_lo = nullptr);
 // In-place stage k over rows S apart (the work-efficient schedule); the state
 // planes hold rows_cap rows, a multiple of S.  Tiles flagged TILE_FINAL_FUSED
 // also form y = C v + D u for their rows (u, y may be null otherwise).

@@ -50,6 +50,8 @@
 #include "common.cuh"
 #include "ptx.cuh"
 
+#include <cstring>
+
 namespace cascade {
 namespace {
 
@@ -62,6 +64,13 @@ constexpr int RING_MAX = 8;                   // staging slots (runtime ring <= 
 constexpr uint32_t ROWB = 64;                 // bytes per row of every shared tile
 constexpr uint32_t PLANE_TILE = BM * ROWB;    // one plane of a 128-row chunk: 8 KB
 constexpr uint32_t SLOT_BYTES = 2 * PLANE_TILE;
+
+// Tensor maps of the output on the tensor cores (YM): C and D (hi, lo) planes,
+// [nsys q, m] and [nsys q, p], boxes of 32 K entries x q rows; u (hi, lo) planes
+// [rows, p], boxes of 32 x 128 rows.
+struct YMaps {
+  CUtensorMap chi, clo, uhi, ulo, dhi, dlo;
+};
 
 template <int ELEM>
 struct Fmt;
@@ -195,24 +204,50 @@ __device__ __forceinline__ void raise_timeout(const StageArgs& a, volatile int* 
 // Per-item facts every role derives identically from the tile table.
 struct Item {
   Tile t;
+  int nb;         // column block of the tile
   int n0;
   bool copy;      // every source row precedes the sequence: no MMA, output = residual
   bool fused;     // last stage with y = C v + D u formed in the epilogue
   bool ragged;    // last tile of a sequence: rows past its end must not be written
+  bool acc;       // holds a TMEM accumulator (MMA items, and fused items with YM)
 };
 
-template <int QMAX>
+// Work items are (tile, column block) pairs, w = tile * nblocks + block.  The
+// usual order gives block b the items b, b + grid, ...; with the output on the
+// tensor cores (YM) a block takes whole tiles, their column blocks one after
+// the other, so that it can sum a tile's partial outputs itself.
+template <int YM>
+__device__ __forceinline__ int first_item(const StageArgs& a) {
+  return YM ? (int)blockIdx.x * a.nblocks : (int)blockIdx.x;
+}
+template <int YM>
+__device__ __forceinline__ int next_item(const StageArgs& a, int w) {
+  if (!YM) return w + (int)gridDim.x;
+  return (w % a.nblocks != a.nblocks - 1) ? w + 1 : w + 1 + ((int)gridDim.x - 1) * a.nblocks;
+}
+
+template <int QMAX, int YM = 0>
 __device__ __forceinline__ Item load_item(const StageArgs& a, int w) {
   Item it;
   it.t = a.tiles[w / a.nblocks];
-  it.n0 = (w % a.nblocks) * a.BN;
+  it.nb = w % a.nblocks;
+  it.n0 = it.nb * a.BN;
   // every source row lies outside the sequence: before its start (forward
   // stages) or past its end (adjoint stages, source l + s)
   it.copy = a.S ? false
                  : a.reverse ? (it.t.t0 + a.shift >= it.t.len) : (it.t.t0 + BM <= a.shift);
-  it.fused = (QMAX > 0) && (it.t.flags & TILE_FINAL_FUSED);
+  it.fused = (QMAX > 0 || YM) && (it.t.flags & TILE_FINAL_FUSED);
   it.ragged = it.t.t0 + BM > it.t.len;
+  it.acc = !it.copy || (YM && it.fused);
   return it;
+}
+
+// Column chunks the staging ring carries for an item: the residual's, then,
+// for the first column block of a tile whose output is formed on the tensor
+// cores, the (u, D) chunks of the D u term.
+template <int YM>
+__device__ __forceinline__ int item_chunks(const StageArgs& a, const Item& it, int nch) {
+  return nch + ((YM && it.fused && it.nb == 0) ? (a.p + 31) / 32 : 0);
 }
 
 // QMAX: 0 = never fuse the output; otherwise the largest q the fused
@@ -227,14 +262,25 @@ __device__ __forceinline__ Item load_item(const StageArgs& a, int w) {
 // residual from u, the operand rows come by TMA as usual.  Both round v^(1) to
 // the state format as the first-stage kernel does: the results equal those of
 // the path through memory bit for bit.
-template <int ELEM, int QMAX, int G, int GEN>
-__global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 1)
+// YM = 1 (BF16 pairs, p and q multiples of 16, q <= 64): tiles flagged
+// TILE_FINAL_FUSED form y = C v + D u on the tensor cores.  The finished (hi,
+// lo) state chunk the epilogue leaves in its staging slot is the A operand of a
+// second product whose B operand, a 64-byte K chunk of C, the ring manager
+// loads into the same slot next to the residual; the first column block of a
+// tile adds D u from (u, D) chunks that follow its residual chunks.  One more
+// warp (the y issuer) issues these products into TMEM columns [0, q) of the
+// tile's own accumulator, once the epilogue has read those columns.  Epilogue
+// group 0 reads the tile's y from there and, when m spans several column
+// blocks (taken one after the other by the same block), sums them in order.
+template <int ELEM, int QMAX, int G, int GEN, int YM>
+__global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHREADS + 32 : NTHREADS, 1)
     stage_tc_kernel(const __grid_constant__ CUtensorMap tm_vhi,
                     const __grid_constant__ CUtensorMap tm_vlo,
                     const __grid_constant__ CUtensorMap tm_phi,
                     const __grid_constant__ CUtensorMap tm_plo,
                     const __grid_constant__ CUtensorMap tm_ohi,
-                    const __grid_constant__ CUtensorMap tm_olo, const StageArgs args) {
+                    const __grid_constant__ CUtensorMap tm_olo,
+                    const __grid_constant__ YMaps ym, const StageArgs args) {
   constexpr int KC = (int)ROWB / ELEM;   // K elements per 64-byte operand row
   constexpr int UK = 32 / ELEM;          // K per tcgen05.mma
   constexpr int CW = Fmt<ELEM>::CW;      // epilogue chunk: columns per 64-byte row
@@ -250,6 +296,10 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
   const int nch = BN / CW;
   const int shift = args.shift;
   const int nwork = args.ntiles * args.nblocks;
+  const int q = args.q;
+  // a staging slot: the residual's (hi, lo) chunk, then (YM) a (hi, lo) K chunk
+  // of C or D, q rows of 64 bytes each
+  const uint32_t slot_bytes = YM ? SLOT_BYTES + 2u * (uint32_t)q * ROWB : SLOT_BYTES;
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -259,7 +309,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
   const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
   uint8_t* bufs = smem;
   uint8_t* ring = smem + (size_t)S * stage_bytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)RING * SLOT_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)RING * slot_bytes);
   uint64_t* empty = full + S;
   uint64_t* acc_full = empty + S;
   uint64_t* acc_empty = acc_full + 2;
@@ -268,9 +318,13 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
   uint64_t* drain = res_done + RING_MAX;
   uint64_t* ypart = drain + 1;      // group 1's partial y sums of a fused tile are ready
   uint64_t* yfree = ypart + 1;      // group 0 has taken them
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(yfree + 1);
+  uint64_t* ymma_done = yfree + 1;  // [RING_MAX] (YM) the y issuer is done with a slot
+  uint64_t* yfull = ymma_done + RING_MAX;   // [2] (YM) a tile's y products completed
+  uint64_t* ydrain = yfull + 2;             // (YM) the y issuer's products completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ydrain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* ysum = reinterpret_cast<float*>(tmem_slot + 4);   // [QN][128]
+  float* ysm = ysum + QN * 128;     // (YM, several column blocks) [q][128] partial y
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -293,6 +347,12 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
     ptx::mbar_init(drain, 1);
     ptx::mbar_init(ypart, 128);
     ptx::mbar_init(yfree, 128);
+    if (YM) {
+      for (int s = 0; s < RING; ++s) ptx::mbar_init(&ymma_done[s], 1);
+      ptx::mbar_init(&yfull[0], 1);
+      ptx::mbar_init(&yfull[1], 1);
+      ptx::mbar_init(ydrain, 1);
+    }
     *abort_flag = 0;
     ptx::fence_mbar_init();
     ptx::prefetch_tmap(&tm_vhi);
@@ -301,6 +361,14 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
     ptx::prefetch_tmap(&tm_plo);
     ptx::prefetch_tmap(&tm_ohi);
     ptx::prefetch_tmap(&tm_olo);
+    if (YM) {
+      ptx::prefetch_tmap(&ym.chi);
+      ptx::prefetch_tmap(&ym.clo);
+      ptx::prefetch_tmap(&ym.uhi);
+      ptx::prefetch_tmap(&ym.ulo);
+      ptx::prefetch_tmap(&ym.dhi);
+      ptx::prefetch_tmap(&ym.dlo);
+    }
   }
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, tmem_cols);
@@ -324,8 +392,8 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
       int issued_parity[8];
       for (int s = 0; s < 8; ++s) issued_parity[s] = -1;
       bool waited = false;
-      for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
-        const Item it = load_item<QMAX>(args, w);
+      for (int w = first_item<YM>(args); w < nwork && !*abort_flag; w = next_item<YM>(args, w)) {
+        const Item it = load_item<QMAX, YM>(args, w);
         if (it.copy) continue;                                   // no operands
         // source rows l - s (forward) or l + s (adjoint); may fall outside the
         // tensor (zero fill) or in a neighbouring sequence (zeroed below)
@@ -407,9 +475,9 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
     int stage = 0;
     uint32_t phase = 0;
     int acc_i = 0;
-    for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
-      const Item it = load_item<QMAX>(args, w);
-      if (it.copy) continue;
+    for (int w = first_item<YM>(args); w < nwork && !*abort_flag; w = next_item<YM>(args, w)) {
+      const Item it = load_item<QMAX, YM>(args, w);
+      if (!it.acc) continue;
       const int abuf = acc_i & 1;
       const uint32_t aph = (uint32_t)((acc_i >> 1) & 1);
       // lane-uniform outcome: the warp leaves its loop as a whole
@@ -425,7 +493,8 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
       const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * ACC);
       const uint32_t c_tmem = d_tmem + (SEP ? (uint32_t)BN : 0u);   // correction accumulator
       bool ok = true;
-      for (int c = 0; c < nkc; ++c) {
+      // (YM: a fused copy item only takes the accumulator, for its y products)
+      for (int c = 0; c < (it.copy ? 0 : nkc); ++c) {
         if (!__all_sync(0xffffffffu, ptx::mbar_wait(&full[stage], phase, limit, abort_flag))) {
           raise_timeout(args, abort_flag, 3, w, stage);
           ok = false;
@@ -483,14 +552,38 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
     // ------------------------------------------------------------ ring manager
     if (lane == 0) {
       ptx::griddep_wait();             // the residual rows are the previous launch's output
-      int lw = blockIdx.x, lcc = 0;    // load cursor, up to RING chunks ahead of the epilogue
+      int lw = first_item<YM>(args), lcc = 0;   // load cursor, RING chunks ahead of the epilogue
       uint32_t issued = 0;
       auto issue_next = [&](int slot) {
         if (lw >= nwork) return;
-        const Tile lt = args.tiles[lw / args.nblocks];
-        const int x = (lw % args.nblocks) * BN + lcc * CW;
+        const Item li = load_item<QMAX, YM>(args, lw);
+        const Tile& lt = li.t;
+        const int lnck = item_chunks<YM>(args, li, nch);
+        const int x = li.n0 + lcc * CW;
         const int yrow = (int)(lt.seq_row0 + lt.t0);
-        uint8_t* sh = ring + (size_t)slot * SLOT_BYTES;
+        uint8_t* sh = ring + (size_t)slot * slot_bytes;
+        if (YM && li.fused) {
+          // the residual chunk and the matching K chunk of C, or a (u, D) chunk of
+          // the D u term (K chunk j of u's p columns; past p, TMA fills zeros)
+          const uint32_t cb = (uint32_t)q * ROWB;
+          ptx::mbar_arrive_expect_tx(&res_full[slot], SLOT_BYTES + 2 * cb);
+          const int crow = lt.sys * q;
+          if (lcc < nch) {
+            ptx::tma_load_2d(sh, &tm_vhi, &res_full[slot], x, yrow);
+            ptx::tma_load_2d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow);
+            ptx::tma_load_2d(sh + SLOT_BYTES, &ym.chi, &res_full[slot], x, crow);
+            ptx::tma_load_2d(sh + SLOT_BYTES + cb, &ym.clo, &res_full[slot], x, crow);
+          } else {
+            const int ux = (lcc - nch) * 32;
+            ptx::tma_load_2d(sh, &ym.uhi, &res_full[slot], ux, yrow);
+            ptx::tma_load_2d(sh + PLANE_TILE, &ym.ulo, &res_full[slot], ux, yrow);
+            ptx::tma_load_2d(sh + SLOT_BYTES, &ym.dhi, &res_full[slot], ux, crow);
+            ptx::tma_load_2d(sh + SLOT_BYTES + cb, &ym.dlo, &res_full[slot], ux, crow);
+          }
+          ++issued;
+          if (++lcc == lnck) { lcc = 0; lw = next_item<YM>(args, lw); }
+          return;
+        }
         if (GEN != 0) {
           ptx::mbar_arrive(&res_full[slot]);   // the epilogue forms the residual from u
         } else {
@@ -505,7 +598,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
           }
         }
         ++issued;
-        if (++lcc == nch) { lcc = 0; lw += gridDim.x; }
+        if (++lcc == lnck) { lcc = 0; lw = next_item<YM>(args, lw); }
       };
       for (int s = 0; s < RING; ++s) issue_next(s);
       uint32_t g = 0;                  // chunks retired
@@ -514,22 +607,29 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
       // store of the newest chunk reads shared memory while the older one's
       // slot is reloaded (bulk wait with one group allowed in flight).
       int pend_slot = -1;
-      for (int w = blockIdx.x; w < nwork && alive; w += gridDim.x) {
-        const Item it = load_item<QMAX>(args, w);
+      for (int w = first_item<YM>(args); w < nwork && alive; w = next_item<YM>(args, w)) {
+        const Item it = load_item<QMAX, YM>(args, w);
         const bool tma_out = (!it.fused || args.keep_v) && !it.ragged;
         const int ytile = (int)(it.t.seq_row0 + it.t.t0);
-        for (int cc = 0; cc < nch; ++cc, ++g) {
+        const int nck = item_chunks<YM>(args, it, nch);
+        for (int cc = 0; cc < nck; ++cc, ++g) {
           const int slot = (int)(g % RING);
-          uint8_t* sh = ring + (size_t)slot * SLOT_BYTES;
+          uint8_t* sh = ring + (size_t)slot * slot_bytes;
           // Every chunk passes through both barriers of its slot, also a pure
           // copy that the epilogue forwards untouched: a parity wait is then
-          // never more than one phase ahead of the barrier it polls.
+          // never more than one phase ahead of the barrier it polls.  With YM
+          // every chunk also passes the y issuer's release of the slot.
           if (!ptx::mbar_wait(&res_done[slot], (g / RING) & 1u, limit, abort_flag)) {
             raise_timeout(args, abort_flag, 5, w, (int)g);
             alive = false;
             break;
           }
-          if (tma_out) {
+          if (YM && !ptx::mbar_wait(&ymma_done[slot], (g / RING) & 1u, limit, abort_flag)) {
+            raise_timeout(args, abort_flag, 14, w, (int)g);
+            alive = false;
+            break;
+          }
+          if (tma_out && cc < nch) {
             if (args.S) {
               ptx::tma_store_3d(&tm_ohi, sh, it.n0 + cc * CW, ytile % args.S, ytile / args.S);
               ptx::tma_store_3d(&tm_olo, sh + PLANE_TILE, it.n0 + cc * CW, ytile % args.S,
@@ -543,7 +643,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
           if (pend_slot >= 0) {
             // the previous chunk's store (if any) has read its slot: all bulk
             // groups but this chunk's (the newest, when it stored) are done reading
-            if (tma_out) ptx::bulk_wait_read1();
+            if (tma_out && cc < nch) ptx::bulk_wait_read1();
             else ptx::bulk_wait_read0();
             issue_next(pend_slot);
           }
@@ -555,6 +655,78 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
       for (uint32_t h = g; h < issued; ++h)
         ptx::mbar_wait(&res_full[h % RING], (h / RING) & 1u, limit, nullptr);
     }
+  } else if (YM && warp == NTHREADS / 32) {
+    // ------------------------------------------------------------ y issuer (YM)
+    // y = C v + D u of fused tiles: per staged chunk (A: the state chunk, or u;
+    // B: the K chunk of C, or D, in the same slot) three BF16 products into TMEM
+    // columns [0, q) of the tile's accumulator; the slot is released by a commit.
+    // Chunks of other tiles pass through (plain arrive), so the release barrier
+    // stays phase-locked with the slot.
+    if (lane == 0) {
+      const uint32_t idesc_y = ptx::make_idesc(FMT, BM, q);
+      const int nq = min(nch, (q + CW - 1) / CW);   // chunks covering columns [0, q)
+      const uint32_t cb = (uint32_t)q * ROWB;
+      uint32_t g = 0;
+      int acc_i = 0;
+      bool alive = true;
+      for (int w = first_item<YM>(args); w < nwork && alive; w = next_item<YM>(args, w)) {
+        const Item it = load_item<QMAX, YM>(args, w);
+        const int nck = item_chunks<YM>(args, it, nch);
+        if (!it.fused) {
+          for (int cc = 0; cc < nck; ++cc, ++g) {
+            const int slot = (int)(g % RING);
+            if (!ptx::mbar_wait(&res_done[slot], (g / RING) & 1u, limit, abort_flag)) {
+              raise_timeout(args, abort_flag, 17, w, (int)g);
+              alive = false;
+              break;
+            }
+            ptx::mbar_arrive(&ymma_done[slot]);
+          }
+          if (it.acc) ++acc_i;
+          continue;
+        }
+        const int abuf = acc_i & 1;
+        const uint32_t ycol = tmem_base + (uint32_t)(abuf * ACC);
+        // columns [0, q) are free once the epilogue has read chunks 0 .. nq - 1
+        for (int h = 0; h < nq && alive; ++h) {
+          const uint32_t gh = g + (uint32_t)h;
+          if (!ptx::mbar_wait(&res_done[gh % RING], (gh / RING) & 1u, limit, abort_flag)) {
+            raise_timeout(args, abort_flag, 13, w, (int)gh);
+            alive = false;
+          }
+        }
+        if (!alive) break;
+        for (int cc = 0; cc < nck; ++cc, ++g) {
+          const int slot = (int)(g % RING);
+          if (cc >= nq && !ptx::mbar_wait(&res_done[slot], (g / RING) & 1u, limit, abort_flag)) {
+            raise_timeout(args, abort_flag, 13, w, (int)g);
+            alive = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          uint8_t* sh = ring + (size_t)slot * slot_bytes;
+          const uint64_t dah = ptx::make_sdesc_sw64(ptx::smem_addr(sh));
+          const uint64_t dal = ptx::make_sdesc_sw64(ptx::smem_addr(sh + PLANE_TILE));
+          const uint64_t dbh = ptx::make_sdesc_sw64(ptx::smem_addr(sh + SLOT_BYTES));
+          const uint64_t dbl = ptx::make_sdesc_sw64(ptx::smem_addr(sh + SLOT_BYTES + cb));
+#pragma unroll
+          for (int kk = 0; kk < KC / UK; ++kk) {
+            const uint64_t adv = (uint64_t)((kk * UK * ELEM) >> 4);
+            ptx::mma_bf16(ycol, dah + adv, dbh + adv, idesc_y, (cc | kk) != 0);
+            ptx::mma_bf16(ycol, dah + adv, dbl + adv, idesc_y, 1u);
+            ptx::mma_bf16(ycol, dal + adv, dbh + adv, idesc_y, 1u);
+          }
+          ptx::tc_commit(&ymma_done[slot]);
+        }
+        if (!alive) break;
+        ptx::tc_commit(&yfull[abuf]);
+        ++acc_i;
+      }
+      // every product issued here has completed before TMEM is freed
+      ptx::tc_commit(ydrain);
+      ptx::mbar_wait(ydrain, 0u, limit, nullptr);
+    }
+    __syncwarp();
   } else if (GEN == 1 && warp >= NTHREADS / 32) {
     // ------------------------------------------------------------ first-stage rows
     // Operand rows v^(1)_(l-s) = Bbar u_(l-s) + Abar Bbar u_(l-s-1) of each K
@@ -566,8 +738,8 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
     ptx::griddep_wait();
     int stage = 0;
     uint32_t phase = 0;
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-      const Item it = load_item<QMAX>(args, w);
+    for (int w = first_item<YM>(args); w < nwork; w = next_item<YM>(args, w)) {
+      const Item it = load_item<QMAX, YM>(args, w);
       if (it.copy) continue;
       const int src = it.t.t0 + r - shift;
       const bool live = it.t.t0 + r < it.t.len && src >= 0;
@@ -624,9 +796,10 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
     uint32_t g = 0;                            // chunks consumed (by either group)
     int nfused = 0;                            // fused tiles seen (ypart / yfree phases)
     int acc_i = 0;
+    int ycnt[2] = {0, 0};                      // (YM) fused tiles seen per accumulator
     bool alive = true;                         // warp-uniform
-    for (int w = blockIdx.x; w < nwork && alive; w += gridDim.x) {
-      const Item it = load_item<QMAX>(args, w);
+    for (int w = first_item<YM>(args); w < nwork && alive; w = next_item<YM>(args, w)) {
+      const Item it = load_item<QMAX, YM>(args, w);
       const bool tma_out = (!it.fused || args.keep_v) && !it.ragged;
       const int tr = it.t.t0 + r;
       const bool valid = tr < it.t.len;
@@ -664,7 +837,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
         }
         continue;
       }
-      if (!it.copy) {
+      if (it.acc) {
         const uint32_t aph = (uint32_t)((acc_i >> 1) & 1);
         if (!__all_sync(0xffffffffu, ptx::mbar_wait(&acc_full[abuf], aph, limit, abort_flag))) {
           raise_timeout(args, abort_flag, 6, w, acc_i);
@@ -688,7 +861,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
 #pragma unroll
         for (int h = 0; h < G; ++h) {
           slot[h] = (int)((g + h) % RING);
-          sh[h] = ring + (size_t)slot[h] * SLOT_BYTES;
+          sh[h] = ring + (size_t)slot[h] * slot_bytes;
           got = got && ptx::mbar_wait(&res_full[slot[h]], ((g + h) / RING) & 1u, limit, abort_flag);
         }
         if (!__all_sync(0xffffffffu, got)) {     // tcgen05.ld below is warp-collective
@@ -783,7 +956,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
 #pragma unroll
             for (int c = 0; c < 4; ++c) Fmt<ELEM>::add16(hq[h][c], lq[h][c], v[h] + c * (CW / 4));
         }
-        if (it.fused) {
+        if (QMAX > 0 && it.fused) {
           if (valid) {
 #pragma unroll
             for (int qq = 0; qq < QN; ++qq) {
@@ -807,12 +980,13 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
             }
           }
         }
-        if (!it.fused || args.keep_v) {
+        if (!it.fused || args.keep_v || YM) {
 #pragma unroll
           for (int h = 0; h < G; ++h)
 #pragma unroll
             for (int c = 0; c < 4; ++c) Fmt<ELEM>::split16(v[h] + c * (CW / 4), hq[h][c], lq[h][c]);
-          if (tma_out) {
+          // (YM: a fused tile's finished chunk is the A operand of its y products)
+          if (tma_out || (YM && it.fused)) {
 #pragma unroll
             for (int h = 0; h < G; ++h)
 #pragma unroll
@@ -820,8 +994,9 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
                 *reinterpret_cast<uint4*>(sh[h] + ptx::sw64_offset(r, c)) = hq[h][c];
                 *reinterpret_cast<uint4*>(sh[h] + PLANE_TILE + ptx::sw64_offset(r, c)) = lq[h][c];
               }
-            ptx::fence_proxy_async_smem();      // visible to the manager's TMA store
-          } else if (valid) {
+            ptx::fence_proxy_async_smem();      // visible to the TMA store and the MMA
+          }
+          if (!tma_out && valid && (!it.fused || args.keep_v)) {
 #pragma unroll
             for (int h = 0; h < G; ++h) {
               const int64_t off = (grow * (int64_t)m + it.n0 + (cc + h) * CW) * ELEM;
@@ -832,16 +1007,67 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
             }
           }
         }
+        // (YM: the y issuer's products write TMEM columns this chunk's loads read)
+        if (YM && it.fused) ptx::tc_fence_before();
 #pragma unroll
         for (int h = 0; h < G; ++h) ptx::mbar_arrive(&res_done[slot[h]]);
       }
       if (!alive) break;
-      if (!it.copy) {
+      if (YM && it.fused) {
+        // the (u, D) chunks of the first column block go to the y issuer as they
+        // are; each passes both slot barriers like any other chunk
+        const int nck = item_chunks<YM>(args, it, nch);
+        for (int cc = nch; cc < nck; ++cc, ++g) {
+          if (((g / G) & 1) != (uint32_t)egrp) continue;
+          const int slot = (int)(g % RING);
+          if (!__all_sync(0xffffffffu,
+                          ptx::mbar_wait(&res_full[slot], (g / RING) & 1u, limit, abort_flag))) {
+            raise_timeout(args, abort_flag, 15, w, (int)g);
+            alive = false;
+            break;
+          }
+          ptx::mbar_arrive(&res_done[slot]);
+        }
+        if (!alive) break;
+        if (egrp == 0) {
+          // y of this column block from TMEM columns [0, q) of the tile's
+          // accumulator; summed over the column blocks in order, plus D u (in
+          // the first block's products), and stored by the last block
+          // yfull[b] completes once per fused tile that used accumulator b
+          const uint32_t yph = (uint32_t)(ycnt[abuf]++ & 1);
+          if (!__all_sync(0xffffffffu, ptx::mbar_wait(&yfull[abuf], yph, limit, abort_flag))) {
+            raise_timeout(args, abort_flag, 16, w, acc_i);
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(abuf * ACC);
+          const bool last = it.nb == args.nblocks - 1;
+          for (int j0 = 0; j0 < q; j0 += 16) {
+            float t[16];
+            ptx::tmem_ld16(trow + (uint32_t)j0, t);
+            if (args.nblocks > 1) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                float* a = ysm + (j0 + e) * 128 + r;
+                t[e] = it.nb == 0 ? t[e] : *a + t[e];
+                if (!last) *a = t[e];
+              }
+            }
+            if (last && valid) {
+              float4* yo = reinterpret_cast<float4*>(args.y + grow * q + j0);
+#pragma unroll
+              for (int e4 = 0; e4 < 4; ++e4)
+                yo[e4] = make_float4(t[4 * e4], t[4 * e4 + 1], t[4 * e4 + 2], t[4 * e4 + 3]);
+            }
+          }
+        }
+      }
+      if (it.acc) {
         ptx::tc_fence_before();
         ptx::mbar_arrive(&acc_empty[abuf]);
         ++acc_i;
       }
-      if (it.fused) {
+      if (QMAX > 0 && it.fused) {
         // y sums over all columns: group 1 hands its partial sums to group 0
         const uint32_t fph = (uint32_t)(nfused & 1);
         ++nfused;
@@ -864,7 +1090,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
         for (int qq = 0; qq < QN; ++qq) yacc[qq] += ysum[qq * 128 + r];
         ptx::mbar_arrive(yfree);
       }
-      if (it.fused && valid) {
+      if (QMAX > 0 && it.fused && valid) {
         const float* Ds = args.D32 + (int64_t)it.t.sys * args.q * args.p;
         const float* ur = args.u + grow * args.p;
 #pragma unroll
@@ -885,17 +1111,17 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS, 
   if (warp == 1) ptx::tmem_dealloc(tmem_base, tmem_cols);
 }
 
-template <int ELEM, int QMAX, int G, int GEN>
-cudaError_t launch_variant(const CUtensorMap* maps, const StageArgs& a, int grid, size_t smem,
-                           cudaStream_t st) {
-  auto kern = stage_tc_kernel<ELEM, QMAX, G, GEN>;
+template <int ELEM, int QMAX, int G, int GEN, int YM = 0>
+cudaError_t launch_variant(const CUtensorMap* maps, const YMaps& ym, const StageArgs& a, int grid,
+                           size_t smem, cudaStream_t st) {
+  auto kern = stage_tc_kernel<ELEM, QMAX, G, GEN, YM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // programmatic dependent launch: the prologue (barriers, TMEM, the first
   // power chunks) overlaps the previous launch's tail on the SMs it leaves free
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(GEN == 1 ? NTHREADS + GEN_THREADS : NTHREADS);
+  cfg.blockDim = dim3(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHREADS + 32 : NTHREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -903,7 +1129,7 @@ cudaError_t launch_variant(const CUtensorMap* maps, const StageArgs& a, int grid
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
+  e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], ym, a);
   CASCADE_LAUNCHED();
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -915,17 +1141,24 @@ size_t stage_bytes_for(int BN) { return 2 * (size_t)PLANE_TILE + 2 * (size_t)BN 
 // the mbarriers (room for RING_MAX ring barriers of each kind), the TMEM slot and,
 // when one tile spans all m columns (the output may be formed in the epilogue),
 // the partial y sums.
-size_t fixed_smem_bytes(int S, int ring, bool ysum) {
-  return 1024 + (size_t)ring * SLOT_BYTES + 8 * (2 * S + 7 + 2 * RING_MAX) + 16 +
-         (ysum ? sizeof(float) * 4 * 128 : 0);
+// ym_q > 0 (output on the tensor cores): slots also carry a K chunk of C or D
+// (q rows, both planes), and with several column blocks the partial y sums
+// ([q][128] floats) stay in shared memory.
+size_t fixed_smem_bytes(int S, int ring, bool ysum, int ym_q = 0, bool ym_sum = false) {
+  const size_t slot = SLOT_BYTES + (ym_q > 0 ? 2 * (size_t)ym_q * ROWB : 0);
+  return 1024 + (size_t)ring * slot + 8 * (2 * S + 10 + 3 * RING_MAX) + 16 +
+         (ysum ? sizeof(float) * 4 * 128 : sizeof(float) * 128) +
+         (ym_sum ? sizeof(float) * 128 * (size_t)ym_q : 0);
 }
 
-bool tc_config_fits(int m, int BN, const TcConfig& c) {
+bool tc_config_fits(int m, int BN, const TcConfig& c, int ym_q = 0) {
   if (c.group != 1 && c.group != 2) return false;
+  if (ym_q > 0 && c.group != 1) return false;
   // each ring slot always serves the same epilogue group: ring % (2 group) == 0
   if (c.ring < 2 * c.group || c.ring > RING_MAX || c.ring % (2 * c.group) != 0) return false;
   if (c.stages < 2 || c.stages > 8) return false;
-  return fixed_smem_bytes(c.stages, c.ring, BN >= m) + (size_t)c.stages * stage_bytes_for(BN) <=
+  return fixed_smem_bytes(c.stages, c.ring, BN >= m, ym_q, ym_q > 0 && BN < m) +
+             (size_t)c.stages * stage_bytes_for(BN) <=
          227 * 1024;
 }
 
@@ -965,7 +1198,8 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
                           uint64_t rows_cap, const void* vin_hi, const void* vin_lo,
                           void* vout_hi, void* vout_lo, const float* u, float* y,
                           cudaStream_t st, bool reverse, bool even_resid = false,
-                          int shape_key = -1) {
+                          int shape_key = -1, const void* u_hi = nullptr,
+                          const void* u_lo = nullptr) {
   if (ntiles == 0) return cudaSuccess;
   if (!(reverse ? p.PThi : p.Phi) || !vin_hi || !vin_lo || !vout_hi || !vout_lo) {
     set_global_error("stage launch without its power or state planes");
@@ -1030,7 +1264,13 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   // the row warps' registers fit only that variant), or the last down-sweep
   // level forming its even rows' v^(1) (also one chunk per step: fewer
   // kernel variants)
-  const bool fuse = p.fuse_output && !reverse && y != nullptr;
+  const bool fuse = (p.fuse_output || p.fuse_output_mma) && !reverse && y != nullptr;
+  // the output on the tensor cores (BF16 pairs, §3 schedule; u as (hi, lo) planes)
+  const bool ym = fuse && p.fuse_output_mma && S == 0;
+  if (ym && (!u_hi || !u_lo || elem != 2 || !p.pc_hi)) {
+    set_global_error("fused tensor-core output without its u or coefficient planes");
+    return cudaErrorInvalidValue;
+  }
   const int gen = (p.fuse_first && k == 1 && !reverse && S == 0 && u != nullptr) ? 1
                   : (even_resid && fuse && S > 0 && u != nullptr)               ? 2
                                                                                : 0;
@@ -1044,22 +1284,55 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
     a.stages = cfg.stages;
     a.ring = cfg.ring;
   }
+  const int q = p.d.q;
+  YMaps ymaps;
+  memset(&ymaps, 0, sizeof(ymaps));
+  if (ym) {
+    // one chunk per step, and slots that also hold a K chunk of C or D: the
+    // deepest shape at or below the chosen one that fits
+    TcConfig c1{cfg.stages, cfg.ring, 1};
+    while (!tc_config_fits(m, BN, c1, q) && c1.stages > 2) --c1.stages;
+    while (!tc_config_fits(m, BN, c1, q) && c1.ring > 2) c1.ring -= 2;
+    if (!tc_config_fits(m, BN, c1, q)) {
+      set_global_error("fused tensor-core output does not fit shared memory");
+      return cudaErrorInvalidValue;
+    }
+    cfg = c1;
+    a.stages = cfg.stages;
+    a.ring = cfg.ring;
+    const auto* ch = static_cast<const __nv_bfloat16*>(p.pc_hi) + p.pc_off[PC_C];
+    const auto* cl = static_cast<const __nv_bfloat16*>(p.pc_lo) + p.pc_off[PC_C];
+    const auto* dh = static_cast<const __nv_bfloat16*>(p.pc_hi) + p.pc_off[PC_D];
+    const auto* dl = static_cast<const __nv_bfloat16*>(p.pc_lo) + p.pc_off[PC_D];
+    const uint64_t crows = (uint64_t)p.d.nsys * q;
+    if (!encode_tmap_2d(&ymaps.chi, ch, 2, m, crows, 32, q, &err, 64) ||
+        !encode_tmap_2d(&ymaps.clo, cl, 2, m, crows, 32, q, &err, 64) ||
+        !encode_tmap_2d(&ymaps.dhi, dh, 2, p.d.p, crows, 32, q, &err, 64) ||
+        !encode_tmap_2d(&ymaps.dlo, dl, 2, p.d.p, crows, 32, q, &err, 64) ||
+        !encode_tmap_2d(&ymaps.uhi, u_hi, 2, p.d.p, (uint64_t)p.rows, 32, BM, &err, 64) ||
+        !encode_tmap_2d(&ymaps.ulo, u_lo, 2, p.d.p, (uint64_t)p.rows, 32, BM, &err, 64)) {
+      set_global_error("tensor map encode failed: " + err);
+      return cudaErrorInvalidValue;
+    }
+  }
   a.err = p.err;
   a.diag = p.err + 1;
   a.timeout_ns = 2000000000ull;
-  const size_t smem =
-      fixed_smem_bytes(a.stages, a.ring, BN >= m) + (size_t)a.stages * stage_bytes_for(BN);
+  const size_t smem = fixed_smem_bytes(a.stages, a.ring, BN >= m, ym ? q : 0, ym && BN < m) +
+                      (size_t)a.stages * stage_bytes_for(BN);
   const int nwork = ntiles * a.nblocks;
-  const int grid = nwork < p.num_sms ? nwork : p.num_sms;
-  const int q = p.d.q;
+  // YM: a block takes whole tiles
+  const int nunits = ym ? ntiles : nwork;
+  const int grid = nunits < p.num_sms ? nunits : p.num_sms;
+  if (ym) return launch_variant<2, 0, 1, 0, 1>(maps, ymaps, a, grid, smem, st);
   // the fused output applies to forward stages that are given y (the stages
   // the backward recomputes are not)
   const int G = cfg.group;
 #define CASCADE_TC_DISPATCH(E, Q, GEN2)                                               \
-  return gen == 1 ? launch_variant<E, Q, 1, 1>(maps, a, grid, smem, st)                \
-         : gen == 2 ? launch_variant<E, Q, 1, GEN2>(maps, a, grid, smem, st)           \
-         : G == 2 ? launch_variant<E, Q, 2, 0>(maps, a, grid, smem, st)                \
-                  : launch_variant<E, Q, 1, 0>(maps, a, grid, smem, st)
+  return gen == 1 ? launch_variant<E, Q, 1, 1>(maps, ymaps, a, grid, smem, st)         \
+         : gen == 2 ? launch_variant<E, Q, 1, GEN2>(maps, ymaps, a, grid, smem, st)    \
+         : G == 2 ? launch_variant<E, Q, 2, 0>(maps, ymaps, a, grid, smem, st)         \
+                  : launch_variant<E, Q, 1, 0>(maps, ymaps, a, grid, smem, st)
   // (mode 2 needs the fused output: the Q = 0 variants never take it)
   if (elem == 2) {
     if (!fuse) CASCADE_TC_DISPATCH(2, 0, 0);
@@ -1077,10 +1350,10 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
 
 cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
                             void* vout_hi, void* vout_lo, const float* u, float* y,
-                            cudaStream_t st, bool reverse) {
+                            cudaStream_t st, bool reverse, const void* u_hi, const void* u_lo) {
   return stage_tc_core(p, k, reverse ? p.d_adj_tiles[k] : p.d_tiles[k],
                        reverse ? p.n_adj_tiles[k] : p.n_tiles[k], 0, (uint64_t)p.rows, vin_hi,
-                       vin_lo, vout_hi, vout_lo, u, y, st, reverse);
+                       vin_lo, vout_hi, vout_lo, u, y, st, reverse, false, -1, u_hi, u_lo);
 }
 
 cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,

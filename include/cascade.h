@@ -124,7 +124,14 @@ enum {
      with a triangular product that leaves out only exact zeros.  Where the
      dense elimination exchanges no rows either (small delta), the powers are
      the same bit for bit.                                                  */
-  CASCADE_FLAG_DENSE_SETUP = 128
+  CASCADE_FLAG_DENSE_SETUP = 128,
+  /* Form y = C v + D u on the tensor cores in the last stage also when m spans
+     several column blocks of the stage kernel (m > 256): one block then takes
+     a tile's column blocks one after the other and adds their partial y in a
+     fixed order.  Off by default: at m = 1024, q = 64 the slots' K chunks of C
+     leave room for only two operand stages, and the last stage with the output
+     took 2.2 ms against 1.3 ms plus a 0.45 ms separate projection (GB300). */
+  CASCADE_FLAG_FUSE_WIDE_OUTPUT = 256
 };
 
 typedef struct cascade_plan_s* cascade_plan_t;
@@ -219,11 +226,10 @@ cascade_status_t cascade_get_matvec_count(cascade_plan_t plan, int64_t* h_count)
    separate projection after the last stage.  Fixed at plan creation: FP32
    or BF16-split plans with q <= 4 whose stage tiles span all m columns (y on
    the CUDA cores), and BF16-split plans on the §3 schedule with p and q
-   multiples of 16 and q <= 64 (y on the tensor cores: the finished (hi, lo)
-   state chunks times C, plus u times D, accumulated in TMEM; with m above
-   one column block the partial sums over the blocks are added in a fixed
-   order), unless created with CASCADE_FLAG_NO_FUSED_OUTPUT.  *h_fused = 1
-   or 0. */
+   multiples of 16, q <= 64 and m <= 256 (one column block; y on the tensor
+   cores: the finished (hi, lo) state chunks times C, plus u times D,
+   accumulated in TMEM), or any m with CASCADE_FLAG_FUSE_WIDE_OUTPUT, unless
+   created with CASCADE_FLAG_NO_FUSED_OUTPUT.  *h_fused = 1 or 0. */
 cascade_status_t cascade_get_output_fused(cascade_plan_t plan, int32_t* h_fused);
 
 /* Whether first-stage values v^(1) = Bbar u_l + Abar Bbar u_(l-1) are formed

@@ -32,6 +32,7 @@ CASCADE_FLAG_SCAN = 16
 CASCADE_FLAG_ZOH = 32
 CASCADE_FLAG_NO_FUSED_FIRST = 64
 CASCADE_FLAG_DENSE_SETUP = 128
+CASCADE_FLAG_FUSE_WIDE_OUTPUT = 256
 
 PRECISIONS = {"fp64": CASCADE_FP64, "fp32": CASCADE_FP32, "bf16_split": CASCADE_BF16_SPLIT}
 

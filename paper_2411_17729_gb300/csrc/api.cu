@@ -1155,10 +1155,14 @@ cascade_status_t cascade_plan_create(cascade_plan_t* out, const cascade_desc_t* 
   // wider outputs of BF16-split plans whose projections run on the tensor cores
   // (p, q multiples of 16): y = C v + D u as a second tensor-core product in the
   // last stage, C v from the staged final state chunks (q <= 64: the y columns
-  // fit inside one tile's accumulator)
+  // fit inside one tile's accumulator); by default only where one tile spans all
+  // m columns (measured slower than the separate pass at m = 1024)
   p->fuse_output_mma = !p->fuse_output && d.precision == CASCADE_BF16_SPLIT &&
                        !(d.flags & (CASCADE_FLAG_NO_FUSED_OUTPUT | CASCADE_FLAG_SCAN)) &&
-                       d.m % 64 == 0 && d.p % 16 == 0 && d.q % 16 == 0 && d.q <= 64;
+                       d.m % 64 == 0 && d.p % 16 == 0 && d.q % 16 == 0 && d.q <= 64 &&
+                       d.q <= block_n(d.m, d.precision) &&
+                       (block_n(d.m, d.precision) >= d.m ||
+                        (d.flags & CASCADE_FLAG_FUSE_WIDE_OUTPUT));
   e = cudaMalloc(&p->err, 8 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(p->err, 0, 8 * sizeof(int32_t));
   if (e != cudaSuccess) {
@@ -1503,6 +1507,7 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
   for (const Tile& t : all)
     if (t.fbuf != p->all_fbuf) p->all_fbuf = -1;
   p->h_tiles.assign(std::max(maxN + 1, 1), {});
+  p->stage_fused.assign(std::max(maxN + 1, 1), 0);
   for (int i = 0; i < nseq; ++i) {
     const int64_t L = h_offsets[i + 1] - h_offsets[i];
     if (L == 0) continue;
@@ -1511,6 +1516,7 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     // (the work-efficient schedule forms y in its down-sweep levels instead)
     for (int k = 1; k <= N && !scans(*p); ++k) {   // stage schedule (§3)
       const bool fused = fused_last && k == N;
+      if (fused) p->stage_fused[k] = 1;
       const int64_t prev_shift = int64_t(1) << (k - 1);
       for (int64_t t = 0; t < L; t += BM) {
         // Ping-pong buffers: rows below 2^(k-1) already hold their final value in the

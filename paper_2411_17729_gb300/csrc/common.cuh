@@ -175,6 +175,7 @@ struct Plan {
   // y = C v + D u formed on the tensor cores in the last stage (BF16 pairs, p and
   // q multiples of 16, q <= 64, §3 schedule), where fuse_output does not apply
   bool fuse_output_mma = false;
+  std::vector<char> stage_fused;   // stage k of the §3 schedule holds fused tiles (per batch)
   // stage 1 forms v^(1) = Bbar u_l + Abar Bbar u_(l-1) on chip; the first-stage
   // kernel does not run (set per batch)
   bool fuse_first = false;

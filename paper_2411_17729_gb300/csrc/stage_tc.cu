@@ -271,7 +271,8 @@ __device__ __forceinline__ int item_chunks(const StageArgs& a, const Item& it, i
 // warp (the y issuer) issues these products into TMEM columns [0, q) of the
 // tile's own accumulator, once the epilogue has read those columns.  Epilogue
 // group 0 reads the tile's y from there and, when m spans several column
-// blocks (taken one after the other by the same block), sums them in order.
+// blocks (taken one after the other by the same block), adds them in order in
+// its rows of y.
 template <int ELEM, int QMAX, int G, int GEN, int YM>
 __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHREADS + 32 : NTHREADS, 1)
     stage_tc_kernel(const __grid_constant__ CUtensorMap tm_vhi,
@@ -324,7 +325,6 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ydrain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* ysum = reinterpret_cast<float*>(tmem_slot + 4);   // [QN][128]
-  float* ysm = ysum + QN * 128;     // (YM, several column blocks) [q][128] partial y
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -869,6 +869,13 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
           alive = false;
           break;
         }
+        if (YM && it.copy && it.fused) {
+          // every source precedes the sequence: the slot already holds the final
+          // (hi, lo) state, which is the y products' A operand as it stands
+#pragma unroll
+          for (int h = 0; h < G; ++h) ptx::mbar_arrive(&res_done[slot[h]]);
+          continue;
+        }
         // GEN = 2 (p = 1): the even rows' residual Bbar u_l, formed before the
         // TMEM load it does not depend on, so its coefficient loads overlap it
         float xr[GEN == 2 ? G : 1][GEN == 2 ? CW : 1];
@@ -1040,24 +1047,26 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
             break;
           }
           ptx::tc_fence_after();
+          // (the partial sums of earlier column blocks wait in this thread's own
+          // row of y: it wrote them, so it reads them back in program order)
           const uint32_t trow = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(abuf * ACC);
-          const bool last = it.nb == args.nblocks - 1;
+          // tcgen05.ld is warp-collective: every lane loads, rows past the
+          // sequence end only skip the memory accesses
           for (int j0 = 0; j0 < q; j0 += 16) {
             float t[16];
             ptx::tmem_ld16(trow + (uint32_t)j0, t);
-            if (args.nblocks > 1) {
+            if (!valid) continue;
+            float4* yo = reinterpret_cast<float4*>(args.y + grow * q + j0);
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                float* a = ysm + (j0 + e) * 128 + r;
-                t[e] = it.nb == 0 ? t[e] : *a + t[e];
-                if (!last) *a = t[e];
+            for (int e4 = 0; e4 < 4; ++e4) {
+              if (it.nb > 0) {
+                const float4 o = yo[e4];
+                t[4 * e4] = o.x + t[4 * e4];
+                t[4 * e4 + 1] = o.y + t[4 * e4 + 1];
+                t[4 * e4 + 2] = o.z + t[4 * e4 + 2];
+                t[4 * e4 + 3] = o.w + t[4 * e4 + 3];
               }
-            }
-            if (last && valid) {
-              float4* yo = reinterpret_cast<float4*>(args.y + grow * q + j0);
-#pragma unroll
-              for (int e4 = 0; e4 < 4; ++e4)
-                yo[e4] = make_float4(t[4 * e4], t[4 * e4 + 1], t[4 * e4 + 2], t[4 * e4 + 3]);
+              yo[e4] = make_float4(t[4 * e4], t[4 * e4 + 1], t[4 * e4 + 2], t[4 * e4 + 3]);
             }
           }
         }
@@ -1142,22 +1151,24 @@ size_t stage_bytes_for(int BN) { return 2 * (size_t)PLANE_TILE + 2 * (size_t)BN 
 // when one tile spans all m columns (the output may be formed in the epilogue),
 // the partial y sums.
 // ym_q > 0 (output on the tensor cores): slots also carry a K chunk of C or D
-// (q rows, both planes), and with several column blocks the partial y sums
-// ([q][128] floats) stay in shared memory.
-size_t fixed_smem_bytes(int S, int ring, bool ysum, int ym_q = 0, bool ym_sum = false) {
+// (q rows, both planes).
+size_t fixed_smem_bytes(int S, int ring, bool ysum, int ym_q = 0) {
   const size_t slot = SLOT_BYTES + (ym_q > 0 ? 2 * (size_t)ym_q * ROWB : 0);
   return 1024 + (size_t)ring * slot + 8 * (2 * S + 10 + 3 * RING_MAX) + 16 +
-         (ysum ? sizeof(float) * 4 * 128 : sizeof(float) * 128) +
-         (ym_sum ? sizeof(float) * 128 * (size_t)ym_q : 0);
+         (ysum ? sizeof(float) * 4 * 128 : 0);
 }
 
 bool tc_config_fits(int m, int BN, const TcConfig& c, int ym_q = 0) {
   if (c.group != 1 && c.group != 2) return false;
   if (ym_q > 0 && c.group != 1) return false;
+  // the y issuer waits for the chunks covering TMEM columns [0, q) before it
+  // releases the first of them, and a slot is refilled one chunk after the
+  // next one is retired: the ring needs one slot more than those chunks
+  if (ym_q > 0 && c.ring < (ym_q + 31) / 32 + 1) return false;
   // each ring slot always serves the same epilogue group: ring % (2 group) == 0
   if (c.ring < 2 * c.group || c.ring > RING_MAX || c.ring % (2 * c.group) != 0) return false;
   if (c.stages < 2 || c.stages > 8) return false;
-  return fixed_smem_bytes(c.stages, c.ring, BN >= m, ym_q, ym_q > 0 && BN < m) +
+  return fixed_smem_bytes(c.stages, c.ring, BN >= m, ym_q) +
              (size_t)c.stages * stage_bytes_for(BN) <=
          227 * 1024;
 }
@@ -1264,9 +1275,11 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   // the row warps' registers fit only that variant), or the last down-sweep
   // level forming its even rows' v^(1) (also one chunk per step: fewer
   // kernel variants)
-  const bool fuse = (p.fuse_output || p.fuse_output_mma) && !reverse && y != nullptr;
-  // the output on the tensor cores (BF16 pairs, §3 schedule; u as (hi, lo) planes)
-  const bool ym = fuse && p.fuse_output_mma && S == 0;
+  const bool fuse = p.fuse_output && !reverse && y != nullptr;
+  // the output on the tensor cores (BF16 pairs, §3 schedule; u as (hi, lo)
+  // planes), for the stages that are some sequence's last
+  const bool ym = p.fuse_output_mma && !reverse && y != nullptr && S == 0 && k >= 0 &&
+                  k < (int)p.stage_fused.size() && p.stage_fused[k];
   if (ym && (!u_hi || !u_lo || elem != 2 || !p.pc_hi)) {
     set_global_error("fused tensor-core output without its u or coefficient planes");
     return cudaErrorInvalidValue;
@@ -1289,10 +1302,12 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   memset(&ymaps, 0, sizeof(ymaps));
   if (ym) {
     // one chunk per step, and slots that also hold a K chunk of C or D: the
-    // deepest shape at or below the chosen one that fits
-    TcConfig c1{cfg.stages, cfg.ring, 1};
+    // deepest shape at or below the chosen one that fits, with a slot more than
+    // the chunks covering columns [0, q) that the y issuer waits for at once
+    const int need = ((q + 31) / 32 + 2) & ~1;
+    TcConfig c1{cfg.stages, std::max(cfg.ring, need), 1};
     while (!tc_config_fits(m, BN, c1, q) && c1.stages > 2) --c1.stages;
-    while (!tc_config_fits(m, BN, c1, q) && c1.ring > 2) c1.ring -= 2;
+    while (!tc_config_fits(m, BN, c1, q) && c1.ring > need) c1.ring -= 2;
     if (!tc_config_fits(m, BN, c1, q)) {
       set_global_error("fused tensor-core output does not fit shared memory");
       return cudaErrorInvalidValue;
@@ -1318,7 +1333,7 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   a.err = p.err;
   a.diag = p.err + 1;
   a.timeout_ns = 2000000000ull;
-  const size_t smem = fixed_smem_bytes(a.stages, a.ring, BN >= m, ym ? q : 0, ym && BN < m) +
+  const size_t smem = fixed_smem_bytes(a.stages, a.ring, BN >= m, ym ? q : 0) +
                       (size_t)a.stages * stage_bytes_for(BN);
   const int nwork = ntiles * a.nblocks;
   // YM: a block takes whole tiles

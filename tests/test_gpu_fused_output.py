@@ -1,5 +1,6 @@
 """GPU parity of the output y = C v + D u (end of §3) formed on the tensor cores
-inside the last stage (BF16 split, p and q multiples of 16, q <= 64): the
+inside the last stage (BF16 split, p and q multiples of 16, q <= 64; m <= 256
+by default, wider m with CASCADE_FLAG_FUSE_WIDE_OUTPUT): the
 finished state chunks the stage kernel stages for its store are the A operand
 of a second tcgen05 product with C, the first column block adds D u, and with
 m above one column block the partial sums over the blocks are added in order.
@@ -45,6 +46,12 @@ def two_systems(m, p, q, N=11, lengths=LENGTHS, seed=41):
     return cast_inputs(w, "bf16_split")
 
 
+def wide(m):
+    """The flag that fuses the output when m spans several column blocks."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_FUSE_WIDE_OUTPUT
+    return CASCADE_FLAG_FUSE_WIDE_OUTPUT if m > 256 else 0
+
+
 def forward(lib, w, flags=0):
     import torch
     c = lib.from_workload(w, precision="bf16_split", flags=flags)
@@ -57,9 +64,12 @@ def forward(lib, w, flags=0):
 
 def test_output_fused_query(lib):
     """cascade_get_output_fused for the tensor-core form of the fused output."""
-    from paper_2411_17729_gb300._abi import CASCADE_FLAG_NO_FUSED_OUTPUT, CASCADE_FLAG_SCAN
+    from paper_2411_17729_gb300._abi import (CASCADE_FLAG_FUSE_WIDE_OUTPUT,
+                                             CASCADE_FLAG_NO_FUSED_OUTPUT, CASCADE_FLAG_SCAN)
     cases = [(256, 16, 16, "bf16_split", 0, True), (128, 16, 64, "bf16_split", 0, True),
-             (1024, 64, 64, "bf16_split", 0, True), (512, 32, 48, "bf16_split", 0, True),
+             (1024, 64, 64, "bf16_split", 0, False), (512, 32, 48, "bf16_split", 0, False),
+             (1024, 64, 64, "bf16_split", CASCADE_FLAG_FUSE_WIDE_OUTPUT, True),
+             (512, 32, 48, "bf16_split", CASCADE_FLAG_FUSE_WIDE_OUTPUT, True),
              (256, 16, 80, "bf16_split", 0, False), (128, 16, 16, "fp32", 0, False),
              (256, 3, 16, "bf16_split", 0, False),
              (256, 16, 16, "bf16_split", CASCADE_FLAG_NO_FUSED_OUTPUT, False),
@@ -77,7 +87,7 @@ def test_fused_output_matches_oracle_and_separate_pass(lib, m, p, q):
     chunks), ragged lengths, two systems."""
     from paper_2411_17729_gb300._abi import CASCADE_FLAG_NO_FUSED_OUTPUT
     w = two_systems(m, p, q)
-    c1, y1 = forward(lib, w)
+    c1, y1 = forward(lib, w, wide(m))
     assert c1.output_fused()
     c2, y2 = forward(lib, w, CASCADE_FLAG_NO_FUSED_OUTPUT)
     assert not c2.output_fused()
@@ -92,7 +102,7 @@ def test_fused_output_matches_oracle_and_separate_pass(lib, m, p, q):
 def test_fused_output_truncated(lib, m, N):
     """A truncated cascade (2^(N+1) < L): every sequence's last stage is N."""
     w = two_systems(m, 16, 32, N=N)
-    c, y = forward(lib, w)
+    c, y = forward(lib, w, wide(m))
     assert c.output_fused()
     gate(w, y, oracle.cascade_forward(w, N_per_seq=c.seq_N()), "bf16_split")
 
@@ -102,7 +112,8 @@ def test_fused_output_many_tiles_per_block(lib):
     stage walks many tiles, both column blocks of each, fused copies (all
     sources before the sequence start) interleaved with computed tiles."""
     w = two_systems(512, 16, 64, lengths=(2048,) * 40)
-    c, y = forward(lib, w)
+    c, y = forward(lib, w, wide(512))
+    assert c.output_fused()
     gate(w, y, oracle.cascade_forward(w, N_per_seq=c.seq_N()), "bf16_split")
 
 
@@ -120,7 +131,7 @@ def test_fused_output_backward_bitwise(lib, m, p, q):
     grads = []
     for flags in (CASCADE_FLAG_SAVE_STATES, CASCADE_FLAG_SAVE_STATES | CASCADE_FLAG_NO_FUSED_OUTPUT,
                   CASCADE_FLAG_RECOMPUTE):
-        c = lib.from_workload(w, precision="bf16_split", flags=flags)
+        c = lib.from_workload(w, precision="bf16_split", flags=flags | wide(m))
         c.forward(u)
         g = c.backward(u, torch.as_tensor(dy).cuda())
         torch.cuda.synchronize()

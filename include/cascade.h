@@ -131,7 +131,15 @@ enum {
      fixed order.  Off by default: at m = 1024, q = 64 the slots' K chunks of C
      leave room for only two operand stages, and the last stage with the output
      took 2.2 ms against 1.3 ms plus a 0.45 ms separate projection (GB300). */
-  CASCADE_FLAG_FUSE_WIDE_OUTPUT = 256
+  CASCADE_FLAG_FUSE_WIDE_OUTPUT = 256,
+  /* Run stages 1, 2, 3 of the §3 schedule as separate launches through device
+     memory (diagnostics).  By default forward-only plans with BF16 pairs,
+     p = 1, m = 128 or 256, whose sequences all run more than 3 stages, run
+     them as one pass over overlapping windows of 128 steps that keeps the
+     states on chip (FP32 between the stages, so the results agree with the
+     separate launches to rounding, not bit for bit); see
+     cascade_get_fused_stages.                                              */
+  CASCADE_FLAG_NO_FUSED_STAGES = 512
 };
 
 typedef struct cascade_plan_s* cascade_plan_t;
@@ -241,6 +249,12 @@ cascade_status_t cascade_get_output_fused(cascade_plan_t plan, int32_t* h_fused)
    down-sweep level forms the even rows' v^(1) = Bbar u_l from u and writes
    only y.  *h_fused = 1 or 0; CASCADE_ERR_STATE before cascade_set_batch. */
 cascade_status_t cascade_get_first_fused(cascade_plan_t plan, int32_t* h_fused);
+
+/* Number of leading stages (1 .. J) of the §3 schedule that the current
+   batch's forward runs as one pass from u with the states on chip, or 0
+   (CASCADE_FLAG_NO_FUSED_STAGES).  *h_J; CASCADE_ERR_STATE before
+   cascade_set_batch. */
+cascade_status_t cascade_get_fused_stages(cascade_plan_t plan, int32_t* h_J);
 
 /* Size of the fixed device scratch array behind cascade_forward_fixed_scratch. */
 #define CASCADE_FIXED_SCRATCH_BYTES ((size_t)32 << 20)

@@ -20,7 +20,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libcascade.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "precompute.cu", "stage_simt.cu", "stage_tc.cu", "backward.cu", "grad_tc.cu", "proj.cu", "zoh.cu", "chain_tc.cu", "proj_tc.cu", "scan_top.cu",
-           "noalloc.cu"]
+           "stage_fused.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -178,6 +178,13 @@ class Cascade:
         self._check(self.lib.cascade_get_first_fused(self.plan, C.byref(f)))
         return bool(f.value)
 
+    def fused_stages(self):
+        """Leading stages 1 .. J that the forward runs as one pass with the states
+        on chip (0: none)."""
+        j = C.c_int32()
+        self._check(self.lib.cascade_get_fused_stages(self.plan, C.byref(j)))
+        return j.value
+
     def stage_shapes(self):
         """{entry: (stages, ring slots, chunks per step)} chosen per stage by autotune
         (entry k: stage k; work-efficient schedule: up-sweep level k, 100 + k: down-sweep

@@ -259,6 +259,10 @@ void free_batch(Plan* p) {
   p->n_adj_tiles.clear();
   p->saved_ws = nullptr;
   p->n_out_tiles = p->n_stage0_tiles = 0;
+  dfree(p->d_fwin);
+  p->d_fwin = nullptr;
+  p->n_fwin = 0;
+  p->fused_J = 0;
   for (Plan::ScanLevel& lv : p->scan) dfree(lv.d_tiles);
   p->scan.clear();
   dfree(p->d_scan_rows);
@@ -607,7 +611,20 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
   auto out_buf = [&](int k) { return fwd_buf(*p, k + 1); };
   // stage 0 fused with v^(0) = Bbar u (formed inside stage 1 with fuse_first,
   // here only for the sequences without a stage 1)
-  if (p->fuse_first)
+  if (p->fused_J > 0) {
+    // stages 1 .. fused_J in one pass from u (no first-stage launch: every
+    // sequence runs past those stages); timed as stage 1
+    const int J = p->fused_J;
+    if (timing) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
+    CK(launch_fused_stages(*p, static_cast<const float*>(u), V.hi(in_buf(J + 1)),
+                           V.lo(in_buf(J + 1)), st),
+       "fused first stages");
+    if (timing) {
+      CK(cudaEventRecord(p->ev[2 * p->n_ev + 1], st), "event");
+      p->ev_k.push_back(1);
+      p->n_ev++;
+    }
+  } else if (p->fuse_first)
     CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), 0, st),
        "first stage");
   else if (ptc)
@@ -616,7 +633,7 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
     CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), 0, st), "first stage");
   else
     CK(launch_stage0(*p, u, V.hi(out_buf(0)), V.lo(out_buf(0)), st), "first stage");
-  for (int k = 1; k <= p->maxN; ++k) {
+  for (int k = p->fused_J + 1; k <= p->maxN; ++k) {
     const int in = in_buf(k), out = out_buf(k);
     if (timing && p->n_tiles[k] > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
     if (p->d.precision == CASCADE_FP64) {
@@ -1547,6 +1564,36 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
   }
   CK(upload(t0s, &p->d_stage0_tiles), "upload first-stage schedule");
   p->n_stage0_tiles = (int)t0s.size();
+  // Stages 1 .. 3 in one pass over windows of 128 steps with the states on chip
+  // (stage_fused.cu), for forward-only §3 plans with p = 1 at m = 128 or 256
+  // whose sequences all run past stage 3 (none forms its output there).
+  {
+    const int J = 3, H = (2 << J) - 2;
+    bool ok = fused_stages_supported(*p) && !scans(*p) &&
+              !(p->d.flags & (CASCADE_FLAG_SAVE_STATES | CASCADE_FLAG_RECOMPUTE |
+                              CASCADE_FLAG_NO_FUSED_STAGES));
+    bool any = false;
+    for (int i = 0; i < nseq && ok; ++i) {
+      if (h_offsets[i + 1] == h_offsets[i]) continue;
+      any = true;
+      ok = p->seq_N[i] >= J + 1;
+    }
+    if (ok && any) {
+      std::vector<FusedWindow> fw;
+      for (int i = 0; i < nseq; ++i) {
+        const int64_t L = h_offsets[i + 1] - h_offsets[i];
+        for (int64_t o = 0; o < L; o += BM - H)
+          fw.push_back(FusedWindow{h_offsets[i], (int32_t)(o - H), (int32_t)L,
+                                   p->sys_of_seq[i], 0});
+      }
+      CK(cudaMalloc(&p->d_fwin, fw.size() * sizeof(FusedWindow)), "alloc fused windows");
+      CK(cudaMemcpy(p->d_fwin, fw.data(), fw.size() * sizeof(FusedWindow),
+                    cudaMemcpyHostToDevice),
+         "upload fused windows");
+      p->n_fwin = (int)fw.size();
+      p->fused_J = J;
+    }
+  }
   // output tiles grouped by the buffer holding their final states (the
   // tensor-core output projection reads one buffer per launch)
   std::stable_sort(outs.begin(), outs.end(),
@@ -1671,6 +1718,14 @@ cascade_status_t cascade_get_first_fused(cascade_plan_t plan, int32_t* h_fused) 
   if (!p || !h_fused) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
   if (!p->have_batch) return fail(p, CASCADE_ERR_STATE, "no batch set");
   *h_fused = (p->fuse_first || p->scan_even_on_chip) ? 1 : 0;
+  return CASCADE_OK;
+}
+
+cascade_status_t cascade_get_fused_stages(cascade_plan_t plan, int32_t* h_J) {
+  Plan* p = plan;
+  if (!p || !h_J) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
+  if (!p->have_batch) return fail(p, CASCADE_ERR_STATE, "no batch set");
+  *h_J = p->fused_J;
   return CASCADE_OK;
 }
 

@@ -34,6 +34,18 @@ struct Tile {
 static_assert(sizeof(Tile) == 32, "Tile is 32 bytes");
 enum { TILE_FINAL_FUSED = 1 };
 
+// Window of the fused first stages (stage_fused.cu): 128 time steps of one
+// sequence from step r0 on (r0 may be negative: steps before the sequence are
+// zero); the pass stores its rows from H on.
+struct FusedWindow {
+  int64_t seq_row0;   // packed row of the sequence's first time step
+  int32_t r0;
+  int32_t len;        // sequence length
+  int32_t sys;
+  int32_t pad;
+};
+static_assert(sizeof(FusedWindow) == 24, "FusedWindow is 24 bytes");
+
 // Sequence record (output kernel, recursion, backward).
 struct Seq {
   int64_t row0;
@@ -176,6 +188,11 @@ struct Plan {
   // q multiples of 16, q <= 64, §3 schedule), where fuse_output does not apply
   bool fuse_output_mma = false;
   std::vector<char> stage_fused;   // stage k of the §3 schedule holds fused tiles (per batch)
+  // stages 1 .. fused_J of the §3 schedule run as one pass over overlapping
+  // windows with the states on chip (0: not used; set per batch)
+  int fused_J = 0;
+  FusedWindow* d_fwin = nullptr;
+  int n_fwin = 0;
   // stage 1 forms v^(1) = Bbar u_l + Abar Bbar u_(l-1) on chip; the first-stage
   // kernel does not run (set per batch)
   bool fuse_first = false;
@@ -323,6 +340,11 @@ bool proj_supported(const Plan& p);
 bool scan_top_supported(const Plan& p);
 cudaError_t launch_scan_top(const Plan& p, void* v_hi, void* v_lo, uint64_t rows_cap,
                             const float* u, float* y, cudaStream_t st);
+// Stages 1 .. fused_J in one pass from u (stage_fused.cu): BF16 split, p = 1,
+// m = 128 or 256; writes v^(fused_J + 1).
+bool fused_stages_supported(const Plan& p);
+cudaError_t launch_fused_stages(const Plan& p, const float* u, void* vout_hi, void* vout_lo,
+                                cudaStream_t st);
 // Tensor-core projections (proj_tc.cu): BF16 split with p and q multiples of 16.
 // The B operands are the PC_* matrices, split at set_system time.
 enum { PC_B = 0, PC_AB, PC_C, PC_D, PC_CT, PC_BT, PC_ABT, PC_DT, PC_COUNT };

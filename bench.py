@@ -361,7 +361,10 @@ def stage_roofline(w, c, stage_ms, precision, args):
     Ns = c.seq_N()
     # stage 1 forming v^(1) on chip is another kernel variant (more warps, bound by
     # instruction issue): reported on its own, with the bytes it moves
-    first = (not f64) and c.first_fused()
+    # stages 1 .. J as one pass with the states on chip (timed as stage 1), or
+    # stage 1 forming v^(1) on chip: other kernels, reported on their own
+    J = 0 if f64 else c.fused_stages()
+    first = (not f64) and (J > 0 or c.first_fused())
     first_ms = float(np.mean(stage_ms[1])) if first and 1 in stage_ms else 0.0
     plain = {k: v for k, v in stage_ms.items() if not (first and k == 1)}
     tot = {k: sum(v) for k, v in plain.items()}
@@ -429,13 +432,43 @@ def stage_roofline(w, c, stage_ms, precision, args):
             "alg_flops_per_launch": alg_flops, "avg_launch_ms": avg_ms,
             "launches_per_step": len(plain), "stage_ms_per_step": stage_total,
             "hbm" if tensor_bound else "tensor": other}
-    if first and first_ms > 0:
+    if J > 0 and first_ms > 0:
+        # reads u, writes v^(J+1) (every row of the sequences); useful products
+        # 6 m^2 per updated row per stage, and the windows' halo on top
+        H = (2 << J) - 2
+        rows = int(Ls.sum())
+        bJ = (esize * m + 4 * w.p) * rows
+        useful = sum(6.0 * m * m * float(np.maximum(Ls - (1 << k), 0).sum()) for k in range(1, J + 1))
+        wins = int(sum((int(L) + (128 - H) - 1) // (128 - H) for L in Ls))
+        executed = 6.0 * m * m * 128 * wins * J
+        tf = useful / (first_ms / 1000.0) / 1e12
+        roof["fused_first_stages"] = {
+            "kernel": f"fused_stages_kernel<{m}>: stages 1..{J} in one pass from u, states on "
+                      f"chip, windows of 128 steps with a {H}-row halo",
+            "stages": J, "ms": first_ms, "alg_bytes": bJ,
+            "achieved_gbs": bJ / (first_ms / 1000.0) / 1e9, "useful_flops": useful,
+            "executed_flops": executed, "achieved": tf, "unit": "TFLOP/s",
+            "frac_of_tensor": tf / (bf16_peak if esize == 4 else bf16_peak * 0.5),
+            "executed_frac_of_tensor": executed / (first_ms / 1000.0) / 1e12 /
+            (bf16_peak if esize == 4 else bf16_peak * 0.5)}
+        roof["kernel"] = kname + f" (stages {J + 1}..N; stages 1..{J} under fused_first_stages)"
+    elif first and first_ms > 0:
         rows1 = int(Ls[Ns >= 1].sum())
         b1 = (esize * m + 4 * w.p) * rows1 + w.nsys * m * m * esize
         roof["stage1_on_chip"] = {
             "kernel": kname + " with v^(1) = Bbar u + Abar Bbar u_(l-1) formed on chip",
             "ms": first_ms, "alg_bytes": b1, "achieved": b1 / (first_ms / 1000.0) / 1e9,
             "unit": "GB/s", "frac_of_hbm": b1 / (first_ms / 1000.0) / 1e9 / hbm_peak}
+    # every stage of a forward together (§3 algorithmic products over the summed
+    # stage launch times, the fused first pass included)
+    all_flops = sum((1 if f64 else 3) * 2.0 * m * m * float(np.maximum(Ls[Ns >= k] - (1 << k), 0).sum())
+                    for k in range(1, int(Ns.max(initial=0)) + 1))
+    all_ms = stage_total + first_ms
+    if all_ms > 0 and not f64:
+        tf = all_flops / (all_ms / 1000.0) / 1e12
+        roof["all_stages"] = {"flops_per_step": all_flops, "ms_per_step": all_ms,
+                              "achieved": tf, "unit": "TFLOP/s", "frac_of_tensor": tf / tpk,
+                              "peak_kind": tpk_kind}
     return roof
 
 

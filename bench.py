@@ -184,19 +184,23 @@ def oracle_sample(w, budget_s=12.0, keep=False):
     return states / dt, desc, dt, outs
 
 
-def seq_errors(yg, yo, Du, out_eps):
+def seq_errors(yg, yo, Du, out_eps, absDu):
     """Relative Frobenius and element-wise errors of one sequence on y and on
-    Cx = y - Du (beyond the rounding of y to float)."""
+    Cx = y - Du, the latter beyond an allowance for the rounding of the
+    delivered y: 2 out_eps ||y|| in norm, (p + 2) out_eps (|y| + |D| |u|) per
+    element (y's last rounding and the p products of D u in the output type)."""
     import numpy as np
     d = yg - yo
     ny, my = np.linalg.norm(yo), np.max(np.abs(yo))
     nd, md = np.linalg.norm(d), np.max(np.abs(d))
     cx = yo - Du
     ncx, mcx = np.linalg.norm(cx), np.max(np.abs(cx))
+    pw = absDu.shape[1]
+    excess = np.max(np.maximum(np.abs(d) - (pw + 2) * out_eps * (np.abs(yo) + absDu), 0.0))
     return (nd / ny if ny > 0 else nd,
             max(nd - 2 * out_eps * ny, 0.0) / ncx if ncx > 0 else 0.0,
             md / my if my > 0 else md,
-            max(md - 2 * out_eps * my, 0.0) / mcx if mcx > 0 else 0.0)
+            excess / mcx if mcx > 0 else 0.0)
 
 
 def error_of(w, y_gpu, outs, precision, sample):
@@ -208,13 +212,15 @@ def error_of(w, y_gpu, outs, precision, sample):
     for i, yo in outs.items():
         sl = w.seq(i)
         D = w.D[min(int(w.sys_of_seq[i]), w.D.shape[0] - 1)]
-        worst = np.maximum(worst, seq_errors(y_gpu[sl], yo, w.u[sl] @ D.T, out_eps))
+        worst = np.maximum(worst, seq_errors(y_gpu[sl], yo, w.u[sl] @ D.T, out_eps,
+                                             np.abs(w.u[sl]) @ np.abs(D).T))
     bar = TOL[precision]
     return {"frob_y": float(worst[0]), "frob_cx": float(worst[1]), "elem_y": float(worst[2]),
             "elem_cx": float(worst[3]), "bar": bar, "pass": bool(np.all(worst <= bar)),
             "sequences": sorted(int(i) for i in outs),
             "what": "per sequence, worst over the sample: ||y - y_o|| / ||y_o|| and on Cx = "
-                    "y - Du; max|y - y_o| / max|y_o| and on Cx; oracle = CPU FP64 cascade",
+                    "y - Du; max|y - y_o| / max|y_o| and on Cx (beyond the rounding of the "
+                    "delivered y and of its FP32 D u); oracle = CPU FP64 cascade",
             "sample": sample}
 
 

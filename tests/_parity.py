@@ -43,11 +43,14 @@ def _test_id():
     return os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
 
 
-def seq_errors(yg, yo, Du=None, out_eps=0.0):
+def seq_errors(yg, yo, Du=None, out_eps=0.0, absDu=None):
     """Errors of one sequence (rows = time): (frob y, frob Cx, elem y, elem Cx).
-    The Cx errors are taken beyond an allowance of 2 out_eps times the norm of
-    y (Frobenius) or its largest element (element-wise) for the rounding of
-    y to its output format.  Without Du the Cx errors are those of y."""
+    The Cx errors are taken beyond an allowance for the rounding of the
+    delivered y: 2 out_eps ||y|| in norm; element-wise, per element,
+    (p + 2) out_eps (|y| + |D| |u|) when absDu = |u| |D|^T is given (y's last
+    rounding and the p products of D u evaluated in the output type; p = the
+    width of u), else 2 out_eps max |y|.  Without Du the Cx errors are those
+    of y."""
     d = yg - yo
     ny, my = np.linalg.norm(yo), np.max(np.abs(yo)) if yo.size else 0.0
     nd, md = np.linalg.norm(d), np.max(np.abs(d)) if d.size else 0.0
@@ -58,7 +61,12 @@ def seq_errors(yg, yo, Du=None, out_eps=0.0):
     cx = yo - Du
     ncx, mcx = np.linalg.norm(cx), np.max(np.abs(cx)) if cx.size else 0.0
     fcx = max(nd - 2.0 * out_eps * ny, 0.0) / ncx if ncx > 0 else 0.0
-    ecx = max(md - 2.0 * out_eps * my, 0.0) / mcx if mcx > 0 else 0.0
+    if absDu is not None and d.size:
+        pw = absDu.shape[1] if absDu.ndim > 1 else 1
+        excess = np.max(np.maximum(np.abs(d) - (pw + 2) * out_eps * (np.abs(yo) + absDu), 0.0))
+    else:
+        excess = max(md - 2.0 * out_eps * my, 0.0)
+    ecx = excess / mcx if mcx > 0 else 0.0
     return fy, fcx, ey, ecx
 
 
@@ -77,7 +85,8 @@ def rel_errors(w, y, yo, out_eps=0.0):
         s = int(w.sys_of_seq[i])
         D = w.D[min(s, w.D.shape[0] - 1)]
         Du = w.u[sl] @ D.T
-        worst = np.maximum(worst, seq_errors(y[sl], yo[sl], Du, out_eps))
+        absDu = np.abs(w.u[sl]) @ np.abs(D).T
+        worst = np.maximum(worst, seq_errors(y[sl], yo[sl], Du, out_eps, absDu))
     return tuple(worst)
 
 
@@ -99,8 +108,8 @@ class SeqGate:
         self.precision, self.what = precision, what
         self.worst = np.zeros(4)
 
-    def add(self, yg, yo, Du):
-        self.worst = np.maximum(self.worst, seq_errors(yg, yo, Du, OUT_EPS[self.precision]))
+    def add(self, yg, yo, Du, absDu=None):
+        self.worst = np.maximum(self.worst, seq_errors(yg, yo, Du, OUT_EPS[self.precision], absDu))
 
     def check(self):
         bar = TOL[self.precision]

@@ -272,7 +272,7 @@ def test_precision_form_full_size(lib):
         Abar, Bbar, C, D = oracle.system_matrices(w, int(w.sys_of_seq[i]))
         uu = w.u[sl]
         yo = oracle.cascade_forward_seq(Abar, Bbar, C, D, uu, 13)
-        g.add(y[sl], yo, uu @ D.T)
+        g.add(y[sl], yo, uu @ D.T, np.abs(uu) @ np.abs(D).T)
     g.check()
 
 
@@ -295,7 +295,7 @@ def test_large_form_full_size(lib):
         n = sl.stop - sl.start if i == w.nseq - 1 else 192
         uu = w.u[sl][:n]
         yo = oracle.cascade_forward_seq(Abar, Bbar, C, D, uu, 15, powers=powers)
-        g.add(y[sl][:n], yo, uu @ D.T)
+        g.add(y[sl][:n], yo, uu @ D.T, np.abs(uu) @ np.abs(D).T)
     g.check()
 
 
@@ -321,7 +321,7 @@ def test_batching_form_full_size(lib):
         sl = w.seq(i)
         uu = w.u[sl] if n is None else w.u[sl][:n]
         yo = oracle.cascade_forward_seq(Abar, Bbar, C, D, uu, int(Ns[i]))
-        g.add(y[sl][: len(uu)], yo, uu @ D.T)
+        g.add(y[sl][: len(uu)], yo, uu @ D.T, np.abs(uu) @ np.abs(D).T)
     g.check()
 
 

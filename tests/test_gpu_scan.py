@@ -170,7 +170,7 @@ def test_scan_precision_form_full_size(lib):
         Abar, Bbar, C, D = oracle.system_matrices(w, int(w.sys_of_seq[i]))
         uu = w.u[sl]
         yo = oracle.cascade_forward_seq(Abar, Bbar, C, D, uu, 13)
-        g.add(y[sl], yo, uu @ D.T)
+        g.add(y[sl], yo, uu @ D.T, np.abs(uu) @ np.abs(D).T)
     g.check()
 
 

@@ -670,6 +670,9 @@ def measure(name, args, dev, world, rank):
         scan = {"value": whole_job_rate(states_per_step, world, scan_ms), "unit": "states/s",
                 "ms_per_step": scan_ms, "matvecs_per_step": int(nmv.value),
                 "levels": nlev, "level_ms_per_step": lev_tot, "top_of_tree_ms_per_step": top_ms,
+                # per launch: up-sweep level k as "k", down-sweep level k as "100+k", the
+                # top of the tree as "300+k0" (median ms)
+                "level_ms": {str(k): round(statistics.median(v), 4) for k, v in sorted(lev_ms.items())},
                 "roofline": ({"bound": "tensor", "achieved": lev_tfs, "peak": tpk,
                               "unit": "TFLOP/s", "frac": lev_tfs / tpk,
                               "hbm_frac": lev_gbs / hbm_peak}

@@ -142,3 +142,28 @@ def test_fused_output_backward_bitwise(lib, m, p, q):
         assert np.array_equal(grads[0][k], grads[2][k]), k
     ref = oracle.cascade_backward(w, dy.astype(np.float64), N_per_seq=c.seq_N())
     gate_grads(w, grads[0], ref, "bf16_split")
+
+
+def test_differentiation_form_forward_full_size(lib):
+    """The differentiation workload's forward at full size (m = 256, p = q = 16,
+    32 x 8192, N = 12), output formed on the tensor cores in the last stage:
+    every sequence against the oracle, and the separate projection pass on the
+    same inputs agrees with it to rounding."""
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_NO_FUSED_OUTPUT
+    from _parity import SeqGate
+    w = cast_inputs(wl.differentiation_form(), "bf16_split")
+    c1, y1 = forward(lib, w)
+    assert c1.output_fused()
+    c2, y2 = forward(lib, w, CASCADE_FLAG_NO_FUSED_OUTPUT)
+    Abar, Bbar, C, D = oracle.system_matrices(w, 0)
+    powers = oracle.squaring_chain(Abar, 12)
+    g1, g2 = SeqGate("bf16_split", "fused"), SeqGate("bf16_split", "pass")
+    for i in range(w.nseq):
+        sl = w.seq(i)
+        uu = w.u[sl]
+        yo = oracle.cascade_forward_seq(Abar, Bbar, C, D, uu, 12, powers=powers)
+        g1.add(y1[sl], yo, uu @ D.T, np.abs(uu) @ np.abs(D).T)
+        g2.add(y2[sl], yo, uu @ D.T, np.abs(uu) @ np.abs(D).T)
+    e1, e2 = g1.check(), g2.check()
+    fy, _, ey, _ = rel_errors(w, y1, y2)
+    assert fy < 1e-5 and ey < 1e-5, (fy, ey, e1, e2)

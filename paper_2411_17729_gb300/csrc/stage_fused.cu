@@ -65,7 +65,8 @@ struct FusedArgs {
 __device__ __forceinline__ void fused_timeout(const FusedArgs& a, volatile int* abort_flag,
                                               int site, int x, int y) {
   if (atomicCAS(a.err, 0, (int32_t)CASCADE_ERR_TIMEOUT) == 0 && a.diag) {
-    a.diag[0] = 300 + site;
+    a.diag[0] = 400 + site;   // (stage kernel 1+, power gradients 100+, projections 200+,
+                              // top of the scan tree 300+)
     a.diag[1] = (int32_t)blockIdx.x;
     a.diag[2] = x;
     a.diag[3] = y;

@@ -62,13 +62,13 @@ SPECS = {
 # full launch (the traffic of these launches grows in proportion to the rows).
 # workload -> (bytes per full launch, the stage captured, note); absent: null.
 TRAFFIC = {
-    "large_form": (8 * 515.6e6, 8,
+    "large_form": (8 * 500.9e6, 8,
                    "ncu dram__bytes_read.sum + dram__bytes_write.sum of stage_tc_kernel, stage 8, "
-                   "1 of 8 sequences (288.4 + 227.2 MB), x8 to the full launch; about 40 MB of "
+                   "1 of 8 sequences (274.2 + 226.7 MB), x8 to the full launch; about 40 MB of "
                    "writes still dirty in L2 at kernel end are not counted"),
-    "precision_form": (4 * 506.6e6, 8,
+    "precision_form": (4 * 506.2e6, 8,
                        "ncu dram__bytes_read.sum + dram__bytes_write.sum of stage_tc_kernel, "
-                       "stage 8, 16 of 64 sequences (285.2 + 221.5 MB), x4 to the full launch; "
+                       "stage 8, 16 of 64 sequences (284.1 + 222.1 MB), x4 to the full launch; "
                        "about 43 MB of writes still dirty in L2 at kernel end are not counted"),
 }
 

@@ -60,15 +60,13 @@ SPECS = {
 # DRAM bytes (read + write) of one stage_tc_kernel launch, from ncu captures of
 # the current kernel on a smaller case, scaled by the rows processed to the
 # full launch (the traffic of these launches grows in proportion to the rows).
-# workload -> (bytes per full launch, the launch's first stage, stages in the
-# launch, note); used only when the timed plan launches that stage the same way
-# (alone, or as a pair with the next); absent: null.
+# workload -> (bytes per full launch, the stage captured, note); absent: null.
 TRAFFIC = {
-    "large_form": (8 * 500.9e6, 8, 1,
+    "large_form": (8 * 500.9e6, 8,
                    "ncu dram__bytes_read.sum + dram__bytes_write.sum of stage_tc_kernel, stage 8, "
                    "1 of 8 sequences (274.2 + 226.7 MB), x8 to the full launch; about 40 MB of "
                    "writes still dirty in L2 at kernel end are not counted"),
-    "precision_form": (4 * 506.2e6, 8, 1,
+    "precision_form": (4 * 506.2e6, 8,
                        "ncu dram__bytes_read.sum + dram__bytes_write.sum of stage_tc_kernel, "
                        "stage 8, 16 of 64 sequences (284.1 + 222.1 MB), x4 to the full launch; "
                        "about 43 MB of writes still dirty in L2 at kernel end are not counted"),
@@ -379,31 +377,22 @@ def stage_roofline(w, c, stage_ms, precision, args):
     nl = sum(len(v) for v in plain.values())
     avg_ms = sum(tot.values()) / max(1, nl)
     fused = c.output_fused()
-    # stages k, k + 1 in one launch (timed as stage k)
-    pairs = set() if f64 else set(c.stage_pairs())
     bytes_l, flops_l = [], []
     for k in plain:
-        b_launch, f_launch = 0, 0
-        for j, kk in enumerate((k, k + 1) if k in pairs else (k,)):
-            s = 1 << kk
-            live = Ns >= kk
-            last = live & (Ns == kk) if fused else np.zeros_like(live)
-            mid = live & ~last
-            upd = int(np.maximum(Ls[live] - s, 0).sum())
-            upd_mid = int(np.maximum(Ls[mid] - s, 0).sum())
-            rows_mid, rows_last = int(Ls[mid].sum()), int(Ls[last].sum())
-            # before a sequence's last stage: read every row of v^(k) once and write the
-            # updated rows of v^(k+1) (esize bytes per element); its last stage with the
-            # output fused reads every row of v^(k) and u and writes y, not v (v as well
-            # when the plan keeps its stage outputs); plus the power's operand planes.
-            # The second stage of a pair reads the middle states the first one has just
-            # written, from L2: not counted again.
-            read = 0 if j == 1 else esize * m * (rows_mid + rows_last)
-            b_launch += (read + esize * m * upd_mid + 4 * (w.p + w.q) * rows_last
-                         + w.nsys * m * m * esize)
-            f_launch += (1 if f64 else 3) * 2 * m * m * upd
-        bytes_l.append(b_launch)
-        flops_l.append(f_launch)
+        s = 1 << k
+        live = Ns >= k
+        last = live & (Ns == k) if fused else np.zeros_like(live)
+        mid = live & ~last
+        upd = int(np.maximum(Ls[live] - s, 0).sum())
+        upd_mid = int(np.maximum(Ls[mid] - s, 0).sum())
+        rows_mid, rows_last = int(Ls[mid].sum()), int(Ls[last].sum())
+        # before a sequence's last stage: read every row of v^(k) once and write the
+        # updated rows of v^(k+1) (esize bytes per element); its last stage with the
+        # output fused reads every row of v^(k) and u and writes y, not v (v as well
+        # when the plan keeps its stage outputs); plus the power's operand planes
+        bytes_l.append(esize * m * (rows_mid + upd_mid) + (esize * m + 4 * (w.p + w.q)) * rows_last
+                       + w.nsys * m * m * esize)
+        flops_l.append((1 if f64 else 3) * 2 * m * m * upd)
     alg_bytes = float(np.mean(bytes_l)) if bytes_l else 0.0
     alg_flops = float(np.mean(flops_l)) if flops_l else 0.0
     gbs = alg_bytes / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else 0.0
@@ -434,8 +423,8 @@ def stage_roofline(w, c, stage_ms, precision, args):
     traffic, traffic_note = None, None
     tr = TRAFFIC.get(args.cur_workload)
     traffic_alg = None
-    if tr and not args.seqs and tr[1] in plain and tr[2] == (2 if tr[1] in pairs else 1):
-        traffic, traffic_note = tr[0], tr[3]
+    if tr and not args.seqs and tr[1] in plain:
+        traffic, traffic_note = tr[0], tr[2]
         traffic_alg = float(bytes_l[list(plain).index(tr[1])])
     roof = {"bound": "tensor" if tensor_bound else "hbm", "achieved": main["achieved"],
             "peak": main["peak"], "unit": main["unit"], "frac": main["frac"],
@@ -444,7 +433,6 @@ def stage_roofline(w, c, stage_ms, precision, args):
             "alg_bytes_traffic_stage": traffic_alg,
             "kernel": kname + (" (stages 2..N; stage 1 with v^(1) formed on chip under "
                                "stage1_on_chip)" if first else " (stages 1..N)"),
-            "stage_pairs": sorted(pairs),
             "peak_kind": main["peak_kind"], "intensity_flop_per_byte": intensity,
             "ridge_flop_per_byte": ridge, "alg_bytes_per_launch": alg_bytes,
             "alg_flops_per_launch": alg_flops, "avg_launch_ms": avg_ms,
@@ -470,10 +458,6 @@ def stage_roofline(w, c, stage_ms, precision, args):
             "executed_frac_of_tensor": executed / (first_ms / 1000.0) / 1e12 /
             (bf16_peak if esize == 4 else bf16_peak * 0.5)}
         roof["kernel"] = kname + f" (stages {J + 1}..N; stages 1..{J} under fused_first_stages)"
-    if pairs:
-        roof["kernel"] += (f"; launches at stages {sorted(pairs)} also run the next stage "
-                           "(stage pairs: alg bytes count the middle states written once and "
-                           "read back from L2)")
     elif first and first_ms > 0:
         rows1 = int(Ls[Ns >= 1].sum())
         b1 = (esize * m + 4 * w.p) * rows1 + w.nsys * m * m * esize

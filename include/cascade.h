@@ -139,19 +139,7 @@ enum {
      states on chip (FP32 between the stages, so the results agree with the
      separate launches to rounding, not bit for bit); see
      cascade_get_fused_stages.                                              */
-  CASCADE_FLAG_NO_FUSED_STAGES = 512,
-  /* Run every stage of the §3 schedule as a launch of its own (diagnostics).
-     By default forward-only plans with BF16 pairs whose tiles span all m
-     columns (m <= 256) and whose sequences are all multiples of 128 steps
-     long run stages k and k + 1 as one launch: blocks take the two stages'
-     tiles from one interleaved list, and a tile of stage k + 1 starts once the
-     blocks holding the stage-k tiles it reads have stored them, which it then
-     reads from L2.  The states then rotate through three buffers instead of
-     two (one more state buffer of workspace).  Results are the same bit for
-     bit; see cascade_get_stage_pairs.  A plan's forwards must not run
-     concurrently (on several streams): the pairs' progress words are the
-     plan's.                                                                */
-  CASCADE_FLAG_NO_STAGE_PAIRS = 1024
+  CASCADE_FLAG_NO_FUSED_STAGES = 512
 };
 
 typedef struct cascade_plan_s* cascade_plan_t;
@@ -267,13 +255,6 @@ cascade_status_t cascade_get_first_fused(cascade_plan_t plan, int32_t* h_fused);
    (CASCADE_FLAG_NO_FUSED_STAGES).  *h_J; CASCADE_ERR_STATE before
    cascade_set_batch. */
 cascade_status_t cascade_get_fused_stages(cascade_plan_t plan, int32_t* h_J);
-
-/* Which stages of the §3 schedule the current batch's forward runs in pairs
-   with the next one (CASCADE_FLAG_NO_STAGE_PAIRS): for k = 0 .. n - 1,
-   h_first[k] = 1 when stages k and k + 1 run as one launch, else 0 (host
-   array of n entries, caller-owned).  CASCADE_ERR_STATE before
-   cascade_set_batch. */
-cascade_status_t cascade_get_stage_pairs(cascade_plan_t plan, int32_t* h_first, int32_t n);
 
 /* Size of the fixed device scratch array behind cascade_forward_fixed_scratch. */
 #define CASCADE_FIXED_SCRATCH_BYTES ((size_t)32 << 20)

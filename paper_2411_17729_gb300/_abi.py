@@ -34,7 +34,6 @@ CASCADE_FLAG_NO_FUSED_FIRST = 64
 CASCADE_FLAG_DENSE_SETUP = 128
 CASCADE_FLAG_FUSE_WIDE_OUTPUT = 256
 CASCADE_FLAG_NO_FUSED_STAGES = 512
-CASCADE_FLAG_NO_STAGE_PAIRS = 1024
 
 PRECISIONS = {"fp64": CASCADE_FP64, "fp32": CASCADE_FP32, "bf16_split": CASCADE_BF16_SPLIT}
 
@@ -66,7 +65,6 @@ SIGNATURES = [
     ("cascade_get_output_fused", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
     ("cascade_get_first_fused", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
     ("cascade_get_fused_stages", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32)]),
-    ("cascade_get_stage_pairs", C.c_int, [cascade_plan_t, C.POINTER(C.c_int32), C.c_int32]),
     ("cascade_get_stage_shapes", C.c_int,
      [cascade_plan_t, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("cascade_set_stage_shapes", C.c_int, [cascade_plan_t, C.c_int32, C.POINTER(C.c_int32)]),

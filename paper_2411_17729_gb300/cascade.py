@@ -185,13 +185,6 @@ class Cascade:
         self._check(self.lib.cascade_get_fused_stages(self.plan, C.byref(j)))
         return j.value
 
-    def stage_pairs(self):
-        """Stages k whose launch also runs stage k + 1 (sorted list)."""
-        n = 64
-        buf = (C.c_int32 * n)()
-        self._check(self.lib.cascade_get_stage_pairs(self.plan, buf, n))
-        return [k for k in range(n) if buf[k]]
-
     def stage_shapes(self):
         """{entry: (stages, ring slots, chunks per step)} chosen per stage by autotune
         (entry k: stage k; work-efficient schedule: up-sweep level k, 100 + k: down-sweep

@@ -10,7 +10,6 @@
 #include <algorithm>
 #include <array>
 #include <mutex>
-#include <unordered_map>
 
 namespace cascade {
 
@@ -208,13 +207,11 @@ bool keeps_states(const Plan& p) { return saves_states(p) || recomputes(p); }
 // the checkpoints v^(1), v^(1+c), v^(1+2c), ... (c = ck_seg) go to buffers
 // 2, 3, ... and the other stage outputs alternate between buffers 0 and 1.
 // A sequence's rows are written only by stages k <= N_i, so its final states
-// v^(N_i+1) stay in fwd_buf(N_i+1).  When stages run in pairs (stage k writes
-// the middle states that stage k + 1 of the same launch reads) three buffers
-// rotate: v^(j) in buffer j mod 3.
+// v^(N_i+1) stay in fwd_buf(N_i+1).
 int fwd_buf(const Plan& p, int j) {
   if (saves_states(p)) return j - 1;
   if (recomputes(p) && j <= p.maxN && (j - 1) % p.ck_seg == 0) return 2 + (j - 1) / p.ck_seg;
-  return j % p.nrot;
+  return j & 1;
 }
 
 int ceil_log2(int64_t L) {
@@ -264,15 +261,6 @@ void free_batch(Plan* p) {
   p->n_out_tiles = p->n_stage0_tiles = 0;
   dfree(p->d_fwin);
   p->d_fwin = nullptr;
-  for (Tile* t : p->d_pair_tiles) dfree(t);
-  p->d_pair_tiles.clear();
-  p->n_pair_tiles.clear();
-  p->pair_first.clear();
-  p->nrot = 2;
-  dfree(p->d_pair_flags);
-  p->d_pair_flags = nullptr;
-  dfree(p->d_pair_ctr);
-  p->d_pair_ctr = nullptr;
   p->n_fwin = 0;
   p->fused_J = 0;
   for (Plan::ScanLevel& lv : p->scan) dfree(lv.d_tiles);
@@ -493,7 +481,7 @@ Layout layout(const Plan& p) {
   if (saves_states(p)) L.nV = std::max(p.maxN + 1, 1);
   else if (recomputes(p)) L.nV = 2 + p.n_ck + std::max(0, p.ck_seg - 3);   // + segment buffers
   else if (scans(p)) L.nV = 1;                                               // in place
-  else L.nV = p.nrot;                                                        // 2, or 3 (pairs)
+  else L.nV = 2;
   size_t off = (size_t)L.nV * L.buf_stride;
   if (save) {
     const size_t m = p.d.m, pp = p.d.p, q = p.d.q, ns = p.d.nsys;
@@ -647,16 +635,8 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
     CK(launch_stage0(*p, u, V.hi(out_buf(0)), V.lo(out_buf(0)), st), "first stage");
   for (int k = p->fused_J + 1; k <= p->maxN; ++k) {
     const int in = in_buf(k), out = out_buf(k);
-    // stages k and k + 1 in one launch (timed as stage k)
-    const bool pair = k < (int)p->pair_first.size() && p->pair_first[k];
-    if (timing && (p->n_tiles[k] > 0 || pair)) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
-    if (pair) {
-      const int out2 = out_buf(k + 1);
-      CK(launch_stage_pair_tc(*p, k, V.hi(in), V.lo(in), V.hi(out), V.lo(out), V.hi(out2),
-                              V.lo(out2), static_cast<const float*>(u), static_cast<float*>(y),
-                              st),
-         "stage pair (tensor core)");
-    } else if (p->d.precision == CASCADE_FP64) {
+    if (timing && p->n_tiles[k] > 0) CK(cudaEventRecord(p->ev[2 * p->n_ev], st), "event");
+    if (p->d.precision == CASCADE_FP64) {
       CK(launch_stage_f64(*p, k, static_cast<const double*>(V.hi(in)),
                           static_cast<double*>(V.hi(out)), st),
          "stage (fp64)");
@@ -666,12 +646,11 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
                          ptc ? U.hi(0) : nullptr, ptc ? U.lo(0) : nullptr),
          "stage (tensor core)");
     }
-    if (timing && (p->n_tiles[k] > 0 || pair)) {
+    if (timing && p->n_tiles[k] > 0) {
       CK(cudaEventRecord(p->ev[2 * p->n_ev + 1], st), "event");
       p->ev_k.push_back(k);
       p->n_ev++;
     }
-    if (pair) ++k;
   }
   if (ptc)
     CK(launch_proj_tc_output(*p, U, static_cast<float*>(y), V, p->rows, st), "output projection");
@@ -1540,33 +1519,6 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     p->ck_seg = 0;
     p->n_ck = 0;
   }
-  // Stages 1 .. FJ in one pass over windows of 128 steps with the states on chip
-  // (stage_fused.cu), for forward-only §3 plans with p = 1 at m = 128 or 256
-  // whose sequences all run past stage FJ (none forms its output there).
-  const int FJ = 3;
-  bool fused_ok = fused_stages_supported(*p) && !scans(*p) &&
-                  !(p->d.flags & (CASCADE_FLAG_SAVE_STATES | CASCADE_FLAG_RECOMPUTE |
-                                  CASCADE_FLAG_NO_FUSED_STAGES));
-  {
-    bool any = false;
-    for (int i = 0; i < nseq && fused_ok; ++i) {
-      if (h_offsets[i + 1] == h_offsets[i]) continue;
-      any = true;
-      fused_ok = p->seq_N[i] >= FJ + 1;
-    }
-    fused_ok = fused_ok && any;
-  }
-  // Stage pairs: stages k and k + 1 of the §3 schedule in one launch, for
-  // forward-only BF16-pair plans whose tiles span all m columns (m <= 256) and
-  // whose sequences are whole tiles long.  The middle states still go through
-  // memory; the pair's gain is that stage k + 1 reads them while they are in L2.
-  const int kfirst = fused_ok ? FJ + 1 : (p->fuse_first ? 2 : 1);
-  bool pairs_ok = !(p->d.flags & CASCADE_FLAG_NO_STAGE_PAIRS) && !scans(*p) && !save &&
-                  p->d.precision == CASCADE_BF16_SPLIT &&
-                  block_n(p->d.m, p->d.precision) == p->d.m && maxN >= kfirst + 1;
-  for (int i = 0; i < nseq && pairs_ok; ++i)
-    pairs_ok = (h_offsets[i + 1] - h_offsets[i]) % BM == 0;
-  p->nrot = pairs_ok ? 3 : 2;
   for (Tile& t : all) t.fbuf = fwd_buf(*p, t.flags + 1);
   p->all_fbuf = all.empty() ? -1 : all[0].fbuf;
   for (const Tile& t : all)
@@ -1582,14 +1534,11 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     for (int k = 1; k <= N && !scans(*p); ++k) {   // stage schedule (§3)
       const bool fused = fused_last && k == N;
       if (fused) p->stage_fused[k] = 1;
-      // rows below 2^(k - nrot + 1) are unchanged since stage k - nrot + 1 last
-      // wrote this stage's output buffer (nrot buffers rotate)
-      const int64_t final_below = int64_t(1) << std::max(k - p->nrot + 1, 0);
+      const int64_t prev_shift = int64_t(1) << (k - 1);
       for (int64_t t = 0; t < L; t += BM) {
-        // Rotating buffers: rows below final_below already hold their final value in
-        // the output buffer.  Kept stage outputs or checkpoints: every stage writes
-        // every row.
-        if (!save && !fused && k >= p->nrot && t + BM <= final_below) continue;
+        // Ping-pong buffers: rows below 2^(k-1) already hold their final value in the
+        // output buffer.  Kept stage outputs or checkpoints: every stage writes every row.
+        if (!save && !fused && k >= 2 && t + BM <= prev_shift) continue;
         p->h_tiles[k].push_back(Tile{h_offsets[i], (int32_t)t, (int32_t)L, sys,
                                      fused ? (int32_t)TILE_FINAL_FUSED : 0, 0, 0});
       }
@@ -1615,10 +1564,21 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
   }
   CK(upload(t0s, &p->d_stage0_tiles), "upload first-stage schedule");
   p->n_stage0_tiles = (int)t0s.size();
-  // the fused first stages' windows (128 steps at a stride of 128 - H)
+  // Stages 1 .. 3 in one pass over windows of 128 steps with the states on chip
+  // (stage_fused.cu), for forward-only §3 plans with p = 1 at m = 128 or 256
+  // whose sequences all run past stage 3 (none forms its output there).
   {
-    const int J = FJ, H = (2 << J) - 2;
-    if (fused_ok) {
+    const int J = 3, H = (2 << J) - 2;
+    bool ok = fused_stages_supported(*p) && !scans(*p) &&
+              !(p->d.flags & (CASCADE_FLAG_SAVE_STATES | CASCADE_FLAG_RECOMPUTE |
+                              CASCADE_FLAG_NO_FUSED_STAGES));
+    bool any = false;
+    for (int i = 0; i < nseq && ok; ++i) {
+      if (h_offsets[i + 1] == h_offsets[i]) continue;
+      any = true;
+      ok = p->seq_N[i] >= J + 1;
+    }
+    if (ok && any) {
       std::vector<FusedWindow> fw;
       for (int i = 0; i < nseq; ++i) {
         const int64_t L = h_offsets[i + 1] - h_offsets[i];
@@ -1632,91 +1592,6 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
          "upload fused windows");
       p->n_fwin = (int)fw.size();
       p->fused_J = J;
-    }
-  }
-  // Stage pairs (k, k + 1) from the first stage that runs as a launch of its own
-  // (not with the output on the tensor cores, whose tiles a block takes whole).
-  p->pair_first.assign(std::max(maxN + 2, 1), 0);
-  p->d_pair_tiles.assign(std::max(maxN + 2, 1), nullptr);
-  p->n_pair_tiles.assign(std::max(maxN + 2, 1), 0);
-  if (pairs_ok) {
-    // Each list interleaves the two stages' tiles.  A block takes positions b,
-    // b + G, ... (G = grid).  A second-stage tile waits only for first-stage
-    // tiles placed before it, and a block stores its own tiles without waiting
-    // for other blocks, so waits cannot close a cycle; the lag (the items a
-    // block's pipeline may have begun, times G, plus half a grid) places each
-    // second-stage tile far enough behind the tiles it reads that they are
-    // normally published by the time it is reached.  Within each run of G
-    // positions one half prefers first-stage tiles and the other second-stage
-    // ones, the halves swapping from run to run, so that every block gets both
-    // stages' tiles in turn (a plain alternation would give each block one
-    // stage only, G being even).
-    const int nch = p->d.m / 32;                      // column chunks per tile
-    const int ahead = (8 + nch - 1) / nch;            // items within 8 chunks or stages
-    size_t max_len = 0;
-    std::vector<std::vector<Tile>> lists(p->pair_first.size());
-    for (int k = kfirst; k + 1 <= maxN; ++k) {
-      const std::vector<Tile>& K1 = p->h_tiles[k];
-      const std::vector<Tile>& K2 = p->h_tiles[k + 1];
-      if (K1.empty() || K2.empty() ||
-          (p->fuse_output_mma && (p->stage_fused[k] || p->stage_fused[k + 1])))
-        continue;
-      const int64_t G = std::min<int64_t>(p->num_sms, (int64_t)(K1.size() + K2.size()));
-      const int64_t lag = (int64_t)(K1.size() + K2.size()) <= p->num_sms
-                              ? 0
-                              : G * (ahead + 1) + G / 2 + 1;
-      const int64_t s2 = int64_t(2) << k;             // the second stage's shift
-      std::unordered_map<int64_t, int> idx;            // packed first row -> index in K1
-      for (int i = 0; i < (int)K1.size(); ++i) idx[K1[i].seq_row0 + K1[i].t0] = i;
-      auto find = [&](const Tile& t, int64_t t0) {
-        if (t0 < 0) return -1;
-        auto f = idx.find(t.seq_row0 + t0 / BM * BM);
-        return f == idx.end() ? -1 : f->second;
-      };
-      std::vector<int64_t> pos1(K1.size(), -1);
-      std::vector<Tile>& out = lists[k];
-      size_t i1 = 0, i2 = 0;
-      while (i1 < K1.size() || i2 < K2.size()) {
-        const int64_t here = (int64_t)out.size();
-        const bool first_half = (here % G) < G / 2;
-        const bool prefer_first = first_half != (((here / G) & 1) != 0);
-        if (i2 < K2.size() && (!prefer_first || i1 == K1.size())) {
-          // the second stage's residual rows [t, t + BM) and source rows from t - 2s
-          const Tile& t2 = K2[i2];
-          const int r = find(t2, t2.t0), a = find(t2, t2.t0 - s2);
-          const int64_t pr = r >= 0 ? pos1[r] : -1, pa = a >= 0 ? pos1[a] : -1;
-          const bool emitted = (r < 0 || pr >= 0) && (a < 0 || pa >= 0);
-          // (once every first-stage tile is placed the rest follow at once)
-          if (emitted && (i1 == K1.size() || here - std::max(pr, pa) > lag)) {
-            Tile t = t2;
-            t.flags |= TILE_SECOND;
-            t.fbuf = (int32_t)pr;
-            t.dep = (int32_t)pa;
-            out.push_back(t);
-            ++i2;
-            continue;
-          }
-        }
-        Tile t = K1[i1];
-        t.fbuf = -1;
-        t.dep = -1;
-        pos1[i1++] = here;
-        out.push_back(t);
-      }
-      p->pair_first[k] = 1;
-      max_len = std::max(max_len, out.size());
-      ++k;                                             // stage k + 1 is this pair's
-    }
-    for (size_t k = 0; k < lists.size(); ++k) {
-      if (!p->pair_first[k]) continue;
-      CK(upload(lists[k], &p->d_pair_tiles[k]), "upload stage pair schedule");
-      p->n_pair_tiles[k] = (int32_t)lists[k].size();
-    }
-    if (max_len > 0) {
-      CK(cudaMalloc(&p->d_pair_flags, max_len * sizeof(int32_t)), "alloc stage pair flags");
-      CK(cudaMemset(p->d_pair_flags, 0, max_len * sizeof(int32_t)), "clear stage pair flags");
-      CK(cudaMalloc(&p->d_pair_ctr, 2 * sizeof(uint32_t)), "alloc stage pair counter");
-      CK(cudaMemset(p->d_pair_ctr, 0, 2 * sizeof(uint32_t)), "clear stage pair counter");
     }
   }
   // output tiles grouped by the buffer holding their final states (the
@@ -1851,15 +1726,6 @@ cascade_status_t cascade_get_fused_stages(cascade_plan_t plan, int32_t* h_J) {
   if (!p || !h_J) return fail(p, CASCADE_ERR_INVALID_ARG, "NULL argument");
   if (!p->have_batch) return fail(p, CASCADE_ERR_STATE, "no batch set");
   *h_J = p->fused_J;
-  return CASCADE_OK;
-}
-
-cascade_status_t cascade_get_stage_pairs(cascade_plan_t plan, int32_t* h_first, int32_t n) {
-  Plan* p = plan;
-  if (!p || (!h_first && n > 0) || n < 0) return fail(p, CASCADE_ERR_INVALID_ARG, "bad argument");
-  if (!p->have_batch) return fail(p, CASCADE_ERR_STATE, "no batch set");
-  for (int k = 0; k < n; ++k)
-    h_first[k] = (k < (int)p->pair_first.size() && p->pair_first[k]) ? 1 : 0;
   return CASCADE_OK;
 }
 

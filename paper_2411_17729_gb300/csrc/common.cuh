@@ -28,16 +28,11 @@ struct Tile {
   int32_t len;        // sequence length L_i
   int32_t sys;        // system index
   int32_t flags;      // TILE_FINAL_FUSED: last stage with y = Cv + Du fused
-  int32_t fbuf;       // workspace state buffer that holds the sequence's final states;
-                      // in a stage pair's list (TILE_SECOND): the list position of the
-                      // first stage's tile whose output rows this tile's residual is (-1: none)
-  int32_t dep;        // stage pair, TILE_SECOND: the list position of the first stage's
-                      // tile holding the first of this tile's source rows (-1: none)
+  int32_t fbuf;       // workspace state buffer that holds the sequence's final states
+  int32_t pad1;
 };
 static_assert(sizeof(Tile) == 32, "Tile is 32 bytes");
-// TILE_SECOND: a tile of the second stage of a stage pair (shift 2s, reads the
-// first stage's output).
-enum { TILE_FINAL_FUSED = 1, TILE_SECOND = 2 };
+enum { TILE_FINAL_FUSED = 1 };
 
 // Window of the fused first stages (stage_fused.cu): 128 time steps of one
 // sequence from step r0 on (r0 may be negative: steps before the sequence are
@@ -94,11 +89,6 @@ struct StageArgs {
   int32_t* err;           // device error word
   int32_t* diag;          // where the first bounded wait gave up (5 words) or null
   unsigned long long timeout_ns;
-  // stage pair (stages k and k + 1 in one launch): per list position, the launch
-  // count at which that first-stage tile's output rows were stored; pair_ctr[0]
-  // counts the pair launches, pair_ctr[1] the blocks that finished this one
-  int32_t* pair_flags;
-  uint32_t* pair_ctr;
 };
 
 // ---------------------------------------------------------------- device side
@@ -203,16 +193,6 @@ struct Plan {
   int fused_J = 0;
   FusedWindow* d_fwin = nullptr;
   int n_fwin = 0;
-  // stage pairs (set per batch): pair_first[k] = 1 when stages k and k + 1 of
-  // the §3 schedule run as one launch over the list d_pair_tiles[k] (the two
-  // stages' tiles interleaved, the second a lag behind the first); the forward
-  // then rotates its states through three buffers (nrot) instead of two
-  std::vector<char> pair_first;
-  std::vector<Tile*> d_pair_tiles;
-  std::vector<int32_t> n_pair_tiles;
-  int nrot = 2;
-  int32_t* d_pair_flags = nullptr;   // one word per list position (largest list)
-  uint32_t* d_pair_ctr = nullptr;    // launch count, finished blocks
   // stage 1 forms v^(1) = Bbar u_l + Abar Bbar u_(l-1) on chip; the first-stage
   // kernel does not run (set per batch)
   bool fuse_first = false;
@@ -304,11 +284,6 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
                             void* vout_hi, void* vout_lo, const float* u, float* y,
                             cudaStream_t st, bool reverse = false, const void* u_hi = nullptr,
                             const void* u_lo = nullptr);
-// Stages k and k + 1 in one launch over the list d_pair_tiles[k]: stage k from
-// (vin) into (vmid), stage k + 1 from (vmid) into (vout).
-cudaError_t launch_stage_pair_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
-                                 void* vmid_hi, void* vmid_lo, void* vout_hi, void* vout_lo,
-                                 const float* u, float* y, cudaStream_t st);
 // In-place stage k over rows S apart (the work-efficient schedule); the state
 // planes hold rows_cap rows, a multiple of S.  Tiles flagged TILE_FINAL_FUSED
 // also form y = C v + D u for their rows (u, y may be null otherwise).

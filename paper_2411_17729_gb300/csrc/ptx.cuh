@@ -71,26 +71,6 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
       "r"(smem_addr(src)), "r"(x), "r"(y)
       : "memory");
 }
-// The same store with an L2 eviction priority (a policy from l2_policy_*).
-__device__ __forceinline__ void tma_store_2d_hint(const CUtensorMap* map, const void* src, int x,
-                                                  int y, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint"
-      " [%0, {%2, %3}], [%1], %4;" ::"l"(reinterpret_cast<uint64_t>(map)),
-      "r"(smem_addr(src)), "r"(x), "r"(y), "l"(policy)
-      : "memory");
-}
-// L2 policies: lines kept in preference to others, or given up first.
-__device__ __forceinline__ uint64_t l2_policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
 // 3-D variants: box (x, 1, z) of a map whose middle dimension is the row
 // offset inside a group of S rows and whose outer dimension is the group, so
 // that consecutive z address rows S apart.
@@ -124,10 +104,6 @@ __device__ __forceinline__ void bulk_wait_read0() {
 // Wait until every committed bulk store of this thread is complete (writes performed).
 __device__ __forceinline__ void bulk_wait0() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
-// Wait until every committed bulk store but the two newest is complete.
-__device__ __forceinline__ void bulk_wait2() {
-  asm volatile("cp.async.bulk.wait_group 2;" ::: "memory");
 }
 // Programmatic dependent launch: let the next kernel of the stream start its
 // prologue on free SMs, and wait (in that kernel) until the previous one has
@@ -182,33 +158,6 @@ __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
 // (tensor core reads of operands, TMA stores).
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// Orders this thread's global-memory accesses through the generic proxy with
-// its accesses through the async proxy (TMA loads and stores).
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-__device__ __forceinline__ int32_t ld_acquire_gpu(const int32_t* p) {
-  int32_t v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_gpu(int32_t* p, int32_t v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-// Bounded wait until another block has published `want` in *flag (false when
-// the limit passed or the block is aborting).
-__device__ __forceinline__ bool flag_wait(const int32_t* flag, int32_t want,
-                                          unsigned long long limit_ns,
-                                          volatile int* abort_flag) {
-  if (ld_acquire_gpu(flag) == want) return true;
-  const unsigned long long t0 = globaltimer_ns();
-  while (true) {
-    __nanosleep(64);
-    if (ld_acquire_gpu(flag) == want) return true;
-    if (abort_flag && *abort_flag) return false;
-    if (globaltimer_ns() - t0 > limit_ns) return false;
-  }
 }
 
 // ------------------------------------------------------------------- tcgen05

@@ -67,11 +67,9 @@ constexpr uint32_t SLOT_BYTES = 2 * PLANE_TILE;
 
 // Tensor maps of the output on the tensor cores (YM): C and D (hi, lo) planes,
 // [nsys q, m] and [nsys q, p], boxes of 32 K entries x q rows; u (hi, lo) planes
-// [rows, p], boxes of 32 x 128 rows.  A stage pair (PAIR) uses mhi, mlo: the
-// (hi, lo) planes of the middle states v^(k+1), which its first stage writes and
-// its second reads.
+// [rows, p], boxes of 32 x 128 rows.
 struct YMaps {
-  CUtensorMap chi, clo, uhi, ulo, dhi, dlo, mhi, mlo;
+  CUtensorMap chi, clo, uhi, ulo, dhi, dlo;
 };
 
 template <int ELEM>
@@ -208,8 +206,6 @@ struct Item {
   Tile t;
   int nb;         // column block of the tile
   int n0;
-  int shift;      // 2^k, or 2^(k+1) for the second stage of a pair
-  bool sec;       // (PAIR) a tile of stage k + 1: reads the middle states' rows
   bool copy;      // every source row precedes the sequence: no MMA, output = residual
   bool fused;     // last stage with y = C v + D u formed in the epilogue
   bool ragged;    // last tile of a sequence: rows past its end must not be written
@@ -230,42 +226,20 @@ __device__ __forceinline__ int next_item(const StageArgs& a, int w) {
   return (w % a.nblocks != a.nblocks - 1) ? w + 1 : w + 1 + ((int)gridDim.x - 1) * a.nblocks;
 }
 
-template <int QMAX, int YM = 0, int PAIR = 0>
+template <int QMAX, int YM = 0>
 __device__ __forceinline__ Item load_item(const StageArgs& a, int w) {
   Item it;
   it.t = a.tiles[w / a.nblocks];
   it.nb = w % a.nblocks;
   it.n0 = it.nb * a.BN;
-  it.sec = PAIR && (it.t.flags & TILE_SECOND);
-  it.shift = it.sec ? 2 * a.shift : a.shift;
   // every source row lies outside the sequence: before its start (forward
   // stages) or past its end (adjoint stages, source l + s)
   it.copy = a.S ? false
-                 : a.reverse ? (it.t.t0 + it.shift >= it.t.len) : (it.t.t0 + BM <= it.shift);
+                 : a.reverse ? (it.t.t0 + a.shift >= it.t.len) : (it.t.t0 + BM <= a.shift);
   it.fused = (QMAX > 0 || YM) && (it.t.flags & TILE_FINAL_FUSED);
   it.ragged = it.t.t0 + BM > it.t.len;
   it.acc = !it.copy || (YM && it.fused);
   return it;
-}
-
-// Stage pair: a tile of the second stage reads rows of the middle states that
-// tiles of the first stage (in any block) store; wait until those blocks have
-// published them (list positions t.fbuf and t.dep, -1: nothing to wait for),
-// then order the TMA reads that follow after what was observed.
-__device__ __forceinline__ bool pair_sources_ready(const StageArgs& a, const Tile& t, int32_t want,
-                                                   unsigned long long limit,
-                                                   volatile int* abort_flag) {
-  if (t.fbuf >= 0 && !ptx::flag_wait(a.pair_flags + t.fbuf, want, limit, abort_flag)) return false;
-  if (t.dep >= 0 && !ptx::flag_wait(a.pair_flags + t.dep, want, limit, abort_flag)) return false;
-  ptx::fence_proxy_async_global();
-  return true;
-}
-
-// The same check without waiting (one poll of each word).
-__device__ __forceinline__ bool pair_sources_published(const StageArgs& a, const Tile& t,
-                                                       int32_t want) {
-  return (t.fbuf < 0 || ptx::ld_acquire_gpu(a.pair_flags + t.fbuf) == want) &&
-         (t.dep < 0 || ptx::ld_acquire_gpu(a.pair_flags + t.dep) == want);
 }
 
 // Column chunks the staging ring carries for an item: the residual's, then,
@@ -299,23 +273,7 @@ __device__ __forceinline__ int item_chunks(const StageArgs& a, const Item& it, i
 // group 0 reads the tile's y from there and, when m spans several column
 // blocks (taken one after the other by the same block), adds them in order in
 // its rows of y.
-// PAIR = 1 (stages k and k + 1 in one launch, BF16 pairs, one column block):
-// the tile list interleaves stage k's tiles (vin -> the middle states, maps
-// ym.mhi/mlo) and stage k + 1's (flag TILE_SECOND, shift 2s: the middle states
-// -> vout), each second-stage tile some positions after the first-stage tiles
-// it reads.  Blocks take list positions b, b + grid, ... as usual.  The ring
-// manager publishes each first-stage tile (pair_flags[position] = this launch's
-// count) once its stores are complete; the producer and the ring manager wait
-// for the tiles a second-stage tile reads before their TMA loads of its rows.
-// Those tiles sit at earlier list positions, and the ring manager defers (does
-// not wait for) a second-stage tile's residual while it still has earlier
-// tiles of its own to store, so a block's stores never wait for another
-// block and the smallest unpublished tile is always being worked on: no chain
-// of waits closes a cycle.  The blocks of one launch must all be resident at
-// once (one per SM, at most the SM count).  The middle states are stored and
-// read back like any stage output: the results equal those of two launches
-// bit for bit.
-template <int ELEM, int QMAX, int G, int GEN, int YM, int PAIR>
+template <int ELEM, int QMAX, int G, int GEN, int YM>
 __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHREADS + 32 : NTHREADS, 1)
     stage_tc_kernel(const __grid_constant__ CUtensorMap tm_vhi,
                     const __grid_constant__ CUtensorMap tm_vlo,
@@ -403,10 +361,6 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
     ptx::prefetch_tmap(&tm_plo);
     ptx::prefetch_tmap(&tm_ohi);
     ptx::prefetch_tmap(&tm_olo);
-    if (PAIR) {
-      ptx::prefetch_tmap(&ym.mhi);
-      ptx::prefetch_tmap(&ym.mlo);
-    }
     if (YM) {
       ptx::prefetch_tmap(&ym.chi);
       ptx::prefetch_tmap(&ym.clo);
@@ -438,21 +392,16 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
       int issued_parity[8];
       for (int s = 0; s < 8; ++s) issued_parity[s] = -1;
       bool waited = false;
-      int32_t want = 0;                 // (PAIR) the value a published tile carries
       for (int w = first_item<YM>(args); w < nwork && !*abort_flag; w = next_item<YM>(args, w)) {
-        const Item it = load_item<QMAX, YM, PAIR>(args, w);
+        const Item it = load_item<QMAX, YM>(args, w);
         if (it.copy) continue;                                   // no operands
         // source rows l - s (forward) or l + s (adjoint); may fall outside the
         // tensor (zero fill) or in a neighbouring sequence (zeroed below)
-        const int src_row =
-            (int)(it.t.seq_row0 + it.t.t0 + (args.reverse ? it.shift : -it.shift));
+        const int src_row = (int)(it.t.seq_row0 + it.t.t0 + (args.reverse ? shift : -shift));
         // strided tiles: the same row as (row in group, group) of the 3-D map
         const int src_y = args.S ? src_row % args.S : src_row;
         const int src_z = args.S ? src_row / args.S : 0;
-        const int prow = (it.t.sys * args.kmax1 + args.k + (it.sec ? 1 : 0)) * m + it.n0;
-        // (PAIR) the second stage reads the middle states
-        const CUtensorMap* mvh = (PAIR && it.sec) ? &ym.mhi : &tm_vhi;
-        const CUtensorMap* mvl = (PAIR && it.sec) ? &ym.mlo : &tm_vlo;
+        const int prow = (it.t.sys * args.kmax1 + args.k) * m + it.n0;
         int c0 = 0;
         if (!waited) {
           // The powers do not depend on the previous launch: the first stages'
@@ -473,13 +422,6 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
           }
           ptx::griddep_wait();
           waited = true;
-          if (PAIR) {
-            want = ptx::ld_acquire_gpu(reinterpret_cast<const int32_t*>(args.pair_ctr)) + 1;
-            // (on a timeout the rows are still requested: every armed stage's
-            // barrier expects them, and the block is leaving anyway)
-            if (it.sec && !pair_sources_ready(args, it.t, want, limit, abort_flag))
-              raise_timeout(args, abort_flag, 18, w, 0);
-          }
           // every armed stage gets its state rows (its barrier expects them)
           for (int c = 0; c < armed && GEN != 1; ++c) {
             uint8_t* sa_hi = bufs + (size_t)c * stage_bytes;
@@ -487,17 +429,14 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
               ptx::tma_load_3d(sa_hi, &tm_vhi, &full[c], c * KC, src_y, src_z);
               ptx::tma_load_3d(sa_hi + a_bytes, &tm_vlo, &full[c], c * KC, src_y, src_z);
             } else {
-              ptx::tma_load_2d(sa_hi, mvh, &full[c], c * KC, src_row);
-              ptx::tma_load_2d(sa_hi + a_bytes, mvl, &full[c], c * KC, src_row);
+              ptx::tma_load_2d(sa_hi, &tm_vhi, &full[c], c * KC, src_row);
+              ptx::tma_load_2d(sa_hi + a_bytes, &tm_vlo, &full[c], c * KC, src_row);
             }
           }
           if (armed < pre) break;
           stage = pre;
           if (stage == S) { stage = 0; phase ^= 1u; }
           c0 = pre;
-        } else if (PAIR && it.sec && !pair_sources_ready(args, it.t, want, limit, abort_flag)) {
-          raise_timeout(args, abort_flag, 18, w, 1);
-          break;
         }
         for (int c = c0; c < nkc; ++c) {
           if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, limit, abort_flag)) {
@@ -515,8 +454,8 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
             ptx::tma_load_3d(sa_hi, &tm_vhi, &full[stage], c * KC, src_y, src_z);
             ptx::tma_load_3d(sa_lo, &tm_vlo, &full[stage], c * KC, src_y, src_z);
           } else {
-            ptx::tma_load_2d(sa_hi, mvh, &full[stage], c * KC, src_row);
-            ptx::tma_load_2d(sa_lo, mvl, &full[stage], c * KC, src_row);
+            ptx::tma_load_2d(sa_hi, &tm_vhi, &full[stage], c * KC, src_row);
+            ptx::tma_load_2d(sa_lo, &tm_vlo, &full[stage], c * KC, src_row);
           }
           ptx::tma_load_2d(sb_hi, &tm_phi, &full[stage], c * KC, prow);
           ptx::tma_load_2d(sb_lo, &tm_plo, &full[stage], c * KC, prow);
@@ -537,7 +476,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
     uint32_t phase = 0;
     int acc_i = 0;
     for (int w = first_item<YM>(args); w < nwork && !*abort_flag; w = next_item<YM>(args, w)) {
-      const Item it = load_item<QMAX, YM, PAIR>(args, w);
+      const Item it = load_item<QMAX, YM>(args, w);
       if (!it.acc) continue;
       const int abuf = acc_i & 1;
       const uint32_t aph = (uint32_t)((acc_i >> 1) & 1);
@@ -549,8 +488,8 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
       ptx::tc_fence_after();
       // tile rows [z0, z1) whose source lies outside the sequence read zero
       // (strided tiles: every source lies inside its sequence)
-      const int z0 = args.reverse ? max(0, it.t.len - it.t.t0 - it.shift) : 0;
-      const int z1 = args.S ? 0 : args.reverse ? BM : min(BM, it.shift - it.t.t0);
+      const int z0 = args.reverse ? max(0, it.t.len - it.t.t0 - shift) : 0;
+      const int z1 = args.S ? 0 : args.reverse ? BM : min(BM, shift - it.t.t0);
       const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * ACC);
       const uint32_t c_tmem = d_tmem + (SEP ? (uint32_t)BN : 0u);   // correction accumulator
       bool ok = true;
@@ -613,28 +552,11 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
     // ------------------------------------------------------------ ring manager
     if (lane == 0) {
       ptx::griddep_wait();             // the residual rows are the previous launch's output
-      // (PAIR) the value this launch publishes first-stage tiles with
-      const int32_t want =
-          PAIR ? ptx::ld_acquire_gpu(reinterpret_cast<const int32_t*>(args.pair_ctr)) + 1 : 0;
       int lw = first_item<YM>(args), lcc = 0;   // load cursor, RING chunks ahead of the epilogue
       uint32_t issued = 0;
-      // Issue the next chunk's load into `slot`.  (PAIR) A second-stage tile's
-      // residual is the middle states' rows, which other blocks store: while
-      // this block still has earlier tiles to store (block = false) the load
-      // is only issued once they are published, otherwise deferred (returns
-      // false), so that this block's own stores never wait for another block.
-      auto issue_next = [&](int slot, bool block) -> bool {
-        if (lw >= nwork) return true;
-        const Item li = load_item<QMAX, YM, PAIR>(args, lw);
-        if (PAIR && li.sec && lcc == 0) {
-          if (!block) {
-            if (!pair_sources_published(args, li.t, want)) return false;
-            ptx::fence_proxy_async_global();
-          } else if (!pair_sources_ready(args, li.t, want, limit, abort_flag)) {
-            raise_timeout(args, abort_flag, 19, lw, slot);
-            return true;
-          }
-        }
+      auto issue_next = [&](int slot) {
+        if (lw >= nwork) return;
+        const Item li = load_item<QMAX, YM>(args, lw);
         const Tile& lt = li.t;
         const int lnck = item_chunks<YM>(args, li, nch);
         const int x = li.n0 + lcc * CW;
@@ -660,7 +582,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
           }
           ++issued;
           if (++lcc == lnck) { lcc = 0; lw = next_item<YM>(args, lw); }
-          return true;
+          return;
         }
         if (GEN != 0) {
           ptx::mbar_arrive(&res_full[slot]);   // the epilogue forms the residual from u
@@ -671,41 +593,14 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
             ptx::tma_load_3d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow % args.S,
                              yrow / args.S);
           } else {
-            ptx::tma_load_2d(sh, (PAIR && li.sec) ? &ym.mhi : &tm_vhi, &res_full[slot], x, yrow);
-            ptx::tma_load_2d(sh + PLANE_TILE, (PAIR && li.sec) ? &ym.mlo : &tm_vlo,
-                             &res_full[slot], x, yrow);
+            ptx::tma_load_2d(sh, &tm_vhi, &res_full[slot], x, yrow);
+            ptx::tma_load_2d(sh + PLANE_TILE, &tm_vlo, &res_full[slot], x, yrow);
           }
         }
         ++issued;
         if (++lcc == lnck) { lcc = 0; lw = next_item<YM>(args, lw); }
-        return true;
       };
-      // slots waiting for their next load, in load order
-      int fq[RING_MAX] = {}, fh = 0, fn = 0;
-      auto refill = [&](bool block) {
-        while (fn > 0 && issue_next(fq[fh], block)) {
-          fh = (fh + 1) % RING_MAX;
-          --fn;
-        }
-      };
-      for (int s = 0; s < RING; ++s) fq[fn++] = s;
-      refill(false);
-      // (PAIR) the first-stage tile whose stores were committed last and are not
-      // yet published, and the bulk groups committed since: it is published once
-      // two newer groups are (its stores are then complete without waiting for
-      // the newest), and always before this thread waits for another block
-      int pub_w = -1;
-      uint32_t pub_after = 0;
-      const uint64_t pol_last = PAIR ? ptx::l2_policy_evict_last() : 0;
-      const uint64_t pol_first = PAIR ? ptx::l2_policy_evict_first() : 0;
-      auto publish = [&](bool now) {
-        if (!PAIR || pub_w < 0) return;
-        if (now || pub_after < 2) ptx::bulk_wait0();
-        else ptx::bulk_wait2();
-        ptx::fence_proxy_async_global();
-        ptx::st_release_gpu(args.pair_flags + pub_w, want);
-        pub_w = -1;
-      };
+      for (int s = 0; s < RING; ++s) issue_next(s);
       uint32_t g = 0;                  // chunks retired
       bool alive = true;
       // A slot is refilled one chunk after its store was issued, so that the
@@ -713,25 +608,13 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
       // slot is reloaded (bulk wait with one group allowed in flight).
       int pend_slot = -1;
       for (int w = first_item<YM>(args); w < nwork && alive; w = next_item<YM>(args, w)) {
-        const Item it = load_item<QMAX, YM, PAIR>(args, w);
+        const Item it = load_item<QMAX, YM>(args, w);
         const bool tma_out = (!it.fused || args.keep_v) && !it.ragged;
         const int ytile = (int)(it.t.seq_row0 + it.t.t0);
-        // (PAIR) the first stage stores the middle states
-        const CUtensorMap* moh = (PAIR && !it.sec) ? &ym.mhi : &tm_ohi;
-        const CUtensorMap* mol = (PAIR && !it.sec) ? &ym.mlo : &tm_olo;
         const int nck = item_chunks<YM>(args, it, nch);
         for (int cc = 0; cc < nck; ++cc, ++g) {
           const int slot = (int)(g % RING);
           uint8_t* sh = ring + (size_t)slot * slot_bytes;
-          // (PAIR) this chunk's load, if it was deferred: every earlier chunk is
-          // retired and every earlier first-stage tile published, so waiting
-          // for other blocks here cannot close a cycle
-          if (PAIR && fn > 0 && issued <= g) publish(true);
-          while (PAIR && fn > 0 && issued <= g && !*abort_flag) {
-            issue_next(fq[fh], true);
-            fh = (fh + 1) % RING_MAX;
-            --fn;
-          }
           // Every chunk passes through both barriers of its slot, also a pure
           // copy that the epilogue forwards untouched: a parity wait is then
           // never more than one phase ahead of the barrier it polls.  With YM
@@ -751,42 +634,23 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
               ptx::tma_store_3d(&tm_ohi, sh, it.n0 + cc * CW, ytile % args.S, ytile / args.S);
               ptx::tma_store_3d(&tm_olo, sh + PLANE_TILE, it.n0 + cc * CW, ytile % args.S,
                                 ytile / args.S);
-            } else if (PAIR) {
-              // the middle states are read back soon (kept in L2 in preference
-              // to the streaming rows); the pair's output is not
-              const uint64_t pol = it.sec ? pol_first : pol_last;
-              ptx::tma_store_2d_hint(moh, sh, it.n0 + cc * CW, ytile, pol);
-              ptx::tma_store_2d_hint(mol, sh + PLANE_TILE, it.n0 + cc * CW, ytile, pol);
             } else {
-              ptx::tma_store_2d(moh, sh, it.n0 + cc * CW, ytile);
-              ptx::tma_store_2d(mol, sh + PLANE_TILE, it.n0 + cc * CW, ytile);
+              ptx::tma_store_2d(&tm_ohi, sh, it.n0 + cc * CW, ytile);
+              ptx::tma_store_2d(&tm_olo, sh + PLANE_TILE, it.n0 + cc * CW, ytile);
             }
             ptx::bulk_commit();
-            if (PAIR) {
-              if (pub_w >= 0 && ++pub_after >= 2) publish(false);
-              if (!it.sec && cc == nch - 1) {
-                publish(true);                 // (an older one, should any be left)
-                pub_w = w / args.nblocks;      // the tile's last store
-                pub_after = 0;
-              }
-            }
-          } else if (PAIR) {
-            publish(true);                     // no newer stores to wait behind
           }
           if (pend_slot >= 0) {
             // the previous chunk's store (if any) has read its slot: all bulk
             // groups but this chunk's (the newest, when it stored) are done reading
             if (tma_out && cc < nch) ptx::bulk_wait_read1();
             else ptx::bulk_wait_read0();
-            fq[(fh + fn) % RING_MAX] = pend_slot;
-            ++fn;
-            refill(false);
+            issue_next(pend_slot);
           }
           pend_slot = slot;
         }
       }
       ptx::bulk_wait0();                // stores complete before the block exits
-      publish(true);
       // loads issued but not retired (only after an abort): let them land
       for (uint32_t h = g; h < issued; ++h)
         ptx::mbar_wait(&res_full[h % RING], (h / RING) & 1u, limit, nullptr);
@@ -806,7 +670,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
       int acc_i = 0;
       bool alive = true;
       for (int w = first_item<YM>(args); w < nwork && alive; w = next_item<YM>(args, w)) {
-        const Item it = load_item<QMAX, YM, PAIR>(args, w);
+        const Item it = load_item<QMAX, YM>(args, w);
         const int nck = item_chunks<YM>(args, it, nch);
         if (!it.fused) {
           for (int cc = 0; cc < nck; ++cc, ++g) {
@@ -875,7 +739,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
     int stage = 0;
     uint32_t phase = 0;
     for (int w = first_item<YM>(args); w < nwork; w = next_item<YM>(args, w)) {
-      const Item it = load_item<QMAX, YM, PAIR>(args, w);
+      const Item it = load_item<QMAX, YM>(args, w);
       if (it.copy) continue;
       const int src = it.t.t0 + r - shift;
       const bool live = it.t.t0 + r < it.t.len && src >= 0;
@@ -935,7 +799,7 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
     int ycnt[2] = {0, 0};                      // (YM) fused tiles seen per accumulator
     bool alive = true;                         // warp-uniform
     for (int w = first_item<YM>(args); w < nwork && alive; w = next_item<YM>(args, w)) {
-      const Item it = load_item<QMAX, YM, PAIR>(args, w);
+      const Item it = load_item<QMAX, YM>(args, w);
       const bool tma_out = (!it.fused || args.keep_v) && !it.ragged;
       const int tr = it.t.t0 + r;
       const bool valid = tr < it.t.len;
@@ -1254,22 +1118,12 @@ __global__ void __launch_bounds__(GEN == 1 ? NTHREADS + GEN_THREADS : YM ? NTHRE
   __syncthreads();
   ptx::tc_fence_after();
   if (warp == 1) ptx::tmem_dealloc(tmem_base, tmem_cols);
-  if (PAIR && threadIdx.x == 0) {
-    // the last block to finish advances the launch count (every block read it
-    // before it got here; the next pair launch reads it after this grid ends)
-    __threadfence();
-    if (atomicAdd(&args.pair_ctr[1], 1u) == gridDim.x - 1) {
-      args.pair_ctr[1] = 0u;
-      __threadfence();
-      atomicAdd(&args.pair_ctr[0], 1u);
-    }
-  }
 }
 
-template <int ELEM, int QMAX, int G, int GEN, int YM = 0, int PAIR = 0>
+template <int ELEM, int QMAX, int G, int GEN, int YM = 0>
 cudaError_t launch_variant(const CUtensorMap* maps, const YMaps& ym, const StageArgs& a, int grid,
                            size_t smem, cudaStream_t st) {
-  auto kern = stage_tc_kernel<ELEM, QMAX, G, GEN, YM, PAIR>;
+  auto kern = stage_tc_kernel<ELEM, QMAX, G, GEN, YM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // programmatic dependent launch: the prologue (barriers, TMEM, the first
@@ -1356,16 +1210,8 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
                           void* vout_hi, void* vout_lo, const float* u, float* y,
                           cudaStream_t st, bool reverse, bool even_resid = false,
                           int shape_key = -1, const void* u_hi = nullptr,
-                          const void* u_lo = nullptr, void* vmid_hi = nullptr,
-                          void* vmid_lo = nullptr) {
+                          const void* u_lo = nullptr) {
   if (ntiles == 0) return cudaSuccess;
-  // stages k and k + 1 in one launch (the middle states given)
-  const bool pair = vmid_hi != nullptr;
-  if (pair && (!vmid_lo || S != 0 || reverse || plane_elem_bytes(p.d.precision) != 2 ||
-               block_n(p.d.m, p.d.precision) != p.d.m || !p.d_pair_flags || !p.d_pair_ctr)) {
-    set_global_error("stage pair outside its supported form");
-    return cudaErrorInvalidValue;
-  }
   if (!(reverse ? p.PThi : p.Phi) || !vin_hi || !vin_lo || !vout_hi || !vout_lo) {
     set_global_error("stage launch without its power or state planes");
     return cudaErrorInvalidValue;
@@ -1432,14 +1278,13 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   const bool fuse = p.fuse_output && !reverse && y != nullptr;
   // the output on the tensor cores (BF16 pairs, §3 schedule; u as (hi, lo)
   // planes), for the stages that are some sequence's last
-  const bool ym = !pair && p.fuse_output_mma && !reverse && y != nullptr && S == 0 && k >= 0 &&
+  const bool ym = p.fuse_output_mma && !reverse && y != nullptr && S == 0 && k >= 0 &&
                   k < (int)p.stage_fused.size() && p.stage_fused[k];
   if (ym && (!u_hi || !u_lo || elem != 2 || !p.pc_hi)) {
     set_global_error("fused tensor-core output without its u or coefficient planes");
     return cudaErrorInvalidValue;
   }
-  const int gen = pair ? 0
-                  : (p.fuse_first && k == 1 && !reverse && S == 0 && u != nullptr) ? 1
+  const int gen = (p.fuse_first && k == 1 && !reverse && S == 0 && u != nullptr) ? 1
                   : (even_resid && fuse && S > 0 && u != nullptr)               ? 2
                                                                                : 0;
   a.gen = gen;
@@ -1488,21 +1333,6 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   a.err = p.err;
   a.diag = p.err + 1;
   a.timeout_ns = 2000000000ull;
-  a.pair_flags = p.d_pair_flags;
-  a.pair_ctr = p.d_pair_ctr;
-  if (pair) {
-    if (!state_map(&ymaps.mhi, vmid_hi) || !state_map(&ymaps.mlo, vmid_lo)) {
-      set_global_error("tensor map encode failed: " + err);
-      return cudaErrorInvalidValue;
-    }
-    // one chunk per epilogue step (fewer kernel variants)
-    if (cfg.group != 1) {
-      const TcConfig c1{cfg.stages, cfg.ring, 1};
-      cfg = tc_config_fits(m, BN, c1) ? c1 : tc_default(m, p.d.precision);
-      a.stages = cfg.stages;
-      a.ring = cfg.ring;
-    }
-  }
   const size_t smem = fixed_smem_bytes(a.stages, a.ring, BN >= m, ym ? q : 0) +
                       (size_t)a.stages * stage_bytes_for(BN);
   const int nwork = ntiles * a.nblocks;
@@ -1510,11 +1340,6 @@ cudaError_t stage_tc_core(const Plan& p, int k, const Tile* tiles, int ntiles, i
   const int nunits = ym ? ntiles : nwork;
   const int grid = nunits < p.num_sms ? nunits : p.num_sms;
   if (ym) return launch_variant<2, 0, 1, 0, 1>(maps, ymaps, a, grid, smem, st);
-  if (pair) {
-    if (!fuse) return launch_variant<2, 0, 1, 0, 0, 1>(maps, ymaps, a, grid, smem, st);
-    if (q == 1) return launch_variant<2, 1, 1, 0, 0, 1>(maps, ymaps, a, grid, smem, st);
-    return launch_variant<2, 4, 1, 0, 0, 1>(maps, ymaps, a, grid, smem, st);
-  }
   // the fused output applies to forward stages that are given y (the stages
   // the backward recomputes are not)
   const int G = cfg.group;
@@ -1544,15 +1369,6 @@ cudaError_t launch_stage_tc(const Plan& p, int k, const void* vin_hi, const void
   return stage_tc_core(p, k, reverse ? p.d_adj_tiles[k] : p.d_tiles[k],
                        reverse ? p.n_adj_tiles[k] : p.n_tiles[k], 0, (uint64_t)p.rows, vin_hi,
                        vin_lo, vout_hi, vout_lo, u, y, st, reverse, false, -1, u_hi, u_lo);
-}
-
-cudaError_t launch_stage_pair_tc(const Plan& p, int k, const void* vin_hi, const void* vin_lo,
-                                 void* vmid_hi, void* vmid_lo, void* vout_hi, void* vout_lo,
-                                 const float* u, float* y, cudaStream_t st) {
-  if (k < 0 || k >= (int)p.d_pair_tiles.size() || !vmid_hi) return cudaErrorInvalidValue;
-  return stage_tc_core(p, k, p.d_pair_tiles[k], p.n_pair_tiles[k], 0, (uint64_t)p.rows, vin_hi,
-                       vin_lo, vout_hi, vout_lo, u, y, st, false, false, -1, nullptr, nullptr,
-                       vmid_hi, vmid_lo);
 }
 
 cudaError_t launch_stage_tc_strided(const Plan& p, int k, int S, const Tile* tiles, int ntiles,

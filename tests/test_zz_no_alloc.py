@@ -11,8 +11,7 @@ after the shared array was left holding another plan's data (another m,
 batch and input scale).  The §3 schedule, the work-efficient schedule and a
 plan that keeps its stage outputs are covered; for the last, a backward
 after a fixed-scratch forward still uses the caller-workspace forward's
-states; stage pairs (three rotating state buffers) are covered too.  A
-batch whose workspace exceeds the array is refused.  This file is
+states.  A batch whose workspace exceeds the array is refused.  This file is
 collected last and builds what it needs, so it passes both alone in a fresh
 process and after the other tests.
 """
@@ -57,16 +56,14 @@ def dirty_the_array(torch, _abi, cascade):
     c.close()
 
 
-@pytest.mark.parametrize("flag", ["default", "scan", "save_states", "stage_pairs"])
+@pytest.mark.parametrize("flag", ["default", "scan", "save_states"])
 def test_fixed_scratch_forward_matches_workspace_forward(mods, flag):
     torch, _abi, cascade = mods
     flags = {"default": 0, "scan": _abi.CASCADE_FLAG_SCAN,
-             "save_states": _abi.CASCADE_FLAG_SAVE_STATES, "stage_pairs": 0}[flag]
+             "save_states": _abi.CASCADE_FLAG_SAVE_STATES}[flag]
     dirty_the_array(torch, _abi, cascade)
-    # (sequences of whole tiles: stages 4..9 run as pairs through three buffers)
-    w = wl.precision_form(m=128, L=1024 if flag == "stage_pairs" else 1000, batch=3, N=9)
+    w = wl.precision_form(m=128, L=1000, batch=3, N=9)
     c = cascade.from_workload(w, precision="bf16_split", flags=flags)
-    assert bool(c.stage_pairs()) == (flag == "stage_pairs")
     assert c.workspace_size() <= (32 << 20)
     rng = np.random.default_rng(11)
     for call in range(2):

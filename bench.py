@@ -149,6 +149,23 @@ def blas_threads():
     return os.cpu_count() or 1
 
 
+def cpu_model():
+    """The host CPU's model name (x86: 'model name'; Arm: implementer and part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return None
+    for key in ("model name", "Model"):
+        for line in info:
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    impl = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")]
+    part = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")]
+    if impl and part:
+        return f"Arm implementer {impl[0]} part {part[0]}"
+    return None
+
+
 def oracle_sample(w, budget_s=12.0, keep=False):
     """The oracle as it stands on whole sequences of the workload, the last one
     of the batch first (its rows sit at the highest offsets), then from the
@@ -182,6 +199,42 @@ def oracle_sample(w, budget_s=12.0, keep=False):
     desc = (f"{len(done)} of {w.nseq} whole sequences ({states} states; the last sequence, "
             f"then from the first), powers included")
     return states / dt, desc, dt, outs
+
+
+ONE_THREAD = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import oracle
+import workloads as wl
+w = wl.WORKLOADS[sys.argv[2]]()
+i = w.nseq - 1
+L = int(w.lengths[i])
+Abar, Bbar, C, D = oracle.system_matrices(w, int(w.sys_of_seq[i]))
+N = oracle.effective_N(w.N if w.N >= 0 else oracle.choose_N(Abar, L, w.eps), L)
+powers = oracle.squaring_chain(Abar, N)
+rows = int(min(L, max(512, 4e9 / (2.0 * w.m * w.m * (N + 1)))))
+u = w.u[w.seq(i)][:rows].astype(np.float32).astype(np.float64)
+t0 = time.perf_counter()
+oracle.cascade_forward_seq(Abar, Bbar, C, D, u, N, powers=powers)
+dt = time.perf_counter() - t0
+print(json.dumps({"value": rows / dt, "rows": rows, "seconds": dt}))
+"""
+
+
+def oracle_one_thread(name):
+    """The oracle on one host thread (BLAS limited to one thread in a child
+    process): the first steps of the last sequence, powers formed beforehand
+    and not timed.  None if it does not finish within a minute."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", ONE_THREAD, ROOT, name], env=env,
+                           capture_output=True, text=True, timeout=60)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return {"value": d["value"], "unit": "states/s", "cores": 1,
+            "sample": f"the first {d['rows']} steps of the last sequence, powers not timed"}
 
 
 def seq_errors(yg, yo, Du, out_eps, absDu):
@@ -328,7 +381,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args.workload, w, 1),
             "cpu_baseline": {"value": value, "unit": "states/s", "cores": cores,
-                             "kind": "oracle", "sample": samples[-1]},
+                             "kind": "oracle", "sample": samples[-1],
+                             "host_cpus": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "states/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -766,7 +820,8 @@ def measure(name, args, dev, world, rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, _, outs = oracle_sample(w, budget_s=12.0, keep=True)
         cpu = {"value": v, "unit": "states/s", "cores": blas_threads(), "kind": "oracle",
-               "sample": sample}
+               "sample": sample, "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
+               "one_thread": oracle_one_thread(name)}
         error = error_of(w, y_host, outs, precision, sample)
 
     Ls = w.lengths.astype(np.int64)

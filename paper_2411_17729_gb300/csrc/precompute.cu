@@ -163,48 +163,50 @@ cudaError_t launch_discretise(const double* A, const double* B, const double* de
 }
 
 // ----------------------------------------------------------------------------
-// Batched FP64 GEMM  C = alpha op(A) op(B) + beta C  (row-major), 64x64 tiles,
-// 4x4 outputs per thread.  Used for the squaring chain P_{k+1} = P_k P_k, the
-// product Abar Bbar, and the adjoint of the squaring chain.
+// Batched FP64 GEMM  C = alpha op(A) op(B) + beta C  (row-major), TM x TM tiles
+// (64, or 32 when 64-wide tiles would leave the grid short of a few waves),
+// (TM / 16)^2 outputs per thread.  Used for the squaring chain P_{k+1} = P_k P_k,
+// the product Abar Bbar, and the adjoint of the squaring chain.
 // ----------------------------------------------------------------------------
-template <typename T, bool TA, bool TB>
+template <typename T, bool TA, bool TB, int TM = 64>
 __global__ void __launch_bounds__(256) gemm_kernel(const T* __restrict__ A, const T* __restrict__ B,
                                                    T* __restrict__ C, int M, int N, int K, int lda,
                                                    int ldb, int ldc, int64_t sA, int64_t sB,
                                                    int64_t sC, T alpha, T beta, int lower = 0) {
-  __shared__ T As[16][65];
-  __shared__ T Bs[16][65];
+  constexpr int R = TM / 16;       // outputs per thread along each axis
+  __shared__ T As[16][TM + 1];
+  __shared__ T Bs[16][TM + 1];
   A += (int64_t)blockIdx.z * sA;
   B += (int64_t)blockIdx.z * sB;
   C += (int64_t)blockIdx.z * sC;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TM;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  T acc[4][4];
+  T acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int j = 0; j < R; ++j) acc[i][j] = 0;
 
   // lower: A and B lower-triangular (C = A B is too).  A tile above the diagonal
   // is zero, and the K loop runs over k in [n0, m0 + 64) only: every product left
   // out has an exactly zero factor, so the sums are the full loop's bit for bit.
   int kbeg = 0, kend = K;
   if (lower) {
-    kbeg = n0 < m0 + 64 ? n0 : 0;
-    kend = n0 < m0 + 64 ? min(K, m0 + 64) : 0;
+    kbeg = n0 < m0 + TM ? n0 : 0;
+    kend = n0 < m0 + TM ? min(K, m0 + TM) : 0;
   }
   for (int k0 = kbeg; k0 < kend; k0 += 16) {
-    for (int e = threadIdx.x; e < 1024; e += 256) {
+    for (int e = threadIdx.x; e < 16 * TM; e += 256) {
       int mm, kk;
-      if (!TA) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
+      if (!TA) { kk = e & 15; mm = e >> 4; } else { mm = e % TM; kk = e / TM; }
       const int gm = m0 + mm, gk = k0 + kk;
       T v = 0;
       if (gm < M && gk < K) v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
       As[kk][mm] = v;
     }
-    for (int e = threadIdx.x; e < 1024; e += 256) {
+    for (int e = threadIdx.x; e < 16 * TM; e += 256) {
       int nn, kk;
-      if (!TB) { nn = e & 63; kk = e >> 6; } else { kk = e & 15; nn = e >> 4; }
+      if (!TB) { nn = e % TM; kk = e / TM; } else { kk = e & 15; nn = e >> 4; }
       const int gn = n0 + nn, gk = k0 + kk;
       T v = 0;
       if (gn < N && gk < K) v = TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
@@ -213,24 +215,24 @@ __global__ void __launch_bounds__(256) gemm_kernel(const T* __restrict__ A, cons
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      T a[4], b[4];
+      T a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     const int gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
       T* c = C + (int64_t)gm * ldc + gn;
@@ -244,6 +246,29 @@ cudaError_t launch_gemm(const T* A, const T* B, T* C, int M, int N, int K, int l
                         int ldc, int64_t sA, int64_t sB, int64_t sC, int batch, T alpha, T beta,
                         bool transA, bool transB, cudaStream_t st) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  // 32-wide tiles when 64-wide ones would give fewer than four blocks per SM
+  // (one system of m = 1024: 256 blocks on 152 SMs, a second wave two thirds full)
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 1;
+  }
+  const int64_t blocks64 = (int64_t)((N + 63) / 64) * ((M + 63) / 64) * batch;
+  if (blocks64 < 4 * (int64_t)nsm) {
+    dim3 grid((N + 31) / 32, (M + 31) / 32, batch);
+    if (!transA && !transB)
+      gemm_kernel<T, false, false, 32><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+    else if (transA && !transB)
+      gemm_kernel<T, true, false, 32><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+    else if (!transA && transB)
+      gemm_kernel<T, false, true, 32><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+    else
+      gemm_kernel<T, true, true, 32><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);
+    CASCADE_LAUNCHED();
+    return cudaGetLastError();
+  }
   dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
   if (!transA && !transB)
     gemm_kernel<T, false, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, lda, ldb, ldc, sA, sB, sC, alpha, beta);

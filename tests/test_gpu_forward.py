@@ -166,6 +166,18 @@ def test_tc_large_m_multiblock(lib, precision):
     check(lib, w, precision)
 
 
+@pytest.mark.parametrize("precision,m", [("bf16_split", 2048), ("fp32", 1024)])
+def test_tc_wide_state(lib, precision, m):
+    """Wide states: m = 2048 with BF16 pairs (eight N-blocks of 256 per tile),
+    m = 1024 with TF32 pairs (eight of 128), ragged sequences, p = 16, q = 20.
+    (The TF32 pair's tensor-core sums truncate once per 8-term K step, so its
+    error grows with m: at m = 2048 it measured 1.5e-5, above the 1e-5 bar.)"""
+    w = wl.large_form(m=m, p=16, q=20, L=8, batch=2, N=8)
+    w.offsets = np.array([0, 300, 300 + 173], dtype=np.int64)
+    w.u = np.random.default_rng(31).standard_normal((473, 16))
+    check(lib, w, precision)
+
+
 @pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
 def test_tc_unfused_matches_fused(lib, precision):
     from paper_2411_17729_gb300._abi import CASCADE_FLAG_NO_FUSED_OUTPUT

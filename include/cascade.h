@@ -63,7 +63,9 @@ typedef enum {
   CASCADE_FP64 = 0,
   /* Stage contractions as three TF32 tensor-core products
      (hi*hi + hi*lo + lo*hi) with FP32 accumulation in TMEM; states stored
-     as a pair of TF32-exact FP32 planes (hi + lo carries ~22 bits).         */
+     as a pair of TF32-exact FP32 planes (hi + lo carries ~22 bits).  The
+     tensor core adds each 8-term K step into the FP32 sum with a truncating
+     add, so the error grows with m (about 1e-5 relative at m = 1024).       */
   CASCADE_FP32 = 1,
   /* Stage contractions as three BF16 tensor-core products with FP32
      accumulation in TMEM; states stored as a BF16 (hi, lo) pair.            */

@@ -274,6 +274,18 @@ cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes);
 cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y,
                                  void* d_workspace, size_t workspace_bytes, void* stream);
 
+/* cascade_forward with the input and the output in host memory (the call a
+   host program makes): copies h_u [rows,p] to d_u, runs cascade_forward into
+   d_y, copies d_y [rows,q] to h_y, and waits for the copy on `stream`.  d_u,
+   d_y and the workspace are caller-owned device buffers as for
+   cascade_forward; h_u, h_y should be page-locked for the copies to run at
+   full speed.  Returns CASCADE_ERR_TIMEOUT when a bounded device wait of this
+   forward gave up (the device error word stays set for
+   cascade_get_device_error).  Synchronous. */
+cascade_status_t cascade_forward_host(cascade_plan_t plan, const void* h_u, void* h_y, void* d_u,
+                                      void* d_y, void* d_workspace, size_t workspace_bytes,
+                                      void* stream);
+
 /* cascade_forward without a workspace argument, for callers that cannot call
    cudaMalloc: for example a plugin that runs inside a host framework whose
    memory pool owns all device memory, or a latency-bound service path where

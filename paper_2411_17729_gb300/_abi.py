@@ -70,6 +70,7 @@ SIGNATURES = [
     ("cascade_set_stage_shapes", C.c_int, [cascade_plan_t, C.c_int32, C.POINTER(C.c_int32)]),
     ("cascade_workspace_size", C.c_int, [cascade_plan_t, C.POINTER(C.c_size_t)]),
     ("cascade_forward", C.c_int, [cascade_plan_t, _P, _P, _P, C.c_size_t, _P]),
+    ("cascade_forward_host", C.c_int, [cascade_plan_t, _P, _P, _P, _P, _P, C.c_size_t, _P]),
     ("cascade_forward_fixed_scratch", C.c_int, [cascade_plan_t, _P, _P, _P]),
     ("cascade_backward", C.c_int, [cascade_plan_t, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                    C.c_size_t, _P]),

@@ -127,6 +127,24 @@ class Cascade:
                                              _stream(stream)))
         return y
 
+    def forward_host(self, h_u, h_y, d_u=None, d_y=None, stream=None):
+        """The forward from host memory to host memory (cascade_forward_host):
+        h_u [rows, p] and h_y [rows, q] CPU tensors (page-locked for full-speed
+        copies), d_u, d_y device staging tensors (allocated when omitted).
+        Returns h_y once y is there."""
+        for t, n in ((h_u, self.p), (h_y, self.q)):
+            assert t.device.type == "cpu" and t.dtype == self.dtype and t.is_contiguous()
+            assert t.shape == (self.rows, n)
+        if d_u is None:
+            d_u = torch.empty((self.rows, self.p), dtype=self.dtype, device=self.device)
+        if d_y is None:
+            d_y = torch.empty((self.rows, self.q), dtype=self.dtype, device=self.device)
+        ws = self.workspace()
+        self._check(self.lib.cascade_forward_host(self.plan, _ptr(h_u), _ptr(h_y), _ptr(d_u),
+                                                  _ptr(d_y), _ptr(ws), ws.numel(),
+                                                  _stream(stream)))
+        return h_y
+
     def backward(self, u, dy, stream=None, want=("du", "dAbar", "dBbar", "dC", "dD", "dA", "dB")):
         """Gradients of sum(dy * y) for the last forward (plan created with
         CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE).  Returns a dict of

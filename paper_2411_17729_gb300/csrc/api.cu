@@ -1788,6 +1788,31 @@ cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y
   return run_forward(p, d_u, d_y, d_workspace, st);
 }
 
+cascade_status_t cascade_forward_host(cascade_plan_t plan, const void* h_u, void* h_y, void* d_u,
+                                      void* d_y, void* d_workspace, size_t workspace_bytes,
+                                      void* stream) {
+  Plan* p = plan;
+  if (!p) return fail(p, CASCADE_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->have_system || !p->have_batch) return fail(p, CASCADE_ERR_STATE, "system and batch must be set");
+  if (p->rows == 0) return CASCADE_OK;
+  if (!h_u || !h_y || !d_u || !d_y)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "u and y need host and device buffers");
+  const size_t es = p->d.precision == CASCADE_FP64 ? sizeof(double) : sizeof(float);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(d_u, h_u, es * (size_t)p->rows * p->d.p, cudaMemcpyHostToDevice, st),
+     "copy u to the device");
+  const cascade_status_t r = cascade_forward(plan, d_u, d_y, d_workspace, workspace_bytes, stream);
+  if (r != CASCADE_OK) return r;
+  CK(cudaMemcpyAsync(h_y, d_y, es * (size_t)p->rows * p->d.q, cudaMemcpyDeviceToHost, st),
+     "copy y to the host");
+  CK(cudaStreamSynchronize(st), "synchronise");
+  int32_t code = 0;
+  CK(cudaMemcpy(&code, p->err, sizeof(code), cudaMemcpyDeviceToHost), "read error word");
+  if (code != 0)
+    return fail(p, CASCADE_ERR_TIMEOUT, "a bounded device wait gave up (cascade_get_device_error)");
+  return CASCADE_OK;
+}
+
 cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_u, const void* d_dy,
                                   void* d_du, double* d_dAbar, double* d_dBbar, double* d_dC,
                                   double* d_dD, double* d_dA, double* d_dB, void* d_workspace,

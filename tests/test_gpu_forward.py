@@ -178,6 +178,29 @@ def test_tc_wide_state(lib, precision, m):
     check(lib, w, precision)
 
 
+@pytest.mark.parametrize("precision", ["bf16_split", "fp64"])
+def test_forward_host_matches_device_forward(lib, precision):
+    """cascade_forward_host (host u in, host y out, synchronous) gives the
+    device forward's y bit for bit, repeatedly, from page-locked and ordinary
+    host memory."""
+    import torch
+    w = cast_inputs(wl.precision_form(m=128 if precision != "fp64" else 24, L=700, batch=3,
+                                      N=9), precision)
+    c = lib.from_workload(w, precision=precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    u = torch.as_tensor(w.u, dtype=dt).cuda().contiguous()
+    y_dev = c.forward(u).cpu()
+    for pin in (True, False):
+        h_u = torch.as_tensor(w.u, dtype=dt).contiguous()
+        h_y = torch.full((w.rows, w.q), float("nan"), dtype=dt)
+        if pin:
+            h_u, h_y = h_u.pin_memory(), h_y.pin_memory()
+        for _ in range(2):
+            c.forward_host(h_u, h_y)
+            assert torch.equal(h_y, y_dev)
+    assert c.device_error() == 0
+
+
 @pytest.mark.parametrize("precision", ["bf16_split", "fp32"])
 def test_tc_unfused_matches_fused(lib, precision):
     from paper_2411_17729_gb300._abi import CASCADE_FLAG_NO_FUSED_OUTPUT

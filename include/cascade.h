@@ -279,7 +279,12 @@ cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y
    d_y, copies d_y [rows,q] to h_y, and waits for the copy on `stream`.  d_u,
    d_y and the workspace are caller-owned device buffers as for
    cascade_forward; h_u, h_y should be page-locked for the copies to run at
-   full speed.  Returns CASCADE_ERR_TIMEOUT when a bounded device wait of this
+   full speed.  When the plan projects u and y on the tensor cores in launches
+   of their own (p, q multiples of 16, output not formed in the last stage, no
+   CASCADE_FLAG_GRAPH), the copies run in row chunks on a plan-owned stream
+   beside those projections; results are the same bit for bit.  The caller's
+   stream then also waits for the copies.  Returns CASCADE_ERR_TIMEOUT when a
+   bounded device wait of this
    forward gave up (the device error word stays set for
    cascade_get_device_error).  Synchronous. */
 cascade_status_t cascade_forward_host(cascade_plan_t plan, const void* h_u, void* h_y, void* d_u,

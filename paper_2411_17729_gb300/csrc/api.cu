@@ -539,7 +539,20 @@ cudaError_t ensure_events(Plan* p, int pairs) {
   return cudaSuccess;
 }
 
-cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStream_t st) {
+// The host side of cascade_forward_host when its copies overlap the projections:
+// u comes from h_u chunk by chunk on the copy stream cs (in), y goes to h_y chunk
+// by chunk (out), chunks as Plan::io_in / io_out.
+struct HostIO {
+  const void* h_u;
+  void* h_y;
+  size_t u_row_bytes, y_row_bytes;
+  cudaStream_t cs;
+  const cudaEvent_t* ev;   // io_in.size() + io_out.size() + 1 events
+  bool in, out;
+};
+
+cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStream_t st,
+                             const HostIO* io = nullptr) {
   const Layout L = layout(*p);
   const Bufs V{static_cast<uint8_t*>(ws), L.buf_stride, L.lo_off};
   const bool save = keeps_states(*p);
@@ -547,7 +560,12 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
   // tensor-core projections read u as (hi, lo) BF16 planes
   const bool ptc = proj_tc_supported(*p);
   const Bufs U{static_cast<uint8_t*>(ws) + L.off_U, 0, L.u_plane};
-  if (ptc)
+  // (the copies overlap the tensor-core first-stage and output projections, when
+  // those run as their own launches over every row)
+  const bool io_in = io && io->in && ptc && !scans(*p) && p->fused_J == 0 && !p->fuse_first &&
+                     !p->io_in.empty();
+  const bool io_out = io && io->out && ptc && !scans(*p) && !p->io_out.empty();
+  if (ptc && !io_in)
     CK(launch_split_rows(static_cast<const float*>(u), p->rows, p->d.p, p->d.p, U.hi(0), U.lo(0),
                          st),
        "input planes");
@@ -627,7 +645,30 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
   } else if (p->fuse_first)
     CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), 0, st),
        "first stage");
-  else if (ptc)
+  else if (ptc && io_in) {
+    // each chunk of u is split and projected once its copy has landed, while the
+    // next chunk is still on its way
+    const size_t n = p->io_in.size();
+    for (size_t c = 0; c < n; ++c) {
+      const auto& ch = p->io_in[c];
+      CK(cudaMemcpyAsync(static_cast<uint8_t*>(const_cast<void*>(u)) + ch[2] * io->u_row_bytes,
+                         static_cast<const uint8_t*>(io->h_u) + ch[2] * io->u_row_bytes,
+                         ch[3] * io->u_row_bytes, cudaMemcpyHostToDevice, io->cs),
+         "copy u to the device");
+      CK(cudaEventRecord(io->ev[c], io->cs), "event");
+    }
+    for (size_t c = 0; c < n; ++c) {
+      const auto& ch = p->io_in[c];
+      CK(cudaStreamWaitEvent(st, io->ev[c], 0), "wait for u");
+      const size_t e0 = (size_t)ch[2] * p->d.p;   // first element of the chunk
+      CK(launch_split_rows(static_cast<const float*>(u) + e0, ch[3], p->d.p, p->d.p,
+                           static_cast<__nv_bfloat16*>(U.hi(0)) + e0,
+                           static_cast<__nv_bfloat16*>(U.lo(0)) + e0, st),
+         "input planes");
+      CK(launch_proj_tc_stage0(*p, U, V, p->rows, out_buf(0), false, st, (int)ch[0], (int)ch[1]),
+         "first stage");
+    }
+  } else if (ptc)
     CK(launch_proj_tc_stage0(*p, U, V, p->rows, out_buf(0), false, st), "first stage");
   else if (proj_supported(*p))
     CK(launch_proj_stage0(*p, static_cast<const float*>(u), V, out_buf(0), 0, st), "first stage");
@@ -652,7 +693,25 @@ cascade_status_t run_forward(Plan* p, const void* u, void* y, void* ws, cudaStre
       p->n_ev++;
     }
   }
-  if (ptc)
+  if (ptc && io_out) {
+    // y chunk by chunk: each chunk's copy to the host overlaps the next chunk's
+    // projection; the stream then waits for the last copy
+    const size_t n0 = p->io_in.size(), n = p->io_out.size();
+    for (size_t c = 0; c < n; ++c) {
+      const auto& ch = p->io_out[c];
+      CK(launch_proj_tc_output(*p, U, static_cast<float*>(y), V, p->rows, st, (int)ch[0],
+                               (int)ch[1]),
+         "output projection");
+      CK(cudaEventRecord(io->ev[n0 + c], st), "event");
+      CK(cudaStreamWaitEvent(io->cs, io->ev[n0 + c], 0), "wait for y");
+      CK(cudaMemcpyAsync(static_cast<uint8_t*>(io->h_y) + ch[2] * io->y_row_bytes,
+                         static_cast<const uint8_t*>(y) + ch[2] * io->y_row_bytes,
+                         ch[3] * io->y_row_bytes, cudaMemcpyDeviceToHost, io->cs),
+         "copy y to the host");
+    }
+    CK(cudaEventRecord(io->ev[n0 + n], io->cs), "event");
+    CK(cudaStreamWaitEvent(st, io->ev[n0 + n], 0), "wait for the copies");
+  } else if (ptc)
     CK(launch_proj_tc_output(*p, U, static_cast<float*>(y), V, p->rows, st), "output projection");
   else if (proj_supported(*p))
     CK(launch_proj_output(*p, static_cast<const float*>(u), static_cast<float*>(y), V, st),
@@ -1195,6 +1254,8 @@ void cascade_plan_destroy(cascade_plan_t plan) {
   cudaDeviceSynchronize();
   for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
   if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+  if (plan->io_stream) cudaStreamDestroy(plan->io_stream);
+  for (cudaEvent_t e : plan->io_ev) cudaEventDestroy(e);
   free_batch(plan);
   free_system(plan);
   dfree(plan->err);
@@ -1606,6 +1667,32 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
   }
   CK(upload(outs, &p->d_out_tiles), "upload output schedule");
   p->n_out_tiles = (int)outs.size();
+  // Chunks of the first-stage and output tile lists for the host-buffer forward,
+  // whose copies overlap the projections (tensor-core projections of one state
+  // buffer: both lists then run in row order, so each chunk is a row range)
+  p->io_in.clear();
+  p->io_out.clear();
+  if (proj_tc_supported(*p) && !scans(*p) && p->out_segs.size() <= 1) {
+    auto chunk = [&](const std::vector<Tile>& v, std::vector<std::array<int64_t, 4>>& out) {
+      const int n = (int)v.size(), CH = 4;
+      for (int c = 0; c < CH && n > 0; ++c) {
+        const int a = (int)((int64_t)n * c / CH), b = (int)((int64_t)n * (c + 1) / CH);
+        if (b <= a) continue;
+        const int64_t r0 = v[a].seq_row0 + v[a].t0;
+        const int64_t r1 = v[b - 1].seq_row0 + std::min<int64_t>(v[b - 1].t0 + BM, v[b - 1].len);
+        out.push_back({a, b - a, r0, r1 - r0});
+      }
+      // contiguous, covering every row in order
+      int64_t next = 0;
+      for (const auto& c : out) {
+        if (c[2] != next) { out.clear(); return; }
+        next = c[2] + c[3];
+      }
+      if (next != p->rows) out.clear();
+    };
+    chunk(t0s, p->io_in);
+    chunk(outs, p->io_out);
+  }
   if (!seqs.empty()) {
     CK(cudaMalloc(&p->d_seqs, seqs.size() * sizeof(Seq)), "alloc sequences");
     CK(cudaMemcpy(p->d_seqs, seqs.data(), seqs.size() * sizeof(Seq), cudaMemcpyHostToDevice),
@@ -1799,12 +1886,49 @@ cascade_status_t cascade_forward_host(cascade_plan_t plan, const void* h_u, void
     return fail(p, CASCADE_ERR_INVALID_ARG, "u and y need host and device buffers");
   const size_t es = p->d.precision == CASCADE_FP64 ? sizeof(double) : sizeof(float);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  CK(cudaMemcpyAsync(d_u, h_u, es * (size_t)p->rows * p->d.p, cudaMemcpyHostToDevice, st),
-     "copy u to the device");
-  const cascade_status_t r = cascade_forward(plan, d_u, d_y, d_workspace, workspace_bytes, stream);
-  if (r != CASCADE_OK) return r;
-  CK(cudaMemcpyAsync(h_y, d_y, es * (size_t)p->rows * p->d.q, cudaMemcpyDeviceToHost, st),
-     "copy y to the host");
+  // With the tensor-core projections as launches of their own (and no graph), the
+  // copies run chunk by chunk on a plan-owned stream beside them.
+  const bool in = proj_tc_supported(*p) && !scans(*p) && p->fused_J == 0 && !p->fuse_first &&
+                  !p->io_in.empty();
+  const bool out = proj_tc_supported(*p) && !scans(*p) && !p->io_out.empty();
+  if ((in || out) && !(p->d.flags & CASCADE_FLAG_GRAPH)) {
+    if (!d_workspace) return fail(p, CASCADE_ERR_INVALID_ARG, "workspace must be a device pointer");
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0)
+      return fail(p, CASCADE_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (workspace_bytes < forward_workspace(*p, p->rows))
+      return fail(p, CASCADE_ERR_INVALID_ARG, "workspace too small");
+    if (!p->io_stream)
+      CK(cudaStreamCreateWithFlags(&p->io_stream, cudaStreamNonBlocking), "copy stream");
+    const size_t nev = p->io_in.size() + p->io_out.size() + 2;
+    while (p->io_ev.size() < nev) {
+      cudaEvent_t e;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+      p->io_ev.push_back(e);
+    }
+    // the copy stream starts after what the caller's stream has queued (which
+    // may still read d_u or write d_y)
+    CK(cudaEventRecord(p->io_ev[nev - 1], st), "event");
+    CK(cudaStreamWaitEvent(p->io_stream, p->io_ev[nev - 1], 0), "wait");
+    if (!in)
+      CK(cudaMemcpyAsync(d_u, h_u, es * (size_t)p->rows * p->d.p, cudaMemcpyHostToDevice, st),
+         "copy u to the device");
+    const HostIO io{h_u, h_y, es * (size_t)p->d.p, es * (size_t)p->d.q, p->io_stream,
+                    p->io_ev.data(), in, out};
+    p->last_stream = stream;
+    const cascade_status_t r = run_forward(p, d_u, d_y, d_workspace, st, &io);
+    if (r != CASCADE_OK) return r;
+    if (!out)
+      CK(cudaMemcpyAsync(h_y, d_y, es * (size_t)p->rows * p->d.q, cudaMemcpyDeviceToHost, st),
+         "copy y to the host");
+  } else {
+    CK(cudaMemcpyAsync(d_u, h_u, es * (size_t)p->rows * p->d.p, cudaMemcpyHostToDevice, st),
+       "copy u to the device");
+    const cascade_status_t r =
+        cascade_forward(plan, d_u, d_y, d_workspace, workspace_bytes, stream);
+    if (r != CASCADE_OK) return r;
+    CK(cudaMemcpyAsync(h_y, d_y, es * (size_t)p->rows * p->d.q, cudaMemcpyDeviceToHost, st),
+       "copy y to the host");
+  }
   CK(cudaStreamSynchronize(st), "synchronise");
   int32_t code = 0;
   CK(cudaMemcpy(&code, p->err, sizeof(code), cudaMemcpyDeviceToHost), "read error word");

@@ -238,6 +238,12 @@ struct Plan {
   std::vector<cudaEvent_t> ev;            // pairs per stage
   std::vector<int32_t> ev_k;
   int n_ev = 0;
+  // host-buffer forward (cascade_forward_host): chunks of the first-stage and
+  // output tile lists {first tile, tiles, first row, rows}, contiguous in rows, whose
+  // copies overlap the projections; a plan-owned copy stream and its events
+  std::vector<std::array<int64_t, 4>> io_in, io_out;
+  cudaStream_t io_stream = nullptr;
+  std::vector<cudaEvent_t> io_ev;
   // graph cache (recorded on a plan-owned stream: the legacy default stream
   // cannot be captured; the graph is then launched on the caller's stream)
   cudaStream_t cap_stream = nullptr;
@@ -355,10 +361,14 @@ cudaError_t launch_proj_coef(const Plan& p, cudaStream_t st);
 cudaError_t launch_split_rows(const float* x, int64_t rows, int w, int wp, void* hi, void* lo,
                               cudaStream_t st);
 // U, G: (hi, lo) BF16 planes of u [rows, p] and G [rows, q] (buffer 0 of the Bufs)
+// (tile0, ntiles: a range of the first-stage or output tile list; ntiles < 0: to
+// its end)
 cudaError_t launch_proj_tc_stage0(const Plan& p, const Bufs& U, const Bufs& V, int64_t v_rows,
-                                  int buf, bool odd_only, cudaStream_t st);
+                                  int buf, bool odd_only, cudaStream_t st, int tile0 = 0,
+                                  int ntiles = -1);
 cudaError_t launch_proj_tc_output(const Plan& p, const Bufs& U, float* y, const Bufs& V,
-                                  int64_t v_rows, cudaStream_t st);
+                                  int64_t v_rows, cudaStream_t st, int tile0 = 0,
+                                  int ntiles = -1);
 cudaError_t launch_proj_tc_adj_init(const Plan& p, const Bufs& G, const Bufs& W, cudaStream_t st);
 cudaError_t launch_proj_tc_du(const Plan& p, const Bufs& G, const Bufs& W, int wbuf, float* du,
                               cudaStream_t st);

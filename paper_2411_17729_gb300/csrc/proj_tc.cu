@@ -580,20 +580,25 @@ cudaError_t launch_split_rows(const float* x, int64_t rows, int w, int wp, void*
 }
 
 cudaError_t launch_proj_tc_stage0(const Plan& p, const Bufs& U, const Bufs& V, int64_t v_rows,
-                                  int buf, bool odd_only, cudaStream_t st) {
+                                  int buf, bool odd_only, cudaStream_t st, int tile0, int ntiles) {
   const Term t[2] = {{U.hi(0), U.lo(0), p.rows, p.d.p, 0, PC_B},
                      {U.hi(0), U.lo(0), p.rows, p.d.p, -1, PC_AB}};
-  return launch_proj_tc(p, p.d_stage0_tiles, p.n_stage0_tiles, p.d.m, 2, t, odd_only ? 1 : 0,
+  if (ntiles < 0) ntiles = p.n_stage0_tiles - tile0;
+  return launch_proj_tc(p, p.d_stage0_tiles + tile0, ntiles, p.d.m, 2, t, odd_only ? 1 : 0,
                         nullptr, V, v_rows, 0, buf, st);
 }
 
 cudaError_t launch_proj_tc_output(const Plan& p, const Bufs& U, float* y, const Bufs& V,
-                                  int64_t v_rows, cudaStream_t st) {
+                                  int64_t v_rows, cudaStream_t st, int tile0, int ntiles) {
   for (const auto& sg : p.out_segs) {
     const Term t[2] = {{V.hi(sg[0]), V.lo(sg[0]), v_rows, p.d.m, 0, PC_C},
                        {U.hi(0), U.lo(0), p.rows, p.d.p, 0, PC_D}};
-    const cudaError_t e = launch_proj_tc(p, p.d_out_tiles + sg[1], sg[2], p.d.q, 2, t, 0, y, Bufs{},
-                                         0, 0, 0, st);
+    // (a tile range applies within the list of all output tiles)
+    const int a = std::max(sg[1], tile0);
+    const int b = ntiles < 0 ? sg[1] + sg[2] : std::min(sg[1] + sg[2], tile0 + ntiles);
+    if (b <= a) continue;
+    const cudaError_t e = launch_proj_tc(p, p.d_out_tiles + a, b - a, p.d.q, 2, t, 0, y, Bufs{}, 0,
+                                         0, 0, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -178,14 +178,22 @@ def test_tc_wide_state(lib, precision, m):
     check(lib, w, precision)
 
 
-@pytest.mark.parametrize("precision", ["bf16_split", "fp64"])
-def test_forward_host_matches_device_forward(lib, precision):
+@pytest.mark.parametrize("precision,wide", [("bf16_split", False), ("fp64", False),
+                                            ("bf16_split", True)])
+def test_forward_host_matches_device_forward(lib, precision, wide):
     """cascade_forward_host (host u in, host y out, synchronous) gives the
     device forward's y bit for bit, repeatedly, from page-locked and ordinary
-    host memory."""
+    host memory.  wide: p = q = 16 at m = 512, where u's copies overlap the
+    first-stage projection and y's the output projection, chunk by chunk."""
     import torch
-    w = cast_inputs(wl.precision_form(m=128 if precision != "fp64" else 24, L=700, batch=3,
-                                      N=9), precision)
+    if wide:
+        w = wl.large_form(m=512, p=16, q=16, L=8, batch=3, N=9)
+        w.offsets = np.array([0, 700, 700 + 1, 700 + 1 + 1300], dtype=np.int64)
+        w.u = np.random.default_rng(41).standard_normal((2001, 16))
+        w = cast_inputs(w, precision)
+    else:
+        w = cast_inputs(wl.precision_form(m=128 if precision != "fp64" else 24, L=700, batch=3,
+                                          N=9), precision)
     c = lib.from_workload(w, precision=precision)
     dt = torch.float64 if precision == "fp64" else torch.float32
     u = torch.as_tensor(w.u, dtype=dt).cuda().contiguous()

@@ -307,9 +307,11 @@ cudaError_t launch_upper_nonzero(const double* X, int64_t sys_stride, int ns, in
 cudaError_t launch_dgemm_lower(const double* A, const double* B, double* C, int n, int64_t sA,
                                int64_t sB, int64_t sC, int batch, cudaStream_t st) {
   if (n <= 0 || batch <= 0) return cudaSuccess;
-  dim3 grid((n + 63) / 64, (n + 63) / 64, batch);
-  gemm_kernel<double, false, false><<<grid, 256, 0, st>>>(A, B, C, n, n, n, n, n, n, sA, sB, sC,
-                                                          1.0, 0.0, 1);
+  // 32-wide tiles: the products of the tiles that straddle the diagonal, half of
+  // which have a zero factor, are 1.4x the triangle's (1.9x with 64-wide tiles)
+  dim3 grid((n + 31) / 32, (n + 31) / 32, batch);
+  gemm_kernel<double, false, false, 32><<<grid, 256, 0, st>>>(A, B, C, n, n, n, n, n, n, sA, sB,
+                                                              sC, 1.0, 0.0, 1);
   CASCADE_LAUNCHED();
   return cudaGetLastError();
 }

@@ -332,8 +332,10 @@ cascade_status_t cascade_forward_fixed_scratch(cascade_plan_t plan, const void* 
    [nsys,q,m], d_dD [nsys,q,p] (double): the gradients through the squaring
    chain (end of §2) and the stages (§3, derived adjoint: transposed powers,
    reversed shifts).  For continuous systems d_dA [nsys,m,m] and d_dB
-   [nsys,m,p] are the gradients through Eq. (4.2).  Any output pointer may be
-   NULL to skip it.  Asynchronous. */
+   [nsys,m,p] are the gradients through Eq. (4.2).  Every entry of each
+   requested output is written (not accumulated); a batch of no rows writes
+   zeros and needs no u, dy or workspace.  Any output pointer may be NULL to
+   skip it.  Asynchronous. */
 cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_u, const void* d_dy,
                                   void* d_du, double* d_dAbar, double* d_dBbar, double* d_dC,
                                   double* d_dD, double* d_dA, double* d_dB, void* d_workspace,

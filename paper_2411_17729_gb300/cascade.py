@@ -160,7 +160,7 @@ class Cascade:
             shapes.update({"dA": (ns, m, m), "dB": (ns, m, p)})
         for k, shp in shapes.items():
             if k in want:
-                out[k] = torch.zeros(shp, **f64)
+                out[k] = torch.empty(shp, **f64)   # the library writes every entry
         ws = self.workspace()
         g = lambda k: _ptr(out.get(k))
         self._check(self.lib.cascade_backward(self.plan, _ptr(u), _ptr(dy), g("du"), g("dAbar"),

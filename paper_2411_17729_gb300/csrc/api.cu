@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <array>
 #include <mutex>
+#include <utility>
 
 namespace cascade {
 
@@ -1947,12 +1948,21 @@ cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_u, const vo
     return fail(p, CASCADE_ERR_STATE,
                 "backward needs a plan created with CASCADE_FLAG_SAVE_STATES or CASCADE_FLAG_RECOMPUTE");
   if (!p->have_system || !p->have_batch) return fail(p, CASCADE_ERR_STATE, "system and batch must be set");
-  if (p->rows == 0) return CASCADE_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (p->rows == 0) {   // no rows: every parameter gradient of sum(dy * y) is exactly zero
+    const int m = p->d.m, pp = p->d.p, q = p->d.q, ns = p->d.nsys;
+    const std::pair<double*, int64_t> outs[] = {
+        {d_dAbar, (int64_t)m * m}, {d_dBbar, (int64_t)m * pp}, {d_dC, (int64_t)q * m},
+        {d_dD, (int64_t)q * pp},   {p->continuous ? d_dA : nullptr, (int64_t)m * m},
+        {p->continuous ? d_dB : nullptr, (int64_t)m * pp}};
+    for (const auto& o : outs)
+      if (o.first) CK(cudaMemsetAsync(o.first, 0, sizeof(double) * ns * o.second, st), "zero gradient");
+    return CASCADE_OK;
+  }
   if (!d_u || !d_dy || !d_workspace) return fail(p, CASCADE_ERR_INVALID_ARG, "u, dy, workspace required");
   if (p->saved_ws != d_workspace || p->saved_batch != p->batch_id)
     return fail(p, CASCADE_ERR_STATE, "run cascade_forward on this batch and workspace first");
   if (workspace_bytes < layout(*p).total) return fail(p, CASCADE_ERR_INVALID_ARG, "workspace too small");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   p->last_stream = stream;
   const cascade_status_t r =
       run_backward(p, d_u, d_dy, d_du, d_dAbar, d_dBbar, d_dC, d_dD, d_dA, d_dB, d_workspace, st);

@@ -259,3 +259,48 @@ def test_first_stage_adjoint_one_pass(lib, m, p, q):
     dy = np.random.default_rng(19).standard_normal((w.rows, q)).astype(np.float32).astype(np.float64)
     c, _, g = gpu_grads(lib, w, "bf16_split", dy)
     compare(w, c, g, dy, "bf16_split")
+
+
+@pytest.mark.parametrize("lengths", [(0, 0), (130, 0, 7)])
+def test_backward_overwrites_every_output(lib, lengths):
+    """The backward writes each requested gradient in full: outputs filled with
+    NaN before the call come back as the oracle's gradients (all zero for a
+    batch of no rows, which needs no u, dy or workspace)."""
+    import torch
+    from paper_2411_17729_gb300._abi import CASCADE_FLAG_SAVE_STATES
+    from paper_2411_17729_gb300.cascade import _ptr, _stream
+    w = wl.small_system(m=64, p=2, q=3, lengths=lengths, N=8, nsys=2, seed=11, radius=0.98,
+                        discrete=False, delta=0.1, precision="bf16_split")
+    w = cast_inputs(w, "bf16_split")
+    c = lib.from_workload(w, precision="bf16_split", flags=CASCADE_FLAG_SAVE_STATES)
+    m, p, q, ns = w.m, w.p, w.q, c.nsys
+    shapes = {"dAbar": (ns, m, m), "dBbar": (ns, m, p), "dC": (ns, q, m), "dD": (ns, q, p),
+              "dA": (ns, m, m), "dB": (ns, m, p)}
+    out = {k: torch.full(s, float("nan"), dtype=torch.float64, device="cuda")
+           for k, s in shapes.items()}
+    dy = np.random.default_rng(4).standard_normal((w.rows, q))
+    if w.rows:
+        u = torch.as_tensor(w.u, dtype=torch.float32).cuda().contiguous()
+        c.forward(u)
+        dyt = torch.as_tensor(dy, dtype=torch.float32).cuda().contiguous()
+        du = torch.full((w.rows, p), float("nan"), dtype=torch.float32, device="cuda")
+        ws = c.workspace()
+        args = (_ptr(u), _ptr(dyt), _ptr(du), _ptr(ws), ws.numel())
+    else:
+        du = None
+        args = (None, None, None, None, 0)
+    c._check(c.lib.cascade_backward(c.plan, args[0], args[1], args[2], _ptr(out["dAbar"]),
+                                    _ptr(out["dBbar"]), _ptr(out["dC"]), _ptr(out["dD"]),
+                                    _ptr(out["dA"]), _ptr(out["dB"]), args[3], args[4],
+                                    _stream()))
+    torch.cuda.synchronize()
+    assert c.device_error() == 0, c.lib.cascade_last_error(c.plan)
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    for k, v in g.items():
+        assert np.isfinite(v).all(), k
+    if not w.rows:
+        for k, v in g.items():
+            assert not v.any(), k
+        return
+    g["du"] = du.double().cpu().numpy()
+    compare(w, c, g, dy, "bf16_split")

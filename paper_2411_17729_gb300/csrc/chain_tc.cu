@@ -247,7 +247,12 @@ cudaError_t launch_chain_tc(const Plan& p, int k, bool first, float* dP, int64_t
         dP + (int64_t)(k + 1) * mm, kst, m, xh, xl, th, tl);
     CASCADE_LAUNCHED();
   }
-  const int BN = m % 256 == 0 ? 256 : 128;
+  // column blocks narrow enough to occupy every SM, down to 64 (narrower
+  // blocks would read more operand bytes per product than shared memory
+  // delivers): one level is a small product (12 m^3 flops per system), which
+  // blocks of 256 columns spread over 32 SMs at m = 1024 and over 2 at m = 256
+  int BN = 256;
+  while (BN > 64 && (m % BN != 0 || (int64_t)(m / CBM) * (m / BN) * ns < p.num_sms)) BN /= 2;
   CUtensorMap maps[8];
   std::string err;
   const uint64_t xrows = (uint64_t)ns * m, prows = (uint64_t)ns * p.kmax1 * m;

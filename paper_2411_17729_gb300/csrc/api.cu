@@ -1718,8 +1718,14 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
     // Longer runs mean fewer partial sums to write and add; CH shrinks until
     // the reductions have at least three blocks per SM.  The tensor-core power
     // gradients of lists k >= 1 split each chunk further into (m / 128) x
-    // (m / BN) output blocks: with large m their runs grow (up to 64 tiles)
-    // while there are still six blocks per SM, since each partial is m x m.
+    // (m / BN) output blocks, and each chunk leaves an m x m partial: their runs
+    // grow (up to 64 tiles) while there are still three blocks per SM, and on
+    // while the partials' write and read exceed 1/8 of the operand bytes the
+    // chunk's blocks read (2 m^2 x 4 B against CH x 128 rows x 8m B, i.e. CH <
+    // m / 16) and there are still 1.5 blocks per SM.  (Measured at m = 256:
+    // six blocks per SM and no traffic rule took 4.82 ms per backward on 32 x
+    // 8192 steps, p = q = 16, and 12.24 ms on 64 x 16384, p = q = 1; three
+    // blocks, 4.61 and 12.10 ms; with the traffic rule, 4.44 and 12.10 ms.)
     int CH = 16;
     while (CH > 4 && (int64_t)all.size() < (int64_t)CH * 3 * p->num_sms) CH >>= 1;
     // the list of all tiles feeds the wide-by-thin reductions (one block per
@@ -1737,8 +1743,11 @@ cascade_status_t cascade_set_batch(cascade_plan_t plan, const int64_t* h_offsets
       int CHl = li == 0 ? CH0 : CH;
       if (li > 0 && grad_blocks > 0) {
         CHl = 64;
-        while (CHl > CH && (int64_t)tl.size() / CHl * grad_blocks < (int64_t)6 * p->num_sms)
+        while (CHl > CH && (int64_t)tl.size() / CHl * grad_blocks < (int64_t)3 * p->num_sms)
           CHl >>= 1;
+        while (CHl < 64 && CHl < p->d.m / 16 &&
+               2 * ((int64_t)tl.size() / (2 * CHl) * grad_blocks) >= (int64_t)3 * p->num_sms)
+          CHl <<= 1;
       }
       std::vector<std::array<int32_t, 3>> ch;
       for (int ti = 0; ti < (int)tl.size(); ++ti) {

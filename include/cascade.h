@@ -284,9 +284,9 @@ cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y
    CASCADE_FLAG_GRAPH), the copies run in row chunks on a plan-owned stream
    beside those projections; results are the same bit for bit.  The caller's
    stream then also waits for the copies.  Returns CASCADE_ERR_TIMEOUT when a
-   bounded device wait of this
-   forward gave up (the device error word stays set for
-   cascade_get_device_error).  Synchronous. */
+   bounded device wait of this forward gave up (the device error word stays
+   set for cascade_get_device_error).  Synchronous, on errors too: when it
+   returns, no copy it started still reads h_u or writes h_y. */
 cascade_status_t cascade_forward_host(cascade_plan_t plan, const void* h_u, void* h_y, void* d_u,
                                       void* d_y, void* d_workspace, size_t workspace_bytes,
                                       void* stream);

@@ -1926,7 +1926,12 @@ cascade_status_t cascade_forward_host(cascade_plan_t plan, const void* h_u, void
                     p->io_ev.data(), in, out};
     p->last_stream = stream;
     const cascade_status_t r = run_forward(p, d_u, d_y, d_workspace, st, &io);
-    if (r != CASCADE_OK) return r;
+    if (r != CASCADE_OK) {
+      // the call is synchronous: no copy may still read h_u or write h_y
+      cudaStreamSynchronize(p->io_stream);
+      cudaStreamSynchronize(st);
+      return r;
+    }
     if (!out)
       CK(cudaMemcpyAsync(h_y, d_y, es * (size_t)p->rows * p->d.q, cudaMemcpyDeviceToHost, st),
          "copy y to the host");
@@ -1935,7 +1940,10 @@ cascade_status_t cascade_forward_host(cascade_plan_t plan, const void* h_u, void
        "copy u to the device");
     const cascade_status_t r =
         cascade_forward(plan, d_u, d_y, d_workspace, workspace_bytes, stream);
-    if (r != CASCADE_OK) return r;
+    if (r != CASCADE_OK) {
+      cudaStreamSynchronize(st);   // the copy of u has finished reading h_u
+      return r;
+    }
     CK(cudaMemcpyAsync(h_y, d_y, es * (size_t)p->rows * p->d.q, cudaMemcpyDeviceToHost, st),
        "copy y to the host");
   }

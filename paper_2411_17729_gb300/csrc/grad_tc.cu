@@ -382,8 +382,8 @@ cudaError_t launch_grad_tc_xy(const Plan& p, const Tile* tiles, const int32_t* c
   std::string err;
   const uint64_t rows = (uint64_t)p.rows;
   // Operands whose width is a multiple of 32 are read through column-block maps
-  // (one copy per plane and stage); the others (and any map the driver
-  // declines) through one 2-D box per 32-column block.
+  // (one copy per plane and stage); the others (and any such map the tensor-map
+  // encoder rejects) through one 2-D box per 32-column block.
   auto encode = [&](CUtensorMap* m2, const void* base, int ld, int blocks) -> int {
     std::string e3;
     if (ld % 32 == 0 && encode_tmap_colblocks(m2, base, 2, ld, rows, BMK, blocks, &e3, 64))

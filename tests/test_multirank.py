@@ -64,3 +64,34 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = bench.parse()
     assert bench.run_reference(args) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
+    """Rank 0 of the reference arm prints one JSON line with the contract's keys:
+    the oracle's rate as value, cpu_baseline and e2e (no copies), on the
+    workload's own config (oracle samples shortened to keep the test quick)."""
+    import json
+    import sys
+    import bench
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    real = bench.oracle_sample
+    monkeypatch.setattr(bench, "oracle_sample",
+                        lambda w, budget_s=12.0, keep=False: real(w, budget_s=min(budget_s, 0.2),
+                                                                  keep=keep))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "plain_fp64",
+                                      "--steps", "2", "--warmup", "1"])
+    bench.run_reference(bench.parse())
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 == d["e2e"]["d2h_bytes_per_step"]
+    assert "plain_fp64" in d["config"]["workload"]

@@ -268,8 +268,9 @@ cascade_status_t cascade_workspace_size(cascade_plan_t plan, size_t* bytes);
 
 /* Apply the truncated transfer function to the current batch (§3):
    v^(0) = Bbar u, stages k = 0..N_i, y = C v + D u.  d_u [rows,p] and d_y
-   [rows,q] in the plan's element type; d_workspace of at least
-   cascade_workspace_size bytes, 256-byte aligned.  Asynchronous on stream;
+   [rows,q] in the plan's element type, 16-byte aligned (some paths move their
+   rows in 16-byte words; CASCADE_ERR_INVALID_ARG otherwise); d_workspace of at
+   least cascade_workspace_size bytes, 256-byte aligned.  Asynchronous on stream;
    device-side wait timeouts are reported by cascade_get_device_error. */
 cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y,
                                  void* d_workspace, size_t workspace_bytes, void* stream);
@@ -327,7 +328,8 @@ cascade_status_t cascade_forward_fixed_scratch(cascade_plan_t plan, const void* 
    every stage output, or checkpoints, in the workspace; CASCADE_ERR_STATE
    otherwise).  With checkpoints the call overwrites the forward's other state
    buffers; a second backward needs a new forward.  d_u is the forward's input,
-   d_dy [rows,q] the output gradient (plan element type).  Writes d_du
+   d_dy [rows,q] the output gradient (plan element type; d_u, d_dy and d_du
+   16-byte aligned, the double outputs 8-byte aligned).  Writes d_du
    [rows,p] and, per system, d_dAbar [nsys,m,m], d_dBbar [nsys,m,p], d_dC
    [nsys,q,m], d_dD [nsys,q,p] (double): the gradients through the squaring
    chain (end of §2) and the stages (§3, derived adjoint: transposed powers,
@@ -344,7 +346,7 @@ cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_u, const vo
 /* FP64 sequential recursion of Eq. (1.2), x_n = Abar x_(n-1) + Bbar u_n,
    y_n = C x_n + D u_n, one device thread block per sequence (the baseline
    the cascade replaces).  Uses the plan's systems and batch; d_u/d_y are
-   double.  Asynchronous. */
+   double (8-byte aligned).  Asynchronous. */
 cascade_status_t cascade_recursion_forward(cascade_plan_t plan, const double* d_u, double* d_y,
                                            void* stream);
 

@@ -1842,6 +1842,8 @@ cascade_status_t cascade_forward(cascade_plan_t plan, const void* d_u, void* d_y
   if (p->rows == 0) return CASCADE_OK;
   if (!d_u || !d_y || !d_workspace)
     return fail(p, CASCADE_ERR_INVALID_ARG, "u, y, workspace must be device pointers");
+  if (!row_aligned(d_u) || !row_aligned(d_y))
+    return fail(p, CASCADE_ERR_INVALID_ARG, "u and y must be 16-byte aligned");
   if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0)
     return fail(p, CASCADE_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   if (workspace_bytes < forward_workspace(*p, p->rows))
@@ -1894,6 +1896,8 @@ cascade_status_t cascade_forward_host(cascade_plan_t plan, const void* h_u, void
   if (p->rows == 0) return CASCADE_OK;
   if (!h_u || !h_y || !d_u || !d_y)
     return fail(p, CASCADE_ERR_INVALID_ARG, "u and y need host and device buffers");
+  if (!row_aligned(d_u) || !row_aligned(d_y))
+    return fail(p, CASCADE_ERR_INVALID_ARG, "device u and y must be 16-byte aligned");
   const size_t es = p->d.precision == CASCADE_FP64 ? sizeof(double) : sizeof(float);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // With the tensor-core projections as launches of their own (and no graph), the
@@ -1977,6 +1981,11 @@ cascade_status_t cascade_backward(cascade_plan_t plan, const void* d_u, const vo
     return CASCADE_OK;
   }
   if (!d_u || !d_dy || !d_workspace) return fail(p, CASCADE_ERR_INVALID_ARG, "u, dy, workspace required");
+  if (!row_aligned(d_u) || !row_aligned(d_dy) || (d_du && !row_aligned(d_du)))
+    return fail(p, CASCADE_ERR_INVALID_ARG, "u, dy and du must be 16-byte aligned");
+  for (const double* g : {d_dAbar, d_dBbar, d_dC, d_dD, d_dA, d_dB})
+    if (g && (reinterpret_cast<uintptr_t>(g) & (sizeof(double) - 1)) != 0)
+      return fail(p, CASCADE_ERR_INVALID_ARG, "gradient outputs must be 8-byte aligned");
   if (p->saved_ws != d_workspace || p->saved_batch != p->batch_id)
     return fail(p, CASCADE_ERR_STATE, "run cascade_forward on this batch and workspace first");
   if (workspace_bytes < layout(*p).total) return fail(p, CASCADE_ERR_INVALID_ARG, "workspace too small");
@@ -1995,6 +2004,8 @@ cascade_status_t cascade_recursion_forward(cascade_plan_t plan, const double* d_
   if (!p->have_system || !p->have_batch) return fail(p, CASCADE_ERR_STATE, "system and batch must be set");
   if (p->rows == 0) return CASCADE_OK;
   if (!d_u || !d_y) return fail(p, CASCADE_ERR_INVALID_ARG, "u, y must be device pointers");
+  if (((reinterpret_cast<uintptr_t>(d_u) | reinterpret_cast<uintptr_t>(d_y)) & 7) != 0)
+    return fail(p, CASCADE_ERR_INVALID_ARG, "u and y must be 8-byte aligned");
   CK(launch_recursion_f64(*p, d_u, d_y, static_cast<cudaStream_t>(stream)), "recursion");
   return CASCADE_OK;
 }

@@ -57,6 +57,13 @@ struct Seq {
 enum { SEQ_FUSED = 1 };
 
 // Everything a stage launch needs besides tensor maps.
+// Caller row buffers (u, y, dy, du) are read and written with 16-byte vector
+// accesses on some paths; the entry points check this alignment before any launch.
+constexpr uintptr_t ROW_ALIGN = 16;
+inline bool row_aligned(const void* ptr) {
+  return (reinterpret_cast<uintptr_t>(ptr) & (ROW_ALIGN - 1)) == 0;
+}
+
 struct StageArgs {
   const Tile* tiles;
   int32_t ntiles;

@@ -73,6 +73,8 @@ extern "C" cascade_status_t cascade_forward_fixed_scratch(cascade_plan_t plan, c
     return nofail(p, CASCADE_ERR_STATE, "system and batch must be set");
   if (p->rows == 0) return CASCADE_OK;
   if (!d_u || !d_y) return nofail(p, CASCADE_ERR_INVALID_ARG, "u and y must be device pointers");
+  if (!row_aligned(d_u) || !row_aligned(d_y))
+    return nofail(p, CASCADE_ERR_INVALID_ARG, "u and y must be 16-byte aligned");
   if (p->timing)
     return nofail(p, CASCADE_ERR_UNSUPPORTED,
                   "disable stage timing first (it creates CUDA events)");

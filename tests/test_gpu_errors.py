@@ -61,3 +61,42 @@ def test_call_order_and_batch_validation(abi):
     ws = c.workspace()
     st = c.lib.cascade_forward(c.plan, None, None, C.c_void_p(ws.data_ptr()), ws.numel(), None)
     assert st == abi.CASCADE_ERR_INVALID_ARG
+
+
+def test_misaligned_rows_rejected(abi):
+    """u, y, dy and du move through some paths in 16-byte words: a pointer off
+    that alignment is refused with CASCADE_ERR_INVALID_ARG before anything is
+    launched, and the plan stays usable (an aligned forward then matches)."""
+    import torch
+    from paper_2411_17729_gb300 import cascade
+    from paper_2411_17729_gb300.cascade import _stream
+    w = wl.small_system(m=128, p=16, q=16, lengths=(300, 77), N=8, seed=2, radius=0.97,
+                        precision="bf16_split")
+    c = cascade.from_workload(w, precision="bf16_split", flags=abi.CASCADE_FLAG_SAVE_STATES)
+    rows, p, q = w.rows, w.p, w.q
+    u = torch.as_tensor(w.u, dtype=torch.float32).cuda().contiguous()
+    y_ref = c.forward(u).clone()
+    ub = torch.zeros(rows * p + 4, dtype=torch.float32, device="cuda")
+    yb = torch.zeros(rows * q + 4, dtype=torch.float32, device="cuda")
+    ub[1:1 + rows * p].copy_(u.reshape(-1))
+    odd_u, odd_y = C.c_void_p(ub.data_ptr() + 4), C.c_void_p(yb.data_ptr() + 4)
+    ok_u, ok_y = C.c_void_p(u.data_ptr()), C.c_void_p(yb.data_ptr())
+    ws = c.workspace()
+    wsp, n = C.c_void_p(ws.data_ptr()), ws.numel()
+    lib = c.lib
+    E = abi.CASCADE_ERR_INVALID_ARG
+    assert lib.cascade_forward(c.plan, odd_u, ok_y, wsp, n, _stream()) == E
+    assert lib.cascade_forward(c.plan, ok_u, odd_y, wsp, n, _stream()) == E
+    assert lib.cascade_forward_fixed_scratch(c.plan, odd_u, ok_y, _stream()) == E
+    h_u, h_y = u.cpu(), torch.empty((rows, q))
+    assert lib.cascade_forward_host(c.plan, C.c_void_p(h_u.data_ptr()), C.c_void_p(h_y.data_ptr()),
+                                    odd_u, ok_y, wsp, n, _stream()) == E
+    dy = torch.ones((rows, q), device="cuda")
+    du = torch.empty(rows * p + 4, device="cuda")
+    assert lib.cascade_backward(c.plan, ok_u, C.c_void_p(dy.data_ptr()), C.c_void_p(du.data_ptr() + 4),
+                                None, None, None, None, None, None, wsp, n, _stream()) == E
+    torch.cuda.synchronize()
+    assert c.device_error() == 0
+    y = c.forward(u)
+    torch.cuda.synchronize()
+    assert torch.equal(y, y_ref)
